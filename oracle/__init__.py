@@ -1,0 +1,333 @@
+"""Plain FP64 CPU oracle of the 1D ADER-DG / ADER-WENO schemes (arXiv 2409.12483).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package; the product package ``paper_2409_12483_gb300`` never does, and this
+package never imports the product package.  The arithmetic lives in
+``ader_oracle.c`` (plain C, FP64, long double for the basis); this module only
+marshals numpy arrays through ctypes and adds the error norms of Sec. 2.1
+(eq. epsilons), which are plain numpy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ader_oracle.c")
+_HDR = os.path.join(_HERE, "ader_oracle.h")
+_LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
+
+M = 3
+MAXN = 10
+MAXNS = 19
+
+OB_OK = 0
+OB_ERR_ARG = 1
+OB_ERR_NOT_CONVERGED = 4
+OB_ERR_NONPHYSICAL = 5
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Basis(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("n", C.c_int), ("Ns", C.c_int),
+        ("xi", C.c_double * MAXN), ("w", C.c_double * MAXN),
+        ("psi0", C.c_double * MAXN), ("psi1", C.c_double * MAXN),
+        ("dphi", (C.c_double * MAXN) * MAXN),
+        ("lam", (C.c_double * MAXN) * MAXN),
+        ("xi_m", (C.c_double * MAXN) * MAXN),
+        ("ups", (C.c_double * MAXN) * MAXN),
+        ("kap", (C.c_double * MAXN) * MAXN),
+        ("kt", (C.c_double * MAXN) * MAXN),
+        ("dt_m", (C.c_double * MAXN) * MAXN),
+        ("P", (C.c_double * MAXN) * MAXNS),
+    ]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("fixed_iter", C.c_int)]
+
+
+class Weno(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("n", C.c_int), ("shift", C.c_int * 3),
+        ("lin", C.c_double * 3), ("eps", C.c_double), ("r", C.c_int),
+        ("ainv", ((C.c_double * MAXN) * MAXN) * 3),
+        ("sig", (C.c_double * MAXN) * MAXN),
+        ("dal", ((C.c_double * MAXN) * MAXN) * MAXN),
+        ("wq", C.c_double * MAXN),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cells", C.c_int64), ("max_iters", C.c_int), ("min_iters", C.c_int),
+                ("mean_iters", C.c_double), ("status", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_DP = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_IP = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            P = C.POINTER
+            L.ob_basis_build.argtypes = [C.c_int, P(Basis)]
+            L.ob_basis_eval.argtypes = [P(Basis), C.c_double, _DP]
+            L.ob_basis_eval.restype = None
+            L.ob_euler_flux.argtypes = [C.c_double, _DP, _DP]
+            L.ob_euler_flux.restype = None
+            L.ob_wave_speed.argtypes = [C.c_double, _DP]
+            L.ob_wave_speed.restype = C.c_double
+            L.ob_rusanov.argtypes = [C.c_double, _DP, _DP, _DP]
+            L.ob_rusanov.restype = None
+            for name in ("ob_predict_cell", "ob_predict_cell_nested"):
+                f = getattr(L, name)
+                f.argtypes = [P(Basis), P(Params), C.c_double, _DP, _DP, P(C.c_int)]
+            L.ob_dg_lambda_max.argtypes = [P(Basis), C.c_double, C.c_int64, _DP]
+            L.ob_dg_lambda_max.restype = C.c_double
+            L.ob_fv_lambda_max.argtypes = [C.c_double, C.c_int64, _DP]
+            L.ob_fv_lambda_max.restype = C.c_double
+            L.ob_dg_dt.argtypes = [P(Basis), P(Params), C.c_double, C.c_int64, _DP]
+            L.ob_dg_dt.restype = C.c_double
+            L.ob_fv_dt.argtypes = [P(Params), C.c_double, C.c_int64, _DP]
+            L.ob_fv_dt.restype = C.c_double
+            L.ob_dg_correct.argtypes = [P(Basis), P(Params), C.c_int64, C.c_double, C.c_double,
+                                        _DP, _DP, _DP]
+            L.ob_dg_step.argtypes = [P(Basis), P(Params), C.c_int64, C.c_double, C.c_double,
+                                     _DP, _DP, C.c_void_p, P(Stats)]
+            L.ob_dg_step_cells.argtypes = [P(Basis), P(Params), C.c_int64, C.c_double, C.c_double,
+                                           _DP, _IP, C.c_int64, _DP]
+            L.ob_weno_build.argtypes = [C.c_int, P(Basis), P(Weno)]
+            L.ob_weno_sigma.argtypes = [P(Weno), _DP]
+            L.ob_weno_sigma.restype = C.c_double
+            L.ob_weno_reconstruct.argtypes = [P(Weno), C.c_int64, _DP, _DP]
+            L.ob_weno_cell.argtypes = [P(Weno), C.c_int64, _DP, C.c_int64, _DP, C.c_void_p]
+            L.ob_fv_step.argtypes = [P(Basis), P(Weno), P(Params), C.c_int64, C.c_double,
+                                     C.c_double, _DP, _DP, P(Stats)]
+            L.ob_fv_step_cells.argtypes = [P(Basis), P(Weno), P(Params), C.c_int64, C.c_double,
+                                           C.c_double, _DP, _IP, C.c_int64, _DP]
+            L.ob_solve.argtypes = [C.c_int, P(Basis), C.c_void_p, P(Params), C.c_int64,
+                                   C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
+                                   P(C.c_double)]
+            _lib = L
+    return _lib
+
+
+def _arr(x, n=None):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a if n is None else a.reshape(n)
+
+
+class Oracle:
+    """One degree N: basis, operators and (for even N >= 2) WENO tables."""
+
+    def __init__(self, N: int, gamma: float = 1.4, cfl: float = 0.4, tol: float = 1e-13,
+                 max_iter: int | None = None, fixed_iter: int = 0):
+        L = lib()
+        self.N = N
+        self.n = N + 1
+        self.basis = Basis()
+        rc = L.ob_basis_build(N, C.byref(self.basis))
+        if rc != OB_OK:
+            raise ValueError(f"oracle basis build failed for N={N}")
+        self.params = Params(gamma, cfl, tol, max_iter if max_iter else 4 * self.n + 8, fixed_iter)
+        self.weno = None
+        if N >= 2 and N % 2 == 0:
+            self.weno = Weno()
+            if L.ob_weno_build(N, C.byref(self.basis), C.byref(self.weno)) != OB_OK:
+                raise ValueError("oracle WENO build failed")
+
+    # -- operator tables as numpy (views copied) --
+    def table(self, name: str) -> np.ndarray:
+        n, b = self.n, self.basis
+        if name in ("xi", "w", "psi0", "psi1"):
+            return np.array(getattr(b, name)[:n])
+        if name == "P":
+            return np.array([[b.P[j][k] for k in range(n)] for j in range(b.Ns)])
+        m = getattr(b, name)
+        return np.array([[m[i][j] for j in range(n)] for i in range(n)])
+
+    def phi(self, x: float) -> np.ndarray:
+        out = np.zeros(self.n)
+        lib().ob_basis_eval(C.byref(self.basis), float(x), out)
+        return out
+
+    def set(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        return self
+
+    # -- predictor --
+    def predict_cell(self, u_cell, lam: float, nested: bool = False):
+        u = _arr(u_cell, self.n * M)
+        q = np.zeros(self.n * self.n * M)
+        it = C.c_int(0)
+        f = lib().ob_predict_cell_nested if nested else lib().ob_predict_cell
+        rc = f(C.byref(self.basis), C.byref(self.params), lam, u, q, C.byref(it))
+        return q.reshape(self.n, self.n, M), it.value, rc
+
+    def predict(self, u, lam: float):
+        u = _arr(u).reshape(-1, self.n, M)
+        out = np.zeros((u.shape[0], self.n, self.n, M))
+        iters = np.zeros(u.shape[0], dtype=np.int32)
+        for i in range(u.shape[0]):
+            out[i], iters[i], _ = self.predict_cell(u[i], lam)
+        return out, iters
+
+    # -- CFL --
+    def dg_lambda_max(self, u):
+        u = _arr(u)
+        return lib().ob_dg_lambda_max(C.byref(self.basis), self.params.gamma,
+                                      u.size // (self.n * M), u)
+
+    def dg_dt(self, u, dx):
+        u = _arr(u)
+        return lib().ob_dg_dt(C.byref(self.basis), C.byref(self.params), dx,
+                              u.size // (self.n * M), u)
+
+    def fv_dt(self, v, dx):
+        v = _arr(v)
+        return lib().ob_fv_dt(C.byref(self.params), dx, v.size // M, v)
+
+    # -- DG --
+    def dg_correct(self, u, q, dx, dt):
+        u = _arr(u)
+        q = _arr(q)
+        out = np.zeros_like(u)
+        nc = u.size // (self.n * M)
+        rc = lib().ob_dg_correct(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u, q, out)
+        if rc != OB_OK:
+            raise RuntimeError(f"ob_dg_correct rc={rc}")
+        return out
+
+    def dg_step(self, u, dx, dt, want_q: bool = False):
+        u = _arr(u)
+        nc = u.size // (self.n * M)
+        out = np.zeros_like(u)
+        q = np.zeros(nc * self.n * self.n * M) if want_q else None
+        st = Stats()
+        rc = lib().ob_dg_step(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u, out,
+                              q.ctypes.data if want_q else None, C.byref(st))
+        return out, q, st, rc
+
+    def dg_step_cells(self, u, dx, dt, cells):
+        u = _arr(u)
+        nc = u.size // (self.n * M)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size * self.n * M)
+        rc = lib().ob_dg_step_cells(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u,
+                                    cells, cells.size, out)
+        return out.reshape(cells.size, self.n, M), rc
+
+    # -- WENO / FV --
+    def weno_reconstruct(self, v):
+        v = _arr(v)
+        nc = v.size // M
+        out = np.zeros(nc * self.n * M)
+        lib().ob_weno_reconstruct(C.byref(self.weno), nc, v, out)
+        return out.reshape(nc, self.n, M)
+
+    def weno_sigma(self, c):
+        return lib().ob_weno_sigma(C.byref(self.weno), _arr(c, self.n))
+
+    def weno_cell(self, v, i):
+        v = _arr(v)
+        out = np.zeros(self.n * M)
+        om = np.zeros(3 * M)
+        lib().ob_weno_cell(C.byref(self.weno), v.size // M, v, int(i), out, om.ctypes.data)
+        return out.reshape(self.n, M), om.reshape(3, M)
+
+    def fv_step(self, v, dx, dt):
+        v = _arr(v)
+        out = np.zeros_like(v)
+        st = Stats()
+        rc = lib().ob_fv_step(C.byref(self.basis), C.byref(self.weno), C.byref(self.params),
+                              v.size // M, dx, dt, v, out, C.byref(st))
+        return out, st, rc
+
+    def fv_step_cells(self, v, dx, dt, cells):
+        v = _arr(v)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size * M)
+        rc = lib().ob_fv_step_cells(C.byref(self.basis), C.byref(self.weno), C.byref(self.params),
+                                    v.size // M, dx, dt, v, cells, cells.size, out)
+        return out.reshape(cells.size, M), rc
+
+    # -- time loop --
+    def solve(self, scheme: str, u, dx, t_end: float = 0.0, max_steps: int = 0):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        nc = u.size // (self.n * M) if scheme == "dg" else u.size // M
+        steps = C.c_int64(0)
+        t = C.c_double(0.0)
+        wp = C.cast(C.pointer(self.weno), C.c_void_p) if (scheme == "fv") else None
+        rc = lib().ob_solve(0 if scheme == "dg" else 1, C.byref(self.basis), wp,
+                            C.byref(self.params), nc, dx, u, t_end, max_steps, C.byref(steps),
+                            C.byref(t))
+        return u, steps.value, t.value, rc
+
+    # -- node coordinates of the DG representation (Sec. 1, eq. dg_repr) --
+    def node_x(self, ncells: int, x0: float = 0.0, x1: float = 1.0) -> np.ndarray:
+        dx = (x1 - x0) / ncells
+        xi = self.table("xi")
+        return x0 + dx * (np.arange(ncells)[:, None] + xi[None, :])
+
+
+# ---------------------------------------------------------------------------
+# error norms of Sec. 2.1 (eq. epsilons) in 1D: 25-point Gauss-Legendre rule per cell
+# ---------------------------------------------------------------------------
+
+def dg_density_errors(orc: Oracle, u, rho_exact, x0: float = 0.0, x1: float = 1.0, npts: int = 25):
+    """L1 and Linf errors of the density of a DG solution u[cell][k][r].
+
+    rho_exact: callable x -> exact density (vectorised).  The L1 integral and
+    the Linf maximum use the same npts Gauss-Legendre points in each cell.
+    """
+    u = np.asarray(u, dtype=np.float64).reshape(-1, orc.n, M)
+    nc = u.shape[0]
+    dx = (x1 - x0) / nc
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx = 0.5 * (gx + 1.0)
+    gw = 0.5 * gw
+    phi = np.stack([orc.phi(x) for x in gx])  # [npts, n]
+    rho_h = u[:, :, 0] @ phi.T  # [nc, npts]
+    xs = x0 + dx * (np.arange(nc)[:, None] + gx[None, :])
+    err = np.abs(rho_h - rho_exact(xs))
+    return float(dx * (err @ gw).sum()), float(err.max())
+
+
+def fv_density_errors(v, rho_avg_exact, x0: float = 0.0, x1: float = 1.0):
+    """L1 and Linf errors of FV cell averages against exact cell averages."""
+    v = np.asarray(v, dtype=np.float64).reshape(-1, M)
+    nc = v.shape[0]
+    dx = (x1 - x0) / nc
+    edges = x0 + dx * np.arange(nc + 1)
+    err = np.abs(v[:, 0] - rho_avg_exact(edges[:-1], edges[1:]))
+    return float(dx * err.sum()), float(err.max())
+
+
+def order(e1: float, e2: float, h1: float, h2: float) -> float:
+    """Empirical convergence order p = ln(e1/e2)/ln(h1/h2)."""
+    return float(np.log(e1 / e2) / np.log(h1 / h2))

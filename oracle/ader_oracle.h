@@ -1,0 +1,135 @@
+/*
+ * ader_oracle.h -- plain, slow, FP64 CPU oracle for the 1D ADER-DG and
+ * ADER-WENO finite-volume schemes (Popov, arXiv 2409.12483), Euler equations.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only the tests, the smoke check of the graft entry point and
+ * the CPU-baseline leg of bench.py use it.  It shares no code with the CUDA
+ * library; the two meet only through the seeded input generators.
+ *
+ * Notation follows the paper: n = N+1 Gauss-Legendre nodes xi_k on [0,1],
+ * weights w_k, Lagrange basis phi_k, psi_k = phi_k(0), psi~_k = phi_k(1),
+ * mass Lambda, stiffness Xi, Upsilon, kappa~ = Upsilon^-1 Lambda,
+ * k~ = Lambda^-1 Xi, D~_kl = w_l Dphi_kl, subcell projection P.
+ * Space-time coefficients are AoS: q[p0][p1][r] (tau node, xi node, variable).
+ *
+ * Parity pins: every function here is pinned by tests/test_oracle_*.py
+ * against closed forms, invariants, textbook special cases and brute force.
+ */
+#ifndef ADER_ORACLE_H
+#define ADER_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OB_MAXDEG 9
+#define OB_MAXN 10            /* nodes = N+1 */
+#define OB_MAXNS 19           /* subcells = 2N+1 */
+#define OB_M 3                /* conserved variables of 1D Euler */
+
+enum { OB_OK = 0, OB_ERR_ARG = 1, OB_ERR_NOT_CONVERGED = 4, OB_ERR_NONPHYSICAL = 5 };
+
+typedef struct {
+  int N, n, Ns;
+  double xi[OB_MAXN];               /* GL nodes on [0,1], ascending (Sec. 1.1, eq. gl_rule) */
+  double w[OB_MAXN];                /* GL weights, sum = 1 */
+  double psi0[OB_MAXN];             /* phi_k(0) */
+  double psi1[OB_MAXN];             /* phi_k(1) */
+  double dphi[OB_MAXN][OB_MAXN];    /* dphi[k][l] = phi_k'(xi_l) */
+  double lam[OB_MAXN][OB_MAXN];     /* Lambda_kl = int phi_k phi_l */
+  double xi_m[OB_MAXN][OB_MAXN];    /* Xi_kl = int phi_k phi_l' */
+  double ups[OB_MAXN][OB_MAXN];     /* Upsilon_kl = phi_k(1)phi_l(1) - Xi_lk */
+  double kap[OB_MAXN][OB_MAXN];     /* kappa~ = Upsilon^-1 Lambda */
+  double kt[OB_MAXN][OB_MAXN];      /* k~ = Lambda^-1 Xi */
+  double dt_m[OB_MAXN][OB_MAXN];    /* D~_kl = w_l dphi_kl */
+  double P[OB_MAXNS][OB_MAXN];      /* P_jk = Ns int_{j/Ns}^{(j+1)/Ns} phi_k */
+} ob_basis;
+
+typedef struct {
+  double gamma;     /* adiabatic index */
+  double cfl;       /* Courant number */
+  double tol;       /* Picard tolerance eps_0 (relative to max(1, max|q|)) */
+  int max_iter;     /* Picard iteration cap (tolerance mode) */
+  int fixed_iter;   /* >0: exactly this many Picard iterations, no early exit */
+} ob_params;
+
+/* WENO reconstruction tables for odd order N+1 (N even): three stencils. */
+typedef struct {
+  int N, n;
+  int shift[3];                       /* first cell of each stencil, relative to i */
+  double lin[3];                      /* linear weights lambda_S */
+  double eps;                         /* epsilon in (sigma+eps)^r */
+  int r;                              /* power r */
+  double ainv[3][OB_MAXN][OB_MAXN];   /* c^S = ainv[S] v_S (nodal values in cell i) */
+  double sig[OB_MAXN][OB_MAXN];       /* smoothness matrix Sigma (sigma = c^T Sigma c) */
+  double dal[OB_MAXN][OB_MAXN][OB_MAXN]; /* dal[a-1][q][k] = a-th xi-derivative of phi_k at xi_q */
+  double wq[OB_MAXN];                 /* GL weights used to integrate the squared derivatives */
+} ob_weno;
+
+typedef struct {
+  int64_t cells;
+  int max_iters, min_iters;
+  double mean_iters;
+  int status;
+} ob_stats;
+
+/* ---- basis and operators ---- */
+int ob_basis_build(int N, ob_basis* b);
+/* phi_k(x) for all k at one point x (reference coords, any real x) */
+void ob_basis_eval(const ob_basis* b, double x, double* phi_out);
+
+/* ---- pointwise physics ---- */
+void ob_euler_flux(double gamma, const double* U, double* F);
+double ob_wave_speed(double gamma, const double* U);
+void ob_rusanov(double gamma, const double* a, const double* b, double* G);
+
+/* ---- LST-DG predictor (Sec. 1.1, eq. lst_dg_predictor_picard) ---- */
+int ob_predict_cell(const ob_basis* b, const ob_params* p, double lam,
+                    const double* u, double* q, int* iters);
+/* Literal nested-loop form of Algorithm lst_dg_predictor with s = b = 0. */
+int ob_predict_cell_nested(const ob_basis* b, const ob_params* p, double lam,
+                           const double* u, double* q, int* iters);
+
+/* ---- CFL (Sec. 1.5) ---- */
+double ob_dg_lambda_max(const ob_basis* b, double gamma, int64_t ncells, const double* u);
+double ob_fv_lambda_max(double gamma, int64_t ncells, const double* v);
+double ob_dg_dt(const ob_basis* b, const ob_params* p, double dx, int64_t ncells, const double* u);
+double ob_fv_dt(const ob_params* p, double dx, int64_t ncells, const double* v);
+
+/* ---- ADER-DG corrector and step (Sec. 1.2, eq. ader_dg_method_full) ---- */
+int ob_dg_correct(const ob_basis* b, const ob_params* p, int64_t ncells, double dx, double dt,
+                  const double* u, const double* q, double* u_new);
+int ob_dg_step(const ob_basis* b, const ob_params* p, int64_t ncells, double dx, double dt,
+               const double* u, double* u_new, double* q_out, ob_stats* st);
+/* u_new only at the listed cells (needs predictors of i-1, i, i+1). */
+int ob_dg_step_cells(const ob_basis* b, const ob_params* p, int64_t ncells, double dx, double dt,
+                     const double* u, const int64_t* cells, int64_t count, double* u_new_sel);
+
+/* ---- WENO reconstruction and ADER-WENO FV step (Sec. 1.3, eq. weno_reconstr) ---- */
+int ob_weno_build(int N, const ob_basis* b, ob_weno* wt);
+/* sigma = sum_{a=1..N} int_0^1 (p^(a))^2 for p = sum_k c_k phi_k, evaluated as
+ * sum_a sum_q w_q (sum_k dal[a-1][q][k] c_k)^2 (exact: degree 2N-2a <= 2N+1). */
+double ob_weno_sigma(const ob_weno* wt, const double* c);
+int ob_weno_reconstruct(const ob_weno* wt, int64_t ncells, const double* v, double* w);
+int ob_weno_cell(const ob_weno* wt, int64_t ncells, const double* v, int64_t i, double* w_i,
+                 double* omega /* [3][M] or NULL */);
+int ob_fv_step(const ob_basis* b, const ob_weno* wt, const ob_params* p, int64_t ncells, double dx,
+               double dt, const double* v, double* v_new, ob_stats* st);
+int ob_fv_step_cells(const ob_basis* b, const ob_weno* wt, const ob_params* p, int64_t ncells,
+                     double dx, double dt, const double* v, const int64_t* cells, int64_t count,
+                     double* v_new_sel);
+
+/* ---- time loop (steps of Sec. 1 in sequence; dt clipped to t_end) ----
+ * scheme 0 = DG (u is [cell][k][r]), 1 = WENO-FV (u is [cell][r]).
+ * Stops when t reaches t_end (t_end > 0) or after max_steps steps. */
+int ob_solve(int scheme, const ob_basis* b, const ob_weno* wt, const ob_params* p, int64_t ncells,
+             double dx, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
+             double* t_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

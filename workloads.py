@@ -1,0 +1,162 @@
+"""Seeded synthetic inputs for the 1D Euler ADER workloads.
+
+This module only draws random numbers and evaluates closed-form initial
+fields; it holds none of the scheme's arithmetic (no basis, no quadrature
+nodes, no fluxes).  Both the CUDA path (tests, bench) and the CPU oracle take
+their inputs from here: each side supplies its own node coordinates.
+
+Workloads (1D stand-ins for the paper's sine-wave advection of Sec. 2.1:
+constant velocity and pressure, a density perturbation that is advected
+unchanged, exact solution rho0(x - u t) on the periodic unit interval):
+
+* ``sine``     rho = 1 + 0.2 sin(2 pi x), u = 1, p = 1 (DG N=2, 100 cells, t_end = 1)
+* ``modes4``   rho = 1 + sum_{k=1..4} a_k sin(2 pi k x + phi_k), a_k ~ U(0, 0.05),
+               phi_k ~ U(0, 2 pi), u = 1, p = 1 (DG N=5 10^5 cells; WENO5 10^6; DG N=7 10^6)
+* ``serving``  independent requests: cells log-uniform in [64, 65536], N ~ U{1..7},
+               rho, p = 1 + sum_{j=1..3} a_j sin(2 pi j x + phi_j), a_j ~ U(0, 0.1/3), u = 0.5,
+               t_end = 0.5, Poisson arrivals.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DEFAULT_SEED = 12483
+GAMMA = 1.4
+TWO_PI = 2.0 * np.pi
+
+
+@dataclass
+class Field1D:
+    """rho(x) = rho0 + sum a_k sin(2 pi k x + phi_k); same form for p; constant u."""
+    rho0: float = 1.0
+    rho_amp: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    rho_phase: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    rho_k: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    u: float = 1.0
+    p0: float = 1.0
+    p_amp: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    p_phase: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    p_k: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    # -- point values --
+    @staticmethod
+    def _modes(x, base, amp, phase, k):
+        x = np.asarray(x, dtype=np.float64)
+        out = np.full(x.shape, base, dtype=np.float64)
+        for a, ph, kk in zip(amp, phase, k):
+            out = out + a * np.sin(TWO_PI * kk * x + ph)
+        return out
+
+    def rho(self, x, t: float = 0.0):
+        """Density at x; for constant p the exact solution is rho0(x - u t)."""
+        return self._modes(np.asarray(x) - self.u * t, self.rho0, self.rho_amp, self.rho_phase,
+                           self.rho_k)
+
+    def p(self, x, t: float = 0.0):
+        return self._modes(np.asarray(x) - self.u * t, self.p0, self.p_amp, self.p_phase, self.p_k)
+
+    # -- exact cell averages over [xa, xb] --
+    @staticmethod
+    def _avg(xa, xb, base, amp, phase, k):
+        xa = np.asarray(xa, dtype=np.float64)
+        xb = np.asarray(xb, dtype=np.float64)
+        out = np.full(xa.shape, base, dtype=np.float64)
+        h = xb - xa
+        for a, ph, kk in zip(amp, phase, k):
+            w = TWO_PI * kk
+            out = out + a * (np.cos(w * xa + ph) - np.cos(w * xb + ph)) / (w * h)
+        return out
+
+    def rho_avg(self, xa, xb, t: float = 0.0):
+        s = self.u * t
+        return self._avg(np.asarray(xa) - s, np.asarray(xb) - s, self.rho0, self.rho_amp,
+                         self.rho_phase, self.rho_k)
+
+    def p_avg(self, xa, xb, t: float = 0.0):
+        s = self.u * t
+        return self._avg(np.asarray(xa) - s, np.asarray(xb) - s, self.p0, self.p_amp,
+                         self.p_phase, self.p_k)
+
+    @property
+    def pressure_is_constant(self) -> bool:
+        return len(self.p_amp) == 0 or not np.any(self.p_amp)
+
+
+def conserved(rho, u, p, gamma: float = GAMMA):
+    """(rho, rho u, E = p/(gamma-1) + rho u^2 / 2) stacked on a new last axis."""
+    rho = np.asarray(rho, dtype=np.float64)
+    u = np.broadcast_to(np.asarray(u, dtype=np.float64), rho.shape)
+    p = np.broadcast_to(np.asarray(p, dtype=np.float64), rho.shape)
+    return np.stack([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u], axis=-1)
+
+
+def nodal_state(f: Field1D, x_nodes, gamma: float = GAMMA):
+    """Conserved variables at the given node coordinates (any shape) -> [..., 3]."""
+    x = np.asarray(x_nodes, dtype=np.float64)
+    return conserved(f.rho(x), f.u, f.p(x), gamma)
+
+
+def cell_average_state(f: Field1D, ncells: int, x0: float = 0.0, x1: float = 1.0,
+                       gamma: float = GAMMA):
+    """Exact cell averages [ncells, 3]; exact because rho u and E are linear in rho and p."""
+    edges = x0 + (x1 - x0) * np.arange(ncells + 1) / ncells
+    ra = f.rho_avg(edges[:-1], edges[1:])
+    pa = f.p_avg(edges[:-1], edges[1:])
+    return np.stack([ra, ra * f.u, pa / (gamma - 1.0) + 0.5 * ra * f.u * f.u], axis=-1)
+
+
+# ---------------------------------------------------------------------------
+# the named workloads
+# ---------------------------------------------------------------------------
+
+def sine() -> Field1D:
+    return Field1D(rho_amp=np.array([0.2]), rho_phase=np.array([0.0]), rho_k=np.array([1.0]))
+
+
+def modes4(seed: int = DEFAULT_SEED) -> Field1D:
+    g = np.random.Generator(np.random.PCG64(seed))
+    a = g.uniform(0.0, 0.05, size=4)
+    ph = g.uniform(0.0, TWO_PI, size=4)
+    return Field1D(rho_amp=a, rho_phase=ph, rho_k=np.arange(1, 5, dtype=np.float64))
+
+
+def random_state(rng: np.random.Generator, shape, rho=(0.5, 2.0), u=(-1.0, 1.0), p=(0.5, 2.0),
+                 gamma: float = GAMMA):
+    """Independent random positive states (for predictor / Riemann unit cases)."""
+    r = rng.uniform(*rho, size=shape)
+    v = rng.uniform(*u, size=shape)
+    pp = rng.uniform(*p, size=shape)
+    return conserved(r, v, pp, gamma)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float
+    cells: int
+    degree: int
+    field: Field1D
+    t_end: float = 0.5
+
+
+def serving_requests(count: int = 4096, seed: int = DEFAULT_SEED, rate: float = 1.0,
+                     min_cells: int = 64, max_cells: int = 65536, degrees=(1, 7),
+                     t_end: float = 0.5):
+    """Poisson stream of independent solves (arrival times in seconds for the given rate)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    gaps = g.exponential(1.0 / rate, size=count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    cells = np.rint(np.exp(g.uniform(np.log(min_cells), np.log(max_cells), size=count))).astype(int)
+    degs = g.integers(degrees[0], degrees[1] + 1, size=count)
+    out = []
+    for i in range(count):
+        a_r = g.uniform(0.0, 0.1 / 3.0, size=3)
+        ph_r = g.uniform(0.0, TWO_PI, size=3)
+        a_p = g.uniform(0.0, 0.1 / 3.0, size=3)
+        ph_p = g.uniform(0.0, TWO_PI, size=3)
+        k = np.arange(1, 4, dtype=np.float64)
+        f = Field1D(rho_amp=a_r, rho_phase=ph_r, rho_k=k, u=0.5, p_amp=a_p, p_phase=ph_p, p_k=k)
+        out.append(Request(i, float(arrivals[i]), int(cells[i]), int(degs[i]), f, t_end))
+    return out

@@ -1,0 +1,176 @@
+/*
+ * ader.h -- C ABI of the GB300 (sm_103a) ADER-DG / ADER-WENO library for the
+ * 1D Euler equations (gamma-law gas, M = 3 conserved variables rho, rho u, E).
+ *
+ * Method: Popov, "The effective use of BLAS interface for implementation of
+ * finite-element ADER-DG and finite-volume ADER-WENO methods" (arXiv 2409.12483):
+ *   - LST-DG predictor, Picard iteration of Sec. 1.1 eq. lst_dg_predictor_picard
+ *     with the Kronecker-factored operators kappa~ (x) k~ (eq. m_and_kappa_matrices
+ *     and the Kronecker forms below it), initialised by eq. ind_prop;
+ *   - ADER-DG corrector, Sec. 1.2 eq. ader_dg_method_full reduced to 1D;
+ *   - ADER-WENO finite-volume corrector, Sec. 1.3 eq. ader_weno_fv_method_full,
+ *     fed by the WENO reconstruction of eq. weno_reconstr;
+ *   - time step constraint of Sec. 1.5 with the subcell averages of Sec. 1.4.
+ * The Riemann solver is Rusanov (local Lax-Friedrichs); the paper leaves it open.
+ *
+ * Conventions (every entry point):
+ *   - returns an ader_status; nothing aborts or exits; ader_last_error() holds a
+ *     message for the last failure on that context;
+ *   - "device" pointers are CUDA device addresses owned by the caller (for
+ *     example torch tensors); "host" pointers are ordinary host memory;
+ *   - work is enqueued on the stream given to ader_bind() (NULL = legacy default
+ *     stream) and is asynchronous unless the entry point says it synchronises;
+ *   - a context is not thread-safe: use one context per host thread;
+ *   - layouts are AoS, variable fastest:
+ *       DG state      u[cell][k][r]        k < N+1 GL nodes, r < 3
+ *       FV state      v[cell][r]
+ *       predictor     q[cell][p0][p1][r]   p0 = tau node, p1 = xi node
+ *     cell i covers [x0 + i dx, x0 + (i+1) dx], dx = (x1 - x0) / n_cells, periodic.
+ */
+#ifndef ADER_GB300_H
+#define ADER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ADER_OK = 0,
+  ADER_ERR_ARG = 1,            /* invalid argument, size or layout */
+  ADER_ERR_NOMEM = 2,          /* workspace missing or too small */
+  ADER_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  ADER_ERR_NOT_CONVERGED = 4,  /* some cell hit the Picard iteration cap (result still written) */
+  ADER_ERR_NONPHYSICAL = 5,    /* rho <= 0 or p <= 0 (or non-finite) met by the CFL rule */
+  ADER_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  ADER_ERR_STATE = 7           /* call out of order (e.g. no workspace bound) */
+} ader_status;
+
+typedef enum { ADER_SCHEME_DG = 0, ADER_SCHEME_WENO_FV = 1 } ader_scheme;
+
+typedef enum {
+  ADER_PREC_FP64 = 0,            /* whole path in FP64 */
+  ADER_PREC_FP32_PREDICTOR = 1   /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
+} ader_precision;
+
+/* Uniform periodic mesh on [x0, x1]. */
+typedef struct {
+  int64_t n_cells;
+  double x0, x1;
+} ader_mesh;
+
+typedef struct {
+  double gamma;           /* adiabatic index (1.4) */
+  double cfl;             /* Courant number of Sec. 1.5 (0.4) */
+  double picard_tol;      /* eps_0: stop when max|q'-q| <= tol * max(1, max|q'|) (1e-13) */
+  int picard_max_iter;    /* iteration cap in tolerance mode; 0 = 4(N+1)+8 */
+  int picard_fixed_iter;  /* > 0: exactly this many iterations, no early exit */
+  int precision;          /* ader_precision */
+  int fp64_sweeps;        /* FP64 Picard sweeps after the FP32 stage (>= 1) */
+  double fp32_tol;        /* FP32 stage tolerance (relative, as picard_tol) (1e-6) */
+  int profile;            /* 1: ader_solve records CUDA events around every kernel of every
+                             step on the stream it launches them on (graph event nodes) and
+                             waits for each graph, so per-kernel times land in ader_stats */
+} ader_options;
+
+typedef struct {
+  int64_t steps;          /* time steps taken by the last ader_solve* call */
+  double t;               /* simulated time reached */
+  int64_t cells;          /* cells that ran the predictor in the last call */
+  int max_iters;          /* max Picard iterations over those cells (FP64 + FP32 stages) */
+  double mean_iters;      /* mean Picard iterations per cell */
+  int status;             /* sticky device status (ader_status) */
+  int64_t profiled_steps; /* steps timed by the profile option (0 when it is off) */
+  double weno_ms;         /* summed CUDA-event times of the WENO kernel over profiled steps */
+  double predict_ms;      /* ... of the predictor kernel */
+  double face_ms;         /* ... of the interface-flux + update kernel */
+  int64_t kernel_launches;/* kernels the last call launched (including no-op steps after 'done') */
+} ader_stats;
+
+typedef struct ader_ctx ader_ctx;
+
+/* Defaults listed above.  opt: host pointer, written. */
+ader_status ader_default_options(ader_options* opt);
+
+/* Create a context for a mesh, a degree N and a scheme.
+ *   degree: DG 0..7; WENO-FV 2 or 4 (WENO order N+1 feeding an LST-DG predictor of degree N).
+ *   opt: NULL for defaults.  Builds the operator tables of Sec. 1.1 (GL nodes,
+ *   kappa~, k~, D~, psi, psi~, P of Sec. 1.4, WENO tables) on the host; allocates
+ *   no device memory.  *out owns host memory only; free with ader_destroy(). */
+ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_options* opt,
+                      ader_ctx** out);
+void ader_destroy(ader_ctx* ctx);
+const char* ader_last_error(const ader_ctx* ctx);
+const char* ader_status_string(int status);
+
+/* Sizes (in doubles / bytes) the caller must provide. */
+int64_t ader_state_count(const ader_ctx* ctx);      /* DG: n_cells (N+1) 3; FV: n_cells 3 */
+int64_t ader_predictor_count(const ader_ctx* ctx);  /* n_cells (N+1)^2 3 */
+size_t ader_workspace_bytes(const ader_ctx* ctx);   /* device scratch for ader_bind() */
+
+/* Physical coordinates of the state's points: DG: the GL nodes x0 + dx (i + xi_k)
+ * ([cell][k], count = n_cells (N+1)); FV: the cell centres (count = n_cells).
+ * x_host: host array, written. */
+ader_status ader_node_coords(const ader_ctx* ctx, double* x_host, int64_t count);
+
+/* Operator tables (host copies, row-major), for inspection:
+ * name: "xi","w","psi0","psi1" (N+1), "kt","kap","dphi","dtil" ((N+1)^2), "P" ((2N+1)(N+1)). */
+ader_status ader_get_table(const ader_ctx* ctx, const char* name, double* out_host, int64_t count);
+
+/* Bind caller-owned device scratch (>= ader_workspace_bytes, 256-byte aligned)
+ * and a CUDA stream (cudaStream_t, NULL = default stream).  The library never
+ * allocates device memory; the workspace must outlive every call that uses it. */
+ader_status ader_bind(ader_ctx* ctx, void* workspace_dev, size_t bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Hot path.  All state pointers are device pointers of ader_state_count()
+ * doubles (q: ader_predictor_count()).  dt > 0 is used as given; dt <= 0 means
+ * "CFL time step of Sec. 1.5 for the input state" (computed on the device).
+ * ------------------------------------------------------------------------- */
+
+/* CFL time step (Sec. 1.5): DG: CFL/(2N+1) dx / lambda_max over the 2N+1 subcell
+ * averages of Sec. 1.4 in every cell; FV: CFL dx / lambda_max over the cell
+ * averages; lambda = |u| + c.  Clipped to t_end - t when t_end > 0.  Synchronises
+ * the stream and returns the value in *dt_host.  ADER_ERR_NONPHYSICAL when some
+ * subcell state has rho <= 0 or p <= 0. */
+ader_status ader_compute_dt(ader_ctx* ctx, const double* u_dev, double t, double t_end,
+                            double* dt_host);
+
+/* LST-DG predictor for every cell: q for the state u (DG) or for the WENO
+ * reconstruction of v (FV).  Algorithm lst_dg_predictor with S = B = 0. */
+ader_status ader_predict(ader_ctx* ctx, const double* u_dev, double dt, double* q_dev);
+
+/* Corrector that consumes a predictor result q (DG: eq. ader_dg_method_full;
+ * FV: eq. ader_weno_fv_method_full): u_new from u and q.  dt must be > 0. */
+ader_status ader_correct(ader_ctx* ctx, const double* u_dev, const double* q_dev, double dt,
+                         double* u_new_dev);
+
+/* One time step (predictor fused with its trace/volume epilogue, then the fused
+ * interface-flux and update kernel).  u_dev and u_new_dev must not alias. */
+ader_status ader_step(ader_ctx* ctx, const double* u_dev, double* u_new_dev, double dt);
+
+/* WENO reconstruction only (FV contexts): nodal values w[cell][k][r] of eq. weno_reconstr. */
+ader_status ader_weno_reconstruct(ader_ctx* ctx, const double* v_dev, double* w_dev);
+
+/* Time loop with a device-resident time step: repeat {CFL dt, predictor,
+ * corrector} until t = t_end (t_end > 0; the last step is clipped) or until
+ * max_steps steps (max_steps > 0).  The state is updated in place (u_dev);
+ * steps run as CUDA graphs of a fixed number of steps, the host polls the
+ * device 'done' flag once per graph.  Synchronises before returning. */
+ader_status ader_solve(ader_ctx* ctx, double* u_dev, double t_end, int64_t max_steps,
+                       int64_t* steps_out, double* t_out);
+
+/* ader_solve on a HOST state: copies u_host to the device (workspace), solves,
+ * copies the result back to u_host.  Synchronises. */
+ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t max_steps,
+                            int64_t* steps_out, double* t_out);
+
+/* Statistics of the last predictor/solve call (synchronises). */
+ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,275 @@
+"""Thin ctypes binding of include/ader.h (argument marshalling only).
+
+Every step of the method runs in libader_gb300.so; this module converts torch
+tensors to device pointers, passes torch's current CUDA stream, and raises on a
+non-OK status.  There is no CPU fallback: if the library or a GPU is missing the
+calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libader_gb300.so")
+
+ADER_OK = 0
+ADER_ERR_ARG = 1
+ADER_ERR_NOMEM = 2
+ADER_ERR_CUDA = 3
+ADER_ERR_NOT_CONVERGED = 4
+ADER_ERR_NONPHYSICAL = 5
+ADER_ERR_TIMEOUT = 6
+ADER_ERR_STATE = 7
+
+SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+
+class AderError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("x0", C.c_double), ("x1", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
+                ("picard_max_iter", C.c_int), ("picard_fixed_iter", C.c_int),
+                ("precision", C.c_int), ("fp64_sweeps", C.c_int), ("fp32_tol", C.c_double),
+                ("profile", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("cells", C.c_int64),
+                ("max_iters", C.c_int), ("mean_iters", C.c_double), ("status", C.c_int),
+                ("profiled_steps", C.c_int64), ("weno_ms", C.c_double), ("predict_ms", C.c_double),
+                ("face_ms", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = True):
+    """Load libader_gb300.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2409_12483_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        V, P, D, I64, SZ = C.c_void_p, C.POINTER, C.c_double, C.c_int64, C.c_size_t
+        sig = {
+            "ader_default_options": ([P(Options)], C.c_int),
+            "ader_init": ([P(Mesh), C.c_int, C.c_int, P(Options), P(V)], C.c_int),
+            "ader_destroy": ([V], None),
+            "ader_last_error": ([V], C.c_char_p),
+            "ader_status_string": ([C.c_int], C.c_char_p),
+            "ader_state_count": ([V], I64),
+            "ader_predictor_count": ([V], I64),
+            "ader_workspace_bytes": ([V], SZ),
+            "ader_node_coords": ([V, V, I64], C.c_int),
+            "ader_get_table": ([V, C.c_char_p, V, I64], C.c_int),
+            "ader_bind": ([V, V, SZ, V], C.c_int),
+            "ader_compute_dt": ([V, V, D, D, P(D)], C.c_int),
+            "ader_predict": ([V, V, D, V], C.c_int),
+            "ader_correct": ([V, V, V, D, V], C.c_int),
+            "ader_step": ([V, V, V, D], C.c_int),
+            "ader_weno_reconstruct": ([V, V, V], C.c_int),
+            "ader_solve": ([V, V, D, I64, P(I64), P(D)], C.c_int),
+            "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
+            "ader_get_stats": ([V, P(Stats)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return _lib
+
+
+def exported_symbols():
+    """Names the header declares (for the ABI test)."""
+    return ["ader_default_options", "ader_init", "ader_destroy", "ader_last_error",
+            "ader_status_string", "ader_state_count", "ader_predictor_count",
+            "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
+            "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
+            "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats"]
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ader_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """An ader_ctx bound to a torch-allocated workspace and torch's current stream."""
+
+    def __init__(self, n_cells: int, degree: int, scheme: str = "dg", x0: float = 0.0,
+                 x1: float = 1.0, device=None, **options):
+        torch = _torch()
+        L = load()
+        self._L = L
+        self.n_cells = int(n_cells)
+        self.degree = int(degree)
+        self.scheme = scheme
+        self.n = self.degree + 1
+        mesh = Mesh(self.n_cells, float(x0), float(x1))
+        self.options = default_options(**options)
+        ctx = C.c_void_p()
+        rc = L.ader_init(C.byref(mesh), self.degree, SCHEMES[scheme], C.byref(self.options),
+                         C.byref(ctx))
+        if rc != ADER_OK:
+            raise AderError(rc, f"ader_init failed ({L.ader_status_string(rc).decode()})")
+        self._ctx = ctx
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        nbytes = int(L.ader_workspace_bytes(ctx))
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        self._check(L.ader_bind(ctx, C.c_void_p(aligned), nbytes, C.c_void_p(stream)))
+        self.state_count = int(L.ader_state_count(ctx))
+        self.predictor_count = int(L.ader_predictor_count(ctx))
+        self.workspace_bytes = nbytes
+
+    # -- helpers --
+    def _check(self, rc: int, ok=(ADER_OK,)):
+        if rc not in ok:
+            msg = self._L.ader_last_error(self._ctx).decode()
+            raise AderError(rc, msg or self._L.ader_status_string(rc).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.ader_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state_shape(self):
+        return (self.n_cells, self.n, 3) if self.scheme == "dg" else (self.n_cells, 3)
+
+    # -- host-side queries --
+    def node_coords(self):
+        import numpy as np
+        per = self.n if self.scheme == "dg" else 1
+        x = np.zeros(self.n_cells * per)
+        self._check(self._L.ader_node_coords(self._ctx, x.ctypes.data_as(C.c_void_p), x.size))
+        return x.reshape(self.n_cells, per) if per > 1 else x
+
+    def table(self, name: str):
+        import numpy as np
+        n = self.n
+        size = {"xi": n, "w": n, "psi0": n, "psi1": n, "P": (2 * self.degree + 1) * n}.get(name, n * n)
+        out = np.zeros(size)
+        self._check(self._L.ader_get_table(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
+                                           size))
+        if name in ("xi", "w", "psi0", "psi1"):
+            return out
+        return out.reshape(-1, n)
+
+    # -- hot path (same names as the C ABI) --
+    def ader_compute_dt(self, u, t: float = 0.0, t_end: float = 0.0) -> float:
+        dt = C.c_double(0.0)
+        self._check(self._L.ader_compute_dt(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                            t, t_end, C.byref(dt)))
+        return dt.value
+
+    def ader_predict(self, u, dt: float, q):
+        return self._check(self._L.ader_predict(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                                float(dt),
+                                                _ptr(q, numel=self.predictor_count, name="q")))
+
+    def ader_correct(self, u, q, dt: float, u_new):
+        return self._check(self._L.ader_correct(
+            self._ctx, _ptr(u, numel=self.state_count, name="u"),
+            _ptr(q, numel=self.predictor_count, name="q"), float(dt),
+            _ptr(u_new, numel=self.state_count, name="u_new")))
+
+    def ader_step(self, u, u_new, dt: float = 0.0):
+        return self._check(self._L.ader_step(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                             _ptr(u_new, numel=self.state_count, name="u_new"),
+                                             float(dt)))
+
+    def ader_weno_reconstruct(self, v, w):
+        return self._check(self._L.ader_weno_reconstruct(
+            self._ctx, _ptr(v, numel=self.n_cells * 3, name="v"),
+            _ptr(w, numel=self.n_cells * self.n * 3, name="w")))
+
+    def ader_solve(self, u, t_end: float = 0.0, max_steps: int = 0, allow=()):
+        steps = C.c_int64(0)
+        t = C.c_double(0.0)
+        rc = self._L.ader_solve(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                float(t_end), int(max_steps), C.byref(steps), C.byref(t))
+        self._check(rc, ok=(ADER_OK, *allow))
+        return steps.value, t.value, rc
+
+    def ader_solve_host(self, u_host, t_end: float = 0.0, max_steps: int = 0, allow=()):
+        """u_host: a C-contiguous float64 numpy array or CPU torch tensor (pinned is faster)."""
+        import numpy as np
+        torch = _torch()
+        if isinstance(u_host, torch.Tensor):
+            if u_host.is_cuda or u_host.dtype != torch.float64 or not u_host.is_contiguous():
+                raise ValueError("u_host: expected a contiguous CPU float64 tensor")
+            ptr, numel = u_host.data_ptr(), u_host.numel()
+        else:
+            if u_host.dtype != np.float64 or not u_host.flags.c_contiguous:
+                raise ValueError("u_host: expected a C-contiguous float64 array")
+            ptr, numel = u_host.ctypes.data, u_host.size
+        if numel != self.state_count:
+            raise ValueError(f"u_host: expected {self.state_count} elements")
+        steps = C.c_int64(0)
+        t = C.c_double(0.0)
+        rc = self._L.ader_solve_host(self._ctx, C.c_void_p(ptr), float(t_end), int(max_steps),
+                                     C.byref(steps), C.byref(t))
+        self._check(rc, ok=(ADER_OK, *allow))
+        return steps.value, t.value, rc
+
+    def ader_get_stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.ader_get_stats(self._ctx, C.byref(s)))
+        return {"steps": s.steps, "t": s.t, "cells": s.cells, "max_iters": s.max_iters,
+                "mean_iters": s.mean_iters, "status": s.status,
+                "profiled_steps": s.profiled_steps, "weno_ms": s.weno_ms,
+                "predict_ms": s.predict_ms, "face_ms": s.face_ms,
+                "kernel_launches": s.kernel_launches}

@@ -1,0 +1,717 @@
+// ader_capi.cu -- the C ABI of include/ader.h: contexts, caller-owned device
+// workspace, kernel sequencing, the device-resident time loop under CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/ader.h"
+#include "ader_launch.h"
+#include "ader_ops.h"
+
+using namespace ader;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct HostFlags {
+  int done;
+  int status;
+  long long steps;
+  unsigned long long lam;
+  double t;
+};
+
+}  // namespace
+
+struct ader_ctx {
+  Basis basis{};
+  ader_mesh mesh{};
+  ader_options opt{};
+  int N = 0, n = 1, scheme = 0;
+  double dx = 0.0;
+  // workspace (caller-owned)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // private stream for work and graph capture
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_poll[2] = {nullptr, nullptr};
+  HostFlags* hflags = nullptr;    // pinned, 2 entries
+  DevCtl* ctl = nullptr;
+  double* trace = nullptr;
+  double* wrec = nullptr;
+  double* ubuf = nullptr;
+  double* hbuf = nullptr;
+  // cached solve graph
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_u = nullptr;
+  double g_tend = 0.0;
+  long long g_maxsteps = 0;
+  int g_steps = 0;
+  bool prepared = false;
+  char err[512] = {0};
+  // profiling: 4 timing events per graph step (start, predictor start, predictor end, end)
+  static constexpr int kMaxGraphSteps = 64;
+  cudaEvent_t pev[kMaxGraphSteps][4] = {};
+  bool pev_ready = false;
+  long long prof_steps = 0;
+  double prof_ms[3] = {0, 0, 0};  // weno, predict, face
+  long long launches = 0;         // kernels launched by the last call
+};
+
+namespace {
+
+ader_status fail(ader_ctx* c, ader_status st, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, ADER_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_weno_degree(int N) { return N == 2 || N == 4; }
+
+int64_t state_count(const ader_ctx* c) {
+  return c->scheme == ADER_SCHEME_DG ? c->mesh.n_cells * c->n * kM : c->mesh.n_cells * kM;
+}
+
+size_t trace_doubles(const ader_ctx* c) {
+  return (size_t)c->mesh.n_cells * (c->scheme == ADER_SCHEME_DG ? 9 : 6) * c->n;
+}
+
+size_t workspace_bytes(const ader_ctx* c) {
+  size_t b = align_up(sizeof(DevCtl));
+  b += align_up(trace_doubles(c) * sizeof(double));
+  if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
+  b += 2 * align_up((size_t)state_count(c) * sizeof(double));
+  return b;
+}
+
+cudaError_t dispatch_prepare(int N) {
+  switch (N) {
+    case 0: return prepare_degree_0();
+    case 1: return prepare_degree_1();
+    case 2: return prepare_degree_2();
+    case 3: return prepare_degree_3();
+    case 4: return prepare_degree_4();
+    case 5: return prepare_degree_5();
+    case 6: return prepare_degree_6();
+    case 7: return prepare_degree_7();
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define ADER_DISPATCH(fn, N, p, s)            \
+  switch (N) {                                \
+    case 0: return fn##_0(p, s);              \
+    case 1: return fn##_1(p, s);              \
+    case 2: return fn##_2(p, s);              \
+    case 3: return fn##_3(p, s);              \
+    case 4: return fn##_4(p, s);              \
+    case 5: return fn##_5(p, s);              \
+    case 6: return fn##_6(p, s);              \
+    case 7: return fn##_7(p, s);              \
+  }                                           \
+  return cudaErrorInvalidValue;
+
+cudaError_t do_predict(int N, const PredictParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_predict, N, p, s)
+}
+cudaError_t do_face(int N, const FaceParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_face_update, N, p, s)
+}
+cudaError_t do_cfl(int N, const CflParams& p, cudaStream_t s) { ADER_DISPATCH(launch_cfl, N, p, s) }
+cudaError_t do_weno(int N, const WenoParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_weno, N, p, s)
+}
+
+StepParams make_step(const ader_ctx* c, int mode, int par, double dt, double t_end,
+                     long long max_steps) {
+  StepParams sp{};
+  sp.mode = mode;
+  sp.par = par;
+  sp.dt_fixed = dt;
+  sp.t_end = t_end;
+  sp.max_steps = max_steps;
+  sp.cfl_factor = c->scheme == ADER_SCHEME_DG ? c->opt.cfl * c->dx / (double)(2 * c->N + 1)
+                                              : c->opt.cfl * c->dx;
+  sp.inv_dx = 1.0 / c->dx;
+  sp.ctl = c->ctl;
+  return sp;
+}
+
+PredictParams make_predict(const ader_ctx* c, const double* u_nodal, const StepParams& sp) {
+  PredictParams p{};
+  p.u = u_nodal;
+  p.ncells = c->mesh.n_cells;
+  p.out_mode = kOutTrace;
+  p.trace = c->trace;
+  p.dg = c->scheme == ADER_SCHEME_DG;
+  p.prec = c->opt.precision;
+  p.sweeps = c->opt.fp64_sweeps;
+  p.max_iter = c->opt.picard_max_iter;
+  p.fixed_iter = c->opt.picard_fixed_iter;
+  p.tol = c->opt.picard_tol;
+  p.tol32 = (float)c->opt.fp32_tol;
+  p.gamma = c->opt.gamma;
+  p.gm1 = c->opt.gamma - 1.0;
+  p.sp = sp;
+  p.ops = c->basis.d;
+  p.opf = c->basis.f;
+  return p;
+}
+
+FaceParams make_face(const ader_ctx* c, const double* v_old, double* u_new, const StepParams& sp,
+                     int want_lambda) {
+  FaceParams f{};
+  f.trace = c->trace;
+  f.v_old = v_old;
+  f.u_new = u_new;
+  f.ncells = c->mesh.n_cells;
+  f.dg = c->scheme == ADER_SCHEME_DG;
+  f.want_lambda = want_lambda;
+  f.Ns = c->basis.Ns;
+  f.gamma = c->opt.gamma;
+  f.gm1 = c->opt.gamma - 1.0;
+  f.sp = sp;
+  f.ops = c->basis.d;
+  return f;
+}
+
+ader_status need_bound(ader_ctx* ctx) {
+  if (!ctx) return ADER_ERR_ARG;
+  if (!ctx->ws) return fail(ctx, ADER_ERR_STATE, "no workspace bound (call ader_bind first)");
+  return ADER_OK;
+}
+
+// enqueue the CFL kernel into lam[slot] (resets the slot first)
+ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
+  CK(cudaMemsetAsync(&ctx->ctl->lam[slot], 0, sizeof(unsigned long long), ctx->stream));
+  CflParams p{};
+  p.u = u;
+  p.ncells = ctx->mesh.n_cells;
+  p.dg = ctx->scheme == ADER_SCHEME_DG;
+  p.slot = slot;
+  p.Ns = ctx->basis.Ns;
+  p.gamma = ctx->opt.gamma;
+  p.gm1 = ctx->opt.gamma - 1.0;
+  p.ctl = ctx->ctl;
+  p.ops = ctx->basis.d;
+  CK(do_cfl(ctx->N, p, ctx->stream));
+  ctx->launches += 1;
+  return ADER_OK;
+}
+
+// one step from src to dst with the given step parameters; ev (4 events or
+// null) are recorded around the kernels as external event nodes when captured
+ader_status enqueue_step(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
+                         int want_lambda, cudaEvent_t* ev = nullptr) {
+  const double* nodal = src;
+  if (ev) CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
+  if (ctx->scheme == ADER_SCHEME_WENO_FV) {
+    WenoParams w{};
+    w.v = src;
+    w.w = ctx->wrec;
+    w.ncells = ctx->mesh.n_cells;
+    w.wo = ctx->basis.weno;
+    CK(do_weno(ctx->N, w, ctx->stream));
+    nodal = ctx->wrec;
+  }
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], ctx->stream, cudaEventRecordExternal));
+  PredictParams p = make_predict(ctx, nodal, sp);
+  CK(do_predict(ctx->N, p, ctx->stream));
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], ctx->stream, cudaEventRecordExternal));
+  FaceParams f = make_face(ctx, src, dst, sp, want_lambda);
+  CK(do_face(ctx->N, f, ctx->stream));
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
+  ctx->launches += ctx->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
+  return ADER_OK;
+}
+
+// fork the private stream from the caller's stream / join back
+ader_status fork_in(ader_ctx* ctx) {
+  CK(cudaEventRecord(ctx->ev_fork, ctx->user_stream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_fork, 0));
+  return ADER_OK;
+}
+ader_status join_out(ader_ctx* ctx) {
+  CK(cudaEventRecord(ctx->ev_join, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_join, 0));
+  return ADER_OK;
+}
+
+ader_status reset_ctl(ader_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(DevCtl), ctx->stream));
+  ctx->launches = 0;
+  return ADER_OK;
+}
+
+ader_status status_from_flags(ader_ctx* ctx, int st) {
+  if (st & kStNonPhysical)
+    return fail(ctx, ADER_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
+  if (st & kStNotConverged)
+    return fail(ctx, ADER_ERR_NOT_CONVERGED, "Picard iteration cap reached in some cell");
+  return ADER_OK;
+}
+
+int graph_steps_for(int64_t ncells) {
+  if (ncells <= 4096) return 64;
+  if (ncells <= 65536) return 16;
+  if (ncells <= 524288) return 8;
+  return 4;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ader_status_string(int s) {
+  switch (s) {
+    case ADER_OK: return "ok";
+    case ADER_ERR_ARG: return "invalid argument";
+    case ADER_ERR_NOMEM: return "workspace missing or too small";
+    case ADER_ERR_CUDA: return "CUDA error";
+    case ADER_ERR_NOT_CONVERGED: return "Picard iteration did not converge";
+    case ADER_ERR_NONPHYSICAL: return "non-physical state";
+    case ADER_ERR_TIMEOUT: return "device wait timed out";
+    case ADER_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+ader_status ader_default_options(ader_options* o) {
+  if (!o) return ADER_ERR_ARG;
+  o->gamma = 1.4;
+  o->cfl = 0.4;
+  o->picard_tol = 1e-13;
+  o->picard_max_iter = 0;
+  o->picard_fixed_iter = 0;
+  o->precision = ADER_PREC_FP64;
+  o->fp64_sweeps = 1;
+  o->fp32_tol = 1e-6;
+  o->profile = 0;
+  return ADER_OK;
+}
+
+ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_options* opt,
+                      ader_ctx** out) {
+  if (!out) return ADER_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || mesh->n_cells <= 0 || !(mesh->x1 > mesh->x0)) return ADER_ERR_ARG;
+  if (scheme != ADER_SCHEME_DG && scheme != ADER_SCHEME_WENO_FV) return ADER_ERR_ARG;
+  if (degree < 0 || degree > kMaxDeg) return ADER_ERR_ARG;
+  if (scheme == ADER_SCHEME_WENO_FV && !is_weno_degree(degree)) return ADER_ERR_ARG;
+  // every per-cell index fits in int64 with room for the 9 (N+1) 3 doubles per cell
+  if (mesh->n_cells > (int64_t)1 << 36) return ADER_ERR_ARG;
+  ader_ctx* c = new (std::nothrow) ader_ctx();
+  if (!c) return ADER_ERR_NOMEM;
+  c->mesh = *mesh;
+  c->N = degree;
+  c->n = degree + 1;
+  c->scheme = scheme;
+  c->dx = (mesh->x1 - mesh->x0) / (double)mesh->n_cells;
+  if (opt) {
+    c->opt = *opt;
+  } else {
+    ader_default_options(&c->opt);
+  }
+  ader_options& o = c->opt;
+  if (o.picard_max_iter <= 0) o.picard_max_iter = 4 * c->n + 8;
+  if (!(o.gamma > 1.0) || !(o.cfl > 0.0) || !(o.picard_tol >= 0.0) || o.picard_fixed_iter < 0 ||
+      (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR) ||
+      (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000) {
+    delete c;
+    return ADER_ERR_ARG;
+  }
+  if (build_basis(degree, scheme == ADER_SCHEME_WENO_FV, &c->basis) != 0) {
+    delete c;
+    return ADER_ERR_ARG;
+  }
+  *out = c;
+  return ADER_OK;
+}
+
+void ader_destroy(ader_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (auto& e : c->ev_poll)
+    if (e) cudaEventDestroy(e);
+  if (c->hflags) cudaFreeHost(c->hflags);
+  if (c->pev_ready)
+    for (auto& row : c->pev)
+      for (auto& e : row)
+        if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* ader_last_error(const ader_ctx* c) { return c ? c->err : "null context"; }
+
+int64_t ader_state_count(const ader_ctx* c) { return c ? state_count(c) : -1; }
+int64_t ader_predictor_count(const ader_ctx* c) {
+  return c ? c->mesh.n_cells * c->n * c->n * kM : -1;
+}
+size_t ader_workspace_bytes(const ader_ctx* c) { return c ? workspace_bytes(c) : 0; }
+
+ader_status ader_node_coords(const ader_ctx* c, double* x, int64_t count) {
+  if (!c || !x) return ADER_ERR_ARG;
+  const int per = c->scheme == ADER_SCHEME_DG ? c->n : 1;
+  if (count != c->mesh.n_cells * per) return ADER_ERR_ARG;
+  for (int64_t i = 0; i < c->mesh.n_cells; ++i)
+    for (int k = 0; k < per; ++k)
+      x[i * per + k] = c->mesh.x0 + c->dx * ((double)i + (per == 1 ? 0.5 : c->basis.d.xi[k]));
+  return ADER_OK;
+}
+
+ader_status ader_get_table(const ader_ctx* c, const char* name, double* out, int64_t count) {
+  if (!c || !name || !out) return ADER_ERR_ARG;
+  const int n = c->n;
+  const OpsD& d = c->basis.d;
+  auto vec = [&](const double* src, int m) -> ader_status {
+    if (count != m) return ADER_ERR_ARG;
+    std::memcpy(out, src, sizeof(double) * m);
+    return ADER_OK;
+  };
+  auto mat = [&](const double (*src)[kMaxN], int rows) -> ader_status {
+    if (count != (int64_t)rows * n) return ADER_ERR_ARG;
+    for (int i = 0; i < rows; ++i)
+      for (int j = 0; j < n; ++j) out[i * n + j] = src[i][j];
+    return ADER_OK;
+  };
+  if (!strcmp(name, "xi")) return vec(d.xi, n);
+  if (!strcmp(name, "w")) return vec(d.w, n);
+  if (!strcmp(name, "psi0")) return vec(d.psi0, n);
+  if (!strcmp(name, "psi1")) return vec(d.psi1, n);
+  if (!strcmp(name, "kt")) return mat(d.kt, n);
+  if (!strcmp(name, "kap")) return mat(d.kap, n);
+  if (!strcmp(name, "dphi")) return mat(c->basis.dphi, n);
+  if (!strcmp(name, "dtil")) return mat(c->basis.dtil, n);
+  if (!strcmp(name, "P")) return mat(d.P, c->basis.Ns);
+  return ADER_ERR_ARG;
+}
+
+ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
+  if (!ctx || !ws) return ADER_ERR_ARG;
+  if (bytes < workspace_bytes(ctx))
+    return fail(ctx, ADER_ERR_NOMEM, "workspace %zu bytes < required %zu", bytes,
+                workspace_bytes(ctx));
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign)
+    return fail(ctx, ADER_ERR_ARG, "workspace must be %zu-byte aligned", kAlign);
+  if (!ctx->prepared) {
+    CK(dispatch_prepare(ctx->N));
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_poll[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_poll[1], cudaEventDisableTiming));
+    CK(cudaMallocHost(&ctx->hflags, 2 * sizeof(HostFlags)));
+    ctx->prepared = true;
+  }
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  ctx->ws = static_cast<char*>(ws);
+  ctx->ws_bytes = bytes;
+  ctx->user_stream = static_cast<cudaStream_t>(stream);
+  char* p = ctx->ws;
+  ctx->ctl = reinterpret_cast<DevCtl*>(p);
+  p += align_up(sizeof(DevCtl));
+  ctx->trace = reinterpret_cast<double*>(p);
+  p += align_up(trace_doubles(ctx) * sizeof(double));
+  if (ctx->scheme == ADER_SCHEME_WENO_FV) {
+    ctx->wrec = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * ctx->n * kM * 8);
+  }
+  ctx->ubuf = reinterpret_cast<double*>(p);
+  p += align_up((size_t)state_count(ctx) * sizeof(double));
+  ctx->hbuf = reinterpret_cast<double*>(p);
+  return ADER_OK;
+}
+
+ader_status ader_compute_dt(ader_ctx* ctx, const double* u, double t, double t_end,
+                            double* dt_host) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u || !dt_host) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(&ctx->hflags[0].lam, &ctx->ctl->lam[0], sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hflags[0].status, &ctx->ctl->status, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  double lam;
+  std::memcpy(&lam, &ctx->hflags[0].lam, sizeof(lam));
+  if ((ctx->hflags[0].status & kStNonPhysical) || !(lam > 0.0) || !std::isfinite(lam))
+    return fail(ctx, ADER_ERR_NONPHYSICAL, "non-physical state in the CFL reduction");
+  const StepParams sp = make_step(ctx, kDtCfl, 0, 0.0, 0.0, 0);
+  double dt = sp.cfl_factor / lam;
+  if (t_end > 0.0 && t + dt >= t_end) dt = t_end - t;
+  *dt_host = dt;
+  return ADER_OK;
+}
+
+ader_status ader_predict(ader_ctx* ctx, const double* u, double dt, double* q) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u || !q) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (std::isnan(dt)) return fail(ctx, ADER_ERR_ARG, "dt is NaN");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  int mode = kDtFixed;
+  if (!(dt > 0.0)) {
+    if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
+    mode = kDtCfl;
+  }
+  const StepParams sp = make_step(ctx, mode, 0, dt, 0.0, 0);
+  const double* nodal = u;
+  if (ctx->scheme == ADER_SCHEME_WENO_FV) {
+    WenoParams w{};
+    w.v = u;
+    w.w = ctx->wrec;
+    w.ncells = ctx->mesh.n_cells;
+    w.wo = ctx->basis.weno;
+    CK(do_weno(ctx->N, w, ctx->stream));
+    nodal = ctx->wrec;
+  }
+  PredictParams p = make_predict(ctx, nodal, sp);
+  p.out_mode = kOutQ;
+  p.q_out = q;
+  CK(do_predict(ctx->N, p, ctx->stream));
+  return join_out(ctx);
+}
+
+ader_status ader_correct(ader_ctx* ctx, const double* u, const double* q, double dt,
+                         double* u_new) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u || !q || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (!(dt > 0.0)) return fail(ctx, ADER_ERR_ARG, "ader_correct needs dt > 0");
+  if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  const StepParams sp = make_step(ctx, kDtFixed, 0, dt, 0.0, 0);
+  PredictParams p = make_predict(ctx, u, sp);
+  p.from_q = 1;
+  p.q_in = q;
+  CK(do_predict(ctx->N, p, ctx->stream));
+  FaceParams f = make_face(ctx, u, u_new, sp, 0);
+  CK(do_face(ctx->N, f, ctx->stream));
+  return join_out(ctx);
+}
+
+ader_status ader_step(ader_ctx* ctx, const double* u, double* u_new, double dt) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
+  if (std::isnan(dt)) return fail(ctx, ADER_ERR_ARG, "dt is NaN");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  int mode = kDtFixed;
+  if (!(dt > 0.0)) {
+    if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
+    mode = kDtCfl;
+  }
+  const StepParams sp = make_step(ctx, mode, 0, dt, 0.0, 0);
+  if ((st = enqueue_step(ctx, u, u_new, sp, 0)) != ADER_OK) return st;
+  return join_out(ctx);
+}
+
+ader_status ader_weno_reconstruct(ader_ctx* ctx, const double* v, double* w) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (ctx->scheme != ADER_SCHEME_WENO_FV)
+    return fail(ctx, ADER_ERR_ARG, "WENO reconstruction needs a WENO-FV context");
+  if (!v || !w) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  WenoParams p{};
+  p.v = v;
+  p.w = w;
+  p.ncells = ctx->mesh.n_cells;
+  p.wo = ctx->basis.weno;
+  CK(do_weno(ctx->N, p, ctx->stream));
+  return join_out(ctx);
+}
+
+ader_status ader_solve(ader_ctx* ctx, double* u, double t_end, int64_t max_steps,
+                       int64_t* steps_out, double* t_out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (!(t_end > 0.0) && max_steps <= 0)
+    return fail(ctx, ADER_ERR_ARG, "need t_end > 0 or max_steps > 0");
+  if (std::isnan(t_end) || max_steps < 0) return fail(ctx, ADER_ERR_ARG, "bad t_end / max_steps");
+  if (!(t_end > 0.0)) t_end = 0.0;
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
+
+  const int K = graph_steps_for(ctx->mesh.n_cells);
+  const bool prof = ctx->opt.profile != 0;
+  if (prof && !ctx->pev_ready) {
+    for (int j = 0; j < ader_ctx::kMaxGraphSteps; ++j)
+      for (int e = 0; e < 4; ++e) CK(cudaEventCreate(&ctx->pev[j][e]));
+    ctx->pev_ready = true;
+  }
+  ctx->prof_steps = 0;
+  ctx->prof_ms[0] = ctx->prof_ms[1] = ctx->prof_ms[2] = 0.0;
+  if (!ctx->gexec || ctx->g_u != u || ctx->g_tend != t_end || ctx->g_maxsteps != max_steps ||
+      ctx->g_steps != K) {
+    if (ctx->gexec) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    cudaGraph_t g;
+    const long long before = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ader_status cst = ADER_OK;
+    for (int j = 0; j < K && cst == ADER_OK; ++j) {
+      const StepParams sp = make_step(ctx, kDtSolve, j & 1, 0.0, t_end, max_steps);
+      const double* src = (j & 1) ? ctx->ubuf : u;
+      double* dst = (j & 1) ? u : ctx->ubuf;
+      cst = enqueue_step(ctx, src, dst, sp, 1, prof ? ctx->pev[j] : nullptr);
+    }
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (cst != ADER_OK) {
+      if (ce == cudaSuccess) cudaGraphDestroy(g);
+      return cst;
+    }
+    if (ce != cudaSuccess)
+      return fail(ctx, ADER_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess)
+      return fail(ctx, ADER_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+    ctx->launches = before;  // capture launches nothing; replays are counted below
+    ctx->g_u = u;
+    ctx->g_tend = t_end;
+    ctx->g_maxsteps = max_steps;
+    ctx->g_steps = K;
+  }
+  // Replay K-step graphs; keep two in flight and poll the 'done' flag of the
+  // older one.  Steps after 'done' are no-ops on the device.
+  const long long max_launches =
+      max_steps > 0 ? (max_steps + K - 1) / K + 1 : (long long)4e9 / K;
+  long long launches = 0;
+  bool finished = false;
+  long long steps_seen = 0;
+  while (prof && !finished) {
+    // one graph at a time: read the K step timings before the events are re-recorded
+    CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hflags[0].done, &ctx->ctl->done, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hflags[0].steps, &ctx->ctl->steps, sizeof(long long),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ++launches;
+    const long long active = ctx->hflags[0].steps - steps_seen;
+    steps_seen = ctx->hflags[0].steps;
+    for (long long j = 0; j < active && j < K; ++j) {
+      float ms[3];
+      for (int e = 0; e < 3; ++e) CK(cudaEventElapsedTime(&ms[e], ctx->pev[j][e], ctx->pev[j][e + 1]));
+      for (int e = 0; e < 3; ++e) ctx->prof_ms[e] += ms[e];
+      ctx->prof_steps += 1;
+    }
+    if (ctx->hflags[0].done) finished = true;
+    if (launches >= max_launches) break;
+  }
+  while (!finished) {
+    CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    const int slot = (int)(launches & 1);
+    CK(cudaMemcpyAsync(&ctx->hflags[slot].done, &ctx->ctl->done, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_poll[slot], ctx->stream));
+    ++launches;
+    if (launches >= 2) {
+      const int prev = (int)((launches - 2) & 1);
+      CK(cudaEventSynchronize(ctx->ev_poll[prev]));
+      if (ctx->hflags[prev].done) finished = true;
+    }
+    if (launches >= max_launches) break;
+  }
+  ctx->launches += launches * (long long)K * (ctx->scheme == ADER_SCHEME_WENO_FV ? 3 : 2);
+  CK(cudaMemcpyAsync(&ctx->hflags[0].status, &ctx->ctl->status, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hflags[0].steps, &ctx->ctl->steps, sizeof(long long),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->hflags[0].t, &ctx->ctl->t, sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double t_dev = ctx->hflags[0].t;
+  const long long steps = ctx->hflags[0].steps;
+  if (steps & 1) {  // the last completed step wrote ubuf
+    CK(cudaMemcpyAsync(u, ctx->ubuf, (size_t)state_count(ctx) * sizeof(double),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  if (steps_out) *steps_out = steps;
+  if (t_out) *t_out = t_dev;
+  if (!finished && !(max_steps > 0 && steps >= max_steps))
+    return fail(ctx, ADER_ERR_TIMEOUT, "time loop stopped after %lld graph launches", launches);
+  return status_from_flags(ctx, ctx->hflags[0].status);
+}
+
+ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t max_steps,
+                            int64_t* steps_out, double* t_out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u_host) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  const size_t bytes = (size_t)state_count(ctx) * sizeof(double);
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(ctx->hbuf, u_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  ader_status rs = ader_solve(ctx, ctx->hbuf, t_end, max_steps, steps_out, t_out);
+  if (rs != ADER_OK && rs != ADER_ERR_NOT_CONVERGED && rs != ADER_ERR_NONPHYSICAL) return rs;
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(u_host, ctx->hbuf, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  return rs;
+}
+
+ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!out) return ADER_ERR_ARG;
+  DevCtl h{};
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(&h, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  out->steps = h.steps;
+  out->t = h.t;
+  out->cells = h.iter_cells;
+  out->max_iters = h.iter_max;
+  out->mean_iters = h.iter_cells > 0 ? (double)h.iter_sum / (double)h.iter_cells : 0.0;
+  out->status = h.status & kStNonPhysical ? ADER_ERR_NONPHYSICAL
+                : h.status & kStNotConverged ? ADER_ERR_NOT_CONVERGED
+                                             : ADER_OK;
+  out->profiled_steps = ctx->prof_steps;
+  out->weno_ms = ctx->prof_ms[0];
+  out->predict_ms = ctx->prof_ms[1];
+  out->face_ms = ctx->prof_ms[2];
+  out->kernel_launches = ctx->launches;
+  return ADER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// ader_deg.cu -- instantiates the sm_103a kernels for one degree N and exposes
+// plain launchers.  Compiled once per degree with -DADER_DEG=<0..7>, so the
+// degrees build in parallel and each kernel is fully unrolled for its N.
+#include "ader_kernels.cuh"
+
+#ifndef ADER_DEG
+#error "compile with -DADER_DEG=<0..7>"
+#endif
+
+#define ADER_CAT2(a, b) a##b
+#define ADER_CAT(a, b) ADER_CAT2(a, b)
+
+namespace ader {
+
+namespace {
+constexpr int D = ADER_DEG;
+
+unsigned grid_for(long long items, int threads, long long cap) {
+  long long b = (items + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+}  // namespace
+
+cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
+  cudaError_t e = cudaFuncSetAttribute(predict_kernel<D, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PredCfg<D>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(predict_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PredCfg<D>::kSmemBytes);
+}
+
+cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
+  using C = PredCfg<D>;
+  const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
+  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (p.prec == 1 && !p.from_q)
+    predict_kernel<D, true><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+  else
+    predict_kernel<D, false><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {
+  using C = FaceCfg<D>;
+  const long long blocks = (p.ncells + C::C - 1) / C::C;
+  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  face_update_kernel<D><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_cfl_, ADER_DEG)(const CflParams& p, cudaStream_t s) {
+  const long long items = p.dg ? p.ncells * p.Ns : p.ncells;
+  cfl_kernel<D><<<grid_for(items, 256, 152LL * 8), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_weno_, ADER_DEG)(const WenoParams& p, cudaStream_t s) {
+#if ADER_DEG == 2 || ADER_DEG == 4 || ADER_DEG == 6
+  weno_kernel<D><<<grid_for(p.ncells, 128, 0x7fffffffLL), 128, 0, s>>>(p);
+  return cudaGetLastError();
+#else
+  (void)p;
+  (void)s;
+  return cudaErrorNotSupported;
+#endif
+}
+
+}  // namespace ader

@@ -1,0 +1,195 @@
+// ader_device.cuh -- device-side types and pointwise physics shared by the
+// sm_103a kernels: the device control block that keeps the time step on the GPU,
+// the per-launch step parameters, the 1D Euler flux (Sec. 2, eq.
+// system_of_equations), the wave speed |u| + c of Sec. 1.5 and the Rusanov
+// Riemann solver used for the interface flux of eq. ader_dg_method_full.
+#pragma once
+
+#include <cstdint>
+
+#include "ader_ops.h"
+
+namespace ader {
+
+// Sticky device status bits (host maps them to ader_status).
+enum : int { kStNotConverged = 1, kStNonPhysical = 2 };
+
+// Device control block at the start of the workspace.  Written only as noted:
+//   predictor (block 0, thread 0): dt[par], active[par], last[par], lam[par^1] = 0
+//   corrector (block 0, thread 0): t, steps, done
+//   every block (atomics): lam[par^1] (corrector), status, iteration statistics
+struct DevCtl {
+  double t;
+  double dt[2];
+  unsigned long long lam[2];  // bit pattern of lambda_max (>= 0), ordered like the value
+  int active[2];
+  int last[2];
+  int done;
+  int status;
+  long long steps;
+  unsigned long long iter_sum;
+  long long iter_cells;
+  int iter_max;
+  int pad_;
+};
+
+// How a launch gets its time step.
+enum : int {
+  kDtFixed = 0,  // dt_fixed as given
+  kDtCfl = 1,    // dt = cfl_factor / lam[par] (lam from the CFL kernel or the previous corrector)
+  kDtSolve = 2   // as kDtCfl, clipped to t_end - t, stops at t_end / max_steps (sets done)
+};
+
+struct StepParams {
+  int mode;
+  int par;               // launch parity: selects dt/active/last/lam slots
+  double dt_fixed;
+  double t_end;
+  long long max_steps;
+  double cfl_factor;     // DG: CFL dx / (2N+1); FV: CFL dx
+  double inv_dx;
+  DevCtl* ctl;
+};
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+// Predictor side of the time-step protocol.  Every thread evaluates the same
+// expression from the same inputs, so the decision is uniform.
+__device__ __forceinline__ bool predictor_step_dt(const StepParams& sp, double* dt_out) {
+  if (sp.mode == kDtFixed) {
+    *dt_out = sp.dt_fixed;
+    return true;
+  }
+  DevCtl* c = sp.ctl;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (sp.mode == kDtSolve && *(volatile int*)&c->done) {
+    if (lead) c->active[sp.par] = 0;
+    return false;
+  }
+  const double lam = bitsd(*(volatile unsigned long long*)&c->lam[sp.par]);
+  const int st = *(volatile int*)&c->status;
+  if (!(lam > 0.0) || !(lam < 1.0e300) || (st & kStNonPhysical)) {
+    if (lead) {
+      atomicOr(&c->status, kStNonPhysical);
+      c->active[sp.par] = 0;
+      if (sp.mode == kDtSolve) c->done = 1;
+    }
+    return false;
+  }
+  double dt = sp.cfl_factor / lam;
+  int last = 0;  // bit 0: this step is clipped to reach t_end; bit 1: max_steps reached
+  if (sp.mode == kDtSolve) {
+    const double t = *(volatile double*)&c->t;
+    if (sp.t_end > 0.0 && t + dt >= sp.t_end) {
+      dt = sp.t_end - t;
+      last |= 1;
+    }
+    if (sp.max_steps > 0 && *(volatile long long*)&c->steps + 1 >= sp.max_steps) last |= 2;
+  }
+  if (lead) {
+    c->dt[sp.par] = dt;
+    c->active[sp.par] = 1;
+    c->last[sp.par] = last;
+    c->lam[sp.par ^ 1] = 0ull;
+  }
+  *dt_out = dt;
+  return true;
+}
+
+// Corrector side: reads what the predictor of the same launch parity decided.
+__device__ __forceinline__ bool corrector_step_dt(const StepParams& sp, double* dt, int* last) {
+  if (sp.mode == kDtFixed) {
+    *dt = sp.dt_fixed;
+    *last = 0;
+    return true;
+  }
+  const DevCtl* c = sp.ctl;
+  if (!*(const volatile int*)&c->active[sp.par]) return false;
+  *dt = *(const volatile double*)&c->dt[sp.par];
+  *last = *(const volatile int*)&c->last[sp.par];
+  return true;
+}
+
+__device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt, int last) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevCtl* c = sp.ctl;
+    c->t = (sp.mode == kDtSolve && (last & 1)) ? sp.t_end : c->t + dt;
+    c->steps += 1;
+    if (sp.mode == kDtSolve && last) c->done = 1;
+  }
+}
+
+// ---- 1D Euler (rho, m = rho u, E) ----
+
+template <typename T>
+__device__ __forceinline__ void euler_flux(const T* U, T* F, T gm1) {
+  const T inv = T(1) / U[0];
+  const T u = U[1] * inv;
+  const T p = gm1 * fma(T(-0.5) * U[1], u, U[2]);
+  F[0] = U[1];
+  F[1] = fma(U[1], u, p);
+  F[2] = (U[2] + p) * u;
+}
+
+// |u| + c; flags rho <= 0, p <= 0 or non-finite through *bad.
+__device__ __forceinline__ double wave_speed(const double* U, double gamma, double gm1, bool* bad) {
+  const double inv = 1.0 / U[0];
+  const double u = U[1] * inv;
+  const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
+  if (!(U[0] > 0.0) || !(p > 0.0) || !(U[0] < 1.0e300) || !(p < 1.0e300)) {
+    *bad = true;
+    return 0.0;
+  }
+  return fabs(u) + sqrt(gamma * p * inv);
+}
+
+// Rusanov flux between a (left) and b (right): 1/2 (F(a) + F(b)) - 1/2 s (b - a),
+// s = max(|u_a| + c_a, |u_b| + c_b).
+__device__ __forceinline__ void rusanov(const double* a, const double* b, double* G, double gamma,
+                                        double gm1) {
+  const double ia = 1.0 / a[0], ib = 1.0 / b[0];
+  const double ua = a[1] * ia, ub = b[1] * ib;
+  const double pa = gm1 * fma(-0.5 * a[1], ua, a[2]);
+  const double pb = gm1 * fma(-0.5 * b[1], ub, b[2]);
+  const double sa = fabs(ua) + sqrt(gamma * pa * ia);
+  const double sb = fabs(ub) + sqrt(gamma * pb * ib);
+  const double s = fmax(sa, sb);
+  const double Fa0 = a[1], Fa1 = fma(a[1], ua, pa), Fa2 = (a[2] + pa) * ua;
+  const double Fb0 = b[1], Fb1 = fma(b[1], ub, pb), Fb2 = (b[2] + pb) * ub;
+  G[0] = 0.5 * (Fa0 + Fb0) - 0.5 * s * (b[0] - a[0]);
+  G[1] = 0.5 * (Fa1 + Fb1) - 0.5 * s * (b[1] - a[1]);
+  G[2] = 0.5 * (Fa2 + Fb2) - 0.5 * s * (b[2] - a[2]);
+}
+
+__device__ __forceinline__ long long wrap_cell(long long i, long long n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// max over the block of non-negative values given as bit patterns; returns the
+// block maximum in thread 0 (others: undefined).  smem: >= 32 entries.
+__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v,
+                                                             unsigned long long* smem) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? smem[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+  }
+  return v;
+}
+
+}  // namespace ader

@@ -1,0 +1,87 @@
+// ader_launch.h -- launch parameter blocks and per-degree launchers of the
+// sm_103a kernels (one translation unit per degree N, see ader_deg.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ader_device.cuh"
+#include "ader_ops.h"
+
+namespace ader {
+
+enum : int { kOutQ = 0, kOutTrace = 1 };
+
+// LST-DG predictor (Algorithm lst_dg_predictor, S = B = 0) with its epilogue.
+struct PredictParams {
+  const double* u;       // nodal initial data [cell][n][3]: DG u^n, FV WENO reconstruction
+  double* q_out;         // kOutQ: q[cell][p0][p1][3]
+  const double* q_in;    // from_q: q is given, only the epilogue runs
+  double* trace;         // kOutTrace: DG [cell][qR(3n) | qL(3n) | u + volume(3n)], FV [cell][qR | qL]
+  long long ncells;
+  int out_mode;
+  int from_q;
+  int dg;
+  int prec;              // 0 FP64, 1 FP32 Picard + `sweeps` FP64 sweeps
+  int sweeps;
+  int max_iter;
+  int fixed_iter;
+  float tol32;
+  double tol;
+  double gamma, gm1;
+  StepParams sp;
+  OpsD ops;
+  OpsF opf;
+};
+
+// Interface flux (Rusanov at every tau node, GL-weighted in time) fused with the
+// DG / FV update and, optionally, the lambda_max reduction for the next step.
+struct FaceParams {
+  const double* trace;
+  const double* v_old;   // FV: previous cell averages
+  double* u_new;
+  long long ncells;
+  int dg;
+  int want_lambda;
+  int Ns;
+  double gamma, gm1;
+  StepParams sp;
+  OpsD ops;
+};
+
+// lambda_max over subcell (DG) or cell (FV) averages into ctl->lam[slot].
+struct CflParams {
+  const double* u;
+  long long ncells;
+  int dg;
+  int slot;
+  int Ns;
+  double gamma, gm1;
+  DevCtl* ctl;
+  OpsD ops;
+};
+
+struct WenoParams {
+  const double* v;
+  double* w;
+  long long ncells;
+  WenoOps wo;
+};
+
+// Per-degree entry points (defined in ader_deg.cu compiled once per degree).
+#define ADER_DECLARE_DEGREE(D)                                                         \
+  cudaError_t launch_predict_##D(const PredictParams& p, cudaStream_t s);              \
+  cudaError_t launch_face_update_##D(const FaceParams& p, cudaStream_t s);             \
+  cudaError_t launch_cfl_##D(const CflParams& p, cudaStream_t s);                      \
+  cudaError_t launch_weno_##D(const WenoParams& p, cudaStream_t s);                    \
+  cudaError_t prepare_degree_##D();
+
+ADER_DECLARE_DEGREE(0)
+ADER_DECLARE_DEGREE(1)
+ADER_DECLARE_DEGREE(2)
+ADER_DECLARE_DEGREE(3)
+ADER_DECLARE_DEGREE(4)
+ADER_DECLARE_DEGREE(5)
+ADER_DECLARE_DEGREE(6)
+ADER_DECLARE_DEGREE(7)
+
+}  // namespace ader

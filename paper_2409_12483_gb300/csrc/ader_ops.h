@@ -1,0 +1,59 @@
+// ader_ops.h -- operator tables of the LST-DG predictor, the DG corrector, the
+// subcell projection and the WENO reconstruction (Popov, arXiv 2409.12483,
+// Sec. 1.1 eq. gl_rule / eq. m_and_kappa_matrices / Kronecker forms, Sec. 1.2
+// D~, psi, psi~, Sec. 1.4 P, eq. weno_reconstr), built on the host in long double.
+//
+// Construction (deliberately unlike a textbook monomial route):
+//   nodes/weights by Golub-Welsch (Jacobi rotations on the Legendre Jacobi matrix),
+//   Lagrange basis in barycentric form, integrals by Gauss-Legendre quadrature,
+//   inverses by LU with partial pivoting.
+#pragma once
+
+#include <cstdint>
+
+namespace ader {
+
+constexpr int kMaxDeg = 7;
+constexpr int kMaxN = kMaxDeg + 1;        // GL nodes per direction
+constexpr int kMaxNs = 2 * kMaxDeg + 1;   // subcells of Sec. 1.4
+constexpr int kM = 3;                     // conserved variables of 1D Euler
+
+// Tables in the layout the kernels read (row-major, unused entries zero).
+struct OpsD {
+  double xi[kMaxN], w[kMaxN], rw[kMaxN];  // GL nodes on [0,1], weights, 1/w
+  double psi0[kMaxN], psi1[kMaxN];        // phi_k(0), phi_k(1)
+  double kt[kMaxN][kMaxN];                // k~[p][q] = Lambda^-1 Xi = phi_q'(xi_p)
+  double kap[kMaxN][kMaxN];               // kappa~ = Upsilon^-1 Lambda
+  double vt[kMaxN][kMaxN];                // D~[k][l] / w_k, D~[k][l] = w_l phi_k'(xi_l)
+  double P[kMaxNs][kMaxN];                // P[j][k] = Ns int_{j/Ns}^{(j+1)/Ns} phi_k
+};
+
+struct OpsF {
+  float kt[kMaxN][kMaxN];
+  float kap[kMaxN][kMaxN];
+};
+
+// WENO tables for even N (order N+1), three stencils of N+1 cells.
+struct WenoOps {
+  int shift[3];                   // first cell of each stencil relative to i
+  double lin[3];                  // linear weights lambda_S
+  double eps;                     // epsilon of (sigma + eps)^r, r = 8
+  double ainv[3][kMaxN][kMaxN];   // nodal values in cell i = ainv[S] * stencil averages
+  double mono[kMaxN][kMaxN];      // monomial coefficients in t = 2 xi - 1: a_j = sum_k mono[j][k] c_k
+  double smono[kMaxN][kMaxN];     // sigma = sum_{j,l >= 1} a_j smono[j][l] a_l
+};
+
+struct Basis {
+  int N = 0, n = 1, Ns = 1;
+  OpsD d{};
+  OpsF f{};
+  WenoOps weno{};
+  // extra host-only tables for inspection
+  double dphi[kMaxN][kMaxN]{};    // dphi[k][l] = phi_k'(xi_l)
+  double dtil[kMaxN][kMaxN]{};    // D~[k][l]
+};
+
+// Returns 0 on success.  weno != 0 also builds the WENO tables (N even, 2 <= N).
+int build_basis(int N, bool weno, Basis* out);
+
+}  // namespace ader

@@ -18,3 +18,20 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("this test needs a CUDA GPU (run the gpu-marked tests on a GB300)")
+    import paper_2409_12483_gb300 as pkg
+    pkg.load()
+    return torch.device("cuda", 0)
+
+
+def rel_linf(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

@@ -1,0 +1,108 @@
+"""The C-ABI library builds, loads and exports every symbol include/ader.h declares;
+host-only entry points behave (no GPU needed: ader_init and the table queries
+allocate no device memory).  The library's operator tables (Golub-Welsch nodes,
+barycentric basis, quadrature) are cross-checked against the oracle's (Newton
+nodes, exact monomial integrals): two independent constructions of Sec. 1.1.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2409_12483_gb300 as pkg
+    return pkg.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "ader.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ader_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_2409_12483_gb300 as pkg
+    names = header_functions()
+    assert len(names) >= 19
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(pkg.exported_symbols()) == names
+
+
+def test_library_is_sm103a_only():
+    # the build passes exactly one -gencode, for sm_103a
+    from paper_2409_12483_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(build.LIB)
+
+
+def test_init_rejects_bad_arguments(lib):
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    opt = default_options()
+    ctx = C.c_void_p()
+    bad = [
+        (Mesh(0, 0.0, 1.0), 2, 0),     # empty mesh
+        (Mesh(-5, 0.0, 1.0), 2, 0),
+        (Mesh(10, 1.0, 1.0), 2, 0),    # zero length
+        (Mesh(10, 0.0, 1.0), 8, 0),    # degree above 7
+        (Mesh(10, 0.0, 1.0), -1, 0),
+        (Mesh(10, 0.0, 1.0), 3, 1),    # WENO needs an even degree 2 or 4
+        (Mesh(10, 0.0, 1.0), 2, 7),    # unknown scheme
+    ]
+    for mesh, deg, scheme in bad:
+        rc = lib.ader_init(C.byref(mesh), deg, scheme, C.byref(opt), C.byref(ctx))
+        assert rc == 1, (mesh.n_cells, deg, scheme)
+        assert not ctx.value
+    o2 = default_options(fp64_sweeps=0, precision=1)
+    rc = lib.ader_init(C.byref(Mesh(10, 0.0, 1.0)), 2, 0, C.byref(o2), C.byref(ctx))
+    assert rc == 1
+
+
+def test_sizes_and_coordinates(lib):
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    opt = default_options()
+    for scheme, deg, per in [(0, 5, 6), (1, 4, 1)]:
+        ctx = C.c_void_p()
+        assert lib.ader_init(C.byref(Mesh(37, -1.0, 2.0)), deg, scheme, C.byref(opt),
+                             C.byref(ctx)) == 0
+        assert lib.ader_state_count(ctx) == 37 * per * 3
+        assert lib.ader_predictor_count(ctx) == 37 * (deg + 1) ** 2 * 3
+        assert lib.ader_workspace_bytes(ctx) >= 8 * 37 * (deg + 1) * 3
+        x = np.zeros(37 * per)
+        assert lib.ader_node_coords(ctx, x.ctypes.data_as(C.c_void_p), x.size) == 0
+        assert lib.ader_node_coords(ctx, x.ctypes.data_as(C.c_void_p), x.size - 1) == 1
+        assert np.all(np.diff(x) > 0) and x[0] > -1.0 and x[-1] < 2.0
+        # calls that need a bound workspace say so instead of touching the GPU
+        assert lib.ader_step(ctx, None, None, 0.1) in (1, 7)
+        lib.ader_destroy(ctx)
+
+
+@pytest.mark.parametrize("N", range(0, 8))
+def test_library_tables_match_oracle(lib, oracle_mod, N):
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(4, 0.0, 1.0)), N, 0, C.byref(default_options()),
+                         C.byref(ctx)) == 0
+    o = oracle_mod.Oracle(N)
+    n = N + 1
+
+    def get(name, size):
+        out = np.zeros(size)
+        assert lib.ader_get_table(ctx, name.encode(), out.ctypes.data_as(C.c_void_p), size) == 0
+        return out
+
+    for name in ("xi", "w", "psi0", "psi1"):
+        np.testing.assert_allclose(get(name, n), o.table(name), rtol=0, atol=2e-15, err_msg=name)
+    for name, oname in (("kt", "kt"), ("kap", "kap"), ("dphi", "dphi"), ("dtil", "dt_m")):
+        ref = o.table(oname)
+        np.testing.assert_allclose(get(name, n * n).reshape(n, n), ref, rtol=0,
+                                   atol=4e-15 * max(1.0, np.abs(ref).max()), err_msg=name)
+    Ns = 2 * N + 1
+    np.testing.assert_allclose(get("P", Ns * n).reshape(Ns, n), o.table("P"), rtol=0, atol=4e-15)
+    lib.ader_destroy(ctx)

@@ -1,0 +1,216 @@
+"""GPU parity of the ADER-DG path (C ABI through the thin binding) against the oracle.
+
+Bar (the benchmark spec): FP64 GPU path within 1e-12 relative L-infinity of the oracle
+per step and 1e-10 at t_end; relative L-inf = max|gpu - oracle| / max|oracle|.
+Sizes span several predictor tiles (32 cells) and face tiles (64 cells) plus a
+ragged tail; the full-size case (N = 5, 10^5 cells) is checked on sampled cells
+the oracle computes one by one, and by conservation at any size.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import rel_linf
+
+pytestmark = pytest.mark.gpu
+
+NCELLS = 32 * 3 + 7  # three full predictor tiles, a ragged tail, two face tiles
+
+
+def field_nonlinear(seed):
+    g = np.random.default_rng(seed)
+    k = np.arange(1, 4, dtype=float)
+    return W.Field1D(rho_amp=g.uniform(0, 0.1, 3), rho_phase=g.uniform(0, 6.28, 3), rho_k=k,
+                     u=0.5, p_amp=g.uniform(0, 0.1, 3), p_phase=g.uniform(0, 6.28, 3), p_k=k)
+
+
+def make(cuda, nc, N, **kw):
+    from paper_2409_12483_gb300 import Context
+    return Context(nc, N, "dg", **kw)
+
+
+def to_dev(a, cuda):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=cuda)
+
+
+@pytest.mark.parametrize("N", range(0, 8))
+@pytest.mark.parametrize("fixed", [True, False])
+def test_predictor_parity(cuda, oracle_mod, N, fixed):
+    import torch
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(field_nonlinear(N), o.node_x(NCELLS))
+    dx = 1.0 / NCELLS
+    dt = o.dg_dt(u, dx)
+    it = N + 3 if fixed else 0
+    o.set(fixed_iter=it)
+    q_ref, iters = o.predict(u, dt / dx)
+    ctx = make(cuda, NCELLS, N, picard_fixed_iter=it)
+    ud = to_dev(u, cuda)
+    q = torch.empty(ctx.predictor_count, dtype=torch.float64, device=cuda)
+    ctx.ader_predict(ud, dt, q)
+    torch.cuda.synchronize()
+    assert rel_linf(q.cpu().numpy(), q_ref.ravel()) < 1e-12
+    st = ctx.ader_get_stats()
+    assert st["cells"] == NCELLS and st["status"] == 0
+    if fixed:
+        assert st["max_iters"] == it
+    else:
+        assert abs(st["max_iters"] - iters.max()) <= 1
+        assert abs(st["mean_iters"] - iters.mean()) <= 0.5
+
+
+@pytest.mark.parametrize("N", range(0, 8))
+def test_corrector_parity(cuda, oracle_mod, N):
+    import torch
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(field_nonlinear(10 + N), o.node_x(NCELLS))
+    dx = 1.0 / NCELLS
+    dt = o.dg_dt(u, dx)
+    q_ref, _ = o.predict(u, dt / dx)
+    ref = o.dg_correct(u, q_ref, dx, dt)
+    ctx = make(cuda, NCELLS, N)
+    out = torch.empty(ctx.state_count, dtype=torch.float64, device=cuda)
+    ctx.ader_correct(to_dev(u, cuda), to_dev(q_ref, cuda), dt, out)
+    torch.cuda.synchronize()
+    assert rel_linf(out.cpu().numpy(), ref.ravel()) < 1e-12
+
+
+@pytest.mark.parametrize("N", range(0, 8))
+def test_step_parity_fixed_and_cfl_dt(cuda, oracle_mod, N):
+    import torch
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(field_nonlinear(20 + N), o.node_x(NCELLS))
+    dx = 1.0 / NCELLS
+    dt = o.dg_dt(u, dx)
+    ref, _, st, rc = o.dg_step(u, dx, dt)
+    assert rc == 0
+    ctx = make(cuda, NCELLS, N)
+    ud = to_dev(u, cuda)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, dt)
+    torch.cuda.synchronize()
+    assert rel_linf(out.cpu().numpy(), ref.ravel()) < 1e-12
+    # dt <= 0: the CFL time step is computed on the device
+    out2 = torch.empty_like(ud)
+    ctx.ader_step(ud, out2, 0.0)
+    torch.cuda.synchronize()
+    assert rel_linf(out2.cpu().numpy(), ref.ravel()) < 1e-12
+    assert abs(ctx.ader_compute_dt(ud) - dt) <= 1e-14 * dt
+
+
+@pytest.mark.parametrize("nc", [1, 2, 3, 31, 33, 65])
+def test_small_and_ragged_meshes(cuda, oracle_mod, nc):
+    import torch
+    N = 3
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(field_nonlinear(nc), o.node_x(nc))
+    ref, steps_ref, t_ref, rc = o.solve("dg", u, 1.0 / nc, max_steps=5)
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    steps, t, _ = ctx.ader_solve(ud, max_steps=5)
+    torch.cuda.synchronize()
+    assert steps == steps_ref == 5
+    assert abs(t - t_ref) <= 1e-14 * t_ref
+    assert rel_linf(ud.cpu().numpy(), ref) < 1e-12
+
+
+def test_sine_wave_one_period_parity(cuda, oracle_mod):
+    """DG N = 2, 100 cells, rho = 1 + 0.2 sin(2 pi x), u = p = 1, CFL 0.4, t_end = 1."""
+    import torch
+    N, nc = 2, 100
+    o = oracle_mod.Oracle(N)
+    f = W.sine()
+    u = W.nodal_state(f, o.node_x(nc))
+    ref, steps_ref, t_ref, rc = o.solve("dg", u, 1.0 / nc, t_end=1.0)
+    assert rc == 0 and t_ref == 1.0
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    steps, t, rc = ctx.ader_solve(ud, t_end=1.0)
+    torch.cuda.synchronize()
+    got = ud.cpu().numpy()
+    assert steps == steps_ref and t == 1.0
+    assert rel_linf(got, ref) < 1e-10
+    e_gpu = oracle_mod.dg_density_errors(o, got, lambda x: f.rho(x, 1.0))
+    e_ref = oracle_mod.dg_density_errors(o, ref, lambda x: f.rho(x, 1.0))
+    assert abs(e_gpu[0] - e_ref[0]) <= 1e-10 and e_gpu[0] < 3e-7
+
+
+def test_full_size_n5_sampled_and_conservation(cuda, oracle_mod):
+    """DG N = 5, 10^5 cells, four seeded modes: one step checked on sampled cells,
+    then 100 steps checked by conservation and by the error against the exact
+    advected solution."""
+    import torch
+    N, nc = 5, 100_000
+    o = oracle_mod.Oracle(N)
+    f = W.modes4()
+    u = W.nodal_state(f, o.node_x(nc))
+    dx = 1.0 / nc
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, 0.0)  # CFL dt on the device
+    torch.cuda.synchronize()
+    dt = o.dg_dt(u, dx)
+    cells = np.unique(np.concatenate([[0, 1, nc - 1, nc - 2],
+                                      np.random.default_rng(0).integers(0, nc, 60)]))
+    sel, rc = o.dg_step_cells(u, dx, dt, cells)
+    got = out.cpu().numpy().reshape(nc, N + 1, 3)[cells]
+    assert rel_linf(got, sel) < 1e-12
+    w = o.table("w")
+    mass0 = dx * np.einsum("ckr,k->r", u, w)
+    steps, t, rc = ctx.ader_solve(ud, max_steps=100)
+    torch.cuda.synchronize()
+    un = ud.cpu().numpy().reshape(nc, N + 1, 3)
+    assert steps == 100
+    np.testing.assert_allclose(dx * np.einsum("ckr,k->r", un, w), mass0, rtol=1e-13)
+    l1, linf = oracle_mod.dg_density_errors(o, un, lambda x: f.rho(x, t))
+    assert l1 < 1e-12 and linf < 1e-11
+
+
+def test_nonphysical_input_is_reported(cuda, oracle_mod):
+    import torch
+    from paper_2409_12483_gb300 import ADER_ERR_NONPHYSICAL, AderError
+    N, nc = 2, 40
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(W.sine(), o.node_x(nc))
+    u[17, 1, 0] = -0.5
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    with pytest.raises(AderError) as e:
+        ctx.ader_compute_dt(ud)
+    assert e.value.status == ADER_ERR_NONPHYSICAL
+    steps, t, rc = ctx.ader_solve(ud, max_steps=3, allow=(ADER_ERR_NONPHYSICAL,))
+    assert rc == ADER_ERR_NONPHYSICAL and steps == 0
+    # the context stays usable
+    good = to_dev(W.nodal_state(W.sine(), o.node_x(nc)), cuda)
+    steps, t, rc = ctx.ader_solve(good, max_steps=2)
+    assert rc == 0 and steps == 2
+
+
+def test_iteration_cap_is_reported(cuda, oracle_mod):
+    import torch
+    from paper_2409_12483_gb300 import ADER_ERR_NOT_CONVERGED
+    N, nc = 3, 50
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(field_nonlinear(3), o.node_x(nc))
+    ctx = make(cuda, nc, N, picard_max_iter=2)
+    ud = to_dev(u, cuda)
+    steps, t, rc = ctx.ader_solve(ud, max_steps=2, allow=(ADER_ERR_NOT_CONVERGED,))
+    assert rc == ADER_ERR_NOT_CONVERGED and steps == 2
+    assert ctx.ader_get_stats()["max_iters"] == 2
+
+
+def test_host_buffer_solve_matches_device_solve(cuda, oracle_mod):
+    import torch
+    N, nc = 4, 257
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(W.modes4(), o.node_x(nc))
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    ctx.ader_solve(ud, max_steps=7)
+    uh = np.ascontiguousarray(u.copy())
+    steps, t, rc = ctx.ader_solve_host(uh, max_steps=7)
+    torch.cuda.synchronize()
+    assert steps == 7
+    np.testing.assert_array_equal(uh.ravel(), ud.cpu().numpy().ravel())

@@ -170,6 +170,40 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
 /* Statistics of the last predictor/solve call (synchronises). */
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
 
+/* ---------------------------------------------------------------------------
+ * One time step that allocates nothing (no counterpart in the paper: it exists
+ * for callers that cannot allocate device memory -- code running where
+ * cudaMalloc is not allowed or not wanted, e.g. inside a host that owns every
+ * device allocation itself, or a caller with no allocator at hand -- and so
+ * cannot provide the workspace ader_bind() needs).
+ *
+ * Same result as ader_step(ctx, u, u_new, dt) with dt > 0 (same kernels), but
+ * the predictor's trace/volume scratch, the WENO reconstruction (FV) and the
+ * small control block live in one file-scope static device array of
+ * ADER_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library keeps
+ * until the process exits.  The caller passes only the input state u_dev and
+ * the output u_new_dev (device pointers, ader_state_count() doubles each, not
+ * aliased), dt > 0, and a CUDA stream (NULL = legacy default stream).  ctx comes
+ * from ader_init(); ader_bind() is not needed.
+ *
+ *   - needs 256 bytes plus n_cells * 9 (N+1) doubles (DG: traces and volume
+ *     term; FV: traces and reconstruction); larger meshes return ADER_ERR_ARG
+ *     with a message naming the limit (38835 cells at N = 5, 29126 at N = 7,
+ *     46602 for WENO5);
+ *   - calls no cudaMalloc, cudaFree, cudaMallocHost or any other allocating
+ *     routine, and creates no stream or event;
+ *   - the first call on a device sets that device up (looks up the array's
+ *     device address with cudaGetSymbolAddress and raises the kernels' shared
+ *     memory limit): make that first call before any stream capture;
+ *   - every call shares the one array and leaves its contents behind; the
+ *     control block is cleared on the stream at the start of each call, but
+ *     calls whose work overlaps on the GPU (other streams, other threads) race
+ *     on the array: serialise them;
+ *   - asynchronous on the stream; launch errors return ADER_ERR_CUDA. */
+#define ADER_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ader_status ader_step_noalloc(ader_ctx* ctx, const double* u_dev, double* u_new_dev, double dt,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
             "ader_solve": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
+            "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -103,7 +104,8 @@ def exported_symbols():
             "ader_status_string", "ader_state_count", "ader_predictor_count",
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
-            "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats"]
+            "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats",
+            "ader_step_noalloc"]
 
 
 def default_options(**kw) -> Options:
@@ -273,3 +275,48 @@ class Context:
                 "profiled_steps": s.profiled_steps, "weno_ms": s.weno_ms,
                 "predict_ms": s.predict_ms, "face_ms": s.face_ms,
                 "kernel_launches": s.kernel_launches}
+
+
+class NoAllocStep:
+    """ader_step_noalloc for callers that cannot allocate device memory.
+
+    Holds only an ader_ctx from ader_init (host memory); no workspace is bound.
+    Each call runs one time step with its scratch in the library's static device
+    array (ADER_NOALLOC_SCRATCH_BYTES per GPU); the caller passes the input and
+    output states.  Calls whose work overlaps on the GPU race on that array.
+    """
+
+    def __init__(self, n_cells: int, degree: int, scheme: str = "dg", x0: float = 0.0,
+                 x1: float = 1.0, **options):
+        L = load()
+        self._L = L
+        self.n_cells, self.degree, self.scheme = int(n_cells), int(degree), scheme
+        self.options = default_options(**options)
+        ctx = C.c_void_p()
+        rc = L.ader_init(C.byref(Mesh(self.n_cells, float(x0), float(x1))), self.degree,
+                         SCHEMES[scheme], C.byref(self.options), C.byref(ctx))
+        if rc != ADER_OK:
+            raise AderError(rc, f"ader_init failed ({L.ader_status_string(rc).decode()})")
+        self._ctx = ctx
+        self.state_count = int(L.ader_state_count(ctx))
+
+    def step(self, u, u_new, dt: float, stream=None):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = self._L.ader_step_noalloc(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                       _ptr(u_new, numel=self.state_count, name="u_new"),
+                                       float(dt), C.c_void_p(s))
+        if rc != ADER_OK:
+            raise AderError(rc, self._L.ader_last_error(self._ctx).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.ader_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -715,3 +715,102 @@ ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ader_step_noalloc: one step whose scratch is a static device array.
+// For callers that cannot allocate device memory and so cannot bind a workspace.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocBytes = ADER_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kNoallocCtlBytes = 256;  // DevCtl, rounded up
+static_assert(sizeof(DevCtl) <= kNoallocCtlBytes, "control block does not fit");
+
+// The scratch itself: device memory that exists once per GPU for the life of the
+// process.  Host code must not use the symbol as an address (it names a host-side
+// stand-in); the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+bool g_noalloc_degree_ready[kMaxDevices][kMaxDeg + 1] = {};
+
+// Per-device set-up, with that device current: look up the scratch address and
+// raise the predictor's dynamic shared-memory limit for this degree.
+ader_status noalloc_setup(ader_ctx* ctx, int N, void** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(ctx, ADER_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(ctx, ADER_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  if (!g_noalloc_degree_ready[dev][N]) {
+    CK(dispatch_prepare(N));
+    g_noalloc_degree_ready[dev][N] = true;
+  }
+  *out = g_noalloc_ptr[dev];
+  return ADER_OK;
+}
+
+}  // namespace
+
+extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double* u_new, double dt,
+                                         void* stream) {
+  if (!ctx) return ADER_ERR_ARG;
+  if (!u || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, ADER_ERR_ARG, "ader_step_noalloc needs dt > 0");
+  const size_t trace_bytes = trace_doubles(ctx) * sizeof(double);
+  const size_t wrec_bytes =
+      ctx->scheme == ADER_SCHEME_WENO_FV ? (size_t)ctx->mesh.n_cells * ctx->n * kM * sizeof(double) : 0;
+  const size_t need = kNoallocCtlBytes + align_up(trace_bytes) + wrec_bytes;
+  if (need > kNoallocBytes) {
+    const long long per_cell = (long long)(9 * ctx->n * sizeof(double));
+    return fail(ctx, ADER_ERR_ARG,
+                "mesh of %lld cells needs %zu bytes of scratch; the static scratch holds %zu "
+                "bytes (at most %lld cells at N = %d)",
+                (long long)ctx->mesh.n_cells, need, kNoallocBytes,
+                (long long)((kNoallocBytes - kNoallocCtlBytes - 256) / per_cell), ctx->N);
+  }
+  void* base = nullptr;
+  ader_status st = noalloc_setup(ctx, ctx->N, &base);
+  if (st != ADER_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* p = static_cast<char*>(base);
+  DevCtl* ctl = reinterpret_cast<DevCtl*>(p);
+  double* trace = reinterpret_cast<double*>(p + kNoallocCtlBytes);
+  double* wrec = reinterpret_cast<double*>(p + kNoallocCtlBytes + align_up(trace_bytes));
+  // the control block (statistics, status) must start at zero; the traces and
+  // the reconstruction are written in full before they are read
+  CK(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+  StepParams sp = make_step(ctx, kDtFixed, 0, dt, 0.0, 0);
+  sp.ctl = ctl;
+  const double* nodal = u;
+  if (ctx->scheme == ADER_SCHEME_WENO_FV) {
+    WenoParams w{};
+    w.v = u;
+    w.w = wrec;
+    w.ncells = ctx->mesh.n_cells;
+    w.wo = ctx->basis.weno;
+    CK(do_weno(ctx->N, w, s));
+    nodal = wrec;
+  }
+  PredictParams pp = make_predict(ctx, nodal, sp);
+  pp.trace = trace;
+  CK(do_predict(ctx->N, pp, s));
+  FaceParams f = make_face(ctx, u, u_new, sp, 0);
+  f.trace = trace;
+  CK(do_face(ctx->N, f, s));
+  return ADER_OK;
+}

@@ -117,6 +117,53 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+def measure_solve(ctx, u0, time_steps, steps, warmup, flush):
+    """Time `steps` solves of `time_steps` time steps from u0 (after `warmup`),
+    flushing L2 before each; returns (total ms, per-solve stats)."""
+    import torch
+    u = torch.empty_like(u0)
+    prof, times = [], []
+    for i in range(warmup + steps):
+        u.copy_(u0)
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        done, t, rc = ctx.ader_solve(u, max_steps=time_steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        if done != time_steps:
+            raise RuntimeError(f"solve stopped after {done} steps")
+        if i >= warmup:
+            times.append(ev0.elapsed_time(ev1))
+            prof.append(ctx.ader_get_stats())
+    return sum(times), prof, u
+
+
+def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warmup, flush, dg=True,
+                 extra=None):
+    ms, prof, u = measure_solve(ctx, u0, time_steps, steps, warmup, flush)
+    n = degree + 1
+    iters = sum(p["mean_iters"] for p in prof) / len(prof)
+    nsteps = sum(p["profiled_steps"] for p in prof)
+    pred_ms = sum(p["predict_ms"] for p in prof) / max(nsteps, 1)
+    face_ms = sum(p["face_ms"] for p in prof) / max(nsteps, 1)
+    weno_ms = sum(p["weno_ms"] for p in prof) / max(nsteps, 1)
+    out = {"name": name, "workload": workload,
+           "value": cells * time_steps * steps / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms / steps, "mean_picard_iters": iters,
+           "predict_ms_per_launch": pred_ms, "face_update_ms_per_launch": face_ms}
+    if not dg:
+        out["weno_ms_per_launch"] = weno_ms
+    if ctx.options.precision == 0:
+        fl = cells * predictor_flops_per_cell(n, iters, dg)
+        out["predict_fp64_tflops"] = fl / (pred_ms / 1e3) / 1e12
+        out["predict_frac_of_fp64_peak"] = out["predict_fp64_tflops"] / FP64_PEAK_TFLOPS
+    if extra:
+        out.update(extra(u))
+    return out
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -182,12 +229,21 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the secondary workloads (FP32 predictor, WENO5 and N=7 at 10^6 cells)")
+    ap.add_argument("--serving", action="store_true",
+                    help="also run the continuous-batching serving benchmark (scaled Poisson stream)")
+    ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--case", default=None,
+                    help="profiling case instead of the bench line: predict-dg5 | predict-dg7-fp32 | weno5")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.case:
+        return run_case(args)
 
     import numpy as np
     import torch
@@ -300,6 +356,10 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
+        if not args.no_variants:
+            line["variants"] = run_variants(args, dev, flush)
+        if args.serving:
+            line["serving"] = run_serving(dev, args.serving_requests)
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
             line["cpu_baseline"] = {
@@ -308,6 +368,193 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def run_variants(args, dev, flush):
+    """Secondary workloads measured on rank 0 after the headline."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    out = []
+    st = max(2, min(args.steps, 3))
+    # the headline workload with the FP32 predictor (Picard in FP32, 2 FP64 sweeps)
+    ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, precision="fp32", fp64_sweeps=2)
+    u0 = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    ref = Context(CELLS, DEGREE, "dg", device=dev)
+    uref = u0.clone()
+    ref.ader_solve(uref, max_steps=TIME_STEPS)
+
+    def err_vs_fp64(u):
+        d = (u - uref).abs().max().item() / uref.abs().max().item()
+        return {"rel_linf_vs_fp64_path": d}
+    out.append(variant_line("dg5-1e5-fp32pred", "as the headline, FP32 Picard + 2 FP64 sweeps",
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64))
+    del ctx, ref
+    # ADER-WENO5 (WENO N=4 + LST-DG N=4), 10^6 cells, 100 steps, FP64
+    nc = 1_000_000
+    ctx = Context(nc, 4, "fv", device=dev, profile=1)
+    v0 = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
+    out.append(variant_line("weno5-1e6-fp64", "ADER-WENO5 FV, 10^6 cells, modes4, 100 steps, FP64",
+                            ctx, v0, nc, 4, TIME_STEPS, st, 1, flush, dg=False))
+    del ctx, v0
+    # ADER-DG N=7, 10^6 cells: FP64 and FP32-predictor (2 FP64 sweeps), 20 steps
+    ts = 20
+    c64 = Context(nc, 7, "dg", device=dev, profile=1)
+    x = c64.node_coords()
+    u0 = torch.tensor(W.nodal_state(W.modes4(SEED), x), device=dev).reshape(-1)
+    keep = {}
+
+    def grab(u):
+        keep["u64"] = u.clone()
+        return {}
+    out.append(variant_line("dg7-1e6-fp64", "ADER-DG N=7, 10^6 cells, modes4, 20 steps, FP64",
+                            c64, u0, nc, 7, ts, st, 1, flush, extra=grab))
+    del c64
+    c32 = Context(nc, 7, "dg", device=dev, profile=1, precision="fp32", fp64_sweeps=2)
+
+    def err7(u):
+        u64 = keep["u64"]
+        d = (u - u64).abs().max().item() / u64.abs().max().item()
+        return {"rel_linf_vs_fp64_path": d}
+    out.append(variant_line("dg7-1e6-fp32pred", "ADER-DG N=7, 10^6 cells, FP32 Picard + 2 FP64 sweeps",
+                            c32, u0, nc, 7, ts, st, 1, flush, extra=err7))
+    return out
+
+
+SERVING_NOTE = ("scaled stand-in for the 4096-request stream (cells log-uniform in [64, 65536], "
+                "t_end 0.5: ~2.5e13 cell-updates, days of GPU time): {n} requests, cells "
+                "log-uniform in [64, {cmax}], N ~ U{{1..7}}, rho and p = 1 + 3 modes (amplitudes "
+                "<= 0.1/3), u = 0.5, t_end = {tend}, seed 12483; FP32 predictor + FP64 corrector/CFL")
+
+
+def serving_stream(n, cmax, tend, seed=SEED):
+    import workloads as W
+    reqs = W.serving_requests(count=n, seed=seed, rate=1.0, max_cells=cmax, t_end=tend)
+    return reqs
+
+
+def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
+    """Continuous-batching server vs the plain per-solve FP64 path on one GPU.
+
+    Saturation: every request queued at t = 0.  Open loop: Poisson arrivals at
+    fractions of the server's saturation rate, server clock = wall clock.
+    Baseline: each request solved alone with ader_solve (FP64) in arrival order;
+    its latencies replay the same arrival times on a FIFO single server with the
+    measured per-request service times."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    from paper_2409_12483_gb300.capi import REQ_DONE, Server
+    reqs = serving_stream(n, cmax, tend)
+    states = []
+    for r in reqs:
+        ctx = Context(r.cells, r.degree, "dg", device=dev)
+        states.append(W.nodal_state(r.field, ctx.node_coords()).ravel())
+        del ctx
+    pool = sum(Server.request_bytes(r.degree, r.cells) for r in reqs) + (64 << 20)
+
+    def run_server(arrivals):
+        srv = Server(pool_bytes=pool, max_slots=len(reqs), ticks_per_round=16,
+                     precision="fp32", fp64_sweeps=1, device=dev)
+        ids = [srv.submit(r.degree, st, r.t_end, arrival=a) for r, st, a in zip(reqs, states, arrivals)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while True:
+            run, que = srv.progress(time.perf_counter() - t0)
+            if run == 0 and que == 0:
+                break
+            if run == 0:
+                time.sleep(1e-4)
+        wall = time.perf_counter() - t0
+        res = [srv.poll(i) for i in ids]
+        assert all(x["state"] == REQ_DONE for x in res)
+        lat = np.array([x["finished"] - x["arrival"] for x in res])
+        tot = srv.totals()
+        srv.close()
+        return wall, lat, tot
+
+    wall0, lat0, tot0 = run_server([0.0] * len(reqs))
+    sat = len(reqs) / wall0
+    out = {"workload": SERVING_NOTE.format(n=n, cmax=cmax, tend=tend),
+           "cell_updates": tot0["cell_updates"],
+           "saturation": {"solves_per_s": sat, "cell_updates_per_s": tot0["cell_updates"] / wall0,
+                          "makespan_s": wall0, "rounds": tot0["rounds"], "ticks": tot0["ticks"],
+                          "kernel_launches": tot0["kernel_launches"]},
+           "open_loop": []}
+    # plain per-solve FP64 baseline: service time of every request alone
+    service = []
+    for r, st in zip(reqs, states):
+        ctx = Context(r.cells, r.degree, "dg", device=dev)
+        u = torch.tensor(st, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.ader_solve(u, t_end=r.t_end)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        del ctx, u
+    service = np.array(service)
+    base_sat = len(reqs) / service.sum()
+    out["baseline_per_solve_fp64"] = {"solves_per_s": base_sat,
+                                      "cell_updates_per_s": tot0["cell_updates"] / service.sum()}
+    rng = np.random.default_rng(SEED + 1)
+    for frac in rates:
+        rate = frac * sat
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        arr = np.cumsum(gaps) - gaps[0]
+        wall, lat, _ = run_server(list(arr))
+        # FIFO replay of the baseline on the same arrivals
+        end, blat = 0.0, []
+        for a, sv in zip(arr, service):
+            start = max(a, end)
+            end = start + sv
+            blat.append(end - a)
+        blat = np.array(blat)
+        out["open_loop"].append({
+            "arrival_rate_frac_of_saturation": frac, "arrival_rate_solves_per_s": rate,
+            "server": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                       "solves_per_s": len(reqs) / wall},
+            "baseline_per_solve_fp64": {"p50_s": float(np.percentile(blat, 50)),
+                                        "p99_s": float(np.percentile(blat, 99)),
+                                        "solves_per_s": len(reqs) / max(end, 1e-9)}})
+    return out
+
+
+def run_case(args):
+    """Small fixed cases for ncu captures (inputs larger than L2, a few GB at most)."""
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    dev = torch.device("cuda", 0)
+    nc = 1_000_000
+    if args.case == "predict-dg5":
+        ctx = Context(nc, 5, "dg", device=dev)
+        u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    elif args.case == "predict-dg7-fp32":
+        ctx = Context(nc, 7, "dg", device=dev, precision="fp32", fp64_sweeps=2)
+        u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    elif args.case == "weno5":
+        ctx = Context(nc, 4, "fv", device=dev)
+        u = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    out = torch.empty_like(u)
+    times = []
+    for i in range(args.warmup + args.steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        ctx.ader_step(u, out, 0.0)
+        ev1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(ev0.elapsed_time(ev1))
+    print(json.dumps({"case": args.case, "cells": nc, "ms_per_step": sum(times) / len(times),
+                      "stats": ctx.ader_get_stats()}))
 
 
 if __name__ == "__main__":

@@ -171,6 +171,80 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of independent ADER-DG solves (no counterpart in
+ * the paper; its single-mesh step is what every solve runs).
+ *
+ * A server owns a caller-provided device pool, admits queued requests in arrival
+ * order when a slot and enough pool memory are free (admission by device
+ * memory), keeps every admitted solve's state resident, and advances all of them
+ * together: each tick launches, per degree present, one batched predictor and
+ * one batched interface/update kernel over a work list of (solve, tile) items;
+ * every solve keeps its own device-resident time step, CFL rule and stop time.
+ * Ticks run as CUDA graphs of `ticks_per_round` steps; between rounds the host
+ * retires finished solves (copying their state back), admits new ones and
+ * rebuilds the work lists.  Requests that arrive while others run join at the
+ * next round: their work overlaps on the device with the running solves.
+ * A solve's result is the same as running it alone (same kernels per cell).
+ * ------------------------------------------------------------------------- */
+typedef struct ader_server ader_server;
+
+typedef struct {
+  void* pool_dev;           /* caller-owned device memory, 256-byte aligned */
+  size_t pool_bytes;
+  int max_slots;            /* solves resident at once (>= 1) */
+  int ticks_per_round;      /* time steps per graph replay (even, >= 2) */
+  int precision;            /* ader_precision of every solve's predictor */
+  int fp64_sweeps;          /* FP64 sweeps after the FP32 stage (precision 1) */
+  double gamma, cfl;        /* shared physics / CFL (1.4, 0.4) */
+  double picard_tol;        /* 0 = 1e-13 */
+  void* stream;             /* cudaStream_t the server works on (NULL = default) */
+} ader_server_opts;
+
+typedef struct {
+  int degree;               /* DG degree 0..7 */
+  int64_t n_cells;
+  double x0, x1;
+  double t_end;             /* > 0 */
+  double arrival;           /* server-clock time before which it is not admitted */
+  const double* u0_host;    /* initial DG state [cell][k][r]; copied by ader_server_submit */
+} ader_request;
+
+enum { ADER_REQ_QUEUED = 0, ADER_REQ_RUNNING = 1, ADER_REQ_DONE = 2, ADER_REQ_FAILED = 3 };
+
+typedef struct {
+  int state;                /* ADER_REQ_* */
+  int status;               /* ader_status of the solve once done/failed */
+  int64_t steps;
+  double t;                 /* simulated time reached */
+  double arrival, admitted, finished;  /* server-clock times (finished: result on the host) */
+  int64_t n_cells;
+  int degree;
+} ader_result;
+
+/* Defaults (pool and stream NULL). */
+ader_status ader_server_default_options(ader_server_opts* opt);
+ader_status ader_server_create(const ader_server_opts* opt, ader_server** out);
+void ader_server_destroy(ader_server* srv);
+const char* ader_server_last_error(const ader_server* srv);
+/* Device bytes one request needs in the pool (state x2, traces, alignment). */
+size_t ader_server_request_bytes(int degree, int64_t n_cells);
+/* Queue a request (copies u0_host).  ADER_ERR_NOMEM if it could never fit the pool. */
+ader_status ader_server_submit(ader_server* srv, const ader_request* req, uint64_t* id_out);
+/* One round at server-clock time `now`: retire finished solves (their results
+ * reach host memory), admit arrived requests while slots and pool memory allow,
+ * then run ticks_per_round steps of every running solve and wait for them.
+ * Reports the running and queued counts afterwards.  Synchronises. */
+ader_status ader_server_progress(ader_server* srv, double now, int* running, int* queued);
+/* State of a request; when done and u_host != NULL, copies its final state
+ * (n_cells (N+1) 3 doubles) to u_host. */
+ader_status ader_server_poll(ader_server* srv, uint64_t id, ader_result* out, double* u_host);
+/* Forget a finished request (frees its host copy). */
+ader_status ader_server_release(ader_server* srv, uint64_t id);
+/* Totals since creation: cell-updates, ticks, rounds, kernel launches. */
+ader_status ader_server_totals(const ader_server* srv, int64_t* cell_updates, int64_t* ticks,
+                               int64_t* rounds, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
  * One time step that allocates nothing (no counterpart in the paper: it exists
  * for callers that cannot allocate device memory -- code running where
  * cudaMalloc is not allowed or not wanted, e.g. inside a host that owns every

@@ -42,8 +42,9 @@ def _jobs():
         obj = os.path.join(BUILD, f"ader_deg{d}.o")
         jobs.append((obj, [nvcc, *ARCH, *NVCC_FLAGS, f"-DADER_DEG={d}", "-c",
                            os.path.join(CSRC, "ader_deg.cu"), "-o", obj]))
-    obj = os.path.join(BUILD, "ader_capi.o")
-    jobs.append((obj, [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, "ader_capi.cu"), "-o", obj]))
+    for name in ("ader_capi", "ader_server"):
+        obj = os.path.join(BUILD, f"{name}.o")
+        jobs.append((obj, [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, f"{name}.cu"), "-o", obj]))
     obj = os.path.join(BUILD, "ader_ops.o")
     jobs.append((obj, [nvcc, *NVCC_FLAGS, "-x", "c++", "-c", os.path.join(CSRC, "ader_ops.cpp"),
                        "-o", obj]))

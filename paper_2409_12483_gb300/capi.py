@@ -51,6 +51,27 @@ class Stats(C.Structure):
                 ("face_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("pool_dev", C.c_void_p), ("pool_bytes", C.c_size_t), ("max_slots", C.c_int),
+                ("ticks_per_round", C.c_int), ("precision", C.c_int), ("fp64_sweeps", C.c_int),
+                ("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("degree", C.c_int), ("n_cells", C.c_int64), ("x0", C.c_double),
+                ("x1", C.c_double), ("t_end", C.c_double), ("arrival", C.c_double),
+                ("u0_host", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("steps", C.c_int64), ("t", C.c_double),
+                ("arrival", C.c_double), ("admitted", C.c_double), ("finished", C.c_double),
+                ("n_cells", C.c_int64), ("degree", C.c_int)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 _lib = None
 _lock = threading.Lock()
 
@@ -89,6 +110,16 @@ def load(build_if_missing: bool = True):
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
+            "ader_server_default_options": ([P(ServerOpts)], C.c_int),
+            "ader_server_create": ([P(ServerOpts), P(V)], C.c_int),
+            "ader_server_destroy": ([V], None),
+            "ader_server_last_error": ([V], C.c_char_p),
+            "ader_server_request_bytes": ([C.c_int, I64], SZ),
+            "ader_server_submit": ([V, P(Request), P(C.c_uint64)], C.c_int),
+            "ader_server_progress": ([V, D, P(C.c_int), P(C.c_int)], C.c_int),
+            "ader_server_poll": ([V, C.c_uint64, P(Result), V], C.c_int),
+            "ader_server_release": ([V, C.c_uint64], C.c_int),
+            "ader_server_totals": ([V, P(I64), P(I64), P(I64), P(I64)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -105,7 +136,10 @@ def exported_symbols():
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats",
-            "ader_step_noalloc"]
+            "ader_step_noalloc", "ader_server_default_options", "ader_server_create",
+            "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
+            "ader_server_submit", "ader_server_progress", "ader_server_poll",
+            "ader_server_release", "ader_server_totals"]
 
 
 def default_options(**kw) -> Options:
@@ -314,6 +348,103 @@ class NoAllocStep:
         if getattr(self, "_ctx", None):
             self._L.ader_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server of independent ADER-DG solves (ader_server_*).
+
+    torch allocates the device pool; the server sub-allocates it, admits requests
+    by memory and slots, and advances every resident solve each tick."""
+
+    def __init__(self, pool_bytes: int = 1 << 30, max_slots: int = 256, ticks_per_round: int = 16,
+                 precision: str = "fp64", fp64_sweeps: int = 1, device=None, cfl: float = 0.4,
+                 gamma: float = 1.4):
+        torch = _torch()
+        L = load()
+        self._L = L
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self._pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self._pool.data_ptr() + 255) // 256 * 256
+        o = ServerOpts()
+        L.ader_server_default_options(C.byref(o))
+        o.pool_dev = aligned
+        o.pool_bytes = int(pool_bytes)
+        o.max_slots = int(max_slots)
+        o.ticks_per_round = int(ticks_per_round)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.fp64_sweeps = int(fp64_sweeps)
+        o.cfl = float(cfl)
+        o.gamma = float(gamma)
+        o.stream = torch.cuda.current_stream(self.device).cuda_stream
+        srv = C.c_void_p()
+        rc = L.ader_server_create(C.byref(o), C.byref(srv))
+        if rc != ADER_OK:
+            raise AderError(rc, f"ader_server_create failed ({L.ader_status_string(rc).decode()})")
+        self._srv = srv
+        self.opts = o
+
+    def _check(self, rc, ok=(ADER_OK,)):
+        if rc not in ok:
+            raise AderError(rc, self._L.ader_server_last_error(self._srv).decode())
+        return rc
+
+    @staticmethod
+    def request_bytes(degree: int, n_cells: int) -> int:
+        return int(load().ader_server_request_bytes(int(degree), int(n_cells)))
+
+    def submit(self, degree: int, u0, t_end: float, arrival: float = 0.0, x0: float = 0.0,
+               x1: float = 1.0) -> int:
+        import numpy as np
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        n_cells = u0.size // ((degree + 1) * 3)
+        if n_cells * (degree + 1) * 3 != u0.size:
+            raise ValueError("u0 size does not match the degree")
+        rq = Request(int(degree), int(n_cells), float(x0), float(x1), float(t_end), float(arrival),
+                     u0.ctypes.data)
+        rid = C.c_uint64(0)
+        self._check(self._L.ader_server_submit(self._srv, C.byref(rq), C.byref(rid)))
+        return rid.value
+
+    def progress(self, now: float):
+        run, que = C.c_int(0), C.c_int(0)
+        self._check(self._L.ader_server_progress(self._srv, float(now), C.byref(run), C.byref(que)))
+        return run.value, que.value
+
+    def poll(self, rid: int, want_state: bool = False):
+        import numpy as np
+        r = Result()
+        self._check(self._L.ader_server_poll(self._srv, int(rid), C.byref(r), None))
+        out = {"state": r.state, "status": r.status, "steps": r.steps, "t": r.t,
+               "arrival": r.arrival, "admitted": r.admitted, "finished": r.finished,
+               "n_cells": r.n_cells, "degree": r.degree}
+        if want_state and r.state in (REQ_DONE, REQ_FAILED):
+            u = np.zeros(r.n_cells * (r.degree + 1) * 3)
+            self._check(self._L.ader_server_poll(self._srv, int(rid), C.byref(r),
+                                                 u.ctypes.data_as(C.c_void_p)))
+            out["u"] = u
+        return out
+
+    def release(self, rid: int):
+        self._check(self._L.ader_server_release(self._srv, int(rid)))
+
+    def totals(self):
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.ader_server_totals(self._srv, C.byref(a), C.byref(b), C.byref(c),
+                                               C.byref(d)))
+        return {"cell_updates": a.value, "ticks": b.value, "rounds": c.value,
+                "kernel_launches": d.value}
+
+    def close(self):
+        if getattr(self, "_srv", None):
+            self._L.ader_server_destroy(self._srv)
+            self._srv = None
 
     def __del__(self):
         try:

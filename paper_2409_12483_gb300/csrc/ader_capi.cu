@@ -9,6 +9,7 @@
 #include <new>
 
 #include "../../include/ader.h"
+#include "ader_dispatch.h"
 #include "ader_launch.h"
 #include "ader_ops.h"
 
@@ -99,44 +100,6 @@ size_t workspace_bytes(const ader_ctx* c) {
   if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
   b += 2 * align_up((size_t)state_count(c) * sizeof(double));
   return b;
-}
-
-cudaError_t dispatch_prepare(int N) {
-  switch (N) {
-    case 0: return prepare_degree_0();
-    case 1: return prepare_degree_1();
-    case 2: return prepare_degree_2();
-    case 3: return prepare_degree_3();
-    case 4: return prepare_degree_4();
-    case 5: return prepare_degree_5();
-    case 6: return prepare_degree_6();
-    case 7: return prepare_degree_7();
-  }
-  return cudaErrorInvalidValue;
-}
-
-#define ADER_DISPATCH(fn, N, p, s)            \
-  switch (N) {                                \
-    case 0: return fn##_0(p, s);              \
-    case 1: return fn##_1(p, s);              \
-    case 2: return fn##_2(p, s);              \
-    case 3: return fn##_3(p, s);              \
-    case 4: return fn##_4(p, s);              \
-    case 5: return fn##_5(p, s);              \
-    case 6: return fn##_6(p, s);              \
-    case 7: return fn##_7(p, s);              \
-  }                                           \
-  return cudaErrorInvalidValue;
-
-cudaError_t do_predict(int N, const PredictParams& p, cudaStream_t s) {
-  ADER_DISPATCH(launch_predict, N, p, s)
-}
-cudaError_t do_face(int N, const FaceParams& p, cudaStream_t s) {
-  ADER_DISPATCH(launch_face_update, N, p, s)
-}
-cudaError_t do_cfl(int N, const CflParams& p, cudaStream_t s) { ADER_DISPATCH(launch_cfl, N, p, s) }
-cudaError_t do_weno(int N, const WenoParams& p, cudaStream_t s) {
-  ADER_DISPATCH(launch_weno, N, p, s)
 }
 
 StepParams make_step(const ader_ctx* c, int mode, int par, double dt, double t_end,

@@ -28,8 +28,34 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PredCfg<D>::kSmemBytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(predict_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(predict_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)PredCfg<D>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(predict_multi_kernel<D, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PredCfg<D>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(predict_multi_kernel<D, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PredCfg<D>::kSmemBytes);
+}
+
+cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, const MultiArgs& m,
+                                                       int grid, cudaStream_t s) {
+  using C = PredCfg<D>;
+  if (grid <= 0) return cudaErrorInvalidValue;
+  if (p.prec == 1)
+    predict_multi_kernel<D, true><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+  else
+    predict_multi_kernel<D, false><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_face_multi_, ADER_DEG)(const FaceParams& p, const MultiArgs& m, int grid,
+                                                    cudaStream_t s) {
+  using C = FaceCfg<D>;
+  if (grid <= 0) return cudaErrorInvalidValue;
+  face_update_multi_kernel<D><<<(unsigned)grid, C::THREADS, 0, s>>>(p, m);
+  return cudaGetLastError();
 }
 
 cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {

@@ -59,14 +59,14 @@ __device__ __forceinline__ double bitsd(unsigned long long b) {
 }
 
 // Predictor side of the time-step protocol.  Every thread evaluates the same
-// expression from the same inputs, so the decision is uniform.
-__device__ __forceinline__ bool predictor_step_dt(const StepParams& sp, double* dt_out) {
+// expression from the same inputs, so the decision is uniform; `lead` (one
+// thread of the solve's first tile) publishes it.
+__device__ __forceinline__ bool predictor_step_dt(const StepParams& sp, double* dt_out, bool lead) {
   if (sp.mode == kDtFixed) {
     *dt_out = sp.dt_fixed;
     return true;
   }
   DevCtl* c = sp.ctl;
-  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if (sp.mode == kDtSolve && *(volatile int*)&c->done) {
     if (lead) c->active[sp.par] = 0;
     return false;
@@ -115,8 +115,9 @@ __device__ __forceinline__ bool corrector_step_dt(const StepParams& sp, double* 
   return true;
 }
 
-__device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt, int last) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt, int last,
+                                                 bool lead) {
+  if (lead) {
     DevCtl* c = sp.ctl;
     c->t = (sp.mode == kDtSolve && (last & 1)) ? sp.t_end : c->t + dt;
     c->steps += 1;

@@ -150,39 +150,52 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
   return cell_it;
 }
 
+// Per-solve view used by one tile: where the tile reads and writes.
+struct TileIO {
+  const double* u;      // nodal initial data of the solve
+  double* trace;        // trace buffer of the solve
+  double* q_out;        // kOutQ
+  const double* q_in;   // from_q
+  long long ncells;
+  DevCtl* ctl;          // statistics / status of the solve
+};
+
+// Shared memory of one predictor tile.
+template <int N>
+struct PredShared {
+  unsigned long long red[2][32][2];
+  int itmax, ncells, bad;
+  unsigned long long itsum;
+};
+
+// One predictor tile (32 cells x n tau nodes = blockDim) of one solve.
 // PREC32: Picard in FP32 followed by P.sweeps FP64 sweeps (compile-time, so the
 // FP64 form carries no FP32 state in its registers).
 template <int N, bool PREC32>
-__global__ void __launch_bounds__(PredCfg<N>::THREADS)
-    predict_kernel(const __grid_constant__ PredictParams P) {
+__device__ __forceinline__ void predict_tile(const PredictParams& P, const TileIO& io,
+                                             long long tile, double lam, double* smem,
+                                             PredShared<N>& sh) {
   constexpr int n = N + 1, CPB = PredCfg<N>::CPB, THREADS = PredCfg<N>::THREADS;
-  extern __shared__ __align__(16) double smem[];
   double* sg = smem;                        // [CPB][n][n][3]
   double* sfb = smem + CPB * n * n * kM;    // [CPB][n][3]
-  __shared__ unsigned long long s_red[2][32][2];
-  __shared__ int s_itmax, s_ncells, s_bad;
-  __shared__ unsigned long long s_itsum;
-
-  double dt;
-  if (!predictor_step_dt(P.sp, &dt)) return;  // uniform over the grid
-  const double lam = dt * P.sp.inv_dx;
+  unsigned long long(*s_red)[32][2] = sh.red;
 
   const int tid = threadIdx.x;
   const int lc = tid / n, p0 = tid - lc * n;
-  const long long cell = (long long)blockIdx.x * CPB + lc;
-  const bool valid = cell < P.ncells;
+  const long long cell = tile * CPB + lc;
+  const bool valid = cell < io.ncells;
   for (int i = tid; i < 2 * 32 * 2; i += THREADS) (&s_red[0][0][0])[i] = 0ull;
   if (tid == 0) {
-    s_itmax = 0;
-    s_itsum = 0ull;
-    s_ncells = 0;
-    s_bad = 0;
+    sh.itmax = 0;
+    sh.itsum = 0ull;
+    sh.ncells = 0;
+    sh.bad = 0;
   }
 
   // initial data of the cell (every thread of the cell reads the same 3n values)
   double uh[n][kM], u_own[kM];  // u_own: this thread's node p0 (runtime index)
   {
-    const double* src = P.u + (valid ? cell : 0) * (long long)(n * kM);
+    const double* src = io.u + (valid ? cell : 0) * (long long)(n * kM);
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
   bool conv = true;
 
   if (P.from_q) {
-    const double* src = P.q_in + ((valid ? cell : 0) * n + p0) * (long long)(n * kM);
+    const double* src = io.q_in + ((valid ? cell : 0) * n + p0) * (long long)(n * kM);
 #pragma unroll
     for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
 
   if (P.out_mode == kOutQ) {
     if (valid) {
-      double* dst = P.q_out + (cell * n + p0) * (long long)(n * kM);
+      double* dst = io.q_out + (cell * n + p0) * (long long)(n * kM);
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
   } else {
     // traces of the tau row at xi = 1 (qR) and xi = 0 (qL)
     const int stride = (P.dg ? 9 : 6) * n;
-    double* dst = P.trace + (valid ? cell : 0) * (long long)stride;
+    double* dst = io.trace + (valid ? cell : 0) * (long long)stride;
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
       double aR = 0.0, aL = 0.0;
@@ -302,18 +315,50 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
 
   // iteration statistics and convergence flag
   if (valid && p0 == 0 && !P.from_q) {
-    atomicMax(&s_itmax, iters);
-    atomicAdd(&s_itsum, (unsigned long long)iters);
-    atomicAdd(&s_ncells, 1);
-    if (!conv) atomicOr(&s_bad, 1);
+    atomicMax(&sh.itmax, iters);
+    atomicAdd(&sh.itsum, (unsigned long long)iters);
+    atomicAdd(&sh.ncells, 1);
+    if (!conv) atomicOr(&sh.bad, 1);
   }
   __syncthreads();
-  if (tid == 0 && s_ncells > 0) {
-    DevCtl* c = P.sp.ctl;
-    atomicMax(&c->iter_max, s_itmax);
-    atomicAdd(&c->iter_sum, s_itsum);
-    atomicAdd((unsigned long long*)&c->iter_cells, (unsigned long long)s_ncells);
-    if (s_bad) atomicOr(&c->status, kStNotConverged);
+  if (tid == 0 && sh.ncells > 0) {
+    DevCtl* c = io.ctl;
+    atomicMax(&c->iter_max, sh.itmax);
+    atomicAdd(&c->iter_sum, sh.itsum);
+    atomicAdd((unsigned long long*)&c->iter_cells, (unsigned long long)sh.ncells);
+    if (sh.bad) atomicOr(&c->status, kStNotConverged);
+  }
+  __syncthreads();  // shared memory is free for the next tile
+}
+
+template <int N, bool PREC32>
+__global__ void __launch_bounds__(PredCfg<N>::THREADS)
+    predict_kernel(const __grid_constant__ PredictParams P) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ PredShared<N> sh;
+  double dt;
+  if (!predictor_step_dt(P.sp, &dt, blockIdx.x == 0 && threadIdx.x == 0)) return;  // uniform
+  const TileIO io{P.u, P.trace, P.q_out, P.q_in, P.ncells, P.sp.ctl};
+  predict_tile<N, PREC32>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
+}
+
+// Batched predictor: one launch per degree over the tiles of many independent
+// solves (continuous batching).  Every solve keeps its own device time step.
+template <int N, bool PREC32>
+__global__ void __launch_bounds__(PredCfg<N>::THREADS)
+    predict_multi_kernel(const __grid_constant__ PredictParams P, const MultiArgs M) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ PredShared<N> sh;
+  for (long long it = blockIdx.x; it < M.nitems; it += gridDim.x) {
+    const TileItem item = M.items[it];
+    const SlotDesc& d = M.slots[item.slot];
+    const int par = M.tick_par ^ d.par0;
+    StepParams sp = d.sp;
+    sp.par = par;
+    double dt;
+    if (!predictor_step_dt(sp, &dt, item.tile == 0 && threadIdx.x == 0)) continue;  // uniform
+    const TileIO io{d.u[par], d.trace, nullptr, nullptr, d.ncells, sp.ctl};
+    predict_tile<N, PREC32>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
   }
 }
 
@@ -325,40 +370,40 @@ struct FaceCfg {
 };
 
 template <int N>
-__global__ void __launch_bounds__(FaceCfg<N>::THREADS)
-    face_update_kernel(const __grid_constant__ FaceParams P) {
-  constexpr int n = N + 1, C = FaceCfg<N>::C, THREADS = FaceCfg<N>::THREADS;
-  __shared__ double sG[(C + 1) * n * kM];
-  __shared__ double sGs[(C + 1) * kM];
-  __shared__ double su[C * n * kM];
-  __shared__ double sP[kMaxNs * n];
-  __shared__ double sw[n], spsi0[n], spsi1[n], srw[n];
-  __shared__ unsigned long long s_wmax[32];
+struct FaceShared {
+  double G[(FaceCfg<N>::C + 1) * (N + 1) * kM];
+  double Gs[(FaceCfg<N>::C + 1) * kM];
+  double u[FaceCfg<N>::C * (N + 1) * kM];
+  double P[kMaxNs * (N + 1)];
+  double w[N + 1], psi0[N + 1], psi1[N + 1], rw[N + 1];
+  unsigned long long wmax[32];
+};
 
-  double dt;
-  int last;
-  if (!corrector_step_dt(P.sp, &dt, &last)) return;
-  // per-thread table lookups below are divergent: stage the small tables in smem
-  for (int i = threadIdx.x; i < P.Ns * n; i += THREADS) sP[i] = P.ops.P[i / n][i % n];
-  if (threadIdx.x < n) {
-    sw[threadIdx.x] = P.ops.w[threadIdx.x];
-    spsi0[threadIdx.x] = P.ops.psi0[threadIdx.x];
-    spsi1[threadIdx.x] = P.ops.psi1[threadIdx.x];
-    srw[threadIdx.x] = P.ops.rw[threadIdx.x];
-  }
-  __syncthreads();
-  const double lam = dt * P.sp.inv_dx;
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nvalid = (int)((P.ncells - c0) < C ? (P.ncells - c0) : C);
+struct FaceIO {
+  const double* trace;
+  const double* v_old;
+  double* u_new;
+  long long ncells;
+};
+
+// One tile (C cells) of the interface flux + update (+ lambda_max) of one solve.
+template <int N>
+__device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
+                                          const StepParams& sp, long long tile, double dt,
+                                          FaceShared<N>& sh) {
+  constexpr int n = N + 1, C = FaceCfg<N>::C, THREADS = FaceCfg<N>::THREADS;
+  const double lam = dt * sp.inv_dx;
+  const long long c0 = tile * C;
+  const int nvalid = (int)((io.ncells - c0) < C ? (io.ncells - c0) : C);
   const int stride = (P.dg ? 9 : 6) * n;
   const int tid = threadIdx.x;
 
   // Rusanov flux at every tau node of faces c0-1/2 ... c0+nvalid-1/2
   for (int item = tid; item < (nvalid + 1) * n; item += THREADS) {
     const int f = item / n, l0 = item - f * n;
-    const long long cl = wrap_cell(c0 + f - 1, P.ncells), cr = wrap_cell(c0 + f, P.ncells);
-    const double* ta = P.trace + cl * stride + l0 * kM;          // qR of the left cell
-    const double* tb = P.trace + cr * stride + n * kM + l0 * kM; // qL of the right cell
+    const long long cl = wrap_cell(c0 + f - 1, io.ncells), cr = wrap_cell(c0 + f, io.ncells);
+    const double* ta = io.trace + cl * stride + l0 * kM;          // qR of the left cell
+    const double* tb = io.trace + cr * stride + n * kM + l0 * kM; // qL of the right cell
     double a[kM], b[kM], G[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
@@ -366,40 +411,40 @@ __global__ void __launch_bounds__(FaceCfg<N>::THREADS)
       b[r] = tb[r];
     }
     rusanov(a, b, G, P.gamma, P.gm1);
-    const double wl = sw[l0] * lam;
+    const double wl = sh.w[l0] * lam;
 #pragma unroll
-    for (int r = 0; r < kM; ++r) sG[(f * n + l0) * kM + r] = wl * G[r];
+    for (int r = 0; r < kM; ++r) sh.G[(f * n + l0) * kM + r] = wl * G[r];
   }
   __syncthreads();
   for (int item = tid; item < (nvalid + 1) * kM; item += THREADS) {
     const int f = item / kM, r = item - f * kM;
     double s = 0.0;
 #pragma unroll
-    for (int l0 = 0; l0 < n; ++l0) s += sG[(f * n + l0) * kM + r];
-    sGs[f * kM + r] = s;
+    for (int l0 = 0; l0 < n; ++l0) s += sh.G[(f * n + l0) * kM + r];
+    sh.Gs[f * kM + r] = s;
   }
   __syncthreads();
   if (P.dg) {
     for (int item = tid; item < nvalid * n; item += THREADS) {
       const int lc = item / n, k = item - lc * n;
       const long long cell = c0 + lc;
-      const double* up = P.trace + cell * stride + 2 * n * kM + k * kM;
-      double* out = P.u_new + cell * (long long)(n * kM) + k * kM;
+      const double* up = io.trace + cell * stride + 2 * n * kM + k * kM;
+      double* out = io.u_new + cell * (long long)(n * kM) + k * kM;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
-        const double t = spsi1[k] * sGs[(lc + 1) * kM + r] - spsi0[k] * sGs[lc * kM + r];
-        const double un = fma(-t, srw[k], up[r]);
+        const double t = sh.psi1[k] * sh.Gs[(lc + 1) * kM + r] - sh.psi0[k] * sh.Gs[lc * kM + r];
+        const double un = fma(-t, sh.rw[k], up[r]);
         out[r] = un;
-        su[(lc * n + k) * kM + r] = un;
+        sh.u[(lc * n + k) * kM + r] = un;
       }
     }
   } else {
     for (int item = tid; item < nvalid * kM; item += THREADS) {
       const int lc = item / kM, r = item - lc * kM;
       const long long cell = c0 + lc;
-      const double vn = P.v_old[cell * kM + r] - (sGs[(lc + 1) * kM + r] - sGs[lc * kM + r]);
-      P.u_new[cell * kM + r] = vn;
-      su[lc * kM + r] = vn;
+      const double vn = io.v_old[cell * kM + r] - (sh.Gs[(lc + 1) * kM + r] - sh.Gs[lc * kM + r]);
+      io.u_new[cell * kM + r] = vn;
+      sh.u[lc * kM + r] = vn;
     }
   }
   if (P.want_lambda) {
@@ -414,20 +459,68 @@ __global__ void __launch_bounds__(FaceCfg<N>::THREADS)
         for (int r = 0; r < kM; ++r) {
           double acc = 0.0;
 #pragma unroll
-          for (int k = 0; k < n; ++k) acc = fma(sP[j * n + k], su[(lc * n + k) * kM + r], acc);
+          for (int k = 0; k < n; ++k) acc = fma(sh.P[j * n + k], sh.u[(lc * n + k) * kM + r], acc);
           v[r] = acc;
         }
         lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
       }
     } else {
       for (int lc = tid; lc < nvalid; lc += THREADS)
-        lmax = fmax(lmax, wave_speed(&su[lc * kM], P.gamma, P.gm1, &bad));
+        lmax = fmax(lmax, wave_speed(&sh.u[lc * kM], P.gamma, P.gm1, &bad));
     }
-    const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
-    if (tid == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);
-    if (bad) atomicOr(&P.sp.ctl->status, kStNonPhysical);
+    const unsigned long long bm = block_max_bits(dbits(lmax), sh.wmax);
+    if (tid == 0) atomicMax(&sp.ctl->lam[sp.par ^ 1], bm);
+    if (bad) atomicOr(&sp.ctl->status, kStNonPhysical);
   }
-  corrector_finish(P.sp, dt, last);
+  __syncthreads();  // shared memory is free for the next tile
+}
+
+template <int N>
+__device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShared<N>& sh) {
+  constexpr int n = N + 1;
+  // per-thread table lookups in face_tile are divergent: stage the small tables in smem
+  for (int i = threadIdx.x; i < P.Ns * n; i += FaceCfg<N>::THREADS) sh.P[i] = P.ops.P[i / n][i % n];
+  if (threadIdx.x < n) {
+    sh.w[threadIdx.x] = P.ops.w[threadIdx.x];
+    sh.psi0[threadIdx.x] = P.ops.psi0[threadIdx.x];
+    sh.psi1[threadIdx.x] = P.ops.psi1[threadIdx.x];
+    sh.rw[threadIdx.x] = P.ops.rw[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(FaceCfg<N>::THREADS)
+    face_update_kernel(const __grid_constant__ FaceParams P) {
+  __shared__ FaceShared<N> sh;
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  face_stage_tables<N>(P, sh);
+  const FaceIO io{P.trace, P.v_old, P.u_new, P.ncells};
+  face_tile<N>(P, io, P.sp, blockIdx.x, dt, sh);
+  corrector_finish(P.sp, dt, last, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+// Batched interface flux + update over the tiles of many solves (see predict_multi_kernel).
+template <int N>
+__global__ void __launch_bounds__(FaceCfg<N>::THREADS)
+    face_update_multi_kernel(const __grid_constant__ FaceParams P, const MultiArgs M) {
+  __shared__ FaceShared<N> sh;
+  face_stage_tables<N>(P, sh);
+  for (long long it = blockIdx.x; it < M.nitems; it += gridDim.x) {
+    const TileItem item = M.items[it];
+    const SlotDesc& d = M.slots[item.slot];
+    const int par = M.tick_par ^ d.par0;
+    StepParams sp = d.sp;
+    sp.par = par;
+    double dt;
+    int last;
+    if (!corrector_step_dt(sp, &dt, &last)) continue;  // uniform over the block
+    const FaceIO io{d.trace, d.u[par], const_cast<double*>(d.u[par ^ 1]), d.ncells};
+    face_tile<N>(P, io, sp, item.tile, dt, sh);
+    corrector_finish(sp, dt, last, item.tile == 0 && threadIdx.x == 0);
+  }
 }
 
 template <int N>

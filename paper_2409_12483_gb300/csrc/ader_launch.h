@@ -60,6 +60,29 @@ struct CflParams {
   OpsD ops;
 };
 
+// Continuous batching: a work list of tiles over many independent solves of the
+// same degree; each solve has its own state buffers, trace buffer and control block.
+struct SlotDesc {
+  const double* u[2];   // ping-pong state: step with parity p reads u[p], writes u[p ^ 1]
+  double* trace;
+  long long ncells;
+  int par0;             // parity offset: the solve's first step ran at tick parity par0
+  int degree;
+  StepParams sp;        // mode kDtSolve, t_end, max_steps, cfl_factor, inv_dx, ctl
+};
+
+struct TileItem {
+  int slot;
+  int tile;             // 32-cell predictor tile or 64-cell face tile index within the solve
+};
+
+struct MultiArgs {
+  const SlotDesc* slots;
+  const TileItem* items;
+  long long nitems;
+  int tick_par;
+};
+
 struct WenoParams {
   const double* v;
   double* w;
@@ -73,6 +96,10 @@ struct WenoParams {
   cudaError_t launch_face_update_##D(const FaceParams& p, cudaStream_t s);             \
   cudaError_t launch_cfl_##D(const CflParams& p, cudaStream_t s);                      \
   cudaError_t launch_weno_##D(const WenoParams& p, cudaStream_t s);                    \
+  cudaError_t launch_predict_multi_##D(const PredictParams& p, const MultiArgs& m, int grid,  \
+                                       cudaStream_t s);                                 \
+  cudaError_t launch_face_multi_##D(const FaceParams& p, const MultiArgs& m, int grid,     \
+                                    cudaStream_t s);                                    \
   cudaError_t prepare_degree_##D();
 
 ADER_DECLARE_DEGREE(0)

@@ -106,3 +106,17 @@ def test_library_tables_match_oracle(lib, oracle_mod, N):
     Ns = 2 * N + 1
     np.testing.assert_allclose(get("P", Ns * n).reshape(Ns, n), o.table("P"), rtol=0, atol=4e-15)
     lib.ader_destroy(ctx)
+
+
+def test_server_rejects_bad_options_and_requests(lib):
+    from paper_2409_12483_gb300.capi import Request, ServerOpts
+    o = ServerOpts()
+    assert lib.ader_server_default_options(C.byref(o)) == 0
+    srv = C.c_void_p()
+    assert lib.ader_server_create(C.byref(o), C.byref(srv)) == 1  # no pool
+    o.pool_dev = 256
+    o.pool_bytes = 1 << 20
+    o.ticks_per_round = 3  # must be even
+    assert lib.ader_server_create(C.byref(o), C.byref(srv)) == 1
+    assert lib.ader_server_request_bytes(5, 1000) >= 1000 * 6 * 3 * 8 * 2 + 1000 * 54 * 8
+    assert lib.ader_server_request_bytes(8, 10) == 0

@@ -171,6 +171,29 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
 
 /* ---------------------------------------------------------------------------
+ * Autotuning of launch shapes (no counterpart in the paper).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int predict_cells_per_block;  /* predictor tile: 16, 32 or 64 cells x (N+1) threads */
+  int face_cells_per_block;     /* interface/update tile: 32 or 64 cells per 256 threads */
+  int graph_steps;              /* time steps per CUDA-graph replay in ader_solve (even, 2..64) */
+  double predict_ms;            /* measured per launch for the chosen shape (autotune only) */
+  double face_ms;
+  double solve_ms_per_step;     /* measured ader_solve time per step with graph_steps */
+} ader_tuning;
+
+/* Time every valid predictor tile shape, interface tile shape and graph length on
+ * the state u_dev (not modified; the solve trials run on a workspace copy) with
+ * `reps` repetitions each, keep the fastest, and report them.  Valid predictor
+ * shapes have (N+1) * cells a multiple of 32 and at most 512 threads (32 cells
+ * at most for N > 5).  Synchronises. */
+ader_status ader_autotune(ader_ctx* ctx, const double* u_dev, int reps, ader_tuning* out);
+/* Current launch shapes (defaults: 32, 64, mesh-size rule for graph_steps). */
+ader_status ader_get_tuning(const ader_ctx* ctx, ader_tuning* out);
+/* Set launch shapes (e.g. from an earlier autotune); invalid shapes give ADER_ERR_ARG. */
+ader_status ader_set_tuning(ader_ctx* ctx, const ader_tuning* in);
+
+/* ---------------------------------------------------------------------------
  * Serving: continuous batching of independent ADER-DG solves (no counterpart in
  * the paper; its single-mesh step is what every solve runs).
  *

@@ -51,6 +51,12 @@ class Stats(C.Structure):
                 ("face_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("predict_cells_per_block", C.c_int), ("face_cells_per_block", C.c_int),
+                ("graph_steps", C.c_int), ("predict_ms", C.c_double), ("face_ms", C.c_double),
+                ("solve_ms_per_step", C.c_double)]
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("pool_dev", C.c_void_p), ("pool_bytes", C.c_size_t), ("max_slots", C.c_int),
                 ("ticks_per_round", C.c_int), ("precision", C.c_int), ("fp64_sweeps", C.c_int),
@@ -110,6 +116,9 @@ def load(build_if_missing: bool = True):
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
+            "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
+            "ader_get_tuning": ([V, P(Tuning)], C.c_int),
+            "ader_set_tuning": ([V, P(Tuning)], C.c_int),
             "ader_server_default_options": ([P(ServerOpts)], C.c_int),
             "ader_server_create": ([P(ServerOpts), P(V)], C.c_int),
             "ader_server_destroy": ([V], None),
@@ -136,7 +145,8 @@ def exported_symbols():
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats",
-            "ader_step_noalloc", "ader_server_default_options", "ader_server_create",
+            "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
+            "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
             "ader_server_submit", "ader_server_progress", "ader_server_poll",
             "ader_server_release", "ader_server_totals"]
@@ -300,6 +310,24 @@ class Context:
                                      C.byref(steps), C.byref(t))
         self._check(rc, ok=(ADER_OK, *allow))
         return steps.value, t.value, rc
+
+    def ader_autotune(self, u, reps: int = 3) -> dict:
+        t = Tuning()
+        self._check(self._L.ader_autotune(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                          int(reps), C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def ader_get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self._L.ader_get_tuning(self._ctx, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def ader_set_tuning(self, **kw):
+        t = Tuning()
+        self._check(self._L.ader_get_tuning(self._ctx, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(self._L.ader_set_tuning(self._ctx, C.byref(t)))
 
     def ader_get_stats(self) -> dict:
         s = Stats()

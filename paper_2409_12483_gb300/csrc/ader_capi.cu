@@ -2,6 +2,7 @@
 // workspace, kernel sequencing, the device-resident time loop under CUDA graphs.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,6 +64,7 @@ struct ader_ctx {
   long long prof_steps = 0;
   double prof_ms[3] = {0, 0, 0};  // weno, predict, face
   long long launches = 0;         // kernels launched by the last call
+  ader_tuning tune{32, 64, 0, 0.0, 0.0, 0.0};  // graph_steps 0 = mesh-size rule
 };
 
 namespace {
@@ -128,6 +130,7 @@ PredictParams make_predict(const ader_ctx* c, const double* u_nodal, const StepP
   p.sweeps = c->opt.fp64_sweeps;
   p.max_iter = c->opt.picard_max_iter;
   p.fixed_iter = c->opt.picard_fixed_iter;
+  p.cpb = c->tune.predict_cells_per_block;
   p.tol = c->opt.picard_tol;
   p.tol32 = (float)c->opt.fp32_tol;
   p.gamma = c->opt.gamma;
@@ -147,6 +150,7 @@ FaceParams make_face(const ader_ctx* c, const double* v_old, double* u_new, cons
   f.ncells = c->mesh.n_cells;
   f.dg = c->scheme == ADER_SCHEME_DG;
   f.want_lambda = want_lambda;
+  f.cpf = c->tune.face_cells_per_block;
   f.Ns = c->basis.Ns;
   f.gamma = c->opt.gamma;
   f.gm1 = c->opt.gamma - 1.0;
@@ -229,6 +233,12 @@ ader_status status_from_flags(ader_ctx* ctx, int st) {
   if (st & kStNotConverged)
     return fail(ctx, ADER_ERR_NOT_CONVERGED, "Picard iteration cap reached in some cell");
   return ADER_OK;
+}
+
+bool valid_cpb(int N, int cpb) {
+  const int threads = cpb * (N + 1);
+  return (cpb == 16 || cpb == 32 || cpb == 64) && threads % 32 == 0 && threads <= 512 &&
+         (N <= 5 || cpb <= 32);
 }
 
 int graph_steps_for(int64_t ncells) {
@@ -529,7 +539,7 @@ ader_status ader_solve(ader_ctx* ctx, double* u, double t_end, int64_t max_steps
   if ((st = reset_ctl(ctx)) != ADER_OK) return st;
   if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
 
-  const int K = graph_steps_for(ctx->mesh.n_cells);
+  const int K = ctx->tune.graph_steps > 0 ? ctx->tune.graph_steps : graph_steps_for(ctx->mesh.n_cells);
   const bool prof = ctx->opt.profile != 0;
   if (prof && !ctx->pev_ready) {
     for (int j = 0; j < ader_ctx::kMaxGraphSteps; ++j)
@@ -775,5 +785,157 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
   FaceParams f = make_face(ctx, u, u_new, sp, 0);
   f.trace = trace;
   CK(do_face(ctx->N, f, s));
+  return ADER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning of launch shapes
+// ---------------------------------------------------------------------------
+
+extern "C" ader_status ader_get_tuning(const ader_ctx* ctx, ader_tuning* out) {
+  if (!ctx || !out) return ADER_ERR_ARG;
+  *out = ctx->tune;
+  if (out->graph_steps <= 0) out->graph_steps = graph_steps_for(ctx->mesh.n_cells);
+  return ADER_OK;
+}
+
+extern "C" ader_status ader_set_tuning(ader_ctx* ctx, const ader_tuning* in) {
+  if (!ctx || !in) return ADER_ERR_ARG;
+  if (!valid_cpb(ctx->N, in->predict_cells_per_block) ||
+      (in->face_cells_per_block != 32 && in->face_cells_per_block != 64) || in->graph_steps < 2 ||
+      in->graph_steps > ader_ctx::kMaxGraphSteps || (in->graph_steps & 1))
+    return fail(ctx, ADER_ERR_ARG, "invalid tuning");
+  ctx->tune = *in;
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  return ADER_OK;
+}
+
+extern "C" ader_status ader_autotune(ader_ctx* ctx, const double* u, int reps, ader_tuning* out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (reps < 1) reps = 3;
+  double dt = 0.0;
+  if ((st = ader_compute_dt(ctx, u, 0.0, 0.0, &dt)) != ADER_OK) return st;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](auto&& launch, double* ms_out) -> ader_status {
+    ader_status s2 = launch();  // warm-up
+    if (s2 != ADER_OK) return s2;
+    CK(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < reps; ++r)
+      if ((s2 = launch()) != ADER_OK) return s2;
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_out = ms / reps;
+    return ADER_OK;
+  };
+  const ader_tuning saved = ctx->tune;
+  ader_tuning best = saved;
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  const StepParams sp = make_step(ctx, kDtFixed, 0, dt, 0.0, 0);
+  const double* nodal = u;
+  if (ctx->scheme == ADER_SCHEME_WENO_FV) {
+    WenoParams w{};
+    w.v = u;
+    w.w = ctx->wrec;
+    w.ncells = ctx->mesh.n_cells;
+    w.wo = ctx->basis.weno;
+    CK(do_weno(ctx->N, w, ctx->stream));
+    nodal = ctx->wrec;
+  }
+  // predictor tile shapes
+  double best_ms = 1e300;
+  for (int cpb : {16, 32, 64}) {
+    if (!valid_cpb(ctx->N, cpb)) continue;
+    ctx->tune.predict_cells_per_block = cpb;
+    double ms;
+    st = timed([&]() -> ader_status {
+      PredictParams p = make_predict(ctx, nodal, sp);
+      CK(do_predict(ctx->N, p, ctx->stream));
+      return ADER_OK;
+    }, &ms);
+    if (st != ADER_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.predict_cells_per_block = cpb;
+      best.predict_ms = ms;
+    }
+  }
+  // interface/update tile shapes (the traces of the last predictor run are valid)
+  best_ms = 1e300;
+  for (int cpf : {32, 64}) {
+    if (st != ADER_OK) break;
+    ctx->tune.face_cells_per_block = cpf;
+    double ms;
+    st = timed([&]() -> ader_status {
+      FaceParams f = make_face(ctx, u, ctx->ubuf, sp, 1);
+      CK(do_face(ctx->N, f, ctx->stream));
+      return ADER_OK;
+    }, &ms);
+    if (ms < best_ms && st == ADER_OK) {
+      best_ms = ms;
+      best.face_cells_per_block = cpf;
+      best.face_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ADER_OK) {
+    ctx->tune = saved;
+    return st;
+  }
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  // graph length: solve 64 steps on a workspace copy of u for every candidate
+  ctx->tune = best;
+  const size_t bytes = (size_t)state_count(ctx) * sizeof(double);
+  double best_solve = 1e300;
+  const int prof_saved = ctx->opt.profile;
+  ctx->opt.profile = 0;
+  for (int K : {4, 8, 16, 32, 64}) {
+    ctx->tune.graph_steps = K;
+    if (ctx->gexec) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    double total = 0.0;
+    for (int r = 0; r < 2; ++r) {  // first run captures the graph
+      if ((st = fork_in(ctx)) != ADER_OK) break;
+      CK(cudaMemcpyAsync(ctx->hbuf, u, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      const auto t0 = std::chrono::steady_clock::now();
+      int64_t steps = 0;
+      st = ader_solve(ctx, ctx->hbuf, 0.0, 64, &steps, nullptr);
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (st != ADER_OK && st != ADER_ERR_NOT_CONVERGED) break;
+      st = ADER_OK;
+      if (r == 1) total = ms / 64.0;
+    }
+    if (st != ADER_OK) break;
+    if (total < best_solve) {
+      best_solve = total;
+      best.graph_steps = K;
+      best.solve_ms_per_step = total;
+    }
+  }
+  ctx->opt.profile = prof_saved;
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  if (st != ADER_OK) {
+    ctx->tune = saved;
+    return st;
+  }
+  ctx->tune = best;
+  if (out) *out = best;
   return ADER_OK;
 }

@@ -21,22 +21,80 @@ unsigned grid_for(long long items, int threads, long long cap) {
   if (b > cap) b = cap;
   return (unsigned)b;
 }
+
+// The helpers below are instantiated in every per-degree translation unit with
+// different bodies (they depend on ADER_DEG), so they must have internal linkage.
+template <int CPB>
+cudaError_t prepare_cpb() {
+  if constexpr (!PredCfg<D, CPB>::kValid) {
+    return cudaSuccess;
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(predict_kernel<D, false, CPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PredCfg<D, CPB>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(predict_kernel<D, true, CPB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PredCfg<D, CPB>::kSmemBytes);
+  }
+}
+
+template <int CPB>
+cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
+  if constexpr (!PredCfg<D, CPB>::kValid) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using C = PredCfg<D, CPB>;
+    const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (p.prec == 1 && !p.from_q)
+      predict_kernel<D, true, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else
+      predict_kernel<D, false, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+  }
+}
+
+template <int CF>
+cudaError_t launch_face_cf(const FaceParams& p, cudaStream_t s) {
+  using C = FaceCfg<D, CF>;
+  const long long blocks = (p.ncells + C::C - 1) / C::C;
+  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  face_update_kernel<D, CF><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
 }  // namespace
 
 cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
-  cudaError_t e = cudaFuncSetAttribute(predict_kernel<D, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PredCfg<D>::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(predict_kernel<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)PredCfg<D>::kSmemBytes);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if ((e = prepare_cpb<16>()) != cudaSuccess) return e;
+  if ((e = prepare_cpb<32>()) != cudaSuccess) return e;
+  if ((e = prepare_cpb<64>()) != cudaSuccess) return e;
   e = cudaFuncSetAttribute(predict_multi_kernel<D, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PredCfg<D>::kSmemBytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(predict_multi_kernel<D, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PredCfg<D>::kSmemBytes);
+}
+
+cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
+  switch (p.cpb) {
+    case 16: return launch_predict_cpb<16>(p, s);
+    case 64: return launch_predict_cpb<64>(p, s);
+    case 0:
+    case 32: return launch_predict_cpb<32>(p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {
+  switch (p.cpf) {
+    case 32: return launch_face_cf<32>(p, s);
+    case 0:
+    case 64: return launch_face_cf<64>(p, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, const MultiArgs& m,
@@ -55,25 +113,6 @@ cudaError_t ADER_CAT(launch_face_multi_, ADER_DEG)(const FaceParams& p, const Mu
   using C = FaceCfg<D>;
   if (grid <= 0) return cudaErrorInvalidValue;
   face_update_multi_kernel<D><<<(unsigned)grid, C::THREADS, 0, s>>>(p, m);
-  return cudaGetLastError();
-}
-
-cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
-  using C = PredCfg<D>;
-  const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
-  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (p.prec == 1 && !p.from_q)
-    predict_kernel<D, true><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
-  else
-    predict_kernel<D, false><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
-  return cudaGetLastError();
-}
-
-cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {
-  using C = FaceCfg<D>;
-  const long long blocks = (p.ncells + C::C - 1) / C::C;
-  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  face_update_kernel<D><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
   return cudaGetLastError();
 }
 

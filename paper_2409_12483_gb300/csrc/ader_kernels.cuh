@@ -31,13 +31,18 @@
 
 namespace ader {
 
-template <int N>
+// Predictor tile: CPB cells x n tau nodes = blockDim threads.  CPB is a tuning
+// choice (16, 32 or 64 cells); the autotuner only picks shapes whose blockDim is
+// a multiple of 32 (no idle lanes) and whose registers fit.
+template <int N, int CPB_ = 32>
 struct PredCfg {
   static constexpr int n = N + 1;
-  static constexpr int CPB = 32;  // cells per block: blockDim = 32 n, no idle lanes
+  static constexpr int CPB = CPB_;
   static constexpr int THREADS = CPB * n;
   static constexpr size_t kSmemBytes = (size_t)CPB * kM * n * (n + 1) * sizeof(double);
+  static constexpr bool kValid = (THREADS % 32 == 0) && THREADS <= 512 && (N <= 5 || CPB <= 32);
 };
+constexpr int kMaxCpb = 64;
 
 template <typename T>
 __device__ __forceinline__ unsigned long long abs_bits(T x);
@@ -64,12 +69,17 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 // (in: initial iterate, out: result); uh: the cell's initial data; kr: the thread's
 // row of kappa~ scaled by dt/dx; kt: k~ (n x n).  Returns the number of
 // iterations the thread's cell ran; *conv = converged (or fixed count).
-template <int N, typename T>
+// first_from_u: q enters equal to uh in every tau row.  Then the flux and k~ f
+// are the same in every row, so iteration 1 is done once per cell: thread p0
+// evaluates the flux at node p0 only, forms row p0 of g = k~ f(u), and
+// q'[p0] = u - (dt/dx) (sum_q0 kappa~[p0][q0]) g, using kappa~ 1 = tau.
+template <int N, typename T, int CPB = 32>
 __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 1][kM],
                                            const T (&kr)[N + 1], const T (&kt)[kMaxN][kMaxN],
-                                           T* sg, unsigned long long (*s_red)[32][2], int lc,
+                                           T* sg, unsigned long long (*s_red)[kMaxCpb][2], int lc,
                                            int p0, bool valid, int cap, bool fixed, T tol,
-                                           T gm1, bool* conv) {
+                                           T gm1, bool* conv, bool first_from_u = false,
+                                           T krow = T(0)) {
   constexpr int n = N + 1;
   bool done = !valid;
   bool ok = !valid || fixed;
@@ -84,33 +94,70 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
   }
   while (__syncthreads_or(!done && it < cap)) {
     ++it;
-    // rescaled point-wise flux of the row, then k~ along xi (k_ksi_kernel)
-    {
-      T f[n][kM];
+    T qn[n][kM];
+    if (N >= 1 && first_from_u && it == 1) {
+      // iteration 1 from q = u (x) 1, once per cell
+      T* fcell = sg + (size_t)(lc * n) * kM;            // F(u) at the n nodes  [n][3]
+      T* gcell = sg + (size_t)(CPB * n + lc * n) * kM;  // g = k~ F(u)          [n][3]
+      {
+        // u at node p0 (selected without a runtime register index)
+        T up[kM], F[kM];
 #pragma unroll
-      for (int p1 = 0; p1 < n; ++p1) euler_flux<T>(q[p1], f[p1], gm1);
+        for (int r = 0; r < kM; ++r) up[r] = uh[0][r];
+#pragma unroll
+        for (int k = 1; k < n; ++k)
+          if (k == p0)
+#pragma unroll
+            for (int r = 0; r < kM; ++r) up[r] = uh[k][r];
+        euler_flux<T>(up, F, gm1);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) fcell[p0 * kM + r] = F[r];
+      }
+      __syncthreads();
+      {
+        T g[kM] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int q1 = 0; q1 < n; ++q1) {
+          const T a = kt[p0][q1];
+#pragma unroll
+          for (int r = 0; r < kM; ++r) g[r] = fma(a, fcell[q1 * kM + r], g[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kM; ++r) gcell[p0 * kM + r] = g[r];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) qn[p1][r] = fma(-krow, gcell[p1 * kM + r], uh[p1][r]);
+    } else {
+      // rescaled point-wise flux of the row, then k~ along xi (k_ksi_kernel)
+      {
+        T f[n][kM];
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1) euler_flux<T>(q[p1], f[p1], gm1);
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            T acc = T(0);
+#pragma unroll
+            for (int q1 = 0; q1 < n; ++q1) acc = fma(kt[p1][q1], f[q1][r], acc);
+            my_row[p1 * kM + r] = acc;
+          }
+      }
+      __syncthreads();
+      // kappa~ along tau (kappa_kernel): q'[p0] = u - sum_q0 (dt/dx) kappa~[p0][q0] g[q0]
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
-          T acc = T(0);
+          T acc = uh[p1][r];
 #pragma unroll
-          for (int q1 = 0; q1 < n; ++q1) acc = fma(kt[p1][q1], f[q1][r], acc);
-          my_row[p1 * kM + r] = acc;
+          for (int q0 = 0; q0 < n; ++q0) acc = fma(-kr[q0], cell_g[(q0 * n + p1) * kM + r], acc);
+          qn[p1][r] = acc;
         }
     }
-    __syncthreads();
-    // kappa~ along tau (kappa_kernel): q'[p0] = u - sum_q0 (dt/dx) kappa~[p0][q0] g[q0]
-    T qn[n][kM];
-#pragma unroll
-    for (int p1 = 0; p1 < n; ++p1)
-#pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        T acc = uh[p1][r];
-#pragma unroll
-        for (int q0 = 0; q0 < n; ++q0) acc = fma(-kr[q0], cell_g[(q0 * n + p1) * kM + r], acc);
-        qn[p1][r] = acc;
-      }
     if (!done && !fixed) {
       unsigned long long dmax = 0ull, qmax = 0ull;
 #pragma unroll
@@ -163,7 +210,7 @@ struct TileIO {
 // Shared memory of one predictor tile.
 template <int N>
 struct PredShared {
-  unsigned long long red[2][32][2];
+  unsigned long long red[2][kMaxCpb][2];
   int itmax, ncells, bad;
   unsigned long long itsum;
 };
@@ -171,20 +218,20 @@ struct PredShared {
 // One predictor tile (32 cells x n tau nodes = blockDim) of one solve.
 // PREC32: Picard in FP32 followed by P.sweeps FP64 sweeps (compile-time, so the
 // FP64 form carries no FP32 state in its registers).
-template <int N, bool PREC32>
+template <int N, bool PREC32, int CPB = 32>
 __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileIO& io,
                                              long long tile, double lam, double* smem,
                                              PredShared<N>& sh) {
-  constexpr int n = N + 1, CPB = PredCfg<N>::CPB, THREADS = PredCfg<N>::THREADS;
+  constexpr int n = N + 1, THREADS = PredCfg<N, CPB>::THREADS;
   double* sg = smem;                        // [CPB][n][n][3]
   double* sfb = smem + CPB * n * n * kM;    // [CPB][n][3]
-  unsigned long long(*s_red)[32][2] = sh.red;
+  unsigned long long(*s_red)[kMaxCpb][2] = sh.red;
 
   const int tid = threadIdx.x;
   const int lc = tid / n, p0 = tid - lc * n;
   const long long cell = tile * CPB + lc;
   const bool valid = cell < io.ncells;
-  for (int i = tid; i < 2 * 32 * 2; i += THREADS) (&s_red[0][0][0])[i] = 0ull;
+  for (int i = tid; i < 2 * kMaxCpb * 2; i += THREADS) (&s_red[0][0][0])[i] = 0ull;
   if (tid == 0) {
     sh.itmax = 0;
     sh.itsum = 0ull;
@@ -228,9 +275,9 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     for (int q0 = 0; q0 < n; ++q0) krf[q0] = (float)(lam * P.ops.kap[p0][q0]);
     bool conv32;
     const int cap32 = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop<N, float>(qf, uf, krf, P.opf.kt, reinterpret_cast<float*>(sg), s_red, lc,
+    iters = picard_loop<N, float, CPB>(qf, uf, krf, P.opf.kt, reinterpret_cast<float*>(sg), s_red, lc,
                                   p0, valid, cap32, P.fixed_iter > 0, P.tol32, (float)P.gm1,
-                                  &conv32);
+                                  &conv32, true, (float)(lam * P.ops.kaprow[p0]));
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -239,7 +286,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
     bool dummy;
-    iters += picard_loop<N, double>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, P.sweeps, true,
+    iters += picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, P.sweeps, true,
                                     P.tol, P.gm1, &dummy);
     conv = conv32;
   }
@@ -252,8 +299,9 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
     const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop<N, double>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, cap,
-                                   P.fixed_iter > 0, P.tol, P.gm1, &conv);
+    iters = picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, cap,
+                                   P.fixed_iter > 0, P.tol, P.gm1, &conv, true,
+                                   lam * P.ops.kaprow[p0]);
   }
 
   if (P.out_mode == kOutQ) {
@@ -331,15 +379,15 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   __syncthreads();  // shared memory is free for the next tile
 }
 
-template <int N, bool PREC32>
-__global__ void __launch_bounds__(PredCfg<N>::THREADS)
+template <int N, bool PREC32, int CPB = 32>
+__global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
     predict_kernel(const __grid_constant__ PredictParams P) {
   extern __shared__ __align__(16) double smem[];
   __shared__ PredShared<N> sh;
   double dt;
   if (!predictor_step_dt(P.sp, &dt, blockIdx.x == 0 && threadIdx.x == 0)) return;  // uniform
   const TileIO io{P.u, P.trace, P.q_out, P.q_in, P.ncells, P.sp.ctl};
-  predict_tile<N, PREC32>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
+  predict_tile<N, PREC32, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
 }
 
 // Batched predictor: one launch per degree over the tiles of many independent
@@ -362,20 +410,25 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
   }
 }
 
-template <int N>
+// Interface/update tile: C cells per 256-thread block (tuning choice: 32 or 64).
+template <int N, int C_ = 64>
 struct FaceCfg {
   static constexpr int n = N + 1;
-  static constexpr int C = 64;  // cells per block
+  static constexpr int C = C_;
   static constexpr int THREADS = 256;
 };
 
-template <int N>
+template <int N, int C = 64>
 struct FaceShared {
-  double G[(FaceCfg<N>::C + 1) * (N + 1) * kM];
-  double Gs[(FaceCfg<N>::C + 1) * kM];
-  double u[FaceCfg<N>::C * (N + 1) * kM];
+  double G[(C + 1) * (N + 1) * kM];
+  double Gs[(C + 1) * kM];
+  double u[C * (N + 1) * kM];
   double P[kMaxNs * (N + 1)];
   double w[N + 1], psi0[N + 1], psi1[N + 1], rw[N + 1];
+  float lt[C * kMaxNs];       // FP32 screening value per subcell (CFL)
+  float uf[C * (N + 1) * kM];  // FP32 copy of the updated state (one conversion per value)
+  float Pf[kMaxNs * (N + 1)];
+  float lt_cut;
   unsigned long long wmax[32];
 };
 
@@ -387,11 +440,11 @@ struct FaceIO {
 };
 
 // One tile (C cells) of the interface flux + update (+ lambda_max) of one solve.
-template <int N>
+template <int N, int C = 64>
 __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
                                           const StepParams& sp, long long tile, double dt,
-                                          FaceShared<N>& sh) {
-  constexpr int n = N + 1, C = FaceCfg<N>::C, THREADS = FaceCfg<N>::THREADS;
+                                          FaceShared<N, C>& sh) {
+  constexpr int n = N + 1, THREADS = FaceCfg<N, C>::THREADS;
   const double lam = dt * sp.inv_dx;
   const long long c0 = tile * C;
   const int nvalid = (int)((io.ncells - c0) < C ? (io.ncells - c0) : C);
@@ -436,6 +489,7 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
         const double un = fma(-t, sh.rw[k], up[r]);
         out[r] = un;
         sh.u[(lc * n + k) * kM + r] = un;
+        sh.uf[(lc * n + k) * kM + r] = (float)un;
       }
     }
   } else {
@@ -445,16 +499,60 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
       const double vn = io.v_old[cell * kM + r] - (sh.Gs[(lc + 1) * kM + r] - sh.Gs[lc * kM + r]);
       io.u_new[cell * kM + r] = vn;
       sh.u[lc * kM + r] = vn;
+      sh.uf[lc * kM + r] = (float)vn;
     }
   }
   if (P.want_lambda) {
+    // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
+    // speeds are needed only where the maximum can be: a first FP32 pass screens
+    // every subcell (speeds within 1e-3 of the block's FP32 maximum, and any
+    // subcell whose FP32 state is doubtful, go on to FP64), so the FP64 result is
+    // the same as evaluating every subcell in FP64.
     __syncthreads();
+    const int items = P.dg ? nvalid * P.Ns : nvalid;
+    const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+    float lt_loc = 0.f;
+    for (int item = tid; item < items; item += THREADS) {
+      float v[kM];
+      if (P.dg) {
+        const int lc = item / P.Ns, j = item - lc * P.Ns;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < n; ++k) acc = fmaf(sh.Pf[j * n + k], sh.uf[(lc * n + k) * kM + r], acc);
+          v[r] = acc;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kM; ++r) v[r] = sh.uf[item * kM + r];
+      }
+      const float inv = 1.f / v[0];
+      const float uu = v[1] * inv;
+      const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
+      float lt;
+      if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
+        lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
+      else
+        lt = fabsf(uu) + sqrtf(gf * pp * inv);
+      sh.lt[item] = lt;
+      lt_loc = fmaxf(lt_loc, lt);
+    }
+    const unsigned long long fm =
+        block_max_bits((unsigned long long)__float_as_uint(lt_loc), sh.wmax);
+    if (tid == 0) {
+      const float m = __uint_as_float((unsigned)fm);
+      sh.lt_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+    }
+    __syncthreads();
+    const float cut = sh.lt_cut;
     double lmax = 0.0;
     bool bad = false;
-    if (P.dg) {
-      for (int item = tid; item < nvalid * P.Ns; item += THREADS) {
+    for (int item = tid; item < items; item += THREADS) {
+      if (!(sh.lt[item] >= cut)) continue;
+      double v[kM];
+      if (P.dg) {
         const int lc = item / P.Ns, j = item - lc * P.Ns;
-        double v[kM];
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           double acc = 0.0;
@@ -462,11 +560,11 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
           for (int k = 0; k < n; ++k) acc = fma(sh.P[j * n + k], sh.u[(lc * n + k) * kM + r], acc);
           v[r] = acc;
         }
-        lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
+      } else {
+#pragma unroll
+        for (int r = 0; r < kM; ++r) v[r] = sh.u[item * kM + r];
       }
-    } else {
-      for (int lc = tid; lc < nvalid; lc += THREADS)
-        lmax = fmax(lmax, wave_speed(&sh.u[lc * kM], P.gamma, P.gm1, &bad));
+      lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
     }
     const unsigned long long bm = block_max_bits(dbits(lmax), sh.wmax);
     if (tid == 0) atomicMax(&sp.ctl->lam[sp.par ^ 1], bm);
@@ -475,11 +573,14 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
   __syncthreads();  // shared memory is free for the next tile
 }
 
-template <int N>
-__device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShared<N>& sh) {
+template <int N, int C = 64>
+__device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShared<N, C>& sh) {
   constexpr int n = N + 1;
   // per-thread table lookups in face_tile are divergent: stage the small tables in smem
-  for (int i = threadIdx.x; i < P.Ns * n; i += FaceCfg<N>::THREADS) sh.P[i] = P.ops.P[i / n][i % n];
+  for (int i = threadIdx.x; i < P.Ns * n; i += FaceCfg<N, C>::THREADS) {
+    sh.P[i] = P.ops.P[i / n][i % n];
+    sh.Pf[i] = (float)P.ops.P[i / n][i % n];
+  }
   if (threadIdx.x < n) {
     sh.w[threadIdx.x] = P.ops.w[threadIdx.x];
     sh.psi0[threadIdx.x] = P.ops.psi0[threadIdx.x];
@@ -489,16 +590,16 @@ __device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShare
   __syncthreads();
 }
 
-template <int N>
-__global__ void __launch_bounds__(FaceCfg<N>::THREADS)
+template <int N, int C = 64>
+__global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
     face_update_kernel(const __grid_constant__ FaceParams P) {
-  __shared__ FaceShared<N> sh;
+  __shared__ FaceShared<N, C> sh;
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
-  face_stage_tables<N>(P, sh);
+  face_stage_tables<N, C>(P, sh);
   const FaceIO io{P.trace, P.v_old, P.u_new, P.ncells};
-  face_tile<N>(P, io, P.sp, blockIdx.x, dt, sh);
+  face_tile<N, C>(P, io, P.sp, blockIdx.x, dt, sh);
   corrector_finish(P.sp, dt, last, blockIdx.x == 0 && threadIdx.x == 0);
 }
 

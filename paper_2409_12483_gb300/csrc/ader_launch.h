@@ -25,6 +25,7 @@ struct PredictParams {
   int sweeps;
   int max_iter;
   int fixed_iter;
+  int cpb;               // predictor cells per block (16, 32, 64; tuned), 0 = 32
   float tol32;
   double tol;
   double gamma, gm1;
@@ -42,6 +43,7 @@ struct FaceParams {
   long long ncells;
   int dg;
   int want_lambda;
+  int cpf;               // interface/update cells per block (32, 64; tuned), 0 = 64
   int Ns;
   double gamma, gm1;
   StepParams sp;

@@ -182,6 +182,10 @@ int build_basis(int N, bool weno, Basis* out) {
 
   OpsD& d = out->d;
   for (int k = 0; k < n; ++k) {
+    ld rs = 0;
+    for (int l = 0; l < n; ++l) rs += kap[k][l];
+    d.kaprow[k] = (double)rs;
+    out->f.kaprow[k] = (float)rs;
     d.xi[k] = (double)xi[k];
     d.w[k] = (double)w[k];
     d.rw[k] = (double)(1 / w[k]);

@@ -24,6 +24,7 @@ struct OpsD {
   double psi0[kMaxN], psi1[kMaxN];        // phi_k(0), phi_k(1)
   double kt[kMaxN][kMaxN];                // k~[p][q] = Lambda^-1 Xi = phi_q'(xi_p)
   double kap[kMaxN][kMaxN];               // kappa~ = Upsilon^-1 Lambda
+  double kaprow[kMaxN];                   // row sums of kappa~ (= tau nodes: kappa~ 1 = tau)
   double vt[kMaxN][kMaxN];                // D~[k][l] / w_k, D~[k][l] = w_l phi_k'(xi_l)
   double P[kMaxNs][kMaxN];                // P[j][k] = Ns int_{j/Ns}^{(j+1)/Ns} phi_k
 };
@@ -31,6 +32,7 @@ struct OpsD {
 struct OpsF {
   float kt[kMaxN][kMaxN];
   float kap[kMaxN][kMaxN];
+  float kaprow[kMaxN];
 };
 
 // WENO tables for even N (order N+1), three stencils of N+1 cells.

@@ -120,3 +120,37 @@ def test_server_rejects_bad_options_and_requests(lib):
     assert lib.ader_server_create(C.byref(o), C.byref(srv)) == 1
     assert lib.ader_server_request_bytes(5, 1000) >= 1000 * 6 * 3 * 8 * 2 + 1000 * 54 * 8
     assert lib.ader_server_request_bytes(8, 10) == 0
+
+
+def test_tuning_validation_without_gpu(lib):
+    from paper_2409_12483_gb300.capi import Mesh, Tuning, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(100, 0.0, 1.0)), 7, 0, C.byref(default_options()),
+                         C.byref(ctx)) == 0
+    t = Tuning()
+    assert lib.ader_get_tuning(ctx, C.byref(t)) == 0
+    assert (t.predict_cells_per_block, t.face_cells_per_block) == (32, 64)
+    assert t.graph_steps >= 2 and t.graph_steps % 2 == 0
+    for cpb, cpf, k in [(64, 64, 8), (8, 64, 8), (32, 48, 8), (32, 64, 7), (32, 64, 0)]:
+        bad = Tuning(cpb, cpf, k, 0.0, 0.0, 0.0)  # 64 cells x 8 nodes is too big at N = 7
+        assert lib.ader_set_tuning(ctx, C.byref(bad)) == 1
+    ok = Tuning(32, 32, 16, 0.0, 0.0, 0.0)
+    assert lib.ader_set_tuning(ctx, C.byref(ok)) == 0
+    assert lib.ader_get_tuning(ctx, C.byref(t)) == 0 and t.face_cells_per_block == 32
+    lib.ader_destroy(ctx)
+
+
+def test_per_degree_helpers_are_not_merged_across_degrees():
+    """Launch helpers compiled once per degree must have internal linkage: a weak
+    (mergeable) definition would make every degree launch one degree's kernels."""
+    import shutil
+    import subprocess
+    from paper_2409_12483_gb300 import build
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-C", build.LIB], capture_output=True, text=True).stdout
+    weak = [l for l in out.splitlines()
+            if l.split()[1:2] and l.split()[1] in ("W", "V", "u")
+            and ("ader::" in l) and ("launch" in l or "prepare" in l)]
+    assert not weak, weak[:5]

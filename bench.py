@@ -171,6 +171,21 @@ def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warm
     return out
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Max of a per-rank time over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most max_seconds."""
+    return world * units_per_rank / max_seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -303,13 +318,9 @@ def main():
     torch.cuda.nvtx.range_pop()
     if pg:
         pg.barrier()
-    total_ms = sum(times)
-    if pg:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(times), pg, dev)
     cu_per_step = CELLS * TIME_STEPS
-    value = world * cu_per_step * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(cu_per_step * args.steps, world, total_ms / 1e3)
 
     # dominant kernel: the predictor (FP64 ALU bound)
     pred_ms = sum(p["predict_ms"] for p in prof)
@@ -342,13 +353,9 @@ def main():
         ctx.ader_solve_host(uh, max_steps=TIME_STEPS)
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times)
-    if pg:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(sum(e2e_times), pg, dev)
     state_bytes = u0.numel() * 8
-    e2e = {"value": world * cu_per_step * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": whole_job_rate(cu_per_step * args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
     launches = sum(p["kernel_launches"] for p in prof)
 

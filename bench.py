@@ -410,6 +410,12 @@ def run_variants(args, dev, flush):
         return {"rel_linf_vs_fp64_path": d}
     out.append(variant_line("dg5-1e5-fp32pred", "as the headline, FP32 Picard + 2 FP64 sweeps",
                             ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64))
+    del ctx
+    # the headline with the FP64-accurate float-float Picard (FP32 pipes)
+    ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, precision="ff")
+    ctx.ader_autotune(u0, reps=2)
+    out.append(variant_line("dg5-1e5-ffpred", "as the headline, float-float Picard (FP64-accurate)",
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64))
     del ctx, ref
     # ADER-WENO5 (WENO N=4 + LST-DG N=4), 10^6 cells, 100 steps, FP64
     nc = 1_000_000
@@ -431,6 +437,14 @@ def run_variants(args, dev, flush):
     out.append(variant_line("dg7-1e6-fp64", "ADER-DG N=7, 10^6 cells, modes4, 20 steps, FP64",
                             c64, u0, nc, 7, ts, st, 1, flush, extra=grab))
     del c64
+    cff = Context(nc, 7, "dg", device=dev, profile=1, precision="ff")
+
+    def err7ff(u):
+        u64 = keep["u64"]
+        return {"rel_linf_vs_fp64_path": (u - u64).abs().max().item() / u64.abs().max().item()}
+    out.append(variant_line("dg7-1e6-ffpred", "ADER-DG N=7, 10^6 cells, float-float Picard",
+                            cff, u0, nc, 7, ts, st, 1, flush, extra=err7ff))
+    del cff
     c32 = Context(nc, 7, "dg", device=dev, profile=1, precision="fp32", fp64_sweeps=2)
 
     def err7(u):

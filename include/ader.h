@@ -52,7 +52,9 @@ typedef enum { ADER_SCHEME_DG = 0, ADER_SCHEME_WENO_FV = 1 } ader_scheme;
 
 typedef enum {
   ADER_PREC_FP64 = 0,            /* whole path in FP64 */
-  ADER_PREC_FP32_PREDICTOR = 1   /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
+  ADER_PREC_FP32_PREDICTOR = 1,  /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
+  ADER_PREC_FF_PREDICTOR = 2     /* Picard in float-float (~48 bits, FP32 pipes), FP64-accurate;
+                                    predictor epilogue, corrector and CFL in FP64 */
 } ader_precision;
 
 /* Uniform periodic mesh on [x0, x1]. */

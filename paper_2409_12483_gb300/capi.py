@@ -24,7 +24,7 @@ ADER_ERR_TIMEOUT = 6
 ADER_ERR_STATE = 7
 
 SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
-PRECISIONS = {"fp64": 0, "fp32": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2}
 
 
 class AderError(RuntimeError):

@@ -305,7 +305,8 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   ader_options& o = c->opt;
   if (o.picard_max_iter <= 0) o.picard_max_iter = 4 * c->n + 8;
   if (!(o.gamma > 1.0) || !(o.cfl > 0.0) || !(o.picard_tol >= 0.0) || o.picard_fixed_iter < 0 ||
-      (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR) ||
+      (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR &&
+       o.precision != ADER_PREC_FF_PREDICTOR) ||
       (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000) {
     delete c;
     return ADER_ERR_ARG;

@@ -29,13 +29,15 @@ cudaError_t prepare_cpb() {
   if constexpr (!PredCfg<D, CPB>::kValid) {
     return cudaSuccess;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(predict_kernel<D, false, CPB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PredCfg<D, CPB>::kSmemBytes);
+    const int bytes = (int)PredCfg<D, CPB>::kSmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(predict_kernel<D, 0, CPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(predict_kernel<D, true, CPB>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PredCfg<D, CPB>::kSmemBytes);
+    e = cudaFuncSetAttribute(predict_kernel<D, 1, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(predict_kernel<D, 2, CPB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   }
 }
 
@@ -48,9 +50,11 @@ cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
     const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (p.prec == 1 && !p.from_q)
-      predict_kernel<D, true, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+      predict_kernel<D, 1, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else if (p.prec == 2 && !p.from_q)
+      predict_kernel<D, 2, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else
-      predict_kernel<D, false, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+      predict_kernel<D, 0, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     return cudaGetLastError();
   }
 }
@@ -70,12 +74,14 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_cpb<32>()) != cudaSuccess) return e;
   if ((e = prepare_cpb<64>()) != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(predict_multi_kernel<D, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PredCfg<D>::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(predict_multi_kernel<D, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)PredCfg<D>::kSmemBytes);
+  for (int prec = 0; prec < 3; ++prec) {
+    auto k = prec == 0 ? predict_multi_kernel<D, 0>
+                       : (prec == 1 ? predict_multi_kernel<D, 1> : predict_multi_kernel<D, 2>);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PredCfg<D>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
@@ -102,9 +108,11 @@ cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, co
   using C = PredCfg<D>;
   if (grid <= 0) return cudaErrorInvalidValue;
   if (p.prec == 1)
-    predict_multi_kernel<D, true><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+    predict_multi_kernel<D, 1><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+  else if (p.prec == 2)
+    predict_multi_kernel<D, 2><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else
-    predict_multi_kernel<D, false><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+    predict_multi_kernel<D, 0><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   return cudaGetLastError();
 }
 

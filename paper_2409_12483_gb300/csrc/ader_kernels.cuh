@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "ader_device.cuh"
+#include "ader_ff.cuh"
 #include "ader_launch.h"
 
 namespace ader {
@@ -197,6 +198,150 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
   return cell_it;
 }
 
+// Picard iteration in float-float arithmetic (about 48 bits, FP32 pipes): the
+// same iteration as picard_loop<N, double>, including the once-per-cell first
+// iteration from q = u.  q, uh, kr, krow are ff; k~ comes from the (kt, ktlo)
+// float tables; the convergence test compares |q' - q| with tol max(1, |q'|).
+template <int N, int CPB = 32>
+__device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const ff (&uh)[N + 1][kM],
+                                              const ff (&kr)[N + 1], const OpsF& of, double* sgd,
+                                              unsigned long long (*s_red)[kMaxCpb][2], int lc,
+                                              int p0, bool valid, int cap, bool fixed, float tol,
+                                              ff gm1, bool* conv, ff krow) {
+  constexpr int n = N + 1;
+  float2* sg = reinterpret_cast<float2*>(sgd);  // one (hi, lo) pair per double slot
+  bool done = !valid;
+  bool ok = !valid || fixed;
+  int it = 0, cell_it = 0;
+  float2* my_row = sg + (size_t)((lc * n + p0) * n) * kM;
+  const float2* cell_g = sg + (size_t)(lc * n) * n * kM;
+  if (p0 == 0) {
+    s_red[0][lc][0] = s_red[0][lc][1] = 0ull;
+    s_red[1][lc][0] = s_red[1][lc][1] = 0ull;
+  }
+  while (__syncthreads_or(!done && it < cap)) {
+    ++it;
+    ff qn[n][kM];
+    if (N >= 1 && it == 1) {
+      float2* fcell = sg + (size_t)(lc * n) * kM;
+      float2* gcell = sg + (size_t)(CPB * n + lc * n) * kM;
+      {
+        ff up[kM], F[kM];
+#pragma unroll
+        for (int r = 0; r < kM; ++r) up[r] = uh[0][r];
+#pragma unroll
+        for (int k = 1; k < n; ++k)
+          if (k == p0)
+#pragma unroll
+            for (int r = 0; r < kM; ++r) up[r] = uh[k][r];
+        euler_flux_ff(up, F, gm1);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) fcell[p0 * kM + r] = make_float2(F[r].hi, F[r].lo);
+      }
+      __syncthreads();
+      {
+        ff_acc g[kM];
+#pragma unroll
+        for (int r = 0; r < kM; ++r) g[r].zero();
+#pragma unroll
+        for (int q1 = 0; q1 < n; ++q1) {
+          const ff a{of.kt[p0][q1], of.ktlo[p0][q1]};
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            const float2 f = fcell[q1 * kM + r];
+            g[r].fma_add(a, ff{f.x, f.y});
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          const ff gg = g[r].get();
+          gcell[p0 * kM + r] = make_float2(gg.hi, gg.lo);
+        }
+      }
+      __syncthreads();
+      const ff nk{-krow.hi, -krow.lo};
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          ff_acc a;
+          a.set(uh[p1][r]);
+          const float2 g = gcell[p1 * kM + r];
+          a.fma_add(nk, ff{g.x, g.y});
+          qn[p1][r] = a.get();
+        }
+    } else {
+      {
+        ff f[n][kM];
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1) euler_flux_ff(q[p1], f[p1], gm1);
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            ff_acc acc;
+            acc.zero();
+#pragma unroll
+            for (int q1 = 0; q1 < n; ++q1) acc.fma_add(ff{of.kt[p1][q1], of.ktlo[p1][q1]}, f[q1][r]);
+            const ff g = acc.get();
+            my_row[p1 * kM + r] = make_float2(g.hi, g.lo);
+          }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          ff_acc acc;
+          acc.set(uh[p1][r]);
+#pragma unroll
+          for (int q0 = 0; q0 < n; ++q0) {
+            const float2 g = cell_g[(q0 * n + p1) * kM + r];
+            acc.fma_add(ff{-kr[q0].hi, -kr[q0].lo}, ff{g.x, g.y});
+          }
+          qn[p1][r] = acc.get();
+        }
+    }
+    if (!done && !fixed) {
+      unsigned long long dmax = 0ull, qmax = 0ull;
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          const float d = (qn[p1][r].hi - q[p1][r].hi) + (qn[p1][r].lo - q[p1][r].lo);
+          const unsigned long long db = abs_bits<float>(d);
+          const unsigned long long mb = abs_bits<float>(qn[p1][r].hi);
+          dmax = db > dmax ? db : dmax;
+          qmax = mb > qmax ? mb : qmax;
+        }
+      atomicMax(&s_red[it & 1][lc][0], dmax);
+      atomicMax(&s_red[it & 1][lc][1], qmax);
+    }
+    __syncthreads();
+    if (!done) {
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) q[p1][r] = qn[p1][r];
+      cell_it = it;
+      if (!fixed) {
+        const float dl = from_bits<float>(s_red[it & 1][lc][0]);
+        const float qm = from_bits<float>(s_red[it & 1][lc][1]);
+        if (dl <= tol * (qm > 1.0f ? qm : 1.0f)) {
+          done = true;
+          ok = true;
+        }
+      }
+    }
+    if (p0 == 0) {
+      s_red[(it + 1) & 1][lc][0] = 0ull;
+      s_red[(it + 1) & 1][lc][1] = 0ull;
+    }
+  }
+  *conv = ok;
+  return cell_it;
+}
+
 // Per-solve view used by one tile: where the tile reads and writes.
 struct TileIO {
   const double* u;      // nodal initial data of the solve
@@ -216,9 +361,12 @@ struct PredShared {
 };
 
 // One predictor tile (32 cells x n tau nodes = blockDim) of one solve.
-// PREC32: Picard in FP32 followed by P.sweeps FP64 sweeps (compile-time, so the
-// FP64 form carries no FP32 state in its registers).
-template <int N, bool PREC32, int CPB = 32>
+// PREC (compile-time, so each form carries only its own state in registers):
+//   0: Picard in FP64;
+//   1: Picard in FP32 followed by P.sweeps FP64 sweeps;
+//   2: Picard in float-float (FP64-accurate, FP32 pipes).
+// The epilogue (traces, volume term) is FP64 in every form.
+template <int N, int PREC, int CPB = 32>
 __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileIO& io,
                                              long long tile, double lam, double* smem,
                                              PredShared<N>& sh) {
@@ -261,7 +409,26 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
       for (int r = 0; r < kM; ++r) q[p1][r] = src[p1 * kM + r];
     __syncthreads();
-  } else if constexpr (PREC32) {
+  } else if constexpr (PREC == 2) {
+    ff qf[n][kM], uf[n][kM], krf[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        uf[k][r] = d2ff(uh[k][r]);
+        qf[k][r] = uf[k][r];
+      }
+#pragma unroll
+    for (int q0 = 0; q0 < n; ++q0) krf[q0] = d2ff(lam * P.ops.kap[p0][q0]);
+    const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+    iters = picard_loop_ff<N, CPB>(qf, uf, krf, P.opf, sg, s_red, lc, p0, valid, cap,
+                                   P.fixed_iter > 0, (float)P.tol, d2ff(P.gm1), &conv,
+                                   d2ff(lam * P.ops.kaprow[p0]));
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) q[k][r] = ff2d(qf[k][r]);
+  } else if constexpr (PREC == 1) {
     // FP32 Picard stage, then P.sweeps FP64 sweeps from its result
     float qf[n][kM], uf[n][kM], krf[n];
 #pragma unroll
@@ -290,7 +457,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
                                     P.tol, P.gm1, &dummy);
     conv = conv32;
   }
-  if (!P.from_q && !PREC32) {
+  if (!P.from_q && PREC == 0) {
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -379,7 +546,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   __syncthreads();  // shared memory is free for the next tile
 }
 
-template <int N, bool PREC32, int CPB = 32>
+template <int N, int PREC, int CPB = 32>
 __global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
     predict_kernel(const __grid_constant__ PredictParams P) {
   extern __shared__ __align__(16) double smem[];
@@ -387,12 +554,12 @@ __global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
   double dt;
   if (!predictor_step_dt(P.sp, &dt, blockIdx.x == 0 && threadIdx.x == 0)) return;  // uniform
   const TileIO io{P.u, P.trace, P.q_out, P.q_in, P.ncells, P.sp.ctl};
-  predict_tile<N, PREC32, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
+  predict_tile<N, PREC, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
 }
 
 // Batched predictor: one launch per degree over the tiles of many independent
 // solves (continuous batching).  Every solve keeps its own device time step.
-template <int N, bool PREC32>
+template <int N, int PREC>
 __global__ void __launch_bounds__(PredCfg<N>::THREADS)
     predict_multi_kernel(const __grid_constant__ PredictParams P, const MultiArgs M) {
   extern __shared__ __align__(16) double smem[];
@@ -406,7 +573,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
     double dt;
     if (!predictor_step_dt(sp, &dt, item.tile == 0 && threadIdx.x == 0)) continue;  // uniform
     const TileIO io{d.u[par], d.trace, nullptr, nullptr, d.ncells, sp.ctl};
-    predict_tile<N, PREC32>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
+    predict_tile<N, PREC>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
   }
 }
 

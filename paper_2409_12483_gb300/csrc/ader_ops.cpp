@@ -198,6 +198,7 @@ int build_basis(int N, bool weno, Basis* out) {
       out->dphi[k][l] = (double)D[k][l];
       out->dtil[k][l] = (double)(w[l] * D[k][l]);
       out->f.kt[k][l] = (float)D[l][k];
+      out->f.ktlo[k][l] = (float)(D[l][k] - (ld)out->f.kt[k][l]);
       out->f.kap[k][l] = (float)kap[k][l];
     }
   }

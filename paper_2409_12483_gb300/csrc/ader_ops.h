@@ -33,6 +33,7 @@ struct OpsF {
   float kt[kMaxN][kMaxN];
   float kap[kMaxN][kMaxN];
   float kaprow[kMaxN];
+  float ktlo[kMaxN][kMaxN];  // k~ - (float)k~ rounded to float: k~ = kt + ktlo to ~48 bits
 };
 
 // WENO tables for even N (order N+1), three stencils of N+1 cells.

@@ -148,7 +148,7 @@ def measure_solve(ctx, u0, time_steps, steps, warmup, flush):
 
 
 def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warmup, flush, dg=True,
-                 extra=None):
+                 extra=None, field=None):
     ms, prof, u = measure_solve(ctx, u0, time_steps, steps, warmup, flush)
     n = degree + 1
     iters = sum(p["mean_iters"] for p in prof) / len(prof)
@@ -168,6 +168,8 @@ def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warm
         out["predict_frac_of_fp64_peak"] = out["predict_fp64_tflops"] / FP64_PEAK_TFLOPS
     if extra:
         out.update(extra(u))
+    if field is not None and dg:
+        out["l1_density_vs_exact"] = dg_l1_error(ctx, u.cpu().numpy(), field, prof[-1]["t"])
     return out
 
 
@@ -184,6 +186,27 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
 def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
     """Whole-job throughput: every rank processed units_per_rank in at most max_seconds."""
     return world * units_per_rank / max_seconds
+
+
+def dg_l1_error(ctx, u, field, t, npts=25):
+    """L1 density error of a DG state against the exact advected density (eq.
+    epsilons of Sec. 2.1 in 1D: npts-point GL rule per cell), from the library's
+    own nodes; measurement code, not the oracle."""
+    import numpy as np
+    xi = ctx.table("xi")
+    n = len(xi)
+    u = np.asarray(u).reshape(-1, n, 3)
+    nc = u.shape[0]
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    L = np.ones((npts, n))
+    for k in range(n):
+        for m in range(n):
+            if m != k:
+                L[:, k] *= (gx - xi[m]) / (xi[k] - xi[m])
+    rho = u[:, :, 0] @ L.T
+    xs = (np.arange(nc)[:, None] + gx[None, :]) / nc
+    return float((np.abs(rho - field.rho(xs, t)) @ gw).sum() / nc)
 
 
 def dist_env():
@@ -209,10 +232,11 @@ def cpu_oracle_rate(target_s: float = 12.0):
     t2 = 0.0
     if more:
         t0 = time.perf_counter()
-        o.solve("dg", u1, 1.0 / CELLS, max_steps=more)
+        u1, _, _, _ = o.solve("dg", u1, 1.0 / CELLS, max_steps=more)
         t2 = time.perf_counter() - t0
     steps = 1 + more
     secs = t1 + t2
+    cpu_oracle_rate.last = (u, u1, steps)
     return CELLS * steps / secs, steps, secs
 
 
@@ -287,6 +311,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     tuning = ctx.ader_autotune(u0, reps=3)  # launch shapes picked by measurement, before timing
 
+    last = {}
+
     def one(prof):
         u.copy_(u0)
         flush.zero_()
@@ -296,6 +322,7 @@ def main():
         steps, t, rc = ctx.ader_solve(u, max_steps=TIME_STEPS)
         ev1.record()
         torch.cuda.synchronize()
+        last["t"] = t
         st = ctx.ader_get_stats()
         if steps != TIME_STEPS:
             raise RuntimeError(f"solve stopped after {steps} steps")
@@ -319,6 +346,7 @@ def main():
     if pg:
         pg.barrier()
     total_ms = max_over_ranks(sum(times), pg, dev)
+    u_last, t_last = u.cpu().numpy(), last["t"]
     cu_per_step = CELLS * TIME_STEPS
     value = whole_job_rate(cu_per_step * args.steps, world, total_ms / 1e3)
 
@@ -379,8 +407,15 @@ def main():
             line["variants"] = run_variants(args, dev, flush)
         if not args.no_serving:
             line["serving"] = run_serving(dev, args.serving_requests)
+        line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
+            u_in, u_or, k = cpu_oracle_rate.last
+            ug = torch.tensor(u_in, device=dev).reshape(-1)
+            ctx.ader_solve(ug, max_steps=k)
+            torch.cuda.synchronize()
+            par = float(np.abs(ug.cpu().numpy() - u_or.ravel()).max() / np.abs(u_or).max())
+            line["errors"]["rel_linf_vs_fp64_oracle_after_oracle_steps"] = par
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"{steps} time steps of the same 10^5-cell N=5 mesh ({secs:.1f} s, 1 thread)"}
@@ -409,21 +444,44 @@ def run_variants(args, dev, flush):
         d = (u - uref).abs().max().item() / uref.abs().max().item()
         return {"rel_linf_vs_fp64_path": d}
     out.append(variant_line("dg5-1e5-fp32pred", "as the headline, FP32 Picard + 2 FP64 sweeps",
-                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64))
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64,
+                            field=W.modes4(SEED)))
     del ctx
     # the headline with the FP64-accurate float-float Picard (FP32 pipes)
     ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, precision="ff")
     ctx.ader_autotune(u0, reps=2)
     out.append(variant_line("dg5-1e5-ffpred", "as the headline, float-float Picard (FP64-accurate)",
-                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64))
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush, extra=err_vs_fp64,
+                            field=W.modes4(SEED)))
     del ctx, ref
     # ADER-WENO5 (WENO N=4 + LST-DG N=4), 10^6 cells, 100 steps, FP64
     nc = 1_000_000
     ctx = Context(nc, 4, "fv", device=dev, profile=1)
     v0 = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
-    out.append(variant_line("weno5-1e6-fp64", "ADER-WENO5 FV, 10^6 cells, modes4, 100 steps, FP64",
-                            ctx, v0, nc, 4, TIME_STEPS, st, 1, flush, dg=False))
-    del ctx, v0
+    ctx.ader_autotune(v0, reps=2)
+    wl = variant_line("weno5-1e6-fp64", "ADER-WENO5 FV, 10^6 cells, modes4, 100 steps, FP64, "
+                      "autotuned shapes, time loop as device-resident CUDA graphs",
+                      ctx, v0, nc, 4, TIME_STEPS, st, 1, flush, dg=False)
+    # the same 100 steps launched plainly: one host call per step (CFL, WENO,
+    # predictor, update launched from the host; default launch shapes)
+    plain = Context(nc, 4, "fv", device=dev)
+    a = v0.clone()
+    b = torch.empty_like(a)
+    plain.ader_step(a, b, 0.0)
+    torch.cuda.synchronize()
+    a.copy_(v0)
+    flush.zero_()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(TIME_STEPS):
+        plain.ader_step(a, b, 0.0)
+        a, b = b, a
+    ev1.record()
+    torch.cuda.synchronize()
+    wl["plain_host_launched"] = {"value": nc * TIME_STEPS / (ev0.elapsed_time(ev1) / 1e3),
+                                 "unit": UNIT, "ms_per_step": ev0.elapsed_time(ev1)}
+    out.append(wl)
+    del ctx, v0, plain, a, b
     # ADER-DG N=7, 10^6 cells: FP64 and FP32-predictor (2 FP64 sweeps), 20 steps
     ts = 20
     c64 = Context(nc, 7, "dg", device=dev, profile=1)

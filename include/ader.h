@@ -164,6 +164,13 @@ ader_status ader_weno_reconstruct(ader_ctx* ctx, const double* v_dev, double* w_
 ader_status ader_solve(ader_ctx* ctx, double* u_dev, double t_end, int64_t max_steps,
                        int64_t* steps_out, double* t_out);
 
+/* ader_solve starting from simulated time t0 (0 <= t0 < t_end when t_end > 0):
+ * resumes a solve from a checkpoint (the caller's state u_dev and the t reached).
+ * A solve split as ader_solve(max_steps = k) then ader_solve_from(t_k, t_end)
+ * gives the same steps and state bit for bit as one ader_solve(t_end). */
+ader_status ader_solve_from(ader_ctx* ctx, double* u_dev, double t0, double t_end,
+                            int64_t max_steps, int64_t* steps_out, double* t_out);
+
 /* ader_solve on a HOST state: copies u_host to the device (workspace), solves,
  * copies the result back to u_host.  Synchronises. */
 ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t max_steps,

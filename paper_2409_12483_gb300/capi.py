@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
             "ader_weno_reconstruct": ([V, V, V], C.c_int),
             "ader_solve": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
+            "ader_solve_from": ([V, V, D, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
             "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
@@ -144,7 +145,8 @@ def exported_symbols():
             "ader_status_string", "ader_state_count", "ader_predictor_count",
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
-            "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_get_stats",
+            "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_solve_from",
+            "ader_get_stats",
             "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
             "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
@@ -287,6 +289,15 @@ class Context:
         t = C.c_double(0.0)
         rc = self._L.ader_solve(self._ctx, _ptr(u, numel=self.state_count, name="u"),
                                 float(t_end), int(max_steps), C.byref(steps), C.byref(t))
+        self._check(rc, ok=(ADER_OK, *allow))
+        return steps.value, t.value, rc
+
+    def ader_solve_from(self, u, t0: float, t_end: float = 0.0, max_steps: int = 0, allow=()):
+        steps = C.c_int64(0)
+        t = C.c_double(0.0)
+        rc = self._L.ader_solve_from(self._ctx, _ptr(u, numel=self.state_count, name="u"),
+                                     float(t0), float(t_end), int(max_steps), C.byref(steps),
+                                     C.byref(t))
         self._check(rc, ok=(ADER_OK, *allow))
         return steps.value, t.value, rc
 

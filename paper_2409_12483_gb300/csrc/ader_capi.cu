@@ -527,17 +527,24 @@ ader_status ader_weno_reconstruct(ader_ctx* ctx, const double* v, double* w) {
   return join_out(ctx);
 }
 
-ader_status ader_solve(ader_ctx* ctx, double* u, double t_end, int64_t max_steps,
-                       int64_t* steps_out, double* t_out) {
+static ader_status solve_impl(ader_ctx* ctx, double* u, double t0, double t_end,
+                              int64_t max_steps, int64_t* steps_out, double* t_out) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
   if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (!(t_end > 0.0) && max_steps <= 0)
     return fail(ctx, ADER_ERR_ARG, "need t_end > 0 or max_steps > 0");
   if (std::isnan(t_end) || max_steps < 0) return fail(ctx, ADER_ERR_ARG, "bad t_end / max_steps");
+  if (!(t0 >= 0.0) || !std::isfinite(t0) || (t_end > 0.0 && !(t0 < t_end)))
+    return fail(ctx, ADER_ERR_ARG, "need 0 <= t0 < t_end");
   if (!(t_end > 0.0)) t_end = 0.0;
   if ((st = fork_in(ctx)) != ADER_OK) return st;
   if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  if (t0 != 0.0) {  // resume: the device clock starts at t0
+    ctx->hflags[1].t = t0;
+    CK(cudaMemcpyAsync(&ctx->ctl->t, &ctx->hflags[1].t, sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
   if ((st = enqueue_cfl(ctx, u, 0)) != ADER_OK) return st;
 
   const int K = ctx->tune.graph_steps > 0 ? ctx->tune.graph_steps : graph_steps_for(ctx->mesh.n_cells);
@@ -643,6 +650,16 @@ ader_status ader_solve(ader_ctx* ctx, double* u, double t_end, int64_t max_steps
   if (!finished && !(max_steps > 0 && steps >= max_steps))
     return fail(ctx, ADER_ERR_TIMEOUT, "time loop stopped after %lld graph launches", launches);
   return status_from_flags(ctx, ctx->hflags[0].status);
+}
+
+ader_status ader_solve(ader_ctx* ctx, double* u, double t_end, int64_t max_steps,
+                       int64_t* steps_out, double* t_out) {
+  return solve_impl(ctx, u, 0.0, t_end, max_steps, steps_out, t_out);
+}
+
+ader_status ader_solve_from(ader_ctx* ctx, double* u, double t0, double t_end, int64_t max_steps,
+                            int64_t* steps_out, double* t_out) {
+  return solve_impl(ctx, u, t0, t_end, max_steps, steps_out, t_out);
 }
 
 ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t max_steps,

@@ -214,3 +214,29 @@ def test_host_buffer_solve_matches_device_solve(cuda, oracle_mod):
     torch.cuda.synchronize()
     assert steps == 7
     np.testing.assert_array_equal(uh.ravel(), ud.cpu().numpy().ravel())
+
+
+@pytest.mark.parametrize("scheme,N,nc", [("dg", 3, 90), ("fv", 4, 120)])
+def test_checkpoint_resume_is_bit_identical(cuda, oracle_mod, scheme, N, nc):
+    """Solve to t_end in one call, or stop after k steps (checkpoint: state + t)
+    and resume from t_k: the same number of steps and the same state, bit for bit."""
+    import torch
+    from paper_2409_12483_gb300 import Context
+    o = oracle_mod.Oracle(N)
+    if scheme == "dg":
+        u = W.nodal_state(field_nonlinear(7), o.node_x(nc))
+    else:
+        u = W.cell_average_state(field_nonlinear(7), nc)
+    t_end = 0.05
+    ctx = Context(nc, N, scheme)
+    a = to_dev(u, cuda)
+    steps_a, t_a, _ = ctx.ader_solve(a, t_end=t_end)
+    b = to_dev(u, cuda)
+    k = steps_a // 3
+    s1, t1, _ = ctx.ader_solve(b, max_steps=k)
+    ckpt = b.cpu().clone()                      # a checkpoint is the state and t1
+    c = ckpt.to(cuda)
+    s2, t2, _ = ctx.ader_solve_from(c, t1, t_end=t_end)
+    torch.cuda.synchronize()
+    assert s1 == k and s1 + s2 == steps_a and t2 == t_a == t_end
+    assert torch.equal(a, c)

@@ -281,7 +281,8 @@ def main():
                     help="skip the continuous-batching serving benchmark (scaled Poisson stream)")
     ap.add_argument("--serving-requests", type=int, default=128)
     ap.add_argument("--case", default=None,
-                    help="profiling case instead of the bench line: predict-dg5 | predict-dg7-fp32 | weno5")
+                    help="profiling case instead of the bench line: "
+                         "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -624,6 +625,9 @@ def run_case(args):
     nc = 1_000_000
     if args.case == "predict-dg5":
         ctx = Context(nc, 5, "dg", device=dev)
+        u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    elif args.case == "predict-dg5-ff":
+        ctx = Context(nc, 5, "dg", device=dev, precision="ff")
         u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
     elif args.case == "predict-dg7-fp32":
         ctx = Context(nc, 7, "dg", device=dev, precision="fp32", fp64_sweeps=2)

@@ -118,7 +118,12 @@ size_t ader_workspace_bytes(const ader_ctx* ctx);   /* device scratch for ader_b
 ader_status ader_node_coords(const ader_ctx* ctx, double* x_host, int64_t count);
 
 /* Operator tables (host copies, row-major), for inspection:
- * name: "xi","w","psi0","psi1" (N+1), "kt","kap","dphi","dtil" ((N+1)^2), "P" ((2N+1)(N+1)). */
+ * name: "xi","w","psi0","psi1" (N+1), "kt","kap","dphi","dtil" ((N+1)^2), "P" ((2N+1)(N+1)),
+ * "ksa","ksb" (H^2, H = (N+2)/2: k~ in even/odd form, used by the predictor for
+ * N >= 4; with h = (N+1)/2, ksa[p][q] = (k~[p][q] + k~[p][N-q])/2 for p, q < h and
+ * ksa[p][h] = k~[p][h] for odd N+1; ksb[p][q] = (k~[p][q] - k~[p][N-q])/2 for
+ * p < H, q < h; other entries 0).  count must equal the table's size; a wrong
+ * count or an unknown name returns ADER_ERR_ARG. */
 ader_status ader_get_table(const ader_ctx* ctx, const char* name, double* out_host, int64_t count);
 
 /* Bind caller-owned device scratch (>= ader_workspace_bytes, 256-byte aligned)

@@ -248,13 +248,15 @@ class Context:
     def table(self, name: str):
         import numpy as np
         n = self.n
-        size = {"xi": n, "w": n, "psi0": n, "psi1": n, "P": (2 * self.degree + 1) * n}.get(name, n * n)
+        H = (n + 1) // 2
+        size = {"xi": n, "w": n, "psi0": n, "psi1": n, "P": (2 * self.degree + 1) * n,
+                "ksa": H * H, "ksb": H * H}.get(name, n * n)
         out = np.zeros(size)
         self._check(self._L.ader_get_table(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
                                            size))
         if name in ("xi", "w", "psi0", "psi1"):
             return out
-        return out.reshape(-1, n)
+        return out.reshape(-1, H if name in ("ksa", "ksb") else n)
 
     # -- hot path (same names as the C ABI) --
     def ader_compute_dt(self, u, t: float = 0.0, t_end: float = 0.0) -> float:

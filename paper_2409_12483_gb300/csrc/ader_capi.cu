@@ -377,6 +377,15 @@ ader_status ader_get_table(const ader_ctx* c, const char* name, double* out, int
   if (!strcmp(name, "dphi")) return mat(c->basis.dphi, n);
   if (!strcmp(name, "dtil")) return mat(c->basis.dtil, n);
   if (!strcmp(name, "P")) return mat(d.P, c->basis.Ns);
+  const int H = (n + 1) / 2;
+  auto half = [&](const double (*src)[kMaxH]) -> ader_status {
+    if (count != (int64_t)H * H) return ADER_ERR_ARG;
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < H; ++j) out[i * H + j] = src[i][j];
+    return ADER_OK;
+  };
+  if (!strcmp(name, "ksa")) return half(d.ksa);
+  if (!strcmp(name, "ksb")) return half(d.ksb);
   return ADER_ERR_ARG;
 }
 

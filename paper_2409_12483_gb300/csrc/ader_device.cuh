@@ -127,11 +127,26 @@ __device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt
 
 // ---- 1D Euler (rho, m = rho u, E) ----
 
+// -x / 2.  In FP64 this runs on the integer pipe (GB300 issues FP64 at 1/64 of
+// the FP32 rate): sign flip and exponent - 1, exact for every normal x above the
+// smallest binade; zero, subnormals and that binade return -x, which enters
+// p = (gamma - 1)(E - m u / 2) only far below ulp(E).
+template <typename T>
+__device__ __forceinline__ T neg_half(T x) {
+  return T(-0.5) * x;
+}
+template <>
+__device__ __forceinline__ double neg_half<double>(double x) {
+  int hi = __double2hiint(x);
+  if ((hi & 0x7ff00000) > 0x00100000) hi -= 0x00100000;
+  return __hiloint2double(hi ^ (int)0x80000000, __double2loint(x));
+}
+
 template <typename T>
 __device__ __forceinline__ void euler_flux(const T* U, T* F, T gm1) {
   const T inv = T(1) / U[0];
   const T u = U[1] * inv;
-  const T p = gm1 * fma(T(-0.5) * U[1], u, U[2]);
+  const T p = gm1 * fma(neg_half(U[1]), u, U[2]);
   F[0] = U[1];
   F[1] = fma(U[1], u, p);
   F[2] = (U[2] + p) * u;

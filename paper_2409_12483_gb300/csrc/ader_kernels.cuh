@@ -66,6 +66,58 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
   return __uint_as_float(static_cast<unsigned>(b));
 }
 
+// One tau row of g = k~ f (k_ksi_kernel), written to out[p1 * 3 + r].  For N >= 4
+// the even/odd form of k~ is used: the GL nodes are symmetric about 1/2, so
+// k~[n-1-p][n-1-q] = -k~[p][q]; with e_q = f_q + f_{n-1-q}, o_q = f_q - f_{n-1-q}
+// (q < h = n/2; the middle node of odd n enters e alone), S_p = sum_q ka[p][q] e_q
+// and T_p = sum_q kb[p][q] o_q give g_p = S_p + T_p and g_{n-1-p} = T_p - S_p
+// (and g_h = T_h for odd n): n^2/2 + 2n operations per variable instead of n^2.
+template <int N, typename T>
+__device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
+                                        const T (&kt)[kMaxN][kMaxN],
+                                        const T (&ka)[kMaxH][kMaxH],
+                                        const T (&kb)[kMaxH][kMaxH]) {
+  constexpr int n = N + 1, h = n / 2, H = (n + 1) / 2;
+  if constexpr (N < 4) {
+#pragma unroll
+    for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        T acc = T(0);
+#pragma unroll
+        for (int q1 = 0; q1 < n; ++q1) acc = fma(kt[p1][q1], f[q1][r], acc);
+        out[p1 * kM + r] = acc;
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      T e[H], o[h];
+#pragma unroll
+      for (int q = 0; q < h; ++q) {
+        e[q] = f[q][r] + f[n - 1 - q][r];
+        o[q] = f[q][r] - f[n - 1 - q][r];
+      }
+      if constexpr (H > h) e[h] = f[h][r];
+#pragma unroll
+      for (int p = 0; p < h; ++p) {
+        T S = T(0), Tt = T(0);
+#pragma unroll
+        for (int q = 0; q < H; ++q) S = fma(ka[p][q], e[q], S);
+#pragma unroll
+        for (int q = 0; q < h; ++q) Tt = fma(kb[p][q], o[q], Tt);
+        out[p * kM + r] = Tt + S;
+        out[(n - 1 - p) * kM + r] = Tt - S;
+      }
+      if constexpr (H > h) {
+        T Tt = T(0);
+#pragma unroll
+        for (int q = 0; q < h; ++q) Tt = fma(kb[h][q], o[q], Tt);
+        out[h * kM + r] = Tt;
+      }
+    }
+  }
+}
+
 // Picard iteration of one block of cells in precision T.  q: the thread's tau row
 // (in: initial iterate, out: result); uh: the cell's initial data; kr: the thread's
 // row of kappa~ scaled by dt/dx; kt: k~ (n x n).  Returns the number of
@@ -77,7 +129,8 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 template <int N, typename T, int CPB = 32>
 __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 1][kM],
                                            const T (&kr)[N + 1], const T (&kt)[kMaxN][kMaxN],
-                                           T* sg, unsigned long long (*s_red)[kMaxCpb][2], int lc,
+                                           const T (&ka)[kMaxH][kMaxH],
+                                           const T (&kb)[kMaxH][kMaxH], T* sg, unsigned long long (*s_red)[kMaxCpb][2], int lc,
                                            int p0, bool valid, int cap, bool fixed, T tol,
                                            T gm1, bool* conv, bool first_from_u = false,
                                            T krow = T(0)) {
@@ -127,25 +180,38 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
         for (int r = 0; r < kM; ++r) gcell[p0 * kM + r] = g[r];
       }
       __syncthreads();
+      unsigned long long gmax = 0ull;
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
-        for (int r = 0; r < kM; ++r) qn[p1][r] = fma(-krow, gcell[p1 * kM + r], uh[p1][r]);
+        for (int r = 0; r < kM; ++r) {
+          const T g = gcell[p1 * kM + r];
+          qn[p1][r] = fma(-krow, g, uh[p1][r]);
+          const unsigned long long gb = abs_bits<T>(g);
+          gmax = gb > gmax ? gb : gmax;
+        }
+      // q' - q = -(dt/dx) tau_p0 g in this iteration: its largest magnitude is
+      // (dt/dx) tau_p0 max|g| (up to the rounding of q'), one multiplication
+      // instead of a subtraction per value
+      if (!done && !fixed) {
+        unsigned long long qmax = 0ull;
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            const unsigned long long m = abs_bits<T>(qn[p1][r]);
+            qmax = m > qmax ? m : qmax;
+          }
+        atomicMax(&s_red[it & 1][lc][0], abs_bits<T>(krow * from_bits<T>(gmax)));
+        atomicMax(&s_red[it & 1][lc][1], qmax);
+      }
     } else {
       // rescaled point-wise flux of the row, then k~ along xi (k_ksi_kernel)
       {
         T f[n][kM];
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1) euler_flux<T>(q[p1], f[p1], gm1);
-#pragma unroll
-        for (int p1 = 0; p1 < n; ++p1)
-#pragma unroll
-          for (int r = 0; r < kM; ++r) {
-            T acc = T(0);
-#pragma unroll
-            for (int q1 = 0; q1 < n; ++q1) acc = fma(kt[p1][q1], f[q1][r], acc);
-            my_row[p1 * kM + r] = acc;
-          }
+        kxi_row<N, T>(f, my_row, kt, ka, kb);
       }
       __syncthreads();
       // kappa~ along tau (kappa_kernel): q'[p0] = u - sum_q0 (dt/dx) kappa~[p0][q0] g[q0]
@@ -159,7 +225,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
           qn[p1][r] = acc;
         }
     }
-    if (!done && !fixed) {
+    if (!done && !fixed && !(N >= 1 && first_from_u && it == 1)) {
       unsigned long long dmax = 0ull, qmax = 0ull;
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
@@ -360,12 +426,80 @@ struct PredShared {
   unsigned long long itsum;
 };
 
+// Epilogue of the float-float form: the traces at xi = 0 and 1, the space-time
+// average of the flux and the volume term (Sec. 1.2) evaluated in float-float
+// from the float-float q; each output is converted to FP64 once, and the volume
+// term is added to the FP64 initial data in FP64.  Same shared-memory layout as
+// the FP64 epilogue, one (hi, lo) float pair per double slot.
+template <int N, int CPB>
+__device__ __forceinline__ void epilogue_ff(const PredictParams& P, const ff (&q)[N + 1][kM],
+                                            const double (&u_own)[kM], ff lam, double* dst,
+                                            bool valid, int lc, int p0, double* smem) {
+  constexpr int n = N + 1;
+  const OpsF& of = P.opf;
+#pragma unroll
+  for (int r = 0; r < kM; ++r) {
+    ff_acc aR, aL;
+    aR.zero();
+    aL.zero();
+#pragma unroll
+    for (int p1 = 0; p1 < n; ++p1) {
+      aR.fma_add(ff{of.psi1[p1], of.psi1lo[p1]}, q[p1][r]);
+      aL.fma_add(ff{of.psi0[p1], of.psi0lo[p1]}, q[p1][r]);
+    }
+    if (valid) {
+      dst[p0 * kM + r] = ff2d(aR.get());
+      dst[n * kM + p0 * kM + r] = ff2d(aL.get());
+    }
+  }
+  if (!P.dg) return;
+  __syncthreads();  // the exchange buffer is reused below
+  float2* sg = reinterpret_cast<float2*>(smem);  // [CPB][n][n][3]
+  float2* sfb = sg + CPB * n * n * kM;           // [CPB][n][3]
+  float2* my_row = sg + (size_t)((lc * n + p0) * n) * kM;
+  const ff gm1 = d2ff(P.gm1);
+#pragma unroll
+  for (int p1 = 0; p1 < n; ++p1) {
+    ff F[kM];
+    euler_flux_ff(q[p1], F, gm1);
+#pragma unroll
+    for (int r = 0; r < kM; ++r) my_row[p1 * kM + r] = make_float2(F[r].hi, F[r].lo);
+  }
+  __syncthreads();
+  // fbar[p0] = (dt/dx) sum_l0 w_l0 F(q[l0][p0])
+#pragma unroll
+  for (int r = 0; r < kM; ++r) {
+    ff_acc s;
+    s.zero();
+#pragma unroll
+    for (int l0 = 0; l0 < n; ++l0) {
+      const float2 f = sg[((lc * n + l0) * n + p0) * kM + r];
+      s.fma_add(ff{of.w[l0], of.wlo[l0]}, ff{f.x, f.y});
+    }
+    const ff fb = ff_mul(s.get(), lam);
+    sfb[(lc * n + p0) * kM + r] = make_float2(fb.hi, fb.lo);
+  }
+  __syncthreads();
+  // u_k + (sum_l D~_kl fbar_l) / w_k for k = p0
+#pragma unroll
+  for (int r = 0; r < kM; ++r) {
+    ff_acc acc;
+    acc.zero();
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      const float2 f = sfb[(lc * n + l) * kM + r];
+      acc.fma_add(ff{of.vt[p0][l], of.vtlo[p0][l]}, ff{f.x, f.y});
+    }
+    if (valid) dst[2 * n * kM + p0 * kM + r] = u_own[r] + ff2d(acc.get());
+  }
+}
+
 // One predictor tile (32 cells x n tau nodes = blockDim) of one solve.
 // PREC (compile-time, so each form carries only its own state in registers):
 //   0: Picard in FP64;
 //   1: Picard in FP32 followed by P.sweeps FP64 sweeps;
 //   2: Picard in float-float (FP64-accurate, FP32 pipes).
-// The epilogue (traces, volume term) is FP64 in every form.
+// The epilogue (traces, volume term) is float-float in form 2 and FP64 otherwise.
 template <int N, int PREC, int CPB = 32>
 __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileIO& io,
                                              long long tile, double lam, double* smem,
@@ -401,6 +535,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   double q[n][kM];
   int iters = 0;
   bool conv = true;
+  bool epilogue_done = false;
 
   if (P.from_q) {
     const double* src = io.q_in + ((valid ? cell : 0) * n + p0) * (long long)(n * kM);
@@ -418,16 +553,24 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
         uf[k][r] = d2ff(uh[k][r]);
         qf[k][r] = uf[k][r];
       }
+    const ff lamf = d2ff(lam);
 #pragma unroll
-    for (int q0 = 0; q0 < n; ++q0) krf[q0] = d2ff(lam * P.ops.kap[p0][q0]);
+    for (int q0 = 0; q0 < n; ++q0) krf[q0] = ff_mul(lamf, ff{P.opf.kap[p0][q0], P.opf.kaplo[p0][q0]});
     const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
     iters = picard_loop_ff<N, CPB>(qf, uf, krf, P.opf, sg, s_red, lc, p0, valid, cap,
                                    P.fixed_iter > 0, (float)P.tol, d2ff(P.gm1), &conv,
-                                   d2ff(lam * P.ops.kaprow[p0]));
+                                   ff_mul(lamf, ff{P.opf.kaprow[p0], P.opf.kaprowlo[p0]}));
+    if (P.out_mode == kOutQ) {
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+      for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int r = 0; r < kM; ++r) q[k][r] = ff2d(qf[k][r]);
+        for (int r = 0; r < kM; ++r) q[k][r] = ff2d(qf[k][r]);
+    } else {
+      const int stride = (P.dg ? 9 : 6) * n;
+      epilogue_ff<N, CPB>(P, qf, u_own, lamf, io.trace + (valid ? cell : 0) * (long long)stride,
+                          valid, lc, p0, smem);
+      epilogue_done = true;
+    }
   } else if constexpr (PREC == 1) {
     // FP32 Picard stage, then P.sweeps FP64 sweeps from its result
     float qf[n][kM], uf[n][kM], krf[n];
@@ -442,7 +585,8 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     for (int q0 = 0; q0 < n; ++q0) krf[q0] = (float)(lam * P.ops.kap[p0][q0]);
     bool conv32;
     const int cap32 = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop<N, float, CPB>(qf, uf, krf, P.opf.kt, reinterpret_cast<float*>(sg), s_red, lc,
+    iters = picard_loop<N, float, CPB>(qf, uf, krf, P.opf.kt, P.opf.ksa, P.opf.ksb,
+                                       reinterpret_cast<float*>(sg), s_red, lc,
                                   p0, valid, cap32, P.fixed_iter > 0, P.tol32, (float)P.gm1,
                                   &conv32, true, (float)(lam * P.ops.kaprow[p0]));
 #pragma unroll
@@ -453,7 +597,8 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
     bool dummy;
-    iters += picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, P.sweeps, true,
+    iters += picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, P.ops.ksa, P.ops.ksb, sg, s_red, lc,
+                                         p0, valid, P.sweeps, true,
                                     P.tol, P.gm1, &dummy);
     conv = conv32;
   }
@@ -466,12 +611,15 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
     const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, sg, s_red, lc, p0, valid, cap,
+    iters = picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, P.ops.ksa, P.ops.ksb, sg, s_red, lc,
+                                        p0, valid, cap,
                                    P.fixed_iter > 0, P.tol, P.gm1, &conv, true,
                                    lam * P.ops.kaprow[p0]);
   }
 
-  if (P.out_mode == kOutQ) {
+  if (epilogue_done) {
+    // written by the float-float epilogue
+  } else if (P.out_mode == kOutQ) {
     if (valid) {
       double* dst = io.q_out + (cell * n + p0) * (long long)(n * kM);
 #pragma unroll
@@ -498,32 +646,26 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     }
     if (P.dg) {
       __syncthreads();  // the exchange buffer is reused below
-      const double wl = P.ops.w[p0] * lam;
       double* my_row = sg + (size_t)((lc * n + p0) * n) * kM;
 #pragma unroll
-      for (int p1 = 0; p1 < n; ++p1) {
-        double F[kM];
-        euler_flux<double>(q[p1], F, P.gm1);
-#pragma unroll
-        for (int r = 0; r < kM; ++r) my_row[p1 * kM + r] = wl * F[r];
-      }
+      for (int p1 = 0; p1 < n; ++p1) euler_flux<double>(q[p1], my_row + p1 * kM, P.gm1);
       __syncthreads();
-      // fbar[p0] = sum_l0 w_l0 (dt/dx) F(q[l0][p0])
+      // fbar[p0] / (dt/dx) = sum_l0 w_l0 F(q[l0][p0])
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
         double s = 0.0;
 #pragma unroll
-        for (int l0 = 0; l0 < n; ++l0) s += sg[((lc * n + l0) * n + p0) * kM + r];
+        for (int l0 = 0; l0 < n; ++l0) s = fma(P.ops.w[l0], sg[((lc * n + l0) * n + p0) * kM + r], s);
         sfb[(lc * n + p0) * kM + r] = s;
       }
       __syncthreads();
-      // u_k + (sum_l D~_kl fbar_l) / w_k for k = p0
+      // u_k + (dt/dx) (sum_l D~_kl fbar_l / (dt/dx)) / w_k for k = p0
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
         double acc = 0.0;
 #pragma unroll
         for (int l = 0; l < n; ++l) acc = fma(P.ops.vt[p0][l], sfb[(lc * n + l) * kM + r], acc);
-        if (valid) dst[2 * n * kM + p0 * kM + r] = u_own[r] + acc;
+        if (valid) dst[2 * n * kM + p0 * kM + r] = fma(lam, acc, u_own[r]);
       }
     }
   }

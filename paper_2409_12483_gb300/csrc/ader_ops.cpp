@@ -140,6 +140,12 @@ struct Bary {
   }
 };
 
+// v = hi + lo: hi = v rounded to float, lo = the remainder rounded to float
+void split_ff(ld v, float* hi, float* lo) {
+  *hi = (float)v;
+  *lo = (float)(v - (ld)*hi);
+}
+
 ld factorial_ratio(int j, int a) {  // j! / (j-a)!
   ld r = 1;
   for (int i = 0; i < a; ++i) r *= (ld)(j - i);
@@ -184,23 +190,43 @@ int build_basis(int N, bool weno, Basis* out) {
   for (int k = 0; k < n; ++k) {
     ld rs = 0;
     for (int l = 0; l < n; ++l) rs += kap[k][l];
+    OpsF& f = out->f;
     d.kaprow[k] = (double)rs;
-    out->f.kaprow[k] = (float)rs;
+    split_ff(rs, &f.kaprow[k], &f.kaprowlo[k]);
     d.xi[k] = (double)xi[k];
     d.w[k] = (double)w[k];
     d.rw[k] = (double)(1 / w[k]);
     d.psi0[k] = (double)ph0[k];
     d.psi1[k] = (double)ph1[k];
+    split_ff(w[k], &f.w[k], &f.wlo[k]);
+    split_ff(ph0[k], &f.psi0[k], &f.psi0lo[k]);
+    split_ff(ph1[k], &f.psi1[k], &f.psi1lo[k]);
     for (int l = 0; l < n; ++l) {
+      const ld vt = w[l] * D[k][l] / w[k];
       d.kt[k][l] = (double)D[l][k];  // k~ = Lambda^-1 Xi = Dphi^T
       d.kap[k][l] = (double)kap[k][l];
-      d.vt[k][l] = (double)(w[l] * D[k][l] / w[k]);
+      d.vt[k][l] = (double)vt;
       out->dphi[k][l] = (double)D[k][l];
       out->dtil[k][l] = (double)(w[l] * D[k][l]);
-      out->f.kt[k][l] = (float)D[l][k];
-      out->f.ktlo[k][l] = (float)(D[l][k] - (ld)out->f.kt[k][l]);
-      out->f.kap[k][l] = (float)kap[k][l];
+      split_ff(D[l][k], &f.kt[k][l], &f.ktlo[k][l]);
+      split_ff(kap[k][l], &f.kap[k][l], &f.kaplo[k][l]);
+      split_ff(vt, &f.vt[k][l], &f.vtlo[k][l]);
     }
+  }
+  // k~ (= Dphi^T) in even/odd form
+  {
+    const int h = n / 2, H = (n + 1) / 2;
+    for (int p = 0; p < H; ++p)
+      for (int q = 0; q < H; ++q) {
+        ld a = 0, b = 0;
+        if (p < h && q < h) a = (D[q][p] + D[n - 1 - q][p]) / 2;
+        if (p < h && q == h && H > h) a = D[h][p];
+        if (q < h) b = (D[q][p] - D[n - 1 - q][p]) / 2;
+        d.ksa[p][q] = (double)a;
+        d.ksb[p][q] = (double)b;
+        out->f.ksa[p][q] = (float)a;
+        out->f.ksb[p][q] = (float)b;
+      }
   }
   // subcell projection (Sec. 1.4): P_jk = Ns int_{j/Ns}^{(j+1)/Ns} phi_k = sum_q w_q phi_k((j+xi_q)/Ns)
   for (int j = 0; j < out->Ns; ++j)

@@ -16,6 +16,7 @@ namespace ader {
 constexpr int kMaxDeg = 7;
 constexpr int kMaxN = kMaxDeg + 1;        // GL nodes per direction
 constexpr int kMaxNs = 2 * kMaxDeg + 1;   // subcells of Sec. 1.4
+constexpr int kMaxH = (kMaxN + 1) / 2;    // half rows of the symmetric k~ form
 constexpr int kM = 3;                     // conserved variables of 1D Euler
 
 // Tables in the layout the kernels read (row-major, unused entries zero).
@@ -27,13 +28,28 @@ struct OpsD {
   double kaprow[kMaxN];                   // row sums of kappa~ (= tau nodes: kappa~ 1 = tau)
   double vt[kMaxN][kMaxN];                // D~[k][l] / w_k, D~[k][l] = w_l phi_k'(xi_l)
   double P[kMaxNs][kMaxN];                // P[j][k] = Ns int_{j/Ns}^{(j+1)/Ns} phi_k
+  // k~ in even/odd form (the GL nodes are symmetric about 1/2, so
+  // k~[n-1-p][n-1-q] = -k~[p][q]); h = n / 2, H = (n + 1) / 2, m = h the middle
+  // node of odd n:
+  //   ksa[p][q] = (k~[p][q] + k~[p][n-1-q]) / 2, p < h, q < h;  ksa[p][m] = k~[p][m]
+  //   ksb[p][q] = (k~[p][q] - k~[p][n-1-q]) / 2, p < H, q < h
+  double ksa[kMaxH][kMaxH];
+  double ksb[kMaxH][kMaxH];
 };
 
+// Float tables; the *lo members hold x - (float)x rounded to float, so that
+// hi + lo carries a table entry to ~48 bits (the float-float form).
 struct OpsF {
   float kt[kMaxN][kMaxN];
   float kap[kMaxN][kMaxN];
   float kaprow[kMaxN];
-  float ktlo[kMaxN][kMaxN];  // k~ - (float)k~ rounded to float: k~ = kt + ktlo to ~48 bits
+  float ktlo[kMaxN][kMaxN];
+  float kaplo[kMaxN][kMaxN];
+  float kaprowlo[kMaxN];
+  float psi0[kMaxN], psi0lo[kMaxN], psi1[kMaxN], psi1lo[kMaxN];
+  float w[kMaxN], wlo[kMaxN];
+  float vt[kMaxN][kMaxN], vtlo[kMaxN][kMaxN];
+  float ksa[kMaxH][kMaxH], ksb[kMaxH][kMaxH];
 };
 
 // WENO tables for even N (order N+1), three stencils of N+1 cells.

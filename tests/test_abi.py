@@ -105,6 +105,24 @@ def test_library_tables_match_oracle(lib, oracle_mod, N):
                                    atol=4e-15 * max(1.0, np.abs(ref).max()), err_msg=name)
     Ns = 2 * N + 1
     np.testing.assert_allclose(get("P", Ns * n).reshape(Ns, n), o.table("P"), rtol=0, atol=4e-15)
+    # k~ in even/odd form, applied the way the predictor applies it, gives the
+    # oracle's k~ f (the GL nodes are symmetric, so k~ is centro-antisymmetric)
+    H, h = (n + 1) // 2, n // 2
+    ka = get("ksa", H * H).reshape(H, H)
+    kb = get("ksb", H * H).reshape(H, H)
+    kt = o.table("kt")
+    for seed in range(3):
+        f = np.random.default_rng(100 * N + seed).standard_normal(n)
+        e = np.array([f[q] + f[n - 1 - q] for q in range(h)] + ([f[h]] if H > h else []))
+        od = np.array([f[q] - f[n - 1 - q] for q in range(h)])
+        g = np.empty(n)
+        for p in range(h):
+            S, T = ka[p, :H] @ e, kb[p, :h] @ od
+            g[p], g[n - 1 - p] = S + T, T - S
+        if H > h:
+            g[h] = kb[h, :h] @ od
+        np.testing.assert_allclose(g, kt @ f, rtol=0,
+                                   atol=1e-14 * np.abs(kt).sum(1).max() * np.abs(f).max())
     lib.ader_destroy(ctx)
 
 

@@ -127,6 +127,40 @@ __device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt
 
 // ---- 1D Euler (rho, m = rho u, E) ----
 
+// 1/x in FP64 within one unit in the last place of 1.0 / x: a float seed
+// r = rcp.approx(x) (both conversions by integer operations: GB300 executes
+// double <-> float conversions on its FP64 pipe), then the cubically convergent
+// correction 1/x = r / (1 - e) ~ r (1 + e + e^2) with e = 1 - x r (the series
+// form of Newton-Raphson reciprocal refinement, e.g. Muller et al., Handbook of
+// Floating-Point Arithmetic): 3 FP64 FMAs.  The float seed's relative error is
+// ~2^-22, so the truncated series leaves ~2^-66 before the final rounding.
+// Outside 2^-125 <= |x| < 2^126 (also 0, inf, NaN) it returns 1.0 / x.
+__device__ __forceinline__ double rcp64(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex < 898 || ex > 1148) return 1.0 / x;
+  const unsigned lo = (unsigned)__double2loint(x);
+  const float xf = __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(ex - 896) << 23) |
+                                   (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  const unsigned rb = __float_as_uint(rf);
+  const double r = __hiloint2double(
+      (int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
+      (int)((rb & 0x7u) << 29));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  return T(1) / x;
+}
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return rcp64(x);
+}
+
 // -x / 2.  In FP64 this runs on the integer pipe (GB300 issues FP64 at 1/64 of
 // the FP32 rate): sign flip and exponent - 1, exact for every normal x above the
 // smallest binade; zero, subnormals and that binade return -x, which enters
@@ -144,7 +178,7 @@ __device__ __forceinline__ double neg_half<double>(double x) {
 
 template <typename T>
 __device__ __forceinline__ void euler_flux(const T* U, T* F, T gm1) {
-  const T inv = T(1) / U[0];
+  const T inv = recip(U[0]);
   const T u = U[1] * inv;
   const T p = gm1 * fma(neg_half(U[1]), u, U[2]);
   F[0] = U[1];
@@ -154,7 +188,7 @@ __device__ __forceinline__ void euler_flux(const T* U, T* F, T gm1) {
 
 // |u| + c; flags rho <= 0, p <= 0 or non-finite through *bad.
 __device__ __forceinline__ double wave_speed(const double* U, double gamma, double gm1, bool* bad) {
-  const double inv = 1.0 / U[0];
+  const double inv = rcp64(U[0]);
   const double u = U[1] * inv;
   const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
   if (!(U[0] > 0.0) || !(p > 0.0) || !(U[0] < 1.0e300) || !(p < 1.0e300)) {
@@ -168,7 +202,7 @@ __device__ __forceinline__ double wave_speed(const double* U, double gamma, doub
 // s = max(|u_a| + c_a, |u_b| + c_b).
 __device__ __forceinline__ void rusanov(const double* a, const double* b, double* G, double gamma,
                                         double gm1) {
-  const double ia = 1.0 / a[0], ib = 1.0 / b[0];
+  const double ia = rcp64(a[0]), ib = rcp64(b[0]);
   const double ua = a[1] * ia, ub = b[1] * ib;
   const double pa = gm1 * fma(-0.5 * a[1], ua, a[2]);
   const double pb = gm1 * fma(-0.5 * b[1], ub, b[2]);

@@ -152,6 +152,42 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
+// sqrt(x) for 2^-125 <= x < 2^126 within two units in the last place: a float
+// seed y = rsqrt.approx(x) (integer conversions as in rcp64), one cubically
+// convergent correction of the inverse square root from the binomial series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ..., e = 1 - x y^2, then sqrt(x) = x y:
+// 6 FP64 operations.  Other inputs (0, negative, subnormal, inf, NaN, out of the
+// float range) return sqrt(x).
+__device__ __forceinline__ double sqrt64(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (hi < 0 || ex < 898 || ex > 1148) return sqrt(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const float xf = __uint_as_float(((unsigned)(ex - 896) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
+                                   (lo >> 29));
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+  const unsigned yb = __float_as_uint(yf);
+  double y = __hiloint2double((int)(((((yb >> 23) & 0xffu) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)),
+                              (int)((yb & 0x7u) << 29));
+  const double e = fma(-(x * y), y, 1.0);
+  y = fma(y * e, fma(0.375, e, 0.5), y);
+  return x * y;
+}
+
+// double -> float by truncation on the integer pipe (for screening values only):
+// normal doubles in the float range map to the float with the leading 24
+// significant bits; zero, tiny values map to 0, large ones to +-inf.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex < 897) return __uint_as_float(sign);
+  if (ex > 1150) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
+                         ((unsigned)__double2loint(x) >> 29));
+}
+
 template <typename T>
 __device__ __forceinline__ T recip(T x) {
   return T(1) / x;
@@ -190,30 +226,29 @@ __device__ __forceinline__ void euler_flux(const T* U, T* F, T gm1) {
 __device__ __forceinline__ double wave_speed(const double* U, double gamma, double gm1, bool* bad) {
   const double inv = rcp64(U[0]);
   const double u = U[1] * inv;
-  const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
+  const double p = gm1 * fma(neg_half(U[1]), u, U[2]);
   if (!(U[0] > 0.0) || !(p > 0.0) || !(U[0] < 1.0e300) || !(p < 1.0e300)) {
     *bad = true;
     return 0.0;
   }
-  return fabs(u) + sqrt(gamma * p * inv);
+  return fabs(u) + sqrt64(gamma * p * inv);
 }
 
-// Rusanov flux between a (left) and b (right): 1/2 (F(a) + F(b)) - 1/2 s (b - a),
-// s = max(|u_a| + c_a, |u_b| + c_b).
-__device__ __forceinline__ void rusanov(const double* a, const double* b, double* G, double gamma,
-                                        double gm1) {
+// Twice the Rusanov flux between a (left) and b (right):
+// 2 G = F(a) + F(b) - s (b - a), s = max(|u_a| + c_a, |u_b| + c_b); the factor
+// 1/2 is applied once per face together with dt/dx, after the time average.
+__device__ __forceinline__ void rusanov2(const double* a, const double* b, double* G2,
+                                         double gamma, double gm1) {
   const double ia = rcp64(a[0]), ib = rcp64(b[0]);
   const double ua = a[1] * ia, ub = b[1] * ib;
-  const double pa = gm1 * fma(-0.5 * a[1], ua, a[2]);
-  const double pb = gm1 * fma(-0.5 * b[1], ub, b[2]);
-  const double sa = fabs(ua) + sqrt(gamma * pa * ia);
-  const double sb = fabs(ub) + sqrt(gamma * pb * ib);
+  const double pa = gm1 * fma(neg_half(a[1]), ua, a[2]);
+  const double pb = gm1 * fma(neg_half(b[1]), ub, b[2]);
+  const double sa = fabs(ua) + sqrt64(gamma * pa * ia);
+  const double sb = fabs(ub) + sqrt64(gamma * pb * ib);
   const double s = fmax(sa, sb);
-  const double Fa0 = a[1], Fa1 = fma(a[1], ua, pa), Fa2 = (a[2] + pa) * ua;
-  const double Fb0 = b[1], Fb1 = fma(b[1], ub, pb), Fb2 = (b[2] + pb) * ub;
-  G[0] = 0.5 * (Fa0 + Fb0) - 0.5 * s * (b[0] - a[0]);
-  G[1] = 0.5 * (Fa1 + Fb1) - 0.5 * s * (b[1] - a[1]);
-  G[2] = 0.5 * (Fa2 + Fb2) - 0.5 * s * (b[2] - a[2]);
+  G2[0] = fma(-s, b[0] - a[0], a[1] + b[1]);
+  G2[1] = fma(-s, b[1] - a[1], fma(a[1], ua, pa) + fma(b[1], ub, pb));
+  G2[2] = fma(-s, b[2] - a[2], fma(a[2] + pa, ua, (b[2] + pb) * ub));
 }
 
 __device__ __forceinline__ long long wrap_cell(long long i, long long n) {

@@ -766,24 +766,25 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
     const long long cl = wrap_cell(c0 + f - 1, io.ncells), cr = wrap_cell(c0 + f, io.ncells);
     const double* ta = io.trace + cl * stride + l0 * kM;          // qR of the left cell
     const double* tb = io.trace + cr * stride + n * kM + l0 * kM; // qL of the right cell
-    double a[kM], b[kM], G[kM];
+    double a[kM], b[kM], G2[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
       a[r] = ta[r];
       b[r] = tb[r];
     }
-    rusanov(a, b, G, P.gamma, P.gm1);
-    const double wl = sh.w[l0] * lam;
+    rusanov2(a, b, G2, P.gamma, P.gm1);
 #pragma unroll
-    for (int r = 0; r < kM; ++r) sh.G[(f * n + l0) * kM + r] = wl * G[r];
+    for (int r = 0; r < kM; ++r) sh.G[(f * n + l0) * kM + r] = G2[r];
   }
   __syncthreads();
+  // G^ = (dt/dx) sum_l0 w_l0 G(l0) = (dt/dx / 2) sum_l0 w_l0 (2 G(l0))
+  const double hlam = 0.5 * lam;
   for (int item = tid; item < (nvalid + 1) * kM; item += THREADS) {
     const int f = item / kM, r = item - f * kM;
     double s = 0.0;
 #pragma unroll
-    for (int l0 = 0; l0 < n; ++l0) s += sh.G[(f * n + l0) * kM + r];
-    sh.Gs[f * kM + r] = s;
+    for (int l0 = 0; l0 < n; ++l0) s = fma(sh.w[l0], sh.G[(f * n + l0) * kM + r], s);
+    sh.Gs[f * kM + r] = hlam * s;
   }
   __syncthreads();
   if (P.dg) {
@@ -798,7 +799,7 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
         const double un = fma(-t, sh.rw[k], up[r]);
         out[r] = un;
         sh.u[(lc * n + k) * kM + r] = un;
-        sh.uf[(lc * n + k) * kM + r] = (float)un;
+        sh.uf[(lc * n + k) * kM + r] = d2f_trunc(un);
       }
     }
   } else {
@@ -808,7 +809,7 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
       const double vn = io.v_old[cell * kM + r] - (sh.Gs[(lc + 1) * kM + r] - sh.Gs[lc * kM + r]);
       io.u_new[cell * kM + r] = vn;
       sh.u[lc * kM + r] = vn;
-      sh.uf[lc * kM + r] = (float)vn;
+      sh.uf[lc * kM + r] = d2f_trunc(vn);
     }
   }
   if (P.want_lambda) {

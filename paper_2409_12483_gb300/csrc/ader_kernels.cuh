@@ -40,7 +40,8 @@ struct PredCfg {
   static constexpr int n = N + 1;
   static constexpr int CPB = CPB_;
   static constexpr int THREADS = CPB * n;
-  static constexpr size_t kSmemBytes = (size_t)CPB * kM * n * (n + 1) * sizeof(double);
+  // exchange rows [CPB][n][n][3], fbar [CPB][n][3], initial data [CPB][n][3]
+  static constexpr size_t kSmemBytes = (size_t)CPB * kM * n * (n + 2) * sizeof(double);
   static constexpr bool kValid = (THREADS % 32 == 0) && THREADS <= 512 && (N <= 5 || CPB <= 32);
 };
 constexpr int kMaxCpb = 64;
@@ -118,6 +119,37 @@ __device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
   }
 }
 
+// Read access to a cell's initial data u[k][r] for the Picard loop: from the
+// thread's registers (RegRows) or from the tile's shared-memory copy (SmemRows,
+// which keeps 3n doubles per thread out of the register file).  at(k, r) is used
+// with compile-time k; node(p0, r) with the thread's own (run-time) node.
+template <int N, typename T>
+struct RegRows {
+  const T (&a)[N + 1][kM];
+  __device__ __forceinline__ T at(int k, int r) const { return a[k][r]; }
+  __device__ __forceinline__ T node(int p0, int r) const {
+    T v = a[0][r];
+#pragma unroll
+    for (int k = 1; k <= N; ++k)
+      if (k == p0) v = a[k][r];
+    return v;
+  }
+};
+template <typename T>
+struct SmemRows {
+  const T* p;  // [n][3]
+  __device__ __forceinline__ T at(int k, int r) const { return p[k * kM + r]; }
+  __device__ __forceinline__ T node(int p0, int r) const { return p[p0 * kM + r]; }
+};
+struct SmemRowsFF {
+  const float2* p;  // [n][3] (hi, lo)
+  __device__ __forceinline__ ff at(int k, int r) const {
+    const float2 v = p[k * kM + r];
+    return ff{v.x, v.y};
+  }
+  __device__ __forceinline__ ff node(int p0, int r) const { return at(p0, r); }
+};
+
 // Picard iteration of one block of cells in precision T.  q: the thread's tau row
 // (in: initial iterate, out: result); uh: the cell's initial data; kr: the thread's
 // row of kappa~ scaled by dt/dx; kt: k~ (n x n).  Returns the number of
@@ -126,8 +158,8 @@ __device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
 // are the same in every row, so iteration 1 is done once per cell: thread p0
 // evaluates the flux at node p0 only, forms row p0 of g = k~ f(u), and
 // q'[p0] = u - (dt/dx) (sum_q0 kappa~[p0][q0]) g, using kappa~ 1 = tau.
-template <int N, typename T, int CPB = 32>
-__device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 1][kM],
+template <int N, typename T, int CPB = 32, typename UA>
+__device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const UA& uh,
                                            const T (&kr)[N + 1], const T (&kt)[kMaxN][kMaxN],
                                            const T (&ka)[kMaxH][kMaxH],
                                            const T (&kb)[kMaxH][kMaxH], T* sg, unsigned long long (*s_red)[kMaxCpb][2], int lc,
@@ -157,12 +189,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
         // u at node p0 (selected without a runtime register index)
         T up[kM], F[kM];
 #pragma unroll
-        for (int r = 0; r < kM; ++r) up[r] = uh[0][r];
-#pragma unroll
-        for (int k = 1; k < n; ++k)
-          if (k == p0)
-#pragma unroll
-            for (int r = 0; r < kM; ++r) up[r] = uh[k][r];
+        for (int r = 0; r < kM; ++r) up[r] = uh.node(p0, r);
         euler_flux<T>(up, F, gm1);
 #pragma unroll
         for (int r = 0; r < kM; ++r) fcell[p0 * kM + r] = F[r];
@@ -186,7 +213,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           const T g = gcell[p1 * kM + r];
-          qn[p1][r] = fma(-krow, g, uh[p1][r]);
+          qn[p1][r] = fma(-krow, g, uh.at(p1, r));
           const unsigned long long gb = abs_bits<T>(g);
           gmax = gb > gmax ? gb : gmax;
         }
@@ -219,7 +246,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
-          T acc = uh[p1][r];
+          T acc = uh.at(p1, r);
 #pragma unroll
           for (int q0 = 0; q0 < n; ++q0) acc = fma(-kr[q0], cell_g[(q0 * n + p1) * kM + r], acc);
           qn[p1][r] = acc;
@@ -269,7 +296,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const T (&uh)[N + 
 // iteration from q = u.  q, uh, kr, krow are ff; k~ comes from the (kt, ktlo)
 // float tables; the convergence test compares |q' - q| with tol max(1, |q'|).
 template <int N, int CPB = 32>
-__device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const ff (&uh)[N + 1][kM],
+__device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRowsFF& uh,
                                               const ff (&kr)[N + 1], const OpsF& of, double* sgd,
                                               unsigned long long (*s_red)[kMaxCpb][2], int lc,
                                               int p0, bool valid, int cap, bool fixed, float tol,
@@ -294,12 +321,7 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const ff (&uh)
       {
         ff up[kM], F[kM];
 #pragma unroll
-        for (int r = 0; r < kM; ++r) up[r] = uh[0][r];
-#pragma unroll
-        for (int k = 1; k < n; ++k)
-          if (k == p0)
-#pragma unroll
-            for (int r = 0; r < kM; ++r) up[r] = uh[k][r];
+        for (int r = 0; r < kM; ++r) up[r] = uh.node(p0, r);
         euler_flux_ff(up, F, gm1);
 #pragma unroll
         for (int r = 0; r < kM; ++r) fcell[p0 * kM + r] = make_float2(F[r].hi, F[r].lo);
@@ -331,7 +353,7 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const ff (&uh)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           ff_acc a;
-          a.set(uh[p1][r]);
+          a.set(uh.at(p1, r));
           const float2 g = gcell[p1 * kM + r];
           a.fma_add(nk, ff{g.x, g.y});
           qn[p1][r] = a.get();
@@ -359,7 +381,7 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const ff (&uh)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           ff_acc acc;
-          acc.set(uh[p1][r]);
+          acc.set(uh.at(p1, r));
 #pragma unroll
           for (int q0 = 0; q0 < n; ++q0) {
             const float2 g = cell_g[(q0 * n + p1) * kM + r];
@@ -507,6 +529,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   constexpr int n = N + 1, THREADS = PredCfg<N, CPB>::THREADS;
   double* sg = smem;                        // [CPB][n][n][3]
   double* sfb = smem + CPB * n * n * kM;    // [CPB][n][3]
+  double* su = sfb + CPB * n * kM;          // [CPB][n][3] initial data of the tile's cells
   unsigned long long(*s_red)[kMaxCpb][2] = sh.red;
 
   const int tid = threadIdx.x;
@@ -521,17 +544,24 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     sh.bad = 0;
   }
 
-  // initial data of the cell (every thread of the cell reads the same 3n values)
-  double uh[n][kM], u_own[kM];  // u_own: this thread's node p0 (runtime index)
+  // initial data: each thread loads its own node p0 and stores it in the tile's
+  // shared copy, from which every thread of the cell reads the 3n values
+  double u_own[kM];
   {
     const double* src = io.u + (valid ? cell : 0) * (long long)(n * kM);
 #pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int r = 0; r < kM; ++r) uh[k][r] = src[k * kM + r];
-#pragma unroll
-    for (int r = 0; r < kM; ++r) u_own[r] = src[p0 * kM + r];
+    for (int r = 0; r < kM; ++r) {
+      u_own[r] = src[p0 * kM + r];
+      if constexpr (PREC == 2) {  // the float-float form keeps a (hi, lo) copy
+        const ff v = d2ff(u_own[r]);
+        reinterpret_cast<float2*>(su)[(lc * n + p0) * kM + r] = make_float2(v.hi, v.lo);
+      } else {
+        su[(lc * n + p0) * kM + r] = u_own[r];
+      }
+    }
   }
+  __syncthreads();
+  const SmemRows<double> uh{su + lc * n * kM};
   double q[n][kM];
   int iters = 0;
   bool conv = true;
@@ -545,14 +575,12 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
       for (int r = 0; r < kM; ++r) q[p1][r] = src[p1 * kM + r];
     __syncthreads();
   } else if constexpr (PREC == 2) {
-    ff qf[n][kM], uf[n][kM], krf[n];
+    const SmemRowsFF uf{reinterpret_cast<const float2*>(su) + lc * n * kM};
+    ff qf[n][kM], krf[n];
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        uf[k][r] = d2ff(uh[k][r]);
-        qf[k][r] = uf[k][r];
-      }
+      for (int r = 0; r < kM; ++r) qf[k][r] = uf.at(k, r);
     const ff lamf = d2ff(lam);
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) krf[q0] = ff_mul(lamf, ff{P.opf.kap[p0][q0], P.opf.kaplo[p0][q0]});
@@ -578,14 +606,14 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
-        uf[k][r] = (float)uh[k][r];
+        uf[k][r] = (float)uh.at(k, r);
         qf[k][r] = uf[k][r];
       }
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) krf[q0] = (float)(lam * P.ops.kap[p0][q0]);
     bool conv32;
     const int cap32 = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop<N, float, CPB>(qf, uf, krf, P.opf.kt, P.opf.ksa, P.opf.ksb,
+    iters = picard_loop<N, float, CPB>(qf, RegRows<N, float>{uf}, krf, P.opf.kt, P.opf.ksa, P.opf.ksb,
                                        reinterpret_cast<float*>(sg), s_red, lc,
                                   p0, valid, cap32, P.fixed_iter > 0, P.tol32, (float)P.gm1,
                                   &conv32, true, (float)(lam * P.ops.kaprow[p0]));
@@ -606,7 +634,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int r = 0; r < kM; ++r) q[k][r] = uh[k][r];
+      for (int r = 0; r < kM; ++r) q[k][r] = uh.at(k, r);
     double kr[n];
 #pragma unroll
     for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];

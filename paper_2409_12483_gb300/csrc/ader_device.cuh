@@ -57,6 +57,15 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 __device__ __forceinline__ double bitsd(unsigned long long b) {
   return __longlong_as_double(static_cast<long long>(b));
 }
+// Maximum of two bit patterns (of non-negative doubles: the same order as the
+// values) in a PTX integer instruction.  Written in C++ as a compare and select
+// of masked patterns, the compiler recognises absolute values of doubles and
+// emits FP64 additions, extra FP64-pipe instructions in the hot loops.
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("max.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 // Predictor side of the time-step protocol.  Every thread evaluates the same
 // expression from the same inputs, so the decision is uniform; `lead` (one
@@ -135,10 +144,16 @@ __device__ __forceinline__ void corrector_finish(const StepParams& sp, double dt
 // Floating-Point Arithmetic): 3 FP64 FMAs.  The float seed's relative error is
 // ~2^-22, so the truncated series leaves ~2^-66 before the final rounding.
 // Outside 2^-125 <= |x| < 2^126 (also 0, inf, NaN) it returns 1.0 / x.
+// Out-of-range inputs take CUDA's operations through a call, so that the
+// compiler cannot if-convert them into the fast path (predicated-off FP64
+// instructions still occupy FP64 issue slots).
+static __device__ __noinline__ double rcp64_slow(double x) { return 1.0 / x; }
+static __device__ __noinline__ double sqrt64_slow(double x) { return sqrt(x); }
+
 __device__ __forceinline__ double rcp64(double x) {
   const int hi = __double2hiint(x);
   const int ex = (hi >> 20) & 0x7ff;
-  if (ex < 898 || ex > 1148) return 1.0 / x;
+  if (ex < 898 || ex > 1148) return rcp64_slow(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const float xf = __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(ex - 896) << 23) |
                                    (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29));
@@ -161,7 +176,7 @@ __device__ __forceinline__ double rcp64(double x) {
 __device__ __forceinline__ double sqrt64(double x) {
   const int hi = __double2hiint(x);
   const int ex = (hi >> 20) & 0x7ff;
-  if (hi < 0 || ex < 898 || ex > 1148) return sqrt(x);
+  if (hi < 0 || ex < 898 || ex > 1148) return sqrt64_slow(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const float xf = __uint_as_float(((unsigned)(ex - 896) << 23) | (((unsigned)hi & 0xfffffu) << 3) |
                                    (lo >> 29));
@@ -245,7 +260,7 @@ __device__ __forceinline__ void rusanov2(const double* a, const double* b, doubl
   const double pb = gm1 * fma(neg_half(b[1]), ub, b[2]);
   const double sa = fabs(ua) + sqrt64(gamma * pa * ia);
   const double sb = fabs(ub) + sqrt64(gamma * pb * ib);
-  const double s = fmax(sa, sb);
+  const double s = bitsd(umax64(dbits(sa), dbits(sb)));  // both non-negative
   G2[0] = fma(-s, b[0] - a[0], a[1] + b[1]);
   G2[1] = fma(-s, b[1] - a[1], fma(a[1], ua, pa) + fma(b[1], ub, pb));
   G2[2] = fma(-s, b[2] - a[2], fma(a[2] + pa, ua, (b[2] + pb) * ub));

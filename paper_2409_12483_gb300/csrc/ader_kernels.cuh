@@ -46,15 +46,21 @@ struct PredCfg {
 };
 constexpr int kMaxCpb = 64;
 
+// |x| as an ordered bit pattern (sign bit cleared), in a PTX integer
+// instruction (see umax64: in C++ the compiler turns the mask into FP64 work).
 template <typename T>
 __device__ __forceinline__ unsigned long long abs_bits(T x);
 template <>
 __device__ __forceinline__ unsigned long long abs_bits<double>(double x) {
-  return dbits(fabs(x));
+  unsigned long long r;
+  asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(r) : "l"(__double_as_longlong(x)));
+  return r;
 }
 template <>
 __device__ __forceinline__ unsigned long long abs_bits<float>(float x) {
-  return static_cast<unsigned long long>(__float_as_uint(fabsf(x)));
+  unsigned r;
+  asm("and.b32 %0, %1, 0x7fffffff;" : "=r"(r) : "r"(__float_as_uint(x)));
+  return static_cast<unsigned long long>(r);
 }
 template <typename T>
 __device__ __forceinline__ T from_bits(unsigned long long b);
@@ -214,8 +220,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const UA& uh,
         for (int r = 0; r < kM; ++r) {
           const T g = gcell[p1 * kM + r];
           qn[p1][r] = fma(-krow, g, uh.at(p1, r));
-          const unsigned long long gb = abs_bits<T>(g);
-          gmax = gb > gmax ? gb : gmax;
+          gmax = umax64(gmax, abs_bits<T>(g));
         }
       // q' - q = -(dt/dx) tau_p0 g in this iteration: its largest magnitude is
       // (dt/dx) tau_p0 max|g| (up to the rounding of q'), one multiplication
@@ -226,8 +231,7 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const UA& uh,
         for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
           for (int r = 0; r < kM; ++r) {
-            const unsigned long long m = abs_bits<T>(qn[p1][r]);
-            qmax = m > qmax ? m : qmax;
+            qmax = umax64(qmax, abs_bits<T>(qn[p1][r]));
           }
         atomicMax(&s_red[it & 1][lc][0], abs_bits<T>(krow * from_bits<T>(gmax)));
         atomicMax(&s_red[it & 1][lc][1], qmax);
@@ -258,10 +262,8 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const UA& uh,
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
-          const unsigned long long d = abs_bits<T>(qn[p1][r] - q[p1][r]);
-          const unsigned long long m = abs_bits<T>(qn[p1][r]);
-          dmax = d > dmax ? d : dmax;
-          qmax = m > qmax ? m : qmax;
+          dmax = umax64(dmax, abs_bits<T>(qn[p1][r] - q[p1][r]));
+          qmax = umax64(qmax, abs_bits<T>(qn[p1][r]));
         }
       atomicMax(&s_red[it & 1][lc][0], dmax);
       atomicMax(&s_red[it & 1][lc][1], qmax);
@@ -397,10 +399,8 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           const float d = (qn[p1][r].hi - q[p1][r].hi) + (qn[p1][r].lo - q[p1][r].lo);
-          const unsigned long long db = abs_bits<float>(d);
-          const unsigned long long mb = abs_bits<float>(qn[p1][r].hi);
-          dmax = db > dmax ? db : dmax;
-          qmax = mb > qmax ? mb : qmax;
+          dmax = umax64(dmax, abs_bits<float>(d));
+          qmax = umax64(qmax, abs_bits<float>(qn[p1][r].hi));
         }
       atomicMax(&s_red[it & 1][lc][0], dmax);
       atomicMax(&s_red[it & 1][lc][1], qmax);

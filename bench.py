@@ -280,6 +280,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving benchmark (scaled Poisson stream)")
     ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the coarse-mesh convergence sweeps of the four precision forms")
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5")
@@ -408,6 +410,8 @@ def main():
             line["variants"] = run_variants(args, dev, flush)
         if not args.no_serving:
             line["serving"] = run_serving(dev, args.serving_requests)
+        if not args.no_convergence:
+            line["convergence"] = run_convergence(dev)
         line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
@@ -423,6 +427,46 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def run_convergence(dev):
+    """Convergence sweeps on coarse meshes to t_end = 1, where the discretisation
+    error is above FP32 round-off: the L1 density error against the exact advected
+    solution of the FP64, FP32-predictor (1 and 2 FP64 sweeps) and float-float
+    forms, each form's ratio to FP64, and the FP64 order between meshes.  N = 2 on
+    the sine wave (rho = 1 + 0.2 sin 2 pi x), N = 5 on the four-mode data."""
+    import math
+
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    forms = {"fp64": dict(precision="fp64"),
+             "fp32_1sweep": dict(precision="fp32", fp64_sweeps=1),
+             "fp32_2sweeps": dict(precision="fp32", fp64_sweeps=2),
+             "ff": dict(precision="ff")}
+    out = []
+    for N, data, field, meshes in ((2, "sine", W.sine(), (50, 100, 200, 400)),
+                                   (5, "modes4", W.modes4(SEED), (20, 40, 80, 160))):
+        rows = []
+        for nc in meshes:
+            row = {"cells": nc, "l1": {}}
+            for name, kw in forms.items():
+                ctx = Context(nc, N, "dg", device=dev, **kw)
+                u = torch.tensor(W.nodal_state(field, ctx.node_coords()), device=dev).reshape(-1)
+                steps, t, _ = ctx.ader_solve(u, t_end=1.0)
+                torch.cuda.synchronize()
+                row["l1"][name] = dg_l1_error(ctx, u.cpu().numpy(), field, t)
+                row["steps"] = steps
+                del ctx
+            row["ratio_to_fp64"] = {k: v / row["l1"]["fp64"] for k, v in row["l1"].items() if k != "fp64"}
+            rows.append(row)
+        orders = [math.log(a["l1"]["fp64"] / b["l1"]["fp64"]) / math.log(b["cells"] / a["cells"])
+                  for a, b in zip(rows, rows[1:])]
+        out.append({"degree": N, "data": data, "t_end": 1.0, "meshes": rows, "order_fp64": orders,
+                    "within_2x_of_fp64": {k: all(r["ratio_to_fp64"][k] <= 2.0 for r in rows)
+                                          for k in forms if k != "fp64"}})
+    return out
 
 
 def run_variants(args, dev, flush):

@@ -67,9 +67,10 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
   return r;
 }
 
-// Predictor side of the time-step protocol.  Every thread evaluates the same
-// expression from the same inputs, so the decision is uniform; `lead` (one
-// thread of the solve's first tile) publishes it.
+// Predictor side of the time-step protocol.  One thread per block evaluates it
+// and shares the result with its block; every block evaluates the same expression
+// from the same inputs, so the decision is uniform; `lead` (the evaluating thread
+// of the solve's first tile) publishes it.
 __device__ __forceinline__ bool predictor_step_dt(const StepParams& sp, double* dt_out, bool lead) {
   if (sp.mode == kDtFixed) {
     *dt_out = sp.dt_fixed;

@@ -446,7 +446,28 @@ struct PredShared {
   unsigned long long red[2][kMaxCpb][2];
   int itmax, ncells, bad;
   unsigned long long itsum;
+  double dt;
+  int go;
+  double kr[kMaxN][kMaxN];  // (dt/dx) kappa~ of the current tile's time step
+  double krow[kMaxN];       // (dt/dx) tau (row sums of kappa~)
 };
+
+// The predictor's time-step decision (a division and the clipping to t_end) made
+// once per block by thread 0 and shared, instead of by every thread.
+template <int N>
+__device__ __forceinline__ bool block_step_dt(const StepParams& sp, double* dt, bool lead_block,
+                                              PredShared<N>& sh) {
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    sh.go = predictor_step_dt(sp, &d, lead_block) ? 1 : 0;
+    sh.dt = d;
+  }
+  __syncthreads();
+  const bool go = sh.go != 0;
+  *dt = sh.dt;
+  __syncthreads();  // the slots are written again for the next tile
+  return go;
+}
 
 // Epilogue of the float-float form: the traces at xi = 0 and 1, the space-time
 // average of the flux and the volume term (Sec. 1.2) evaluated in float-float
@@ -537,6 +558,10 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   const long long cell = tile * CPB + lc;
   const bool valid = cell < io.ncells;
   for (int i = tid; i < 2 * kMaxCpb * 2; i += THREADS) (&s_red[0][0][0])[i] = 0ull;
+  if constexpr (PREC != 2) {  // (dt/dx) kappa~ once per block (made visible by the barrier below)
+    if (tid < n * n) sh.kr[tid / n][tid % n] = lam * P.ops.kap[tid / n][tid % n];
+    if (tid < n) sh.krow[tid] = lam * P.ops.kaprow[tid];
+  }
   if (tid == 0) {
     sh.itmax = 0;
     sh.itsum = 0ull;
@@ -623,7 +648,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
       for (int r = 0; r < kM; ++r) q[k][r] = (double)qf[k][r];
     double kr[n];
 #pragma unroll
-    for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
+    for (int q0 = 0; q0 < n; ++q0) kr[q0] = sh.kr[p0][q0];
     bool dummy;
     iters += picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, P.ops.ksa, P.ops.ksb, sg, s_red, lc,
                                          p0, valid, P.sweeps, true,
@@ -637,12 +662,11 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
       for (int r = 0; r < kM; ++r) q[k][r] = uh.at(k, r);
     double kr[n];
 #pragma unroll
-    for (int q0 = 0; q0 < n; ++q0) kr[q0] = lam * P.ops.kap[p0][q0];
+    for (int q0 = 0; q0 < n; ++q0) kr[q0] = sh.kr[p0][q0];
     const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
     iters = picard_loop<N, double, CPB>(q, uh, kr, P.ops.kt, P.ops.ksa, P.ops.ksb, sg, s_red, lc,
                                         p0, valid, cap,
-                                   P.fixed_iter > 0, P.tol, P.gm1, &conv, true,
-                                   lam * P.ops.kaprow[p0]);
+                                   P.fixed_iter > 0, P.tol, P.gm1, &conv, true, sh.krow[p0]);
   }
 
   if (epilogue_done) {
@@ -722,7 +746,7 @@ __global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
   extern __shared__ __align__(16) double smem[];
   __shared__ PredShared<N> sh;
   double dt;
-  if (!predictor_step_dt(P.sp, &dt, blockIdx.x == 0 && threadIdx.x == 0)) return;  // uniform
+  if (!block_step_dt<N>(P.sp, &dt, blockIdx.x == 0, sh)) return;  // uniform
   const TileIO io{P.u, P.trace, P.q_out, P.q_in, P.ncells, P.sp.ctl};
   predict_tile<N, PREC, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
 }
@@ -741,7 +765,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
     StepParams sp = d.sp;
     sp.par = par;
     double dt;
-    if (!predictor_step_dt(sp, &dt, item.tile == 0 && threadIdx.x == 0)) continue;  // uniform
+    if (!block_step_dt<N>(sp, &dt, item.tile == 0, sh)) continue;  // uniform
     const TileIO io{d.u[par], d.trace, nullptr, nullptr, d.ncells, sp.ctl};
     predict_tile<N, PREC>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
   }

@@ -122,8 +122,11 @@ ader_status ader_node_coords(const ader_ctx* ctx, double* x_host, int64_t count)
  * "ksa","ksb" (H^2, H = (N+2)/2: k~ in even/odd form, used by the predictor for
  * N >= 4; with h = (N+1)/2, ksa[p][q] = (k~[p][q] + k~[p][N-q])/2 for p, q < h and
  * ksa[p][h] = k~[p][h] for odd N+1; ksb[p][q] = (k~[p][q] - k~[p][N-q])/2 for
- * p < H, q < h; other entries 0).  count must equal the table's size; a wrong
- * count or an unknown name returns ADER_ERR_ARG. */
+ * p < H, q < h; other entries 0); WENO contexts only: "wamono" (3 (N+1)^2:
+ * [S][j][k], the coefficient a_j of stencil S's polynomial in t = 2 xi - 1 from
+ * its k-th cell average, S = central, left, right), "wvnod" ((N+1)^2: [q][j] =
+ * t_q^j, nodal values from monomial coefficients).  count must equal the
+ * table's size; a wrong count or an unknown name returns ADER_ERR_ARG. */
 ader_status ader_get_table(const ader_ctx* ctx, const char* name, double* out_host, int64_t count);
 
 /* Bind caller-owned device scratch (>= ader_workspace_bytes, 256-byte aligned)

@@ -250,7 +250,7 @@ class Context:
         n = self.n
         H = (n + 1) // 2
         size = {"xi": n, "w": n, "psi0": n, "psi1": n, "P": (2 * self.degree + 1) * n,
-                "ksa": H * H, "ksb": H * H}.get(name, n * n)
+                "ksa": H * H, "ksb": H * H, "wamono": 3 * n * n}.get(name, n * n)
         out = np.zeros(size)
         self._check(self._L.ader_get_table(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
                                            size))

@@ -386,6 +386,17 @@ ader_status ader_get_table(const ader_ctx* c, const char* name, double* out, int
   };
   if (!strcmp(name, "ksa")) return half(d.ksa);
   if (!strcmp(name, "ksb")) return half(d.ksb);
+  if (c->scheme == ADER_SCHEME_WENO_FV) {
+    const WenoOps& wo = c->basis.weno;
+    if (!strcmp(name, "wvnod")) return mat(wo.vnod, n);
+    if (!strcmp(name, "wamono")) {
+      if (count != (int64_t)3 * n * n) return ADER_ERR_ARG;
+      for (int S = 0; S < 3; ++S)
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k) out[(S * n + j) * n + k] = wo.amono[S][j][k];
+      return ADER_OK;
+    }
+  }
   return ADER_ERR_ARG;
 }
 

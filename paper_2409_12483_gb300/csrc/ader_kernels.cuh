@@ -1018,64 +1018,99 @@ __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflPar
   if (bad) atomicOr(&P.ctl->status, kStNonPhysical);
 }
 
+// Normalised WENO weights when the product form below would overflow (a
+// smoothness indicator above ~1e37): lambda_S / x8_S, divided by their sum.
+struct Weights3 {
+  double w0, w1, w2;
+};
+static __device__ __noinline__ Weights3 weno_weights_slow(double l0, double l1, double l2, double x0,
+                                                          double x1, double x2) {
+  const double t0 = l0 / x0, t1 = l1 / x1, t2 = l2 / x2;
+  const double ws = t0 + t1 + t2;
+  return Weights3{t0 / ws, t1 / ws, t2 / ws};
+}
+
+// One thread per cell and conserved variable loop.  Each candidate polynomial
+// is formed in monomial coefficients a_j (t = 2 xi - 1) directly from its N+1
+// cell averages (amono = mono * ainv, built in long double); sigma uses only
+// the non-zero entries of smono (j + l even); the normalised weights
+// (lambda_S / x8_S) / sum_T (lambda_T / x8_T), x8 = (sigma + eps)^8, are formed
+// as lambda_S prod_{T != S} x8_T / sum_T lambda_T prod_{U != T} x8_U with one
+// reciprocal; the nodal values come from the weighted monomial coefficients.
 template <int N>
 __global__ void __launch_bounds__(128) weno_kernel(const __grid_constant__ WenoParams P) {
   constexpr int n = N + 1;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.ncells) return;
   const long long nc = P.ncells;
+  const bool small = nc < 2 * N + 1;  // the stencil may wrap more than once
 #pragma unroll 1
   for (int r = 0; r < kM; ++r) {
     double vs[2 * N + 1];
 #pragma unroll
     for (int s = -N; s <= N; ++s) {
-      long long j = (i + s) % nc;
-      if (j < 0) j += nc;
+      long long j = i + s;
+      if (small) {
+        j %= nc;
+        if (j < 0) j += nc;
+      } else {
+        j = wrap_cell(j, nc);
+      }
       vs[s + N] = P.v[j * kM + r];
     }
-    double c[3][n], wt[3], wsum = 0.0;
+    double a[3][n], x8[3];
 #pragma unroll
     for (int S = 0; S < 3; ++S) {
-      const int base = P.wo.shift[S] + N;
+      // stencil starts (central, left, right) as in WenoOps::shift, at compile
+      // time so that vs stays in registers
+      const int base = (S == 0 ? -N / 2 : (S == 1 ? -N : 0)) + N;
 #pragma unroll
-      for (int k = 0; k < n; ++k) {
+      for (int j = 0; j < n; ++j) {
         double acc = 0.0;
 #pragma unroll
-        for (int j = 0; j < n; ++j) acc = fma(P.wo.ainv[S][k][j], vs[base + j], acc);
-        c[S][k] = acc;
-      }
-      // smoothness from the monomial coefficients a_1..a_N of the stencil polynomial
-      double a[n];
-#pragma unroll
-      for (int j = 1; j < n; ++j) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < n; ++k) acc = fma(P.wo.mono[j][k], c[S][k], acc);
-        a[j] = acc;
+        for (int k = 0; k < n; ++k) acc = fma(P.wo.amono[S][j][k], vs[base + k], acc);
+        a[S][j] = acc;
       }
       double sigma = 0.0;
 #pragma unroll
       for (int j = 1; j < n; ++j) {
         double row = 0.0;
 #pragma unroll
-        for (int l = 1; l < n; ++l) row = fma(P.wo.smono[j][l], a[l], row);
-        sigma = fma(a[j], row, sigma);
+        for (int l = 1; l < n; ++l)
+          if (((j + l) & 1) == 0) row = fma(P.wo.smono[j][l], a[S][l], row);
+        sigma = fma(a[S][j], row, sigma);
       }
       const double x = sigma + P.wo.eps;
-      const double x2 = x * x, x4 = x2 * x2, x8 = x4 * x4;
-      wt[S] = P.wo.lin[S] / x8;
-      wsum += wt[S];
+      const double x2 = x * x, x4 = x2 * x2;
+      x8[S] = x4 * x4;
     }
     double om[3];
+    {
+      const double p12 = x8[1] * x8[2], p02 = x8[0] * x8[2], p01 = x8[0] * x8[1];
+      const double n0 = P.wo.lin[0] * p12, n1 = P.wo.lin[1] * p02, n2 = P.wo.lin[2] * p01;
+      const double d = n0 + n1 + n2;
+      if (d < 1.0e300) {
+        const double rd = rcp64(d);
+        om[0] = n0 * rd;
+        om[1] = n1 * rd;
+        om[2] = n2 * rd;
+      } else {
+        const Weights3 w = weno_weights_slow(P.wo.lin[0], P.wo.lin[1], P.wo.lin[2], x8[0], x8[1], x8[2]);
+        om[0] = w.w0;
+        om[1] = w.w1;
+        om[2] = w.w2;
+      }
+    }
+    double ah[n];
 #pragma unroll
-    for (int S = 0; S < 3; ++S) om[S] = wt[S] / wsum;
+    for (int j = 0; j < n; ++j) ah[j] = fma(om[0], a[0][j], fma(om[1], a[1][j], om[2] * a[2][j]));
     double* out = P.w + i * (n * kM) + r;
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
+    for (int q = 0; q < n; ++q) {
       double acc = 0.0;
 #pragma unroll
-      for (int S = 0; S < 3; ++S) acc = fma(om[S], c[S][k], acc);
-      out[k * kM] = acc;
+      for (int j = 0; j < n; ++j) acc = fma(P.wo.vnod[q][j], ah[j], acc);
+      out[q * kM] = acc;
     }
   }
 }

@@ -250,6 +250,23 @@ int build_basis(int N, bool weno, Basis* out) {
     wo.lin[1] = 1.0;
     wo.lin[2] = 1.0;
     wo.eps = 1.0e-14;
+    // monomial coefficients in t = 2 xi - 1: solve Vandermonde V a = c, V_qj = t_q^j
+    ld Mono[kMaxN][kMaxN];
+    {
+      ld V[kMaxN][kMaxN];
+      for (int q = 0; q < n; ++q) {
+        ld tq = 2 * xi[q] - 1, p = 1;
+        for (int j = 0; j < n; ++j) {
+          V[q][j] = p;
+          wo.vnod[q][j] = (double)p;
+          p *= tq;
+          Mono[q][j] = (q == j);
+        }
+      }
+      if (lu_solve(n, V, Mono, n)) return -5;
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) wo.mono[j][k] = (double)Mono[j][k];
+    }
     for (int S = 0; S < 3; ++S) {
       ld A[kMaxN][kMaxN], I[kMaxN][kMaxN];
       for (int j = 0; j < n; ++j)
@@ -265,21 +282,13 @@ int build_basis(int N, bool weno, Basis* out) {
         }
       if (lu_solve(n, A, I, n)) return -4;
       for (int j = 0; j < n; ++j)
-        for (int k = 0; k < n; ++k) wo.ainv[S][j][k] = (double)I[j][k];
+        for (int k = 0; k < n; ++k) {
+          wo.ainv[S][j][k] = (double)I[j][k];
+          ld a = 0;  // mono * ainv[S] in long double
+          for (int m = 0; m < n; ++m) a += Mono[j][m] * I[m][k];
+          wo.amono[S][j][k] = (double)a;
+        }
     }
-    // monomial coefficients in t = 2 xi - 1: solve Vandermonde V a = c, V_qj = t_q^j
-    ld V[kMaxN][kMaxN], I[kMaxN][kMaxN];
-    for (int q = 0; q < n; ++q) {
-      ld tq = 2 * xi[q] - 1, p = 1;
-      for (int j = 0; j < n; ++j) {
-        V[q][j] = p;
-        p *= tq;
-        I[q][j] = (q == j);
-      }
-    }
-    if (lu_solve(n, V, I, n)) return -5;
-    for (int j = 0; j < n; ++j)
-      for (int k = 0; k < n; ++k) wo.mono[j][k] = (double)I[j][k];
     // sigma = sum_{a=1..N} int_0^1 (d^a p / d xi^a)^2 d xi, p = sum_j a_j t^j:
     // d^a t^j / d xi^a = 2^a j!/(j-a)! t^(j-a);  int_0^1 d xi = 1/2 int_{-1}^{1} dt
     for (int j = 1; j < n; ++j)

@@ -59,7 +59,9 @@ struct WenoOps {
   double eps;                     // epsilon of (sigma + eps)^r, r = 8
   double ainv[3][kMaxN][kMaxN];   // nodal values in cell i = ainv[S] * stencil averages
   double mono[kMaxN][kMaxN];      // monomial coefficients in t = 2 xi - 1: a_j = sum_k mono[j][k] c_k
-  double smono[kMaxN][kMaxN];     // sigma = sum_{j,l >= 1} a_j smono[j][l] a_l
+  double smono[kMaxN][kMaxN];     // sigma = sum_{j,l >= 1} a_j smono[j][l] a_l (0 when j + l is odd)
+  double amono[3][kMaxN][kMaxN];  // a_j of stencil S from its averages: sum_k amono[S][j][k] v_{S,k} (= mono ainv[S])
+  double vnod[kMaxN][kMaxN];      // nodal values from monomial coefficients: c_q = sum_j vnod[q][j] a_j, t_q^j
 };
 
 struct Basis {

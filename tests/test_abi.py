@@ -172,3 +172,37 @@ def test_per_degree_helpers_are_not_merged_across_degrees():
             if l.split()[1:2] and l.split()[1] in ("W", "V", "u")
             and ("ader::" in l) and ("launch" in l or "prepare" in l)]
     assert not weak, weak[:5]
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_weno_monomial_tables_reproduce_polynomials(lib, N):
+    """The WENO kernel's tables, applied as the kernel applies them: from the
+    exact cell averages of a degree-N polynomial, every stencil's monomial
+    coefficients (t = 2 xi - 1 in cell i) are the polynomial's own, and the
+    nodal table gives its values at the GL nodes (reconstruction is exact for
+    polynomials of degree <= N whatever the weights)."""
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(16, 0.0, 1.0)), N, 1, C.byref(default_options()),
+                         C.byref(ctx)) == 0
+    n = N + 1
+
+    def get(name, size):
+        out = np.zeros(size)
+        assert lib.ader_get_table(ctx, name.encode(), out.ctypes.data_as(C.c_void_p), size) == 0
+        return out
+
+    amono = get("wamono", 3 * n * n).reshape(3, n, n)
+    vnod = get("wvnod", n * n).reshape(n, n)
+    xi = get("xi", n)
+    P = np.polynomial.Polynomial
+    for seed in range(3):
+        p = P(np.random.default_rng(seed).standard_normal(n))   # in xi, cell i = [0, 1]
+        Pint = p.integ()
+        avg = {j: Pint(j + 1) - Pint(j) for j in range(-N, N + 1)}
+        a_ref = p(P([0.5, 0.5])).coef                             # xi = (t + 1) / 2
+        for S, shift in enumerate((-N // 2, -N, 0)):
+            a = amono[S] @ np.array([avg[shift + k] for k in range(n)])
+            np.testing.assert_allclose(a, a_ref, rtol=0, atol=1e-11 * np.abs(a_ref).max())
+        np.testing.assert_allclose(vnod @ a_ref, p(xi), rtol=0, atol=1e-13 * np.abs(p(xi)).max())
+    lib.ader_destroy(ctx)

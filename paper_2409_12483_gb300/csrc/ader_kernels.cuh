@@ -785,7 +785,7 @@ struct FaceShared {
   double Gs[(C + 1) * kM];
   double u[C * (N + 1) * kM];
   double P[kMaxNs * (N + 1)];
-  double w[N + 1], psi0[N + 1], psi1[N + 1], rw[N + 1];
+  double w[N + 1], psi0w[N + 1], psi1w[N + 1];  // w, psi_k / w_k, psi~_k / w_k
   float lt[C * kMaxNs];       // FP32 screening value per subcell (CFL)
   float uf[C * (N + 1) * kM];  // FP32 copy of the updated state (one conversion per value)
   float Pf[kMaxNs * (N + 1)];
@@ -847,8 +847,9 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
       double* out = io.u_new + cell * (long long)(n * kM) + k * kM;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
-        const double t = sh.psi1[k] * sh.Gs[(lc + 1) * kM + r] - sh.psi0[k] * sh.Gs[lc * kM + r];
-        const double un = fma(-t, sh.rw[k], up[r]);
+        // u + (D~ fbar)/w (from the predictor) - (psi~_k G_{i+1/2} - psi_k G_{i-1/2}) / w_k
+        const double un =
+            fma(-sh.psi1w[k], sh.Gs[(lc + 1) * kM + r], fma(sh.psi0w[k], sh.Gs[lc * kM + r], up[r]));
         out[r] = un;
         sh.u[(lc * n + k) * kM + r] = un;
         sh.uf[(lc * n + k) * kM + r] = d2f_trunc(un);
@@ -945,9 +946,8 @@ __device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShare
   }
   if (threadIdx.x < n) {
     sh.w[threadIdx.x] = P.ops.w[threadIdx.x];
-    sh.psi0[threadIdx.x] = P.ops.psi0[threadIdx.x];
-    sh.psi1[threadIdx.x] = P.ops.psi1[threadIdx.x];
-    sh.rw[threadIdx.x] = P.ops.rw[threadIdx.x];
+    sh.psi0w[threadIdx.x] = P.ops.psi0[threadIdx.x] * P.ops.rw[threadIdx.x];
+    sh.psi1w[threadIdx.x] = P.ops.psi1[threadIdx.x] * P.ops.rw[threadIdx.x];
   }
   __syncthreads();
 }

@@ -19,10 +19,12 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ader_oracle.c")
+_SRC_RS = os.path.join(_HERE, "ader_oracle_src.c")
 _HDR = os.path.join(_HERE, "ader_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
 
 M = 3
+MRS = 5  # reacting system: rho, m, E, rho c1, rho c2
 MAXN = 10
 MAXNS = 19
 
@@ -34,11 +36,11 @@ OB_ERR_NONPHYSICAL = 5
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -74,6 +76,11 @@ class Weno(C.Structure):
         ("dal", ((C.c_double * MAXN) * MAXN) * MAXN),
         ("wq", C.c_double * MAXN),
     ]
+
+
+class RSParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("omega", C.c_double), ("cfl", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("fixed_iter", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -132,6 +139,24 @@ def lib():
             L.ob_solve.argtypes = [C.c_int, P(Basis), C.c_void_p, P(Params), C.c_int64,
                                    C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
                                    P(C.c_double)]
+            L.ob_rs_flux.argtypes = [C.c_double, _DP, _DP]
+            L.ob_rs_flux.restype = None
+            L.ob_rs_source.argtypes = [C.c_double, _DP, _DP]
+            L.ob_rs_source.restype = None
+            L.ob_rs_rusanov.argtypes = [C.c_double, _DP, _DP, _DP]
+            L.ob_rs_rusanov.restype = None
+            L.ob_rs_predict_cell.argtypes = [P(Basis), P(RSParams), C.c_double, C.c_double, _DP,
+                                             _DP, P(C.c_int), P(C.c_int)]
+            L.ob_rs_predict_cell_direct.argtypes = [P(Basis), P(RSParams), C.c_double, C.c_double,
+                                                    _DP, _DP, P(C.c_int)]
+            L.ob_rs_dg_dt.argtypes = [P(Basis), P(RSParams), C.c_double, C.c_int64, _DP]
+            L.ob_rs_dg_dt.restype = C.c_double
+            L.ob_rs_dg_step.argtypes = [P(Basis), P(RSParams), C.c_int64, C.c_double, C.c_double,
+                                        _DP, _DP, C.c_void_p, P(Stats)]
+            L.ob_rs_dg_step_cells.argtypes = [P(Basis), P(RSParams), C.c_int64, C.c_double,
+                                              C.c_double, _DP, _IP, C.c_int64, _DP]
+            L.ob_rs_solve.argtypes = [P(Basis), P(RSParams), C.c_int64, C.c_double, _DP, C.c_double,
+                                      C.c_int64, C.c_double, P(C.c_int64), P(C.c_double)]
             _lib = L
     return _lib
 
@@ -293,6 +318,131 @@ class Oracle:
         dx = (x1 - x0) / ncells
         xi = self.table("xi")
         return x0 + dx * (np.arange(ncells)[:, None] + xi[None, :])
+
+
+class ReactingOracle:
+    """ADER-DG for the 1D two-component reacting flow (Sec. 2, eq. pdes_2_comps in
+    1D): state [cell][k][5] = (rho, m, E, rho c1, rho c2), source
+    (0, 0, 0, rho c2, -omega^2 rho c1); nested Picard predictor
+    (eq. lst_dg_predictor_nested_picards) and the corrector's source term."""
+
+    def __init__(self, N: int, omega: float = 1.0, gamma: float = 1.4, cfl: float = 0.4,
+                 tol: float = 1e-13, max_iter: int | None = None, fixed_iter: int = 0):
+        self.N, self.n = N, N + 1
+        self.base = Oracle(N, gamma=gamma, cfl=cfl, tol=tol)
+        self.basis = self.base.basis
+        self.params = RSParams(gamma, omega, cfl, tol,
+                               max_iter if max_iter else 4 * self.n + 8, fixed_iter)
+
+    def table(self, name):
+        return self.base.table(name)
+
+    def set(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        return self
+
+    def node_x(self, ncells, x0=0.0, x1=1.0):
+        return self.base.node_x(ncells, x0, x1)
+
+    def flux(self, U):
+        F = np.zeros(MRS)
+        lib().ob_rs_flux(self.params.gamma, _arr(U, MRS), F)
+        return F
+
+    def source(self, U):
+        S = np.zeros(MRS)
+        lib().ob_rs_source(self.params.omega, _arr(U, MRS), S)
+        return S
+
+    def rusanov(self, a, b):
+        G = np.zeros(MRS)
+        lib().ob_rs_rusanov(self.params.gamma, _arr(a, MRS), _arr(b, MRS), G)
+        return G
+
+    def predict_cell(self, u_cell, lam: float, dt: float, direct: bool = False):
+        u = _arr(u_cell, self.n * MRS)
+        q = np.zeros(self.n * self.n * MRS)
+        it, inner = C.c_int(0), C.c_int(0)
+        if direct:
+            rc = lib().ob_rs_predict_cell_direct(C.byref(self.basis), C.byref(self.params), lam,
+                                                 dt, u, q, C.byref(it))
+        else:
+            rc = lib().ob_rs_predict_cell(C.byref(self.basis), C.byref(self.params), lam, dt, u,
+                                          q, C.byref(it), C.byref(inner))
+        return q.reshape(self.n, self.n, MRS), it.value, inner.value, rc
+
+    def predict(self, u, lam: float, dt: float):
+        u = _arr(u).reshape(-1, self.n, MRS)
+        out = np.zeros((u.shape[0], self.n, self.n, MRS))
+        iters = np.zeros(u.shape[0], dtype=np.int32)
+        for i in range(u.shape[0]):
+            out[i], iters[i], _, _ = self.predict_cell(u[i], lam, dt)
+        return out, iters
+
+    def dg_dt(self, u, dx):
+        u = _arr(u)
+        return lib().ob_rs_dg_dt(C.byref(self.basis), C.byref(self.params), dx,
+                                 u.size // (self.n * MRS), u)
+
+    def dg_step(self, u, dx, dt, want_q: bool = False):
+        u = _arr(u)
+        nc = u.size // (self.n * MRS)
+        out = np.zeros_like(u)
+        q = np.zeros(nc * self.n * self.n * MRS) if want_q else None
+        st = Stats()
+        rc = lib().ob_rs_dg_step(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u, out,
+                                 q.ctypes.data if want_q else None, C.byref(st))
+        return out, q, st, rc
+
+    def dg_step_cells(self, u, dx, dt, cells):
+        u = _arr(u)
+        nc = u.size // (self.n * MRS)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size * self.n * MRS)
+        rc = lib().ob_rs_dg_step_cells(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u,
+                                       cells, cells.size, out)
+        return out.reshape(cells.size, self.n, MRS), rc
+
+    def solve(self, u, dx, t_end: float = 0.0, max_steps: int = 0, dt_fixed: float = 0.0):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        nc = u.size // (self.n * MRS)
+        steps, t = C.c_int64(0), C.c_double(0.0)
+        rc = lib().ob_rs_solve(C.byref(self.basis), C.byref(self.params), nc, dx, u, t_end,
+                               max_steps, dt_fixed, C.byref(steps), C.byref(t))
+        return u, steps.value, t.value, rc
+
+
+def ode_errors(orc: "ReactingOracle", dt: float, nodes, locals_, t_end: float, omega: float = 1.0,
+               npts: int = 25):
+    """Errors of the ODE initial-value problem of Sec. 2.1 (eq. harm_osc, eq.
+    epsilons_q): u1 = cos(omega t), u2 = -omega sin(omega t) against the species
+    components (rho c1, rho c2) of a one-cell uniform solve.
+
+    nodes: [K, 2] species values u^n at t_n = n dt, n = 1..K (the solution at
+    time nodes); locals_: [K, n, 2] predictor time coefficients q_{l0} of step n
+    (any xi node: the state is uniform).  Returns ((eps_L1, eps_L2, eps_Linf) at
+    time nodes, (L1, L2, Linf) of the local solution over [0, t_end]), the
+    integrals by the npts-point GL rule per step and vector norms summed over
+    both components."""
+    nodes = np.asarray(nodes)
+    K = nodes.shape[0]
+    t = dt * np.arange(1, K + 1)
+    ex = np.stack([np.cos(omega * t), -omega * np.sin(omega * t)], 1)
+    e = np.abs(nodes - ex).sum(1)
+    glob = (float(dt * e.sum()), float(np.sqrt(dt * (e ** 2).sum())), float(e.max()))
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1.0), 0.5 * gw
+    phi = np.stack([orc.base.phi(x) for x in gx])  # [npts, n]
+    l1 = l2 = linf = 0.0
+    for k in range(K):
+        ts = dt * (k + gx)
+        exk = np.stack([np.cos(omega * ts), -omega * np.sin(omega * ts)], 1)
+        ek = np.abs(phi @ np.asarray(locals_[k]) - exk).sum(1)
+        l1 += dt * float(gw @ ek)
+        l2 += dt * float(gw @ ek ** 2)
+        linf = max(linf, float(ek.max()))
+    return glob, (l1, float(np.sqrt(l2)), linf)
 
 
 # ---------------------------------------------------------------------------

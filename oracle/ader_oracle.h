@@ -129,6 +129,52 @@ int ob_solve(int scheme, const ob_basis* b, const ob_weno* wt, const ob_params* 
              double dx, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
              double* t_out);
 
+/* ------------------------------------------------------------------------
+ * Systems with algebraic source terms (ader_oracle_src.c).
+ *
+ * The 1D reduction of the paper's two-component reacting flow (Sec. 2,
+ * eq. pdes_2_comps): U = (rho, m, E, rho c1, rho c2), Euler fluxes plus the
+ * advected species, F = (m, m u + p, (E + p) u, rho c1 u, rho c2 u), and the
+ * "reaction rates" S = (0, 0, 0, rho c2, -omega^2 rho c1).  The predictor is
+ * the nested Picard iteration of eq. lst_dg_predictor_nested_picards (outer
+ * loop: fluxes; inner loop: sources, L^sigma = kappa~ (x) I acting on the
+ * rescaled source s = dt S); the corrector adds the space-time integral of s
+ * (last term of eq. ader_dg_method_full).  DG only.
+ * ---------------------------------------------------------------------- */
+#define OB_MRS 5
+
+typedef struct {
+  double gamma;
+  double omega;     /* reaction frequency of S */
+  double cfl;
+  double tol;       /* eps_0 for both loops (relative to max(1, max|q|)) */
+  int max_iter;     /* cap of each loop */
+  int fixed_iter;   /* >0: exactly this many outer iterations (inner loops still converge) */
+} ob_rs_params;
+
+void ob_rs_flux(double gamma, const double* U, double* F);
+void ob_rs_source(double omega, const double* U, double* S);
+void ob_rs_rusanov(double gamma, const double* a, const double* b, double* G);
+/* nested Picard; iters: outer count, inner_total: inner iterations summed over
+ * the outer ones (either may be NULL) */
+int ob_rs_predict_cell(const ob_basis* b, const ob_rs_params* p, double lam, double dt,
+                       const double* u, double* q, int* iters, int* inner_total);
+/* one Picard loop updating flux and source together (test variant) */
+int ob_rs_predict_cell_direct(const ob_basis* b, const ob_rs_params* p, double lam, double dt,
+                              const double* u, double* q, int* iters);
+double ob_rs_dg_dt(const ob_basis* b, const ob_rs_params* p, double dx, int64_t ncells,
+                   const double* u);
+int ob_rs_dg_step(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double dx, double dt,
+                  const double* u, double* u_new, double* q_out, ob_stats* st);
+int ob_rs_dg_step_cells(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double dx,
+                        double dt, const double* u, const int64_t* cells, int64_t count,
+                        double* u_new_sel);
+/* time loop: dt_fixed > 0 gives uniform steps (clipped to t_end), else the CFL
+ * rule of Sec. 1.5 over the Euler part of the state */
+int ob_rs_solve(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double dx, double* u,
+                double t_end, int64_t max_steps, double dt_fixed, int64_t* steps_out,
+                double* t_out);
+
 #ifdef __cplusplus
 }
 #endif

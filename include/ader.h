@@ -21,8 +21,9 @@
  *   - work is enqueued on the stream given to ader_bind() (NULL = legacy default
  *     stream) and is asynchronous unless the entry point says it synchronises;
  *   - a context is not thread-safe: use one context per host thread;
- *   - layouts are AoS, variable fastest:
- *       DG state      u[cell][k][r]        k < N+1 GL nodes, r < 3
+ *   - layouts are AoS, variable fastest (M = 3 for the Euler system, 5 for the
+ *     reacting system, see ader_system):
+ *       DG state      u[cell][k][r]        k < N+1 GL nodes, r < M
  *       FV state      v[cell][r]
  *       predictor     q[cell][p0][p1][r]   p0 = tau node, p1 = xi node
  *     cell i covers [x0 + i dx, x0 + (i+1) dx], dx = (x1 - x0) / n_cells, periodic.
@@ -53,9 +54,19 @@ typedef enum { ADER_SCHEME_DG = 0, ADER_SCHEME_WENO_FV = 1 } ader_scheme;
 typedef enum {
   ADER_PREC_FP64 = 0,            /* whole path in FP64 */
   ADER_PREC_FP32_PREDICTOR = 1,  /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
-  ADER_PREC_FF_PREDICTOR = 2     /* Picard in float-float (~48 bits, FP32 pipes), FP64-accurate;
-                                    predictor epilogue, corrector and CFL in FP64 */
+  ADER_PREC_FF_PREDICTOR = 2     /* Picard and predictor epilogue in float-float (~48 bits,
+                                    FP32 pipes); corrector and CFL in FP64 */
 } ader_precision;
+
+/* The system of conservation laws.
+ * ADER_SYSTEM_EULER: 1D Euler, M = 3 variables (rho, rho u, E).
+ * ADER_SYSTEM_REACTING: the paper's two-component reacting flow in 1D (Sec. 2,
+ *   eq. pdes_2_comps), M = 5 variables (rho, rho u, E, rho c1, rho c2), species
+ *   advected with the flow and the source S = (0, 0, 0, rho c2, -omega^2 rho c1);
+ *   predictor by the nested Picard iteration of eq.
+ *   lst_dg_predictor_nested_picards, corrector with the source term of eq.
+ *   ader_dg_method_full.  DG scheme and ADER_PREC_FP64 only. */
+typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1 } ader_system;
 
 /* Uniform periodic mesh on [x0, x1]. */
 typedef struct {
@@ -75,6 +86,8 @@ typedef struct {
   int profile;            /* 1: ader_solve records CUDA events around every kernel of every
                              step on the stream it launches them on (graph event nodes) and
                              waits for each graph, so per-kernel times land in ader_stats */
+  int system;             /* ader_system (ADER_SYSTEM_EULER) */
+  double omega;           /* reaction frequency of ADER_SYSTEM_REACTING (1.0) */
 } ader_options;
 
 typedef struct {
@@ -108,8 +121,8 @@ const char* ader_last_error(const ader_ctx* ctx);
 const char* ader_status_string(int status);
 
 /* Sizes (in doubles / bytes) the caller must provide. */
-int64_t ader_state_count(const ader_ctx* ctx);      /* DG: n_cells (N+1) 3; FV: n_cells 3 */
-int64_t ader_predictor_count(const ader_ctx* ctx);  /* n_cells (N+1)^2 3 */
+int64_t ader_state_count(const ader_ctx* ctx);      /* DG: n_cells (N+1) M; FV: n_cells 3 */
+int64_t ader_predictor_count(const ader_ctx* ctx);  /* n_cells (N+1)^2 M */
 size_t ader_workspace_bytes(const ader_ctx* ctx);   /* device scratch for ader_bind() */
 
 /* Physical coordinates of the state's points: DG: the GL nodes x0 + dx (i + xi_k)

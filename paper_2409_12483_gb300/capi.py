@@ -25,6 +25,8 @@ ADER_ERR_STATE = 7
 
 SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2}
+SYSTEMS = {"euler": 0, "reacting": 1}
+SYSTEM_VARS = {0: 3, 1: 5}
 
 
 class AderError(RuntimeError):
@@ -41,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
                 ("picard_max_iter", C.c_int), ("picard_fixed_iter", C.c_int),
                 ("precision", C.c_int), ("fp64_sweeps", C.c_int), ("fp32_tol", C.c_double),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("system", C.c_int), ("omega", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -160,6 +162,8 @@ def default_options(**kw) -> Options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "system" and isinstance(v, str):
+            v = SYSTEMS[v]
         setattr(o, k, v)
     return o
 
@@ -215,6 +219,7 @@ class Context:
         self.state_count = int(L.ader_state_count(ctx))
         self.predictor_count = int(L.ader_predictor_count(ctx))
         self.workspace_bytes = nbytes
+        self.vars = SYSTEM_VARS[self.options.system] if scheme == "dg" else 3
 
     # -- helpers --
     def _check(self, rc: int, ok=(ADER_OK,)):
@@ -235,7 +240,7 @@ class Context:
             pass
 
     def state_shape(self):
-        return (self.n_cells, self.n, 3) if self.scheme == "dg" else (self.n_cells, 3)
+        return (self.n_cells, self.n, self.vars) if self.scheme == "dg" else (self.n_cells, 3)
 
     # -- host-side queries --
     def node_coords(self):

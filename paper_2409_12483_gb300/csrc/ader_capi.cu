@@ -36,6 +36,7 @@ struct ader_ctx {
   ader_mesh mesh{};
   ader_options opt{};
   int N = 0, n = 1, scheme = 0;
+  int M = kM;  // variables per node: 3 (Euler) or kMR (reacting system)
   double dx = 0.0;
   // workspace (caller-owned)
   char* ws = nullptr;
@@ -89,11 +90,12 @@ ader_status fail(ader_ctx* c, ader_status st, const char* fmt, ...) {
 bool is_weno_degree(int N) { return N == 2 || N == 4; }
 
 int64_t state_count(const ader_ctx* c) {
-  return c->scheme == ADER_SCHEME_DG ? c->mesh.n_cells * c->n * kM : c->mesh.n_cells * kM;
+  return c->scheme == ADER_SCHEME_DG ? c->mesh.n_cells * c->n * c->M : c->mesh.n_cells * kM;
 }
 
+// DG: [cell][qR | qL | u + volume (+ source)], M n doubles each; FV: [cell][qR | qL]
 size_t trace_doubles(const ader_ctx* c) {
-  return (size_t)c->mesh.n_cells * (c->scheme == ADER_SCHEME_DG ? 9 : 6) * c->n;
+  return (size_t)c->mesh.n_cells * (c->scheme == ADER_SCHEME_DG ? 3 : 2) * c->M * c->n;
 }
 
 size_t workspace_bytes(const ader_ctx* c) {
@@ -131,6 +133,8 @@ PredictParams make_predict(const ader_ctx* c, const double* u_nodal, const StepP
   p.max_iter = c->opt.picard_max_iter;
   p.fixed_iter = c->opt.picard_fixed_iter;
   p.cpb = c->tune.predict_cells_per_block;
+  p.sys = c->opt.system;
+  p.om2 = c->opt.omega * c->opt.omega;
   p.tol = c->opt.picard_tol;
   p.tol32 = (float)c->opt.fp32_tol;
   p.gamma = c->opt.gamma;
@@ -151,6 +155,7 @@ FaceParams make_face(const ader_ctx* c, const double* v_old, double* u_new, cons
   f.dg = c->scheme == ADER_SCHEME_DG;
   f.want_lambda = want_lambda;
   f.cpf = c->tune.face_cells_per_block;
+  f.sys = c->opt.system;
   f.Ns = c->basis.Ns;
   f.gamma = c->opt.gamma;
   f.gm1 = c->opt.gamma - 1.0;
@@ -171,6 +176,7 @@ ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
   CflParams p{};
   p.u = u;
   p.ncells = ctx->mesh.n_cells;
+  p.vars = ctx->scheme == ADER_SCHEME_DG ? ctx->M : kM;
   p.dg = ctx->scheme == ADER_SCHEME_DG;
   p.slot = slot;
   p.Ns = ctx->basis.Ns;
@@ -277,6 +283,8 @@ ader_status ader_default_options(ader_options* o) {
   o->fp64_sweeps = 1;
   o->fp32_tol = 1e-6;
   o->profile = 0;
+  o->system = ADER_SYSTEM_EULER;
+  o->omega = 1.0;
   return ADER_OK;
 }
 
@@ -307,10 +315,14 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   if (!(o.gamma > 1.0) || !(o.cfl > 0.0) || !(o.picard_tol >= 0.0) || o.picard_fixed_iter < 0 ||
       (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR &&
        o.precision != ADER_PREC_FF_PREDICTOR) ||
-      (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000) {
+      (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000 ||
+      (o.system != ADER_SYSTEM_EULER && o.system != ADER_SYSTEM_REACTING) ||
+      (o.system == ADER_SYSTEM_REACTING &&
+       (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || !std::isfinite(o.omega)))) {
     delete c;
     return ADER_ERR_ARG;
   }
+  c->M = o.system == ADER_SYSTEM_REACTING ? kMR : kM;
   if (build_basis(degree, scheme == ADER_SCHEME_WENO_FV, &c->basis) != 0) {
     delete c;
     return ADER_ERR_ARG;
@@ -339,7 +351,7 @@ const char* ader_last_error(const ader_ctx* c) { return c ? c->err : "null conte
 
 int64_t ader_state_count(const ader_ctx* c) { return c ? state_count(c) : -1; }
 int64_t ader_predictor_count(const ader_ctx* c) {
-  return c ? c->mesh.n_cells * c->n * c->n * kM : -1;
+  return c ? c->mesh.n_cells * c->n * c->n * c->M : -1;
 }
 size_t ader_workspace_bytes(const ader_ctx* c) { return c ? workspace_bytes(c) : 0; }
 
@@ -787,7 +799,7 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
       ctx->scheme == ADER_SCHEME_WENO_FV ? (size_t)ctx->mesh.n_cells * ctx->n * kM * sizeof(double) : 0;
   const size_t need = kNoallocCtlBytes + align_up(trace_bytes) + wrec_bytes;
   if (need > kNoallocBytes) {
-    const long long per_cell = (long long)(9 * ctx->n * sizeof(double));
+    const long long per_cell = (long long)(3 * ctx->M * ctx->n * sizeof(double));
     return fail(ctx, ADER_ERR_ARG,
                 "mesh of %lld cells needs %zu bytes of scratch; the static scratch holds %zu "
                 "bytes (at most %lld cells at N = %d)",

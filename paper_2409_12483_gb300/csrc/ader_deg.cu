@@ -2,6 +2,7 @@
 // plain launchers.  Compiled once per degree with -DADER_DEG=<0..7>, so the
 // degrees build in parallel and each kernel is fully unrolled for its N.
 #include "ader_kernels.cuh"
+#include "ader_source.cuh"
 
 #ifndef ADER_DEG
 #error "compile with -DADER_DEG=<0..7>"
@@ -59,6 +60,46 @@ cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
   }
 }
 
+// reacting system (ader_source.cuh): predictor tiles of 16 or 32 cells, interface tiles of 32
+template <int CPB>
+cudaError_t prepare_src_cpb() {
+  if constexpr (!SrcCfg<D, CPB>::kValid) {
+    return cudaSuccess;
+  } else {
+    return cudaFuncSetAttribute(predict_src_kernel<D, CPB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SrcCfg<D, CPB>::kSmemBytes);
+  }
+}
+
+template <int CPB>
+cudaError_t launch_predict_src_cpb(const PredictParams& p, cudaStream_t s) {
+  if constexpr (!SrcCfg<D, CPB>::kValid) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using C = SrcCfg<D, CPB>;
+    const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    predict_src_kernel<D, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t launch_predict_src(const PredictParams& p, cudaStream_t s) {
+  if (p.prec != 0) return cudaErrorInvalidValue;  // the reacting system runs in FP64
+  if (p.cpb == 16 && SrcCfg<D, 16>::kValid) return launch_predict_src_cpb<16>(p, s);
+  if (SrcCfg<D, 32>::kValid) return launch_predict_src_cpb<32>(p, s);
+  return launch_predict_src_cpb<16>(p, s);
+}
+
+cudaError_t launch_face_src(const FaceParams& p, cudaStream_t s) {
+  using C = FaceCfg<D, 32>;
+  const long long blocks = (p.ncells + C::C - 1) / C::C;
+  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  face_src_kernel<D, 32><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int CF>
 cudaError_t launch_face_cf(const FaceParams& p, cudaStream_t s) {
   using C = FaceCfg<D, CF>;
@@ -74,6 +115,8 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_cpb<32>()) != cudaSuccess) return e;
   if ((e = prepare_cpb<64>()) != cudaSuccess) return e;
+  if ((e = prepare_src_cpb<16>()) != cudaSuccess) return e;
+  if ((e = prepare_src_cpb<32>()) != cudaSuccess) return e;
   for (int prec = 0; prec < 3; ++prec) {
     auto k = prec == 0 ? predict_multi_kernel<D, 0>
                        : (prec == 1 ? predict_multi_kernel<D, 1> : predict_multi_kernel<D, 2>);
@@ -85,6 +128,7 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
 }
 
 cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
+  if (p.sys == kSysReacting) return launch_predict_src(p, s);
   switch (p.cpb) {
     case 16: return launch_predict_cpb<16>(p, s);
     case 64: return launch_predict_cpb<64>(p, s);
@@ -95,6 +139,7 @@ cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStre
 }
 
 cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {
+  if (p.sys == kSysReacting) return launch_face_src(p, s);
   switch (p.cpf) {
     case 32: return launch_face_cf<32>(p, s);
     case 0:

@@ -79,8 +79,8 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 // (q < h = n/2; the middle node of odd n enters e alone), S_p = sum_q ka[p][q] e_q
 // and T_p = sum_q kb[p][q] o_q give g_p = S_p + T_p and g_{n-1-p} = T_p - S_p
 // (and g_h = T_h for odd n): n^2/2 + 2n operations per variable instead of n^2.
-template <int N, typename T>
-__device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
+template <int N, typename T, int M = kM>
+__device__ __forceinline__ void kxi_row(const T (&f)[N + 1][M], T* out,
                                         const T (&kt)[kMaxN][kMaxN],
                                         const T (&ka)[kMaxH][kMaxH],
                                         const T (&kb)[kMaxH][kMaxH]) {
@@ -89,15 +89,15 @@ __device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
 #pragma unroll
     for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
+      for (int r = 0; r < M; ++r) {
         T acc = T(0);
 #pragma unroll
         for (int q1 = 0; q1 < n; ++q1) acc = fma(kt[p1][q1], f[q1][r], acc);
-        out[p1 * kM + r] = acc;
+        out[p1 * M + r] = acc;
       }
   } else {
 #pragma unroll
-    for (int r = 0; r < kM; ++r) {
+    for (int r = 0; r < M; ++r) {
       T e[H], o[h];
 #pragma unroll
       for (int q = 0; q < h; ++q) {
@@ -112,14 +112,14 @@ __device__ __forceinline__ void kxi_row(const T (&f)[N + 1][kM], T* out,
         for (int q = 0; q < H; ++q) S = fma(ka[p][q], e[q], S);
 #pragma unroll
         for (int q = 0; q < h; ++q) Tt = fma(kb[p][q], o[q], Tt);
-        out[p * kM + r] = Tt + S;
-        out[(n - 1 - p) * kM + r] = Tt - S;
+        out[p * M + r] = Tt + S;
+        out[(n - 1 - p) * M + r] = Tt - S;
       }
       if constexpr (H > h) {
         T Tt = T(0);
 #pragma unroll
         for (int q = 0; q < h; ++q) Tt = fma(kb[h][q], o[q], Tt);
-        out[h * kM + r] = Tt;
+        out[h * M + r] = Tt;
       }
     }
   }
@@ -800,6 +800,82 @@ struct FaceIO {
   long long ncells;
 };
 
+// lambda_max of the updated state of a tile for the next step's CFL rule, from
+// the tile's shared copies sh.u (FP64) and sh.uf (float) of the Euler variables
+// (rho, m, E) in [cell][k][3] layout; atomically maxed into ctl->lam[par ^ 1].
+template <int N, int C>
+__device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParams& sp, int nvalid,
+                                            FaceShared<N, C>& sh) {
+  constexpr int n = N + 1, THREADS = FaceCfg<N, C>::THREADS;
+  const int tid = threadIdx.x;
+  // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
+  // speeds are needed only where the maximum can be: a first FP32 pass screens
+  // every subcell (speeds within 1e-3 of the block's FP32 maximum, and any
+  // subcell whose FP32 state is doubtful, go on to FP64), so the FP64 result is
+  // the same as evaluating every subcell in FP64.
+  __syncthreads();
+  const int items = P.dg ? nvalid * P.Ns : nvalid;
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  float lt_loc = 0.f;
+  for (int item = tid; item < items; item += THREADS) {
+    float v[kM];
+    if (P.dg) {
+      const int lc = item / P.Ns, j = item - lc * P.Ns;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc = fmaf(sh.Pf[j * n + k], sh.uf[(lc * n + k) * kM + r], acc);
+        v[r] = acc;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kM; ++r) v[r] = sh.uf[item * kM + r];
+    }
+    const float inv = 1.f / v[0];
+    const float uu = v[1] * inv;
+    const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
+    float lt;
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
+      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
+    else
+      lt = fabsf(uu) + sqrtf(gf * pp * inv);
+    sh.lt[item] = lt;
+    lt_loc = fmaxf(lt_loc, lt);
+  }
+  const unsigned long long fm =
+      block_max_bits((unsigned long long)__float_as_uint(lt_loc), sh.wmax);
+  if (tid == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    sh.lt_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  const float cut = sh.lt_cut;
+  double lmax = 0.0;
+  bool bad = false;
+  for (int item = tid; item < items; item += THREADS) {
+    if (!(sh.lt[item] >= cut)) continue;
+    double v[kM];
+    if (P.dg) {
+      const int lc = item / P.Ns, j = item - lc * P.Ns;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc = fma(sh.P[j * n + k], sh.u[(lc * n + k) * kM + r], acc);
+        v[r] = acc;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kM; ++r) v[r] = sh.u[item * kM + r];
+    }
+    lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), sh.wmax);
+  if (tid == 0) atomicMax(&sp.ctl->lam[sp.par ^ 1], bm);
+  if (bad) atomicOr(&sp.ctl->status, kStNonPhysical);
+}
+
 // One tile (C cells) of the interface flux + update (+ lambda_max) of one solve.
 template <int N, int C = 64>
 __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
@@ -865,74 +941,7 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
       sh.uf[lc * kM + r] = d2f_trunc(vn);
     }
   }
-  if (P.want_lambda) {
-    // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
-    // speeds are needed only where the maximum can be: a first FP32 pass screens
-    // every subcell (speeds within 1e-3 of the block's FP32 maximum, and any
-    // subcell whose FP32 state is doubtful, go on to FP64), so the FP64 result is
-    // the same as evaluating every subcell in FP64.
-    __syncthreads();
-    const int items = P.dg ? nvalid * P.Ns : nvalid;
-    const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-    float lt_loc = 0.f;
-    for (int item = tid; item < items; item += THREADS) {
-      float v[kM];
-      if (P.dg) {
-        const int lc = item / P.Ns, j = item - lc * P.Ns;
-#pragma unroll
-        for (int r = 0; r < kM; ++r) {
-          float acc = 0.f;
-#pragma unroll
-          for (int k = 0; k < n; ++k) acc = fmaf(sh.Pf[j * n + k], sh.uf[(lc * n + k) * kM + r], acc);
-          v[r] = acc;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < kM; ++r) v[r] = sh.uf[item * kM + r];
-      }
-      const float inv = 1.f / v[0];
-      const float uu = v[1] * inv;
-      const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
-      float lt;
-      if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
-        lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
-      else
-        lt = fabsf(uu) + sqrtf(gf * pp * inv);
-      sh.lt[item] = lt;
-      lt_loc = fmaxf(lt_loc, lt);
-    }
-    const unsigned long long fm =
-        block_max_bits((unsigned long long)__float_as_uint(lt_loc), sh.wmax);
-    if (tid == 0) {
-      const float m = __uint_as_float((unsigned)fm);
-      sh.lt_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-    }
-    __syncthreads();
-    const float cut = sh.lt_cut;
-    double lmax = 0.0;
-    bool bad = false;
-    for (int item = tid; item < items; item += THREADS) {
-      if (!(sh.lt[item] >= cut)) continue;
-      double v[kM];
-      if (P.dg) {
-        const int lc = item / P.Ns, j = item - lc * P.Ns;
-#pragma unroll
-        for (int r = 0; r < kM; ++r) {
-          double acc = 0.0;
-#pragma unroll
-          for (int k = 0; k < n; ++k) acc = fma(sh.P[j * n + k], sh.u[(lc * n + k) * kM + r], acc);
-          v[r] = acc;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < kM; ++r) v[r] = sh.u[item * kM + r];
-      }
-      lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
-    }
-    const unsigned long long bm = block_max_bits(dbits(lmax), sh.wmax);
-    if (tid == 0) atomicMax(&sp.ctl->lam[sp.par ^ 1], bm);
-    if (bad) atomicOr(&sp.ctl->status, kStNonPhysical);
-  }
+  if (P.want_lambda) face_lambda<N, C>(P, sp, nvalid, sh);
   __syncthreads();  // shared memory is free for the next tile
 }
 
@@ -997,14 +1006,16 @@ __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflPar
        it += (long long)gridDim.x * blockDim.x) {
     double v[kM];
     if (P.dg) {
+      // the Euler variables (rho, m, E) lead each node's record of P.vars values
       const long long cell = it / P.Ns;
       const int j = (int)(it - cell * P.Ns);
-      const double* u = P.u + cell * (n * kM);
+      const int stride = P.vars;
+      const double* u = P.u + cell * (n * stride);
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
         double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], u[k * kM + r], acc);
+        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], u[k * stride + r], acc);
         v[r] = acc;
       }
     } else {

@@ -10,6 +10,7 @@
 namespace ader {
 
 enum : int { kOutQ = 0, kOutTrace = 1 };
+enum : int { kSysEuler = 0, kSysReacting = 1 };
 
 // LST-DG predictor (Algorithm lst_dg_predictor, S = B = 0) with its epilogue.
 struct PredictParams {
@@ -26,9 +27,11 @@ struct PredictParams {
   int max_iter;
   int fixed_iter;
   int cpb;               // predictor cells per block (16, 32, 64; tuned), 0 = 32
+  int sys;               // kSysEuler or kSysReacting (ader_source.cuh)
   float tol32;
   double tol;
   double gamma, gm1;
+  double om2;            // omega^2 of the reacting system's source
   StepParams sp;
   OpsD ops;
   OpsF opf;
@@ -44,6 +47,7 @@ struct FaceParams {
   int dg;
   int want_lambda;
   int cpf;               // interface/update cells per block (32, 64; tuned), 0 = 64
+  int sys;               // kSysEuler or kSysReacting
   int Ns;
   double gamma, gm1;
   StepParams sp;
@@ -54,6 +58,7 @@ struct FaceParams {
 struct CflParams {
   const double* u;
   long long ncells;
+  int vars;              // values per node record (3 Euler, 5 reacting); Euler variables first
   int dg;
   int slot;
   int Ns;

@@ -18,6 +18,7 @@ constexpr int kMaxN = kMaxDeg + 1;        // GL nodes per direction
 constexpr int kMaxNs = 2 * kMaxDeg + 1;   // subcells of Sec. 1.4
 constexpr int kMaxH = (kMaxN + 1) / 2;    // half rows of the symmetric k~ form
 constexpr int kM = 3;                     // conserved variables of 1D Euler
+constexpr int kMR = 5;                    // variables of the 1D two-component reacting flow
 
 // Tables in the layout the kernels read (row-major, unused entries zero).
 struct OpsD {

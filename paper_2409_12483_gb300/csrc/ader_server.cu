@@ -199,6 +199,7 @@ ader_status admit(ader_server* srv, Req* r, int slot_id, double now) {
   CflParams cp{};
   cp.u = sl.u[0];
   cp.ncells = r->ncells;
+  cp.vars = kM;
   cp.dg = 1;
   cp.slot = 0;
   cp.Ns = b.Ns;

@@ -206,3 +206,30 @@ def test_weno_monomial_tables_reproduce_polynomials(lib, N):
             np.testing.assert_allclose(a, a_ref, rtol=0, atol=1e-11 * np.abs(a_ref).max())
         np.testing.assert_allclose(vnod @ a_ref, p(xi), rtol=0, atol=1e-13 * np.abs(p(xi)).max())
     lib.ader_destroy(ctx)
+
+
+def test_reacting_system_options_and_sizes(lib):
+    """The reacting system: DG + FP64 only; M = 5 variables in the state and
+    predictor sizes; an unknown system id is rejected."""
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    N, nc = 3, 10
+    ctx = C.c_void_p()
+    o = default_options(system="reacting", omega=2.0)
+    assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), N, 0, C.byref(o), C.byref(ctx)) == 0
+    assert lib.ader_state_count(ctx) == nc * (N + 1) * 5
+    assert lib.ader_predictor_count(ctx) == nc * (N + 1) ** 2 * 5
+    e = default_options()
+    eul = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), N, 0, C.byref(e), C.byref(eul)) == 0
+    # trace records grow from 3 x 3 (N+1) to 3 x 5 (N+1) doubles per cell
+    assert lib.ader_workspace_bytes(ctx) > lib.ader_workspace_bytes(eul)
+    lib.ader_destroy(ctx)
+    lib.ader_destroy(eul)
+    for kw, scheme, deg in ((dict(system="reacting"), 1, 4),             # FV
+                            (dict(system="reacting", precision="ff"), 0, 3),
+                            (dict(system="reacting", precision="fp32"), 0, 3),
+                            (dict(system=7), 0, 3),
+                            (dict(system="reacting", omega=float("nan")), 0, 3)):
+        bad = C.c_void_p()
+        assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), deg, scheme,
+                             C.byref(default_options(**kw)), C.byref(bad)) == 1, kw

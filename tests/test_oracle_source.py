@@ -32,10 +32,8 @@ def pade_stability(N, Z):
     return np.linalg.solve(Q, P)
 
 
-def ode_state(n, c1=1.0, c2=0.0):
-    """uniform rho = 1, u = 1, p = 1 (E = 1/0.4 + 1/2), species (c1, c2)"""
-    U = np.array([1.0, 1.0, 1.0 / 0.4 + 0.5, c1, c2])
-    return np.tile(U, (1, n, 1))
+def ode_state(n):
+    return W.ode_state(n)[None]
 
 
 # The data are uniform, so the cell width does not enter the exact solution;
@@ -95,22 +93,8 @@ def test_ode_orders_global_2n1_local_n1(oracle_mod, N):
         assert abs(pl - (N + 1)) < 0.35, (i, pl)
 
 
-def field(seed):
-    g = np.random.default_rng(seed)
-    return (g.uniform(0, 0.1, 3), g.uniform(0, 6.28, 3))
-
-
-def reacting_state(orc, nc, seed=1, u0=0.5):
-    """smooth positive rho, p (three modes), velocity u0, species c1, c2 smooth"""
-    a, ph = field(seed)
-    x = orc.node_x(nc)
-    k = np.arange(1, 4)
-    rho = 1 + (a[:, None, None] * np.sin(2 * np.pi * k[:, None, None] * x + ph[:, None, None])).sum(0)
-    p = 1 + 0.5 * (a[:, None, None] * np.cos(2 * np.pi * k[:, None, None] * x + ph[:, None, None])).sum(0)
-    c1 = 0.5 + 0.3 * np.sin(2 * np.pi * x)
-    c2 = 0.2 * np.cos(2 * np.pi * x)
-    U = np.stack([rho, rho * u0, p / 0.4 + 0.5 * rho * u0 ** 2, rho * c1, rho * c2], -1)
-    return U
+def reacting_state(orc, nc, seed=1):
+    return W.reacting_state(orc.node_x(nc), seed)
 
 
 @pytest.mark.parametrize("N", [1, 2, 3])

@@ -15,6 +15,11 @@ unchanged, exact solution rho0(x - u t) on the periodic unit interval):
 * ``serving``  independent requests: cells log-uniform in [64, 65536], N ~ U{1..7},
                rho, p = 1 + sum_{j=1..3} a_j sin(2 pi j x + phi_j), a_j ~ U(0, 0.1/3), u = 0.5,
                t_end = 0.5, Poisson arrivals.
+* ``reacting`` the two-component reacting flow of Sec. 2 (eq. pdes_2_comps) in 1D:
+               (rho, rho u, E, rho c1, rho c2) with rho, p = 1 + three seeded modes,
+               u = 0.5, c1 = 0.5 + 0.3 sin 2 pi x, c2 = 0.2 cos 2 pi x; and the uniform
+               state of the ODE test of Sec. 2.1 (eq. harm_osc): rho = u = p = 1,
+               c1 = 1, c2 = 0.
 """
 from __future__ import annotations
 
@@ -160,3 +165,27 @@ def serving_requests(count: int = 4096, seed: int = DEFAULT_SEED, rate: float = 
         f = Field1D(rho_amp=a_r, rho_phase=ph_r, rho_k=k, u=0.5, p_amp=a_p, p_phase=ph_p, p_k=k)
         out.append(Request(i, float(arrivals[i]), int(cells[i]), int(degs[i]), f, t_end))
     return out
+
+
+def reacting_state(x, seed: int = 1, u0: float = 0.5, gamma: float = GAMMA):
+    """(rho, rho u, E, rho c1, rho c2) at points x (any shape) for the 1D
+    two-component reacting flow: rho = 1 + sum_{k=1..3} a_k sin(2 pi k x + phi_k),
+    p = 1 + 0.5 sum_k a_k cos(2 pi k x + phi_k), a_k ~ U(0, 0.1), phi_k ~ U(0, 2 pi),
+    velocity u0, c1 = 0.5 + 0.3 sin 2 pi x, c2 = 0.2 cos 2 pi x."""
+    g = np.random.default_rng(seed)
+    a, ph = g.uniform(0, 0.1, 3), g.uniform(0, TWO_PI, 3)
+    x = np.asarray(x, dtype=np.float64)
+    k = np.arange(1, 4).reshape((3,) + (1,) * x.ndim)
+    arg = TWO_PI * k * x + ph.reshape(k.shape)
+    rho = 1 + (a.reshape(k.shape) * np.sin(arg)).sum(0)
+    p = 1 + 0.5 * (a.reshape(k.shape) * np.cos(arg)).sum(0)
+    c1 = 0.5 + 0.3 * np.sin(TWO_PI * x)
+    c2 = 0.2 * np.cos(TWO_PI * x)
+    return np.stack([rho, rho * u0, p / (gamma - 1) + 0.5 * rho * u0 ** 2, rho * c1, rho * c2], -1)
+
+
+def ode_state(npts: int, c1: float = 1.0, c2: float = 0.0, gamma: float = GAMMA):
+    """The uniform state of the ODE initial-value problem of Sec. 2.1: rho = 1,
+    u = 1, p = 1, species (c1, c2), repeated at npts points."""
+    U = np.array([1.0, 1.0, 1.0 / (gamma - 1) + 0.5, c1, c2])
+    return np.tile(U, (npts, 1))

@@ -282,6 +282,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=128)
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the coarse-mesh convergence sweeps of the four precision forms")
+    ap.add_argument("--no-source", action="store_true",
+                    help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5")
@@ -412,6 +414,8 @@ def main():
             line["serving"] = run_serving(dev, args.serving_requests)
         if not args.no_convergence:
             line["convergence"] = run_convergence(dev)
+        if not args.no_source:
+            line["source_terms"] = run_source(args, dev, flush)
         line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
@@ -466,6 +470,101 @@ def run_convergence(dev):
         out.append({"degree": N, "data": data, "t_end": 1.0, "meshes": rows, "order_fp64": orders,
                     "within_2x_of_fp64": {k: all(r["ratio_to_fp64"][k] <= 2.0 for r in rows)
                                           for k in forms if k != "fp64"}})
+    return out
+
+
+def lagrange_matrix(x, nodes):
+    """L[i, k] = phi_k(x_i) for the Lagrange basis on the given nodes."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    L = np.ones((x.size, len(nodes)))
+    for k in range(len(nodes)):
+        for m in range(len(nodes)):
+            if m != k:
+                L[:, k] *= (x - nodes[m]) / (nodes[k] - nodes[m])
+    return L
+
+
+def ode_errors(xi, dt, nodes, locs, omega=1.0, npts=25):
+    """Errors of the ODE problem of Sec. 2.1 (eq. harm_osc; norms of eq.
+    epsilons_q, vector norms summed over the two components): at the time nodes
+    t_n = n dt (the corrector's u^n) and of the local predictor solution over
+    each step (npts-point GL rule in time); measurement code, not the oracle."""
+    import numpy as np
+    nodes = np.asarray(nodes)
+    K = len(nodes)
+    t = dt * np.arange(1, K + 1)
+    e = np.abs(nodes - np.stack([np.cos(omega * t), -omega * np.sin(omega * t)], 1)).sum(1)
+    glob = [float(dt * e.sum()), float(np.sqrt(dt * (e ** 2).sum())), float(e.max())]
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1.0), 0.5 * gw
+    L = lagrange_matrix(gx, xi)
+    l1 = l2 = linf = 0.0
+    for k in range(K):
+        ts = dt * (k + gx)
+        ek = np.abs(L @ np.asarray(locs[k]) -
+                    np.stack([np.cos(omega * ts), -omega * np.sin(omega * ts)], 1)).sum(1)
+        l1 += dt * float(gw @ ek)
+        l2 += dt * float(gw @ ek ** 2)
+        linf = max(linf, float(ek.max()))
+    return glob, [l1, float(np.sqrt(l2)), linf]
+
+
+def run_source(args, dev, flush):
+    """The system with algebraic sources (Sec. 2 eq. pdes_2_comps in 1D: Euler plus
+    two reacting species, nested Picard predictor): throughput at the headline's
+    size for a mild (omega = 1) and a fast (omega dt ~ 0.2) reaction, and the
+    ODE convergence study of Sec. 2.1 (one uniform cell, K uniform steps to 2 pi,
+    errors at the time nodes and of the local predictor solution)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    out = {"throughput": [], "ode": []}
+    st = max(2, min(args.steps, 3))
+    for omega in (1.0, 1.0e6):
+        ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, system="reacting", omega=omega)
+        u0 = torch.tensor(W.reacting_state(ctx.node_coords(), seed=SEED), device=dev).reshape(-1)
+        dt = ctx.ader_compute_dt(u0)
+        line = variant_line(f"reacting-dg5-1e5-omega{omega:g}",
+                            "1D two-component reacting flow, DG N=5, 10^5 cells, 100 steps, FP64, "
+                            "nested Picard (outer: fluxes, inner: sources)",
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st, 2, flush)
+        for k in ("predict_fp64_tflops", "predict_frac_of_fp64_peak"):
+            line.pop(k, None)  # the Euler FLOP model does not cover the inner source loop
+        line["omega_dt"] = omega * dt
+        out["throughput"].append(line)
+        del ctx
+    ode_dx = 1.0e3  # uniform data: a wide cell keeps the inactive spatial operator stable
+    for N, Ks in ((1, (10, 20, 40)), (2, (10, 20, 40)), (3, (10, 20)), (4, (10, 20)), (5, (4, 8))):
+        rows = []
+        for K in Ks:
+            dt = 2 * math.pi / K
+            ctx = Context(1, N, "dg", device=dev, system="reacting", omega=1.0, picard_tol=1e-14,
+                          picard_max_iter=200, x1=ode_dx)
+            n = N + 1
+            u = torch.tensor(W.ode_state(n), device=dev).reshape(-1)
+            q = torch.empty(ctx.predictor_count, dtype=torch.float64, device=dev)
+            nodes, locs = [], []
+            for _ in range(K):
+                ctx.ader_predict(u, dt, q)
+                nxt = torch.empty_like(u)
+                ctx.ader_step(u, nxt, dt)
+                u = nxt
+                locs.append(q.view(n, n, 5)[:, 0, 3:5].cpu().numpy())
+                nodes.append(u.view(n, 5)[0, 3:5].cpu().numpy())
+            g, l = ode_errors(ctx.table("xi"), dt, nodes, locs)
+            rows.append({"steps": K, "global": g, "local": l})
+            del ctx
+        for a, b in zip(rows, rows[1:]):
+            r = math.log(b["steps"] / a["steps"])
+            b["order_global"] = [math.log(x / y) / r for x, y in zip(a["global"], b["global"])]
+            b["order_local"] = [math.log(x / y) / r for x, y in zip(a["local"], b["local"])]
+        out["ode"].append({"degree": N, "theory_global": 2 * N + 1, "theory_local": N + 1,
+                           "rows": rows})
     return out
 
 

@@ -190,17 +190,25 @@ __device__ __forceinline__ void predict_src_tile(const PredictParams& P, const T
         ++m;
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1) {
+          if (m == 1)
 #pragma unroll
-          for (int r = 0; r < 3; ++r) my_d[p1 * M + r] = my_g[p1 * M + r];
+            for (int r = 0; r < 3; ++r) my_d[p1 * M + r] = my_g[p1 * M + r];
           my_d[p1 * M + 3] = fma(-dts, q[p1][4], my_g[p1 * M + 3]);  // - dt rho c2
           my_d[p1 * M + 4] = fma(dtw2, q[p1][3], my_g[p1 * M + 4]);  // + dt omega^2 rho c1
         }
         __syncthreads();
+        // The source acts on the species only and the flux rows are frozen, so
+        // after the first inner iteration the Euler components of the new
+        // iterate are the same numbers again: only the species are recomputed.
         double qn[n][M];
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
           for (int r = 0; r < M; ++r) {
+            if (r < 3 && m > 1) {
+              qn[p1][r] = q[p1][r];
+              continue;
+            }
             double acc = uc[p1 * M + r];
 #pragma unroll
             for (int q0 = 0; q0 < n; ++q0) acc = fma(-kap[q0], cell_d[q0 * RS + p1 * M + r], acc);

@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ader_oracle.c")
 _SRC_RS = os.path.join(_HERE, "ader_oracle_src.c")
+_SRC_LIM = os.path.join(_HERE, "ader_oracle_lim.c")
 _HDR = os.path.join(_HERE, "ader_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
 
@@ -36,11 +37,11 @@ OB_ERR_NONPHYSICAL = 5
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, _SRC_LIM, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -76,6 +77,10 @@ class Weno(C.Structure):
         ("dal", ((C.c_double * MAXN) * MAXN) * MAXN),
         ("wq", C.c_double * MAXN),
     ]
+
+
+class LimParams(C.Structure):
+    _fields_ = [("bc", C.c_int), ("limiter", C.c_int), ("delta0", C.c_double), ("eps", C.c_double)]
 
 
 class RSParams(C.Structure):
@@ -139,6 +144,12 @@ def lib():
             L.ob_solve.argtypes = [C.c_int, P(Basis), C.c_void_p, P(Params), C.c_int64,
                                    C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
                                    P(C.c_double)]
+            L.ob_r_matrix.argtypes = [P(Basis), _DP]
+            L.ob_dgl_step.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double,
+                                      C.c_double, _DP, _DP, C.c_void_p, P(Stats)]
+            L.ob_dgl_solve.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double, _DP,
+                                       C.c_double, C.c_int64, P(C.c_int64), P(C.c_double),
+                                       P(C.c_int64)]
             L.ob_rs_flux.argtypes = [C.c_double, _DP, _DP]
             L.ob_rs_flux.restype = None
             L.ob_rs_source.argtypes = [C.c_double, _DP, _DP]
@@ -312,6 +323,39 @@ class Oracle:
                             C.byref(self.params), nc, dx, u, t_end, max_steps, C.byref(steps),
                             C.byref(t))
         return u, steps.value, t.value, rc
+
+    # -- boundaries and the a posteriori subcell limiter (ader_oracle_lim.c) --
+    def r_matrix(self):
+        R = np.zeros(self.n * self.basis.Ns)
+        if lib().ob_r_matrix(C.byref(self.basis), R) != OB_OK:
+            raise RuntimeError("ob_r_matrix failed")
+        return R.reshape(self.n, self.basis.Ns)
+
+    @staticmethod
+    def lim_params(bc: str = "periodic", limiter: bool = True, delta0: float = 1e-4,
+                   eps: float = 1e-3):
+        return LimParams(1 if bc == "outflow" else 0, 1 if limiter else 0, delta0, eps)
+
+    def dgl_step(self, u, dx, dt, bc: str = "periodic", limiter: bool = True):
+        u = _arr(u)
+        nc = u.size // (self.n * M)
+        out = np.zeros_like(u)
+        tr = np.zeros(nc, dtype=np.int32)
+        st = Stats()
+        lp = self.lim_params(bc, limiter)
+        rc = lib().ob_dgl_step(C.byref(self.basis), C.byref(self.params), C.byref(lp), nc, dx, dt,
+                               u, out, tr.ctypes.data, C.byref(st))
+        return out, tr, rc
+
+    def dgl_solve(self, u, dx, t_end: float = 0.0, max_steps: int = 0, bc: str = "periodic",
+                  limiter: bool = True):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        nc = u.size // (self.n * M)
+        steps, t, ttot = C.c_int64(0), C.c_double(0.0), C.c_int64(0)
+        lp = self.lim_params(bc, limiter)
+        rc = lib().ob_dgl_solve(C.byref(self.basis), C.byref(self.params), C.byref(lp), nc, dx, u,
+                                t_end, max_steps, C.byref(steps), C.byref(t), C.byref(ttot))
+        return u, steps.value, t.value, rc, ttot.value
 
     # -- node coordinates of the DG representation (Sec. 1, eq. dg_repr) --
     def node_x(self, ncells: int, x0: float = 0.0, x1: float = 1.0) -> np.ndarray:

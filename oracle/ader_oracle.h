@@ -175,6 +175,38 @@ int ob_rs_solve(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double
                 double t_end, int64_t max_steps, double dt_fixed, int64_t* steps_out,
                 double* t_out);
 
+/* ------------------------------------------------------------------------
+ * Boundaries and the a posteriori subcell limiter (ader_oracle_lim.c), DG, Euler.
+ *
+ * bc: 0 periodic, 1 outflow (zero gradient: the boundary face sees the
+ * interior state on both sides).  limiter != 0: the candidate u* of eq.
+ * ader_dg_method_full is checked cell by cell on its 2N+1 subcell averages
+ * P u* (Sec. 1.4, eq. p_operator) by the physical admissibility detector
+ * (rho > 0, e > 0) and the relaxed discrete maximum principle of eq. nad_ineq
+ * against the subcell averages P u^n of the cell and its neighbours
+ * (delta = max(delta0, eps (max - min))); troubled cells are recomputed by a
+ * first-order Rusanov finite-volume scheme on their 2N+1 subcells and
+ * reconstructed with the pseudo-inverse R = (P^T P)^-1 P^T (eq. r_operator);
+ * faces next to a troubled cell carry the subcell flux on both sides (the DG
+ * neighbour's update is corrected with it), so the step stays conservative.
+ * If R v has an inadmissible subcell average, the cell takes the mean of v.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int bc;          /* 0 periodic, 1 outflow */
+  int limiter;     /* 0 off, 1 on */
+  double delta0;   /* NAD absolute tolerance (1e-4) */
+  double eps;      /* NAD relative tolerance (1e-3) */
+} ob_lim_params;
+
+/* R = (P^T P)^-1 P^T, [n][Ns] row-major */
+int ob_r_matrix(const ob_basis* b, double* R);
+int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, int64_t ncells,
+                double dx, double dt, const double* u, double* u_new, int* troubled,
+                ob_stats* st);
+int ob_dgl_solve(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, int64_t ncells,
+                 double dx, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
+                 double* t_out, int64_t* troubled_total);
+
 #ifdef __cplusplus
 }
 #endif

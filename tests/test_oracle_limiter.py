@@ -1,0 +1,164 @@
+"""Pins of the oracle's outflow boundaries, a posteriori subcell limiter
+(Sec. 1.4 eq. p_operator / eq. r_operator, PAD and NAD eq. nad_ineq) and of the
+exact Riemann solver used as the reference for the classical tests of Sec. 2
+(Table classical_tests_1d).
+
+Independent pins: the exact Riemann solution conserves mass, momentum and energy
+(its integral changes by the boundary fluxes); R is a left inverse of P and P R
+an orthogonal projector; with the limiter off (or on smooth data, where no cell
+is troubled) the step is the plain DG step; the limited step is conservative
+(periodic) and changes the totals by exactly the boundary fluxes (outflow);
+the limited solutions of the four Riemann problems stay physical and converge
+to the exact ones."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+# Table classical_tests_1d: (rho, u, p) left / right of x = 0.5, t_final = 0.15
+TESTS = {1: ((1.000, 0.000, 1.000), (0.125, 0.000, 0.100)),
+         2: ((0.445, 0.698, 3.528), (0.500, 0.000, 0.571)),
+         3: ((1.000, 1.000, 1.000), (1.000, -1.000, 1.000)),
+         4: ((1.000, -1.000, 1.000), (1.000, 1.000, 1.000))}
+GAMMA = 1.4
+
+
+def conserved(rho, u, p, g=GAMMA):
+    return np.stack([rho, rho * u, p / (g - 1) + 0.5 * rho * u * u], -1)
+
+
+def euler_flux(U, g=GAMMA):
+    rho, m, E = U[..., 0], U[..., 1], U[..., 2]
+    u = m / rho
+    p = (g - 1) * (E - 0.5 * m * u)
+    return np.stack([m, m * u + p, (E + p) * u], -1)
+
+
+def riemann_state(o, nc, test):
+    L, R = TESTS[test]
+    x = o.node_x(nc)
+    prim = np.where(x[..., None] < 0.5, np.array(L), np.array(R))
+    return conserved(prim[..., 0], prim[..., 1], prim[..., 2])
+
+
+@pytest.mark.parametrize("test", [1, 2, 3, 4])
+def test_exact_riemann_solution_is_conservative(test):
+    """int_0^1 U(x, t) dx - int_0^1 U(x, 0) dx = -t (F(U_R) - F(U_L)) while the
+    waves stay inside [0, 1] (trapezoid rule on 4e5 points)."""
+    from oracle import riemann
+    L, R = TESTS[test]
+    t = 0.15
+    x = np.linspace(0.0, 1.0, 400_001)
+    rho, u, p = riemann.solution(L, R, x, t)
+    Ut = conserved(rho, u, p)
+    UL, UR = conserved(*map(np.array, L)), conserved(*map(np.array, R))
+    integ = np.trapezoid(Ut, x, axis=0)
+    init = 0.5 * (UL + UR)
+    np.testing.assert_allclose(integ - init, -t * (euler_flux(UR) - euler_flux(UL)), atol=5e-5)
+    # symmetric data (tests 3, 4) give u* = 0 and a symmetric density
+    if test in (3, 4):
+        from oracle.riemann import star_state
+        assert abs(star_state(L, R)[1]) < 1e-14
+        np.testing.assert_allclose(rho, rho[::-1], atol=1e-12)
+
+
+@pytest.mark.parametrize("N", range(0, 8))
+def test_reconstruction_is_pseudo_inverse_of_projection(oracle_mod, N):
+    o = oracle_mod.Oracle(N)
+    P, R = o.table("P"), o.r_matrix()
+    np.testing.assert_allclose(R @ P, np.eye(N + 1), atol=1e-13)
+    Pr = P @ R
+    np.testing.assert_allclose(Pr, Pr.T, atol=1e-13)
+    np.testing.assert_allclose(Pr @ Pr, Pr, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_limiter_off_periodic_is_the_dg_step(oracle_mod, N):
+    o = oracle_mod.Oracle(N)
+    nc = 40
+    u = W.nodal_state(W.modes4(), o.node_x(nc))
+    dt = o.dg_dt(u, 1.0 / nc)
+    ref, _, _, _ = o.dg_step(u, 1.0 / nc, dt)
+    got, tr, rc = o.dgl_step(u, 1.0 / nc, dt, bc="periodic", limiter=False)
+    assert rc == 0 and not tr.any()
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_smooth_data_is_never_troubled(oracle_mod):
+    N, nc = 3, 50
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(W.sine(), o.node_x(nc))
+    a, steps, t, rc, ttot = o.dgl_solve(u, 1.0 / nc, max_steps=30, limiter=True)
+    b, _, _, _, _ = o.dgl_solve(u, 1.0 / nc, max_steps=30, limiter=False)
+    assert rc == 0 and ttot == 0
+    np.testing.assert_array_equal(a, b)
+
+
+def test_outflow_step_changes_totals_by_boundary_fluxes(oracle_mod):
+    """Sod data: the boundary cells hold the constant left / right states, so the
+    time-integrated boundary fluxes are dt F(U_L) and dt F(U_R) exactly."""
+    N, nc = 3, 100
+    o = oracle_mod.Oracle(N)
+    u = riemann_state(o, nc, 1)
+    dx = 1.0 / nc
+    dt = o.dg_dt(u, dx)
+    new, tr, rc = o.dgl_step(u, dx, dt, bc="outflow", limiter=True)
+    assert rc == 0 and tr.any()
+    w = o.table("w")
+    tot = lambda U: dx * np.einsum("ckr,k->r", U.reshape(nc, N + 1, 3), w)
+    UL, UR = conserved(*map(np.array, TESTS[1][0])), conserved(*map(np.array, TESTS[1][1]))
+    np.testing.assert_allclose(tot(new) - tot(u), -dt * (euler_flux(UR) - euler_flux(UL)),
+                               rtol=0, atol=1e-15)
+
+
+def test_limited_periodic_step_is_conservative(oracle_mod):
+    """Two jumps on a periodic mesh (a Sod tube and its mirror): the limiter
+    acts and the totals stay fixed."""
+    N, nc = 4, 80
+    o = oracle_mod.Oracle(N)
+    x = o.node_x(nc)
+    inside = (x > 0.25) & (x < 0.75)
+    rho = np.where(inside, 1.0, 0.125)
+    p = np.where(inside, 1.0, 0.1)
+    u = conserved(rho, np.zeros_like(rho), p)
+    dx = 1.0 / nc
+    w = o.table("w")
+    tot = lambda U: dx * np.einsum("ckr,k->r", U.reshape(nc, N + 1, 3), w)
+    out, steps, t, rc, ttot = o.dgl_solve(u, dx, max_steps=40, bc="periodic", limiter=True)
+    assert rc == 0 and ttot > 0
+    np.testing.assert_allclose(tot(out), tot(u), rtol=2e-14, atol=2e-15)
+
+
+def density_l1(o, U, nc, test, t):
+    from oracle import riemann
+    L, R = TESTS[test]
+    gx, gw = np.polynomial.legendre.leggauss(25)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    phi = np.stack([o.phi(x) for x in gx])
+    rho_h = U.reshape(nc, o.n, 3)[:, :, 0] @ phi.T
+    xs = (np.arange(nc)[:, None] + gx[None, :]) / nc
+    re, _, _ = riemann.solution(L, R, xs, t)
+    return float((np.abs(rho_h - re) @ gw).sum() / nc)
+
+
+@pytest.mark.parametrize("test", [1, 2, 3, 4])
+def test_riemann_problems_with_limiter(oracle_mod, test):
+    """Sec. 2 classical tests, DG N = 3, outflow, CFL 0.4, t_final = 0.15: every
+    step stays physical, the L1 density error against the exact solution halves
+    (first order, as for any scheme at discontinuities) when the mesh doubles,
+    and only a few cells per step are limited (none or almost none for the two
+    rarefactions)."""
+    N = 3
+    o = oracle_mod.Oracle(N)
+    errs, per_step = [], []
+    for nc in (100, 200):
+        u = riemann_state(o, nc, test)
+        out, steps, t, rc, ttot = o.dgl_solve(u, 1.0 / nc, t_end=0.15, bc="outflow", limiter=True)
+        assert rc == 0 and t == 0.15
+        v = np.einsum("jk,ckr->cjr", o.table("P"), out.reshape(nc, N + 1, 3))
+        e_int = v[..., 2] - 0.5 * v[..., 1] ** 2 / v[..., 0]
+        assert (v[..., 0] > 0).all() and (e_int > 0).all()
+        errs.append(density_l1(o, out, nc, test, 0.15))
+        per_step.append(ttot / steps)
+    assert errs[1] < 0.6 * errs[0] and errs[1] < 0.005, errs
+    assert max(per_step) < (1.0 if test == 4 else 15.0), per_step

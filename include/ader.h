@@ -68,6 +68,10 @@ typedef enum {
  *   ader_dg_method_full.  DG scheme and ADER_PREC_FP64 only. */
 typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1 } ader_system;
 
+/* Boundary condition of the mesh ends.  ADER_BC_OUTFLOW (DG only): a boundary
+ * face sees the interior state on both sides (zero-gradient outflow). */
+typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_OUTFLOW = 1 } ader_bc;
+
 /* Uniform periodic mesh on [x0, x1]. */
 typedef struct {
   int64_t n_cells;
@@ -88,6 +92,17 @@ typedef struct {
                              waits for each graph, so per-kernel times land in ader_stats */
   int system;             /* ader_system (ADER_SYSTEM_EULER) */
   double omega;           /* reaction frequency of ADER_SYSTEM_REACTING (1.0) */
+  int bc;                 /* ader_bc (ADER_BC_PERIODIC) */
+  int limiter;            /* 1: a posteriori subcell limiter (DG, Euler; 0): the candidate of
+                             eq. ader_dg_method_full is checked on its 2N+1 subcell averages
+                             (Sec. 1.4) by the physical admissibility detector (rho > 0, e > 0)
+                             and the relaxed discrete maximum principle of eq. nad_ineq against
+                             the cell and its neighbours; troubled cells are recomputed by
+                             first-order Rusanov finite volumes on their subcells and
+                             reconstructed with R = (P^T P)^-1 P^T (eq. r_operator), the faces
+                             next to them carrying the subcell flux on both sides */
+  double nad_delta0;      /* NAD: delta = max(nad_delta0, nad_eps (max - min)) (1e-4) */
+  double nad_eps;         /* (1e-3) */
 } ader_options;
 
 typedef struct {
@@ -102,6 +117,7 @@ typedef struct {
   double predict_ms;      /* ... of the predictor kernel */
   double face_ms;         /* ... of the interface-flux + update kernel */
   int64_t kernel_launches;/* kernels the last call launched (including no-op steps after 'done') */
+  int64_t troubled_cells; /* cells the limiter recomputed, summed over the steps of the last call */
 } ader_stats;
 
 typedef struct ader_ctx ader_ctx;
@@ -132,6 +148,7 @@ ader_status ader_node_coords(const ader_ctx* ctx, double* x_host, int64_t count)
 
 /* Operator tables (host copies, row-major), for inspection:
  * name: "xi","w","psi0","psi1" (N+1), "kt","kap","dphi","dtil" ((N+1)^2), "P" ((2N+1)(N+1)),
+ * "R" ((N+1)(2N+1): (P^T P)^-1 P^T, the reconstruction of eq. r_operator),
  * "ksa","ksb" (H^2, H = (N+2)/2: k~ in even/odd form, used by the predictor for
  * N >= 4; with h = (N+1)/2, ksa[p][q] = (k~[p][q] + k~[p][N-q])/2 for p, q < h and
  * ksa[p][h] = k~[p][h] for odd N+1; ksb[p][q] = (k~[p][q] - k~[p][N-q])/2 for

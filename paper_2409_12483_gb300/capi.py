@@ -26,6 +26,7 @@ ADER_ERR_STATE = 7
 SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2}
 SYSTEMS = {"euler": 0, "reacting": 1}
+BOUNDARIES = {"periodic": 0, "outflow": 1}
 SYSTEM_VARS = {0: 3, 1: 5}
 
 
@@ -43,14 +44,17 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
                 ("picard_max_iter", C.c_int), ("picard_fixed_iter", C.c_int),
                 ("precision", C.c_int), ("fp64_sweeps", C.c_int), ("fp32_tol", C.c_double),
-                ("profile", C.c_int), ("system", C.c_int), ("omega", C.c_double)]
+                ("profile", C.c_int), ("system", C.c_int), ("omega", C.c_double),
+                ("bc", C.c_int), ("limiter", C.c_int), ("nad_delta0", C.c_double),
+                ("nad_eps", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("t", C.c_double), ("cells", C.c_int64),
                 ("max_iters", C.c_int), ("mean_iters", C.c_double), ("status", C.c_int),
                 ("profiled_steps", C.c_int64), ("weno_ms", C.c_double), ("predict_ms", C.c_double),
-                ("face_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("face_ms", C.c_double), ("kernel_launches", C.c_int64),
+                ("troubled_cells", C.c_int64)]
 
 
 class Tuning(C.Structure):
@@ -164,6 +168,10 @@ def default_options(**kw) -> Options:
             v = PRECISIONS[v]
         if k == "system" and isinstance(v, str):
             v = SYSTEMS[v]
+        if k == "bc" and isinstance(v, str):
+            v = BOUNDARIES[v]
+        if k == "limiter" and isinstance(v, bool):
+            v = int(v)
         setattr(o, k, v)
     return o
 
@@ -255,12 +263,15 @@ class Context:
         n = self.n
         H = (n + 1) // 2
         size = {"xi": n, "w": n, "psi0": n, "psi1": n, "P": (2 * self.degree + 1) * n,
-                "ksa": H * H, "ksb": H * H, "wamono": 3 * n * n}.get(name, n * n)
+                "ksa": H * H, "ksb": H * H, "wamono": 3 * n * n,
+                "R": n * (2 * self.degree + 1)}.get(name, n * n)
         out = np.zeros(size)
         self._check(self._L.ader_get_table(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
                                            size))
         if name in ("xi", "w", "psi0", "psi1"):
             return out
+        if name == "R":
+            return out.reshape(n, -1)
         return out.reshape(-1, H if name in ("ksa", "ksb") else n)
 
     # -- hot path (same names as the C ABI) --
@@ -354,7 +365,7 @@ class Context:
                 "mean_iters": s.mean_iters, "status": s.status,
                 "profiled_steps": s.profiled_steps, "weno_ms": s.weno_ms,
                 "predict_ms": s.predict_ms, "face_ms": s.face_ms,
-                "kernel_launches": s.kernel_launches}
+                "kernel_launches": s.kernel_launches, "troubled_cells": s.troubled_cells}
 
 
 class NoAllocStep:

@@ -50,6 +50,9 @@ struct ader_ctx {
   double* wrec = nullptr;
   double* ubuf = nullptr;
   double* hbuf = nullptr;
+  double* lim_mm = nullptr;   // limiter: subcell extrema of u^n [cell][6]
+  double* lim_vb = nullptr;   // limiter: first / last subcell averages of u^n [cell][6]
+  int* lim_flag = nullptr;    // limiter: troubled flags [cell]
   // cached solve graph
   cudaGraphExec_t gexec = nullptr;
   const double* g_u = nullptr;
@@ -103,7 +106,16 @@ size_t workspace_bytes(const ader_ctx* c) {
   b += align_up(trace_doubles(c) * sizeof(double));
   if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
   b += 2 * align_up((size_t)state_count(c) * sizeof(double));
+  if (c->opt.limiter)
+    b += 2 * align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
+         align_up((size_t)c->mesh.n_cells * sizeof(int));
   return b;
+}
+
+int kernels_per_step(const ader_ctx* c) {
+  int k = c->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
+  if (c->opt.limiter) k += 3;
+  return k;
 }
 
 StepParams make_step(const ader_ctx* c, int mode, int par, double dt, double t_end,
@@ -156,6 +168,7 @@ FaceParams make_face(const ader_ctx* c, const double* v_old, double* u_new, cons
   f.want_lambda = want_lambda;
   f.cpf = c->tune.face_cells_per_block;
   f.sys = c->opt.system;
+  f.bc = c->opt.bc;
   f.Ns = c->basis.Ns;
   f.gamma = c->opt.gamma;
   f.gm1 = c->opt.gamma - 1.0;
@@ -170,9 +183,7 @@ ader_status need_bound(ader_ctx* ctx) {
   return ADER_OK;
 }
 
-// enqueue the CFL kernel into lam[slot] (resets the slot first)
-ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
-  CK(cudaMemsetAsync(&ctx->ctl->lam[slot], 0, sizeof(unsigned long long), ctx->stream));
+CflParams make_cfl(const ader_ctx* ctx, const double* u, int slot) {
   CflParams p{};
   p.u = u;
   p.ncells = ctx->mesh.n_cells;
@@ -184,8 +195,39 @@ ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
   p.gm1 = ctx->opt.gamma - 1.0;
   p.ctl = ctx->ctl;
   p.ops = ctx->basis.d;
+  return p;
+}
+
+// enqueue the CFL kernel into lam[slot] (resets the slot first)
+ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
+  CK(cudaMemsetAsync(&ctx->ctl->lam[slot], 0, sizeof(unsigned long long), ctx->stream));
+  CflParams p = make_cfl(ctx, u, slot);
   CK(do_cfl(ctx->N, p, ctx->stream));
   ctx->launches += 1;
+  return ADER_OK;
+}
+
+// the a posteriori subcell limiter on the candidate in dst (u^n in src)
+ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp) {
+  LimParams l{};
+  l.u_old = src;
+  l.u = dst;
+  l.trace = ctx->trace;
+  l.mm = ctx->lim_mm;
+  l.vb = ctx->lim_vb;
+  l.troubled = ctx->lim_flag;
+  l.ncells = ctx->mesh.n_cells;
+  l.bc = ctx->opt.bc;
+  l.Ns = ctx->basis.Ns;
+  l.gamma = ctx->opt.gamma;
+  l.gm1 = ctx->opt.gamma - 1.0;
+  l.delta0 = ctx->opt.nad_delta0;
+  l.eps = ctx->opt.nad_eps;
+  l.sp = sp;
+  l.ops = ctx->basis.d;
+  std::memcpy(l.R, ctx->basis.R, sizeof(l.R));
+  CK(do_limiter(ctx->N, l, ctx->stream));
+  ctx->launches += 3;
   return ADER_OK;
 }
 
@@ -208,10 +250,21 @@ ader_status enqueue_step(ader_ctx* ctx, const double* src, double* dst, const St
   PredictParams p = make_predict(ctx, nodal, sp);
   CK(do_predict(ctx->N, p, ctx->stream));
   if (ev) CK(cudaEventRecordWithFlags(ev[2], ctx->stream, cudaEventRecordExternal));
-  FaceParams f = make_face(ctx, src, dst, sp, want_lambda);
+  FaceParams f = make_face(ctx, src, dst, sp, ctx->opt.limiter ? 0 : want_lambda);
   CK(do_face(ctx->N, f, ctx->stream));
-  if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
   ctx->launches += ctx->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
+  if (ctx->opt.limiter) {
+    ader_status st = enqueue_limiter(ctx, src, dst, sp);
+    if (st != ADER_OK) return st;
+    // lambda_max of the limited state for the next step (the predictor of this
+    // step has reset the slot)
+    if (want_lambda) {
+      CflParams c = make_cfl(ctx, dst, sp.par ^ 1);
+      CK(do_cfl(ctx->N, c, ctx->stream));
+      ctx->launches += 1;
+    }
+  }
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
   return ADER_OK;
 }
 
@@ -285,6 +338,10 @@ ader_status ader_default_options(ader_options* o) {
   o->profile = 0;
   o->system = ADER_SYSTEM_EULER;
   o->omega = 1.0;
+  o->bc = ADER_BC_PERIODIC;
+  o->limiter = 0;
+  o->nad_delta0 = 1e-4;
+  o->nad_eps = 1e-3;
   return ADER_OK;
 }
 
@@ -318,7 +375,11 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
       (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000 ||
       (o.system != ADER_SYSTEM_EULER && o.system != ADER_SYSTEM_REACTING) ||
       (o.system == ADER_SYSTEM_REACTING &&
-       (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || !std::isfinite(o.omega)))) {
+       (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || !std::isfinite(o.omega))) ||
+      (o.bc != ADER_BC_PERIODIC && o.bc != ADER_BC_OUTFLOW) ||
+      (o.bc == ADER_BC_OUTFLOW && scheme != ADER_SCHEME_DG) || (o.limiter != 0 && o.limiter != 1) ||
+      (o.limiter && (scheme != ADER_SCHEME_DG || o.system != ADER_SYSTEM_EULER)) ||
+      !(o.nad_delta0 >= 0.0) || !(o.nad_eps >= 0.0)) {
     delete c;
     return ADER_ERR_ARG;
   }
@@ -389,6 +450,13 @@ ader_status ader_get_table(const ader_ctx* c, const char* name, double* out, int
   if (!strcmp(name, "dphi")) return mat(c->basis.dphi, n);
   if (!strcmp(name, "dtil")) return mat(c->basis.dtil, n);
   if (!strcmp(name, "P")) return mat(d.P, c->basis.Ns);
+  if (!strcmp(name, "R")) {  // [n][Ns]
+    const int Ns = c->basis.Ns;
+    if (count != (int64_t)n * Ns) return ADER_ERR_ARG;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < Ns; ++j) out[k * Ns + j] = c->basis.R[k][j];
+    return ADER_OK;
+  }
   const int H = (n + 1) / 2;
   auto half = [&](const double (*src)[kMaxH]) -> ader_status {
     if (count != (int64_t)H * H) return ADER_ERR_ARG;
@@ -448,6 +516,14 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
   ctx->ubuf = reinterpret_cast<double*>(p);
   p += align_up((size_t)state_count(ctx) * sizeof(double));
   ctx->hbuf = reinterpret_cast<double*>(p);
+  p += align_up((size_t)state_count(ctx) * sizeof(double));
+  if (ctx->opt.limiter) {
+    ctx->lim_mm = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
+    ctx->lim_vb = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
+    ctx->lim_flag = reinterpret_cast<int*>(p);
+  }
   return ADER_OK;
 }
 
@@ -522,6 +598,7 @@ ader_status ader_correct(ader_ctx* ctx, const double* u, const double* q, double
   CK(do_predict(ctx->N, p, ctx->stream));
   FaceParams f = make_face(ctx, u, u_new, sp, 0);
   CK(do_face(ctx->N, f, ctx->stream));
+  if (ctx->opt.limiter && (st = enqueue_limiter(ctx, u, u_new, sp)) != ADER_OK) return st;
   return join_out(ctx);
 }
 
@@ -662,7 +739,8 @@ static ader_status solve_impl(ader_ctx* ctx, double* u, double t0, double t_end,
     }
     if (launches >= max_launches) break;
   }
-  ctx->launches += launches * (long long)K * (ctx->scheme == ADER_SCHEME_WENO_FV ? 3 : 2);
+  ctx->launches += launches * (long long)K * kernels_per_step(ctx) +
+                   (ctx->opt.limiter ? launches * (long long)K : 0);  // + the CFL after the limiter
   CK(cudaMemcpyAsync(&ctx->hflags[0].status, &ctx->ctl->status, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hflags[0].steps, &ctx->ctl->steps, sizeof(long long),
@@ -734,6 +812,7 @@ ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out) {
   out->predict_ms = ctx->prof_ms[1];
   out->face_ms = ctx->prof_ms[2];
   out->kernel_launches = ctx->launches;
+  out->troubled_cells = (int64_t)h.troubled;
   return ADER_OK;
 }
 
@@ -794,6 +873,8 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
   if (!u || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, ADER_ERR_ARG, "ader_step_noalloc needs dt > 0");
+  if (ctx->opt.limiter)
+    return fail(ctx, ADER_ERR_ARG, "the limiter keeps per-cell data in the bound workspace");
   const size_t trace_bytes = trace_doubles(ctx) * sizeof(double);
   const size_t wrec_bytes =
       ctx->scheme == ADER_SCHEME_WENO_FV ? (size_t)ctx->mesh.n_cells * ctx->n * kM * sizeof(double) : 0;

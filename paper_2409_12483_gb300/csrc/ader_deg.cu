@@ -3,6 +3,7 @@
 // degrees build in parallel and each kernel is fully unrolled for its N.
 #include "ader_kernels.cuh"
 #include "ader_source.cuh"
+#include "ader_limiter.cuh"
 
 #ifndef ADER_DEG
 #error "compile with -DADER_DEG=<0..7>"
@@ -136,6 +137,15 @@ cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStre
     case 32: return launch_predict_cpb<32>(p, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t s) {
+  const unsigned g256 = grid_for(p.ncells, 256, 0x7fffffffLL);
+  const unsigned g128 = grid_for(p.ncells, 128, 0x7fffffffLL);
+  lim_minmax_kernel<D><<<g256, 256, 0, s>>>(p);
+  lim_detect_kernel<D><<<g256, 256, 0, s>>>(p);
+  lim_fix_kernel<D><<<g128, 128, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {

@@ -31,6 +31,7 @@ struct DevCtl {
   long long iter_cells;
   int iter_max;
   int pad_;
+  unsigned long long troubled;  // cells marked by the limiter's detectors (summed over steps)
 };
 
 // How a launch gets its time step.

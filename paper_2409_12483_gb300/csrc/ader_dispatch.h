@@ -42,6 +42,9 @@ inline cudaError_t do_cfl(int N, const CflParams& p, cudaStream_t s) { ADER_DISP
 inline cudaError_t do_weno(int N, const WenoParams& p, cudaStream_t s) {
   ADER_DISPATCH(launch_weno, N, p, s)
 }
+inline cudaError_t do_limiter(int N, const LimParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_limiter, N, p, s)
+}
 
 
 #define ADER_DISPATCH4(fn, N, a, b, c, d) \

@@ -894,6 +894,10 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
     const long long cl = wrap_cell(c0 + f - 1, io.ncells), cr = wrap_cell(c0 + f, io.ncells);
     const double* ta = io.trace + cl * stride + l0 * kM;          // qR of the left cell
     const double* tb = io.trace + cr * stride + n * kM + l0 * kM; // qL of the right cell
+    if (P.bc == kBcOutflow) {  // a boundary face sees the interior trace on both sides
+      if (c0 + f == 0) ta = tb;
+      if (c0 + f == io.ncells) tb = ta;
+    }
     double a[kM], b[kM], G2[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {

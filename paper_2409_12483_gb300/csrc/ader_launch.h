@@ -11,6 +11,7 @@ namespace ader {
 
 enum : int { kOutQ = 0, kOutTrace = 1 };
 enum : int { kSysEuler = 0, kSysReacting = 1 };
+enum : int { kBcPeriodic = 0, kBcOutflow = 1 };
 
 // LST-DG predictor (Algorithm lst_dg_predictor, S = B = 0) with its epilogue.
 struct PredictParams {
@@ -48,6 +49,7 @@ struct FaceParams {
   int want_lambda;
   int cpf;               // interface/update cells per block (32, 64; tuned), 0 = 64
   int sys;               // kSysEuler or kSysReacting
+  int bc;                // kBcPeriodic or kBcOutflow
   int Ns;
   double gamma, gm1;
   StepParams sp;
@@ -97,6 +99,24 @@ struct WenoParams {
   WenoOps wo;
 };
 
+// A posteriori subcell limiter of the DG scheme (ader_limiter.cuh).
+struct LimParams {
+  const double* u_old;   // u^n, [cell][n][3]
+  double* u;             // in: candidate u*, out: u^{n+1} (same layout)
+  const double* trace;   // predictor traces [cell][qR(3n) | qL(3n) | u + volume(3n)]
+  double* mm;            // [cell][6]: min (3), max (3) of the subcell averages of u^n
+  double* vb;            // [cell][6]: P u^n of the first (3) and last (3) subcell
+  int* troubled;         // [cell]
+  long long ncells;
+  int bc;                // kBcPeriodic or kBcOutflow
+  int Ns;
+  double gamma, gm1;
+  double delta0, eps;    // NAD tolerances
+  StepParams sp;
+  OpsD ops;
+  double R[kMaxN][kMaxNs];  // reconstruction from subcell averages
+};
+
 // Per-degree entry points (defined in ader_deg.cu compiled once per degree).
 #define ADER_DECLARE_DEGREE(D)                                                         \
   cudaError_t launch_predict_##D(const PredictParams& p, cudaStream_t s);              \
@@ -107,6 +127,7 @@ struct WenoParams {
                                        cudaStream_t s);                                 \
   cudaError_t launch_face_multi_##D(const FaceParams& p, const MultiArgs& m, int grid,     \
                                     cudaStream_t s);                                    \
+  cudaError_t launch_limiter_##D(const LimParams& p, cudaStream_t s);                   \
   cudaError_t prepare_degree_##D();
 
 ADER_DECLARE_DEGREE(0)

@@ -240,6 +240,28 @@ int build_basis(int N, bool weno, Basis* out) {
       d.P[j][k] = (double)s;
     }
 
+  // pseudo-inverse of the subcell projection: R = (P^T P)^-1 P^T (eq. r_operator)
+  {
+    ld PtP[kMaxN][kMaxN], Pt[kMaxN][kMaxN];
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < n; ++l) {
+        ld s = 0;
+        for (int j = 0; j < out->Ns; ++j) s += (ld)d.P[j][k] * (ld)d.P[j][l];
+        PtP[k][l] = s;
+      }
+    // solve PtP X = P^T column block by block (n x Ns right-hand sides, in chunks of n)
+    for (int j0 = 0; j0 < out->Ns; j0 += n) {
+      const int m = (out->Ns - j0) < n ? (out->Ns - j0) : n;
+      ld A[kMaxN][kMaxN];
+      for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) A[k][l] = PtP[k][l];
+      for (int k = 0; k < n; ++k)
+        for (int c = 0; c < m; ++c) Pt[k][c] = (ld)d.P[j0 + c][k];
+      if (lu_solve(n, A, Pt, m)) return -6;
+      for (int k = 0; k < n; ++k)
+        for (int c = 0; c < m; ++c) out->R[k][j0 + c] = (double)Pt[k][c];
+    }
+  }
   if (weno) {
     if (N < 2 || (N % 2) != 0) return -3;
     WenoOps& wo = out->weno;

@@ -73,6 +73,7 @@ struct Basis {
   // extra host-only tables for inspection
   double dphi[kMaxN][kMaxN]{};    // dphi[k][l] = phi_k'(xi_l)
   double dtil[kMaxN][kMaxN]{};    // D~[k][l]
+  double R[kMaxN][kMaxNs]{};      // (P^T P)^-1 P^T: DG coefficients from subcell averages (eq. r_operator)
 };
 
 // Returns 0 on success.  weno != 0 also builds the WENO tables (N even, 2 <= N).

@@ -392,6 +392,10 @@ __global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
     const long long cl = wrap_cell(c0 + f - 1, P.ncells), cr = wrap_cell(c0 + f, P.ncells);
     const double* ta = P.trace + cl * (3 * RS) + l0 * M;       // qR of the left cell
     const double* tb = P.trace + cr * (3 * RS) + RS + l0 * M;  // qL of the right cell
+    if (P.bc == kBcOutflow) {  // a boundary face sees the interior trace on both sides
+      if (c0 + f == 0) ta = tb;
+      if (c0 + f == P.ncells) tb = ta;
+    }
     double a[M], b[M], G2[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) {

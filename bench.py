@@ -282,6 +282,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=128)
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the coarse-mesh convergence sweeps of the four precision forms")
+    ap.add_argument("--no-limiter", action="store_true",
+                    help="skip the subcell limiter's Riemann problems and throughput")
     ap.add_argument("--no-source", action="store_true",
                     help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
@@ -416,6 +418,8 @@ def main():
             line["convergence"] = run_convergence(dev)
         if not args.no_source:
             line["source_terms"] = run_source(args, dev, flush)
+        if not args.no_limiter:
+            line["limiter"] = run_limiter(args, dev, flush)
         line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
@@ -565,6 +569,77 @@ def run_source(args, dev, flush):
             b["order_local"] = [math.log(x / y) / r for x, y in zip(a["local"], b["local"])]
         out["ode"].append({"degree": N, "theory_global": 2 * N + 1, "theory_local": N + 1,
                            "rows": rows})
+    return out
+
+
+def riemann_density_l1(ctx, u, test, t, npts=25):
+    """L1 density error of a DG state against the exact Riemann solution (the
+    library's own nodes, npts-point GL rule per cell); measurement code."""
+    import numpy as np
+
+    import workloads as W
+    xi = ctx.table("xi")
+    n = len(xi)
+    u = np.asarray(u).reshape(-1, n, 3)
+    nc = u.shape[0]
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    rho = u[:, :, 0] @ lagrange_matrix(gx, xi).T
+    xs = (np.arange(nc)[:, None] + gx[None, :]) / nc
+    L, R = W.RIEMANN_TESTS[test]
+    exact, _, _ = W.riemann_solution(L, R, xs, t)
+    return float((np.abs(rho - exact) @ gw).sum() / nc)
+
+
+def run_limiter(args, dev, flush):
+    """The a posteriori subcell limiter with outflow boundaries: the four
+    classical Riemann problems of Sec. 2 (Table classical_tests_1d) to t = 0.15
+    (L1 density error against the exact solution, troubled cells per step), and
+    throughput at the headline's size: Sod data, and the smooth headline data
+    with the limiter on against off (the limiter's cost where it never acts)."""
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    out = {"riemann": [], "throughput": []}
+    for test in (1, 2, 3, 4):
+        for N in (3, 5):
+            for nc in (200, 1000):
+                ctx = Context(nc, N, "dg", device=dev, bc="outflow", limiter=1)
+                u = torch.tensor(W.riemann_initial(ctx.node_coords(), test), device=dev).reshape(-1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                steps, t, rc = ctx.ader_solve(u, t_end=0.15)
+                e1.record()
+                torch.cuda.synchronize()
+                st = ctx.ader_get_stats()
+                out["riemann"].append({
+                    "test": test, "degree": N, "cells": nc, "steps": steps, "status": rc,
+                    "l1_density_vs_exact": riemann_density_l1(ctx, u.cpu().numpy(), test, t),
+                    "troubled_per_step": st["troubled_cells"] / max(steps, 1),
+                    "ms": e0.elapsed_time(e1)})
+                del ctx
+    st_ = max(2, min(args.steps, 3))
+    ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, bc="outflow", limiter=1)
+    u0 = torch.tensor(W.riemann_initial(ctx.node_coords(), 1), device=dev).reshape(-1)
+    line = variant_line("sod-dg5-1e5-limiter", "Sod data (Table classical_tests_1d test 1), DG N=5, "
+                        "10^5 cells, outflow, subcell limiter, 100 steps, FP64",
+                        ctx, u0, CELLS, DEGREE, TIME_STEPS, st_, 2, flush)
+    line["troubled_per_step"] = ctx.ader_get_stats()["troubled_cells"] / TIME_STEPS
+    for k in ("predict_fp64_tflops", "predict_frac_of_fp64_peak"):
+        line.pop(k, None)
+    out["throughput"].append(line)
+    del ctx
+    for lim in (1, 0):
+        ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, limiter=lim)
+        u0 = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+        line = variant_line(f"dg5-1e5-modes4-limiter{lim}", "the headline workload, limiter "
+                            + ("on (never triggered on smooth data)" if lim else "off"),
+                            ctx, u0, CELLS, DEGREE, TIME_STEPS, st_, 2, flush)
+        line["troubled_cells"] = ctx.ader_get_stats()["troubled_cells"]
+        out["throughput"].append(line)
+        del ctx
     return out
 
 

@@ -68,8 +68,10 @@ typedef enum {
  *   ader_dg_method_full.  DG scheme and ADER_PREC_FP64 only. */
 typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1 } ader_system;
 
-/* Boundary condition of the mesh ends.  ADER_BC_OUTFLOW (DG only): a boundary
- * face sees the interior state on both sides (zero-gradient outflow). */
+/* Boundary condition of the mesh ends.  ADER_BC_OUTFLOW (DG only): free outflow;
+ * the ghost side of a boundary face holds the boundary cell's mean state of the
+ * step's initial data (a uniform state passes unchanged; the Rusanov
+ * dissipation damps trace-mean differences at the boundary). */
 typedef enum { ADER_BC_PERIODIC = 0, ADER_BC_OUTFLOW = 1 } ader_bc;
 
 /* Uniform periodic mesh on [x0, x1]. */

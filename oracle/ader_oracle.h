@@ -178,8 +178,12 @@ int ob_rs_solve(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double
 /* ------------------------------------------------------------------------
  * Boundaries and the a posteriori subcell limiter (ader_oracle_lim.c), DG, Euler.
  *
- * bc: 0 periodic, 1 outflow (zero gradient: the boundary face sees the
- * interior state on both sides).  limiter != 0: the candidate u* of eq.
+ * bc: 0 periodic, 1 outflow (free outflow: the ghost side of a boundary face
+ * holds the boundary cell's mean state of u^n; a first reading, with the
+ * interior trace on both sides, made the high-order boundary cells unstable --
+ * rounding noise of a uniform state grew without bound at N = 5).  For the
+ * limiter's first-order subcell fluxes the ghost subcell is the boundary
+ * subcell.  limiter != 0: the candidate u* of eq.
  * ader_dg_method_full is checked cell by cell on its 2N+1 subcell averages
  * P u* (Sec. 1.4, eq. p_operator) by the physical admissibility detector
  * (rho > 0, e > 0) and the relaxed discrete maximum principle of eq. nad_ineq

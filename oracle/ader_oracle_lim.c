@@ -141,15 +141,28 @@ int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, 
     }
     traces(b, q + i * qs, qR + i * us, qL + i * us);
   }
+  /* outflow ghosts: the boundary cell's mean state of u^n at every tau node */
+  double ghost_l[NM * MM], ghost_r[NM * MM];
+  for (int r = 0; r < MM; ++r) {
+    double ml = 0.0, mr = 0.0;
+    for (int k = 0; k < n; ++k) {
+      ml += b->w[k] * u[k * MM + r];
+      mr += b->w[k] * u[(ncells - 1) * us + k * MM + r];
+    }
+    for (int l0 = 0; l0 < n; ++l0) {
+      ghost_l[l0 * MM + r] = ml;
+      ghost_r[l0 * MM + r] = mr;
+    }
+  }
   /* face fluxes with the boundary condition */
   for (int64_t f = 0; f <= ncells; ++f) {
     const double *left, *right;
     if (f == 0)
-      left = outflow ? qL : qR + (ncells - 1) * us;
+      left = outflow ? ghost_l : qR + (ncells - 1) * us;
     else
       left = qR + (f - 1) * us;
     if (f == ncells)
-      right = outflow ? qR + (ncells - 1) * us : qL;
+      right = outflow ? ghost_r : qL;
     else
       right = qL + f * us;
     dg_face(b, p, lam, left, right, G + f * MM);

@@ -894,15 +894,23 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
     const long long cl = wrap_cell(c0 + f - 1, io.ncells), cr = wrap_cell(c0 + f, io.ncells);
     const double* ta = io.trace + cl * stride + l0 * kM;          // qR of the left cell
     const double* tb = io.trace + cr * stride + n * kM + l0 * kM; // qL of the right cell
-    if (P.bc == kBcOutflow) {  // a boundary face sees the interior trace on both sides
-      if (c0 + f == 0) ta = tb;
-      if (c0 + f == io.ncells) tb = ta;
-    }
     double a[kM], b[kM], G2[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
       a[r] = ta[r];
       b[r] = tb[r];
+    }
+    if (P.bc == kBcOutflow && (c0 + f == 0 || c0 + f == io.ncells)) {
+      // free outflow: the ghost side holds the boundary cell's mean of u^n
+      const long long cb = c0 + f == 0 ? 0 : io.ncells - 1;
+      double* g = c0 + f == 0 ? a : b;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        double m = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) m = fma(sh.w[k], io.v_old[(cb * n + k) * kM + r], m);
+        g[r] = m;
+      }
     }
     rusanov2(a, b, G2, P.gamma, P.gm1);
 #pragma unroll

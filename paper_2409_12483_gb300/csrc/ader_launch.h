@@ -42,7 +42,7 @@ struct PredictParams {
 // DG / FV update and, optionally, the lambda_max reduction for the next step.
 struct FaceParams {
   const double* trace;
-  const double* v_old;   // FV: previous cell averages
+  const double* v_old;   // FV: previous cell averages; DG: u^n (outflow ghost states)
   double* u_new;
   long long ncells;
   int dg;

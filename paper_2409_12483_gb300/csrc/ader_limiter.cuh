@@ -132,13 +132,23 @@ __device__ __forceinline__ void lim_dg_face(const LimParams& P, long long f, dou
                                             double* G) {
   constexpr int n = N + 1, stride = 9 * n;
   const long long cl = lim_neighbour(f - 1, P.ncells, P.bc), cr = lim_neighbour(f, P.ncells, P.bc);
+  // outflow boundary: the ghost side holds the boundary cell's mean of u^n
+  double ghost[kM];
+  if (cl < 0 || cr < 0) {
+    const long long cb = cl < 0 ? cr : cl;
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      double m = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) m = fma(P.ops.w[k], P.u_old[(cb * n + k) * kM + r], m);
+      ghost[r] = m;
+    }
+  }
   double s[kM] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int l0 = 0; l0 < n; ++l0) {
-    const double* ta = cl >= 0 ? P.trace + cl * stride + l0 * kM : nullptr;
-    const double* tb = cr >= 0 ? P.trace + cr * stride + n * kM + l0 * kM : nullptr;
-    if (!ta) ta = tb;  // outflow boundary: the interior trace on both sides
-    if (!tb) tb = ta;
+    const double* ta = cl >= 0 ? P.trace + cl * stride + l0 * kM : ghost;
+    const double* tb = cr >= 0 ? P.trace + cr * stride + n * kM + l0 * kM : ghost;
     double a[kM], b[kM], G2[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {

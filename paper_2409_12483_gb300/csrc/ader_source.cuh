@@ -392,15 +392,23 @@ __global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
     const long long cl = wrap_cell(c0 + f - 1, P.ncells), cr = wrap_cell(c0 + f, P.ncells);
     const double* ta = P.trace + cl * (3 * RS) + l0 * M;       // qR of the left cell
     const double* tb = P.trace + cr * (3 * RS) + RS + l0 * M;  // qL of the right cell
-    if (P.bc == kBcOutflow) {  // a boundary face sees the interior trace on both sides
-      if (c0 + f == 0) ta = tb;
-      if (c0 + f == P.ncells) tb = ta;
-    }
     double a[M], b[M], G2[M];
 #pragma unroll
     for (int r = 0; r < M; ++r) {
       a[r] = ta[r];
       b[r] = tb[r];
+    }
+    if (P.bc == kBcOutflow && (c0 + f == 0 || c0 + f == P.ncells)) {
+      // free outflow: the ghost side holds the boundary cell's mean of u^n
+      const long long cb = c0 + f == 0 ? 0 : P.ncells - 1;
+      double* g = c0 + f == 0 ? a : b;
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        double m = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) m = fma(sh.base.w[k], P.v_old[(cb * n + k) * M + r], m);
+        g[r] = m;
+      }
     }
     rusanov2_src(a, b, G2, P.gamma, P.gm1);
 #pragma unroll

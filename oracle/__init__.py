@@ -145,6 +145,8 @@ def lib():
                                    C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
                                    P(C.c_double)]
             L.ob_r_matrix.argtypes = [P(Basis), _DP]
+            L.ob_lim_weno2.argtypes = [_DP, _DP, _DP, _DP, _DP]
+            L.ob_lim_weno2.restype = None
             L.ob_dgl_step.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double,
                                       C.c_double, _DP, _DP, C.c_void_p, P(Stats)]
             L.ob_dgl_solve.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double, _DP,
@@ -332,9 +334,19 @@ class Oracle:
         return R.reshape(self.n, self.basis.Ns)
 
     @staticmethod
-    def lim_params(bc: str = "periodic", limiter: bool = True, delta0: float = 1e-4,
+    def lim_params(bc: str = "periodic", limiter: bool | int = True, delta0: float = 1e-4,
                    eps: float = 1e-3):
-        return LimParams(1 if bc == "outflow" else 0, 1 if limiter else 0, delta0, eps)
+        """limiter: False / 0 off, True / 1 detect and recompute troubled cells, 2 every
+        cell recomputed by the subcell ADER-WENO2 scheme"""
+        return LimParams(1 if bc == "outflow" else 0, int(limiter), delta0, eps)
+
+    def weno2(self, vm, v0, vp):
+        """degree-1 WENO nodal values [2][3] on a subcell with averages v0 and
+        neighbours vm, vp (the reconstruction of the subcell ADER-WENO2 scheme)"""
+        w = np.zeros(2 * M)
+        xi = Oracle(1).table("xi")
+        lib().ob_lim_weno2(_arr(vm, M), _arr(v0, M), _arr(vp, M), _arr(xi, 2), w)
+        return w.reshape(2, M)
 
     def dgl_step(self, u, dx, dt, bc: str = "periodic", limiter: bool = True):
         u = _arr(u)

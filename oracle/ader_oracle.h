@@ -182,26 +182,33 @@ int ob_rs_solve(const ob_basis* b, const ob_rs_params* p, int64_t ncells, double
  * holds the boundary cell's mean state of u^n; a first reading, with the
  * interior trace on both sides, made the high-order boundary cells unstable --
  * rounding noise of a uniform state grew without bound at N = 5).  For the
- * limiter's first-order subcell fluxes the ghost subcell is the boundary
- * subcell.  limiter != 0: the candidate u* of eq.
+ * limiter's subcell fluxes the ghost subcells are the boundary subcell.
+ * limiter 1 (N >= 1): the candidate u* of eq.
  * ader_dg_method_full is checked cell by cell on its 2N+1 subcell averages
  * P u* (Sec. 1.4, eq. p_operator) by the physical admissibility detector
  * (rho > 0, e > 0) and the relaxed discrete maximum principle of eq. nad_ineq
  * against the subcell averages P u^n of the cell and its neighbours
- * (delta = max(delta0, eps (max - min))); troubled cells are recomputed by a
- * first-order Rusanov finite-volume scheme on their 2N+1 subcells and
- * reconstructed with the pseudo-inverse R = (P^T P)^-1 P^T (eq. r_operator);
- * faces next to a troubled cell carry the subcell flux on both sides (the DG
- * neighbour's update is corrected with it), so the step stays conservative.
- * If R v has an inadmissible subcell average, the cell takes the mean of v.
+ * (delta = max(delta0, eps (max - min))); troubled cells are recomputed by the
+ * finite-volume ADER-WENO2 scheme (WENO reconstruction of degree 1, LST-DG
+ * predictor of degree 1, Rusanov flux) on their 2N+1 subcells, from the subcell
+ * averages P u^n, and reconstructed with the pseudo-inverse R = (P^T P)^-1 P^T
+ * (eq. r_operator); faces next to a troubled cell carry the subcell flux on
+ * both sides (the DG neighbour's update is corrected with it), so the step
+ * stays conservative.  If R v has an inadmissible subcell average, the cell
+ * takes the mean of v.  limiter 2: every cell is troubled (the ADER-WENO2
+ * scheme on the subgrid, with the projection P R after each step).
  * ---------------------------------------------------------------------- */
 typedef struct {
   int bc;          /* 0 periodic, 1 outflow */
-  int limiter;     /* 0 off, 1 on */
+  int limiter;     /* 0 off, 1 on, 2 every cell recomputed on its subcells */
   double delta0;   /* NAD absolute tolerance (1e-4) */
   double eps;      /* NAD relative tolerance (1e-3) */
 } ob_lim_params;
 
+/* degree-1 WENO nodal values w[2][3] at the nodes xi[2] of a subcell with
+ * averages v0 and neighbours vm (left), vp (right) */
+void ob_lim_weno2(const double* vm, const double* v0, const double* vp, const double* xi,
+                  double* w);
 /* R = (P^T P)^-1 P^T, [n][Ns] row-major */
 int ob_r_matrix(const ob_basis* b, double* R);
 int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, int64_t ncells,

@@ -102,6 +102,58 @@ static void project(const ob_basis* b, const double* u, double* v) {
     }
 }
 
+/* WENO reconstruction of degree 1 on one subcell (the reconstruction of the
+ * ADER-WENO2 subcell scheme): the two candidate linear polynomials with the
+ * subcell's average v0 and the average of one neighbour (stencils {j-1, j} and
+ * {j, j+1}); smoothness sigma_S = int_0^1 (dw_S/dxi)^2 dxi = slope_S^2; weights
+ * omega_S = w~_S / sum w~, w~_S = lambda_S / (sigma_S + eps)^r with lambda_S = 1,
+ * eps = 1e-14, r = 8 (the constants of the WENO reading of eq. weno_reconstr);
+ * nodal values at the two Gauss nodes xi_k of the subcell. */
+void ob_lim_weno2(const double* vm, const double* v0, const double* vp, const double* xi,
+                  double* w) {
+  for (int r = 0; r < MM; ++r) {
+    const double sl = v0[r] - vm[r], sr = vp[r] - v0[r];
+    const double al = 1.0 / pow(sl * sl + 1.0e-14, 8.0);
+    const double ar = 1.0 / pow(sr * sr + 1.0e-14, 8.0);
+    const double slope = (al * sl + ar * sr) / (al + ar);
+    for (int k = 0; k < 2; ++k) w[k * MM + r] = v0[r] + slope * (xi[k] - 0.5);
+  }
+}
+
+/* subcell g of the global subcell grid (cell i, subcell j: g = i Ns + j) with
+ * the boundary condition: periodic wrap, or (outflow) the boundary subcell */
+static const double* sub_v(const double* V, int64_t g, int64_t nsub, int outflow) {
+  if (outflow) {
+    if (g < 0) g = 0;
+    if (g >= nsub) g = nsub - 1;
+  } else {
+    while (g < 0) g += nsub;
+    while (g >= nsub) g -= nsub;
+  }
+  return V + g * MM;
+}
+
+/* ADER-WENO2 flux through the face between subcells g-1 and g: WENO
+ * reconstruction of degree 1 on both subcells, the LST-DG predictor of degree 1
+ * on each (subcell width dx / Ns, so dt / (dx / Ns) = Ns lam), and the
+ * time-integrated Rusanov flux of their traces, rescaled by lam = dt / dx like
+ * the DG face fluxes. */
+static int sub_face(const ob_basis* b1, const ob_params* p, double lam, int Ns, const double* V,
+                    int64_t nsub, int outflow, int64_t g, double* G) {
+  double wl[2 * MM], wr[2 * MM], q[4 * MM], qRl[2 * MM], qLl[2 * MM], qRr[2 * MM], qLr[2 * MM];
+  ob_lim_weno2(sub_v(V, g - 2, nsub, outflow), sub_v(V, g - 1, nsub, outflow),
+               sub_v(V, g, nsub, outflow), b1->xi, wl);
+  ob_lim_weno2(sub_v(V, g - 1, nsub, outflow), sub_v(V, g, nsub, outflow),
+               sub_v(V, g + 1, nsub, outflow), b1->xi, wr);
+  int it = 0, status = OB_OK;
+  if (ob_predict_cell(b1, p, (double)Ns * lam, wl, q, &it) != OB_OK) status = OB_ERR_NOT_CONVERGED;
+  traces(b1, q, qRl, qLl);
+  if (ob_predict_cell(b1, p, (double)Ns * lam, wr, q, &it) != OB_OK) status = OB_ERR_NOT_CONVERGED;
+  traces(b1, q, qRr, qLr);
+  dg_face(b1, p, lam, qRl, qLr, G);
+  return status;
+}
+
 static int admissible(double gamma, const double* U) {
   const double rho = U[0];
   const double e = U[2] - 0.5 * U[1] * U[1] / rho;  /* internal energy density */
@@ -112,7 +164,8 @@ static int admissible(double gamma, const double* U) {
 int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, int64_t ncells,
                 double dx, double dt, const double* u, double* u_new, int* troubled_out,
                 ob_stats* st) {
-  if (ncells <= 0 || !lp) return OB_ERR_ARG;
+  if (ncells <= 0 || !lp || lp->limiter < 0 || lp->limiter > 2) return OB_ERR_ARG;
+  if (lp->limiter && b->N < 1) return OB_ERR_ARG;  /* P0: the subcell grid is the mesh */
   const int n = b->n, Ns = b->Ns;
   const double lam = dt / dx;
   const int64_t qs = (int64_t)n * n * MM, us = (int64_t)n * MM, vs = (int64_t)Ns * MM;
@@ -190,8 +243,10 @@ int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, 
   int64_t ntroubled = 0;
   if (lp->limiter) {
     for (int64_t i = 0; i < ncells; ++i) project(b, u + i * us, vn + i * vs);
-    /* detection on the subcell averages of the candidate */
-    for (int64_t i = 0; i < ncells; ++i) {
+    /* detection on the subcell averages of the candidate (limiter 2: every cell) */
+    for (int64_t i = 0; i < ncells && lp->limiter == 2; ++i) tr[i] = 1;
+    ntroubled = lp->limiter == 2 ? ncells : 0;
+    for (int64_t i = 0; i < ncells && lp->limiter == 1; ++i) {
       double vs_[NSM * MM];
       project(b, u_new + i * us, vs_);
       int bad = 0;
@@ -221,25 +276,18 @@ int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, 
       tr[i] = bad;
       ntroubled += bad;
     }
-    /* faces next to a troubled cell carry the first-order subcell flux */
+    /* faces next to a troubled cell carry the ADER-WENO2 subcell flux */
+    ob_basis b1;
+    if (ob_basis_build(1, &b1) != OB_OK) status = OB_ERR_ARG;
+    const int64_t nsub = ncells * Ns;
     memcpy(G2, G, sizeof(double) * (ncells + 1) * MM);
     for (int64_t f = 0; f <= ncells; ++f) {
       const int64_t cl = f - 1, cr = f;
       const int tl = cl >= 0 ? tr[cl] : (outflow ? 0 : tr[ncells - 1]);
       const int tr_ = cr < ncells ? tr[cr] : (outflow ? 0 : tr[0]);
       if (!tl && !tr_) continue;
-      const double *vl, *vr;
-      if (cl >= 0)
-        vl = vn + cl * vs + (Ns - 1) * MM;
-      else
-        vl = outflow ? vn : vn + (ncells - 1) * vs + (Ns - 1) * MM;
-      if (cr < ncells)
-        vr = vn + cr * vs;
-      else
-        vr = outflow ? vn + (ncells - 1) * vs + (Ns - 1) * MM : vn;
-      double g[MM];
-      ob_rusanov(p->gamma, vl, vr, g);
-      for (int r = 0; r < MM; ++r) G2[f * MM + r] = lam * g[r];
+      if (sub_face(&b1, p, lam, Ns, vn, nsub, outflow, f * Ns, G2 + f * MM) != OB_OK)
+        status = OB_ERR_NOT_CONVERGED;
     }
     double R[NM * NSM];
     if (ob_r_matrix(b, R) != OB_OK) status = OB_ERR_ARG;
@@ -253,18 +301,17 @@ int ob_dgl_step(const ob_basis* b, const ob_params* p, const ob_lim_params* lp, 
                                 b->psi0[k] * (G2[i * MM + r] - G[i * MM + r])) / b->w[k];
         continue;
       }
-      /* first-order Rusanov finite volumes on the 2N+1 subcells */
+      /* ADER-WENO2 finite volumes on the 2N+1 subcells (eq.
+       * ader_weno_fv_method_full on the subgrid, with the cell's own faces) */
       const double* v = vn + i * vs;
       double F[(NSM + 1) * MM], vnew[NSM * MM];
       for (int r = 0; r < MM; ++r) {
         F[r] = G2[i * MM + r];
         F[Ns * MM + r] = G2[(i + 1) * MM + r];
       }
-      for (int j = 1; j < Ns; ++j) {
-        double g[MM];
-        ob_rusanov(p->gamma, v + (j - 1) * MM, v + j * MM, g);
-        for (int r = 0; r < MM; ++r) F[j * MM + r] = lam * g[r];
-      }
+      for (int j = 1; j < Ns; ++j)
+        if (sub_face(&b1, p, lam, Ns, vn, nsub, outflow, i * Ns + j, F + j * MM) != OB_OK)
+          status = OB_ERR_NOT_CONVERGED;
       for (int j = 0; j < Ns; ++j)
         for (int r = 0; r < MM; ++r)
           vnew[j * MM + r] = v[j * MM + r] - (double)Ns * (F[(j + 1) * MM + r] - F[j * MM + r]);

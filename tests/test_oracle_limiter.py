@@ -9,7 +9,10 @@ an orthogonal projector; with the limiter off (or on smooth data, where no cell
 is troubled) the step is the plain DG step; the limited step is conservative
 (periodic) and changes the totals by exactly the boundary fluxes (outflow);
 the limited solutions of the four Riemann problems stay physical and converge
-to the exact ones."""
+to the exact ones.  The subcell ADER-WENO2 scheme: its degree-1 WENO
+reconstruction keeps the subcell average, is exact on linear data and takes the
+flat side of a jump; with every cell recomputed on its subcells the step keeps
+a uniform state, conserves, and converges at second order on a smooth wave."""
 import numpy as np
 import pytest
 
@@ -168,4 +171,66 @@ def test_riemann_problems_with_limiter(oracle_mod, test):
         errs.append(density_l1(o, out, nc, test, 0.15))
         per_step.append(ttot / steps)
     assert errs[1] < 0.6 * errs[0] and errs[1] < 0.005, errs
-    assert max(per_step) < (1.0 if test == 4 else 15.0), per_step
+    assert max(per_step) < (2.0 if test == 4 else 15.0), per_step
+
+
+def test_weno2_reconstruction(oracle_mod):
+    """degree-1 WENO on a subcell: the Gauss-node values average to v0 (the
+    subcell mean is kept); linear data give the common slope exactly; a
+    symmetric extremum gives slope 0; at a jump the flat stencil wins."""
+    o = oracle_mod.Oracle(1)
+    xi = o.table("xi")
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        vm, v0, vp = rng.uniform(0.1, 2.0, (3, 3))
+        w = o.weno2(vm, v0, vp)
+        np.testing.assert_allclose(0.5 * (w[0] + w[1]), v0, rtol=0, atol=4e-16)
+    v0, s = np.array([1.0, -0.5, 2.5]), np.array([0.3, -0.2, 0.7])
+    w = o.weno2(v0 - s, v0, v0 + s)
+    np.testing.assert_allclose(w, v0 + np.outer(xi - 0.5, s), rtol=0, atol=1e-15)
+    w = o.weno2(v0 + s, v0, v0 + s)
+    np.testing.assert_allclose(w, np.tile(v0, (2, 1)), rtol=0, atol=1e-15)
+    flat = np.array([1.0, 0.0, 2.5])
+    w = o.weno2(flat, flat, flat + np.array([9.0, 3.0, 20.0]))
+    np.testing.assert_allclose(w, np.tile(flat, (2, 1)), rtol=0, atol=1e-12)
+
+
+def test_all_troubled_keeps_uniform_state_and_conserves(oracle_mod):
+    """limiter 2 (every cell recomputed on its subcells): a uniform state is a
+    fixed point (to rounding) and a periodic step with a jump conserves."""
+    N, nc = 3, 24
+    o = oracle_mod.Oracle(N)
+    U = np.tile(np.array([0.7, 0.2, 1.9]), (nc, N + 1, 1))
+    out, tr, rc = o.dgl_step(U.ravel(), 1.0 / nc, 1e-3, limiter=2)
+    assert rc == 0 and tr.all()
+    np.testing.assert_allclose(out.reshape(U.shape), U, rtol=0, atol=1e-14)
+    x = o.node_x(nc)
+    inside = (x > 0.25) & (x < 0.625)  # jumps on cell faces
+    u = conserved(np.where(inside, 1.0, 0.125), np.where(inside, 0.4, 0.0),
+                  np.where(inside, 1.0, 0.1))
+    dt = o.dg_dt(u, 1.0 / nc)
+    out, tr, rc = o.dgl_step(u, 1.0 / nc, dt, limiter=2)
+    w = o.table("w")
+    tot = lambda V: np.einsum("ckr,k->r", V.reshape(nc, N + 1, 3), w) / nc
+    assert rc == 0
+    np.testing.assert_allclose(tot(out), tot(u), rtol=2e-15, atol=2e-16)
+
+
+def test_all_troubled_is_second_order(oracle_mod):
+    """limiter 2 on the density wave rho = 1 + 0.2 sin(2 pi (x - t)), u = p = 1
+    (an exact Euler solution), DG N = 2, t = 0.25: the L1 error of the density
+    cell means falls at the second order of the ADER-WENO2 subcell scheme."""
+    N = 2
+    o = oracle_mod.Oracle(N)
+    w = o.table("w")
+    errs = []
+    for nc in (16, 32, 64):
+        x = o.node_x(nc)
+        u = conserved(1 + 0.2 * np.sin(2 * np.pi * x), np.ones(x.shape), np.ones(x.shape))
+        out, steps, t, rc, _ = o.dgl_solve(u, 1.0 / nc, t_end=0.25, limiter=2)
+        assert rc == 0 and t == 0.25
+        a = np.arange(nc) / nc - 0.25
+        exact = 1 + 0.2 * nc * (np.cos(2 * np.pi * a) - np.cos(2 * np.pi * (a + 1.0 / nc))) / (2 * np.pi)
+        errs.append(np.abs(np.einsum("ck,k->c", out.reshape(nc, N + 1, 3)[..., 0], w) - exact).mean())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.85 and orders.max() < 2.5, (errs, orders)

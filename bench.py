@@ -595,7 +595,8 @@ def run_limiter(args, dev, flush):
     """The a posteriori subcell limiter with outflow boundaries: the four
     classical Riemann problems of Sec. 2 (Table classical_tests_1d) to t = 0.15
     (L1 density error against the exact solution, troubled cells per step), and
-    throughput at the headline's size: Sod data, and the smooth headline data
+    throughput at the headline's size: Sod data, the smooth headline data with
+    every cell recomputed by the subcell ADER-WENO2 scheme (limiter mode 2), and
     with the limiter on against off (the limiter's cost where it never acts)."""
     import torch
 
@@ -627,6 +628,16 @@ def run_limiter(args, dev, flush):
                         "10^5 cells, outflow, subcell limiter, 100 steps, FP64",
                         ctx, u0, CELLS, DEGREE, TIME_STEPS, st_, 2, flush)
     line["troubled_per_step"] = ctx.ader_get_stats()["troubled_cells"] / TIME_STEPS
+    for k in ("predict_fp64_tflops", "predict_frac_of_fp64_peak"):
+        line.pop(k, None)
+    out["throughput"].append(line)
+    del ctx
+    ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, limiter=2)
+    u0 = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    line = variant_line("dg5-1e5-modes4-limiter2", "the headline workload, every cell recomputed "
+                        "on its 11 subcells by ADER-WENO2 (limiter mode 2)",
+                        ctx, u0, CELLS, DEGREE, TIME_STEPS, st_, 2, flush)
+    line["troubled_cells"] = ctx.ader_get_stats()["troubled_cells"]
     for k in ("predict_fp64_tflops", "predict_frac_of_fp64_peak"):
         line.pop(k, None)
     out["throughput"].append(line)

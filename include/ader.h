@@ -95,14 +95,16 @@ typedef struct {
   int system;             /* ader_system (ADER_SYSTEM_EULER) */
   double omega;           /* reaction frequency of ADER_SYSTEM_REACTING (1.0) */
   int bc;                 /* ader_bc (ADER_BC_PERIODIC) */
-  int limiter;            /* 1: a posteriori subcell limiter (DG, Euler; 0): the candidate of
-                             eq. ader_dg_method_full is checked on its 2N+1 subcell averages
-                             (Sec. 1.4) by the physical admissibility detector (rho > 0, e > 0)
-                             and the relaxed discrete maximum principle of eq. nad_ineq against
-                             the cell and its neighbours; troubled cells are recomputed by
-                             first-order Rusanov finite volumes on their subcells and
-                             reconstructed with R = (P^T P)^-1 P^T (eq. r_operator), the faces
-                             next to them carrying the subcell flux on both sides */
+  int limiter;            /* 1: a posteriori subcell limiter (DG, Euler, N >= 1; 0): the
+                             candidate of eq. ader_dg_method_full is checked on its 2N+1 subcell
+                             averages (Sec. 1.4) by the physical admissibility detector (rho > 0,
+                             e > 0) and the relaxed discrete maximum principle of eq. nad_ineq
+                             against the cell and its neighbours; troubled cells are recomputed
+                             from the subcell averages of u^n by the finite-volume ADER-WENO2
+                             scheme (degree-1 WENO, degree-1 LST-DG predictor, Rusanov flux) on
+                             their subcells and reconstructed with R = (P^T P)^-1 P^T
+                             (eq. r_operator), the faces next to them carrying the subcell flux
+                             on both sides.  2: every cell is recomputed on its subcells. */
   double nad_delta0;      /* NAD: delta = max(nad_delta0, nad_eps (max - min)) (1e-4) */
   double nad_eps;         /* (1e-3) */
 } ader_options;
@@ -218,6 +220,13 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
 
 /* Statistics of the last predictor/solve call (synchronises). */
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
+
+/* Troubled-cell flags of the last limited step (Sec. 1.6: the cells whose
+ * candidate failed PAD or NAD, or every cell in limiter mode 2), one int32 per
+ * cell (1 troubled, 0 not), copied into the DEVICE buffer flags_dev of n_cells
+ * entries (caller-owned) on the context's stream order.  ADER_ERR_ARG without
+ * the limiter, for a null pointer or count != n_cells. */
+ader_status ader_get_troubled(ader_ctx* ctx, int32_t* flags_dev, int64_t count);
 
 /* ---------------------------------------------------------------------------
  * Autotuning of launch shapes (no counterpart in the paper).

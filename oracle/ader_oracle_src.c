@@ -44,7 +44,9 @@ void ob_rs_rusanov(double gamma, const double* a, const double* b, double* G) {
   ob_rs_flux(gamma, a, Fa);
   ob_rs_flux(gamma, b, Fb);
   const double sa = ob_wave_speed(gamma, a), sb = ob_wave_speed(gamma, b);
-  const double s = sa > sb ? sa : sb;
+  /* a non-physical state on either side (NaN speed) makes the flux NaN, so the
+   * candidate fails the admissibility check instead of taking one side's speed */
+  const double s = (isnan(sa) || isnan(sb)) ? NAN : (sa > sb ? sa : sb);
   for (int r = 0; r < MS; ++r) G[r] = 0.5 * (Fa[r] + Fb[r]) - 0.5 * s * (b[r] - a[r]);
 }
 

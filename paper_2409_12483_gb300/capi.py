@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_solve_from": ([V, V, D, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
+            "ader_get_troubled": ([V, V, I64], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
             "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
             "ader_get_tuning": ([V, P(Tuning)], C.c_int),
@@ -152,7 +153,7 @@ def exported_symbols():
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_solve_from",
-            "ader_get_stats",
+            "ader_get_stats", "ader_get_troubled",
             "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
             "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
@@ -357,6 +358,14 @@ class Context:
         for k, v in kw.items():
             setattr(t, k, v)
         self._check(self._L.ader_set_tuning(self._ctx, C.byref(t)))
+
+    def ader_get_troubled(self, flags=None):
+        """troubled-cell flags (int32 per cell, on the device) of the last limited step"""
+        torch = _torch()
+        if flags is None:
+            flags = torch.empty(self.n_cells, dtype=torch.int32, device=self.device)
+        self._check(self._L.ader_get_troubled(self._ctx, C.c_void_p(flags.data_ptr()), flags.numel()))
+        return flags
 
     def ader_get_stats(self) -> dict:
         s = Stats()

@@ -51,8 +51,11 @@ struct ader_ctx {
   double* ubuf = nullptr;
   double* hbuf = nullptr;
   double* lim_mm = nullptr;   // limiter: subcell extrema of u^n [cell][6]
-  double* lim_vb = nullptr;   // limiter: first / last subcell averages of u^n [cell][6]
+  double* lim_vb = nullptr;   // limiter: subcells 0, 1, Ns-2, Ns-1 of P u^n [cell][12]
+  Sub1Ops sub1{};             // limiter: degree-1 operators of the subcell scheme
   int* lim_flag = nullptr;    // limiter: troubled flags [cell]
+  long long* lim_list = nullptr;  // limiter: troubled-cell list [cell]
+  double* lim_gface = nullptr;    // limiter: subcell fluxes of troubled cells' faces [cell][6]
   // cached solve graph
   cudaGraphExec_t gexec = nullptr;
   const double* g_u = nullptr;
@@ -108,13 +111,15 @@ size_t workspace_bytes(const ader_ctx* c) {
   b += 2 * align_up((size_t)state_count(c) * sizeof(double));
   if (c->opt.limiter)
     b += 2 * align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
+         align_up((size_t)c->mesh.n_cells * 12 * sizeof(double)) +
+         align_up((size_t)c->mesh.n_cells * sizeof(long long)) +
          align_up((size_t)c->mesh.n_cells * sizeof(int));
   return b;
 }
 
 int kernels_per_step(const ader_ctx* c) {
   int k = c->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
-  if (c->opt.limiter) k += 3;
+  if (c->opt.limiter) k += 4;
   return k;
 }
 
@@ -216,9 +221,16 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.mm = ctx->lim_mm;
   l.vb = ctx->lim_vb;
   l.troubled = ctx->lim_flag;
+  l.list = ctx->lim_list;
+  l.gface = ctx->lim_gface;
   l.ncells = ctx->mesh.n_cells;
   l.bc = ctx->opt.bc;
   l.Ns = ctx->basis.Ns;
+  l.mode = ctx->opt.limiter;
+  l.max_iter = ctx->opt.picard_max_iter;
+  l.fixed_iter = ctx->opt.picard_fixed_iter;
+  l.tol = ctx->opt.picard_tol;
+  l.s1 = ctx->sub1;
   l.gamma = ctx->opt.gamma;
   l.gm1 = ctx->opt.gamma - 1.0;
   l.delta0 = ctx->opt.nad_delta0;
@@ -227,7 +239,7 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.ops = ctx->basis.d;
   std::memcpy(l.R, ctx->basis.R, sizeof(l.R));
   CK(do_limiter(ctx->N, l, ctx->stream));
-  ctx->launches += 3;
+  ctx->launches += 4;
   return ADER_OK;
 }
 
@@ -377,8 +389,8 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
       (o.system == ADER_SYSTEM_REACTING &&
        (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || !std::isfinite(o.omega))) ||
       (o.bc != ADER_BC_PERIODIC && o.bc != ADER_BC_OUTFLOW) ||
-      (o.bc == ADER_BC_OUTFLOW && scheme != ADER_SCHEME_DG) || (o.limiter != 0 && o.limiter != 1) ||
-      (o.limiter && (scheme != ADER_SCHEME_DG || o.system != ADER_SYSTEM_EULER)) ||
+      (o.bc == ADER_BC_OUTFLOW && scheme != ADER_SCHEME_DG) || (o.limiter < 0 || o.limiter > 2) ||
+      (o.limiter && (scheme != ADER_SCHEME_DG || o.system != ADER_SYSTEM_EULER || degree < 1)) ||
       !(o.nad_delta0 >= 0.0) || !(o.nad_eps >= 0.0)) {
     delete c;
     return ADER_ERR_ARG;
@@ -387,6 +399,23 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   if (build_basis(degree, scheme == ADER_SCHEME_WENO_FV, &c->basis) != 0) {
     delete c;
     return ADER_ERR_ARG;
+  }
+  if (o.limiter) {
+    Basis b1;
+    if (build_basis(1, false, &b1) != 0) {
+      delete c;
+      return ADER_ERR_ARG;
+    }
+    for (int k = 0; k < 2; ++k) {
+      c->sub1.xi[k] = b1.d.xi[k];
+      c->sub1.w[k] = b1.d.w[k];
+      c->sub1.psi0[k] = b1.d.psi0[k];
+      c->sub1.psi1[k] = b1.d.psi1[k];
+      for (int l = 0; l < 2; ++l) {
+        c->sub1.kt[k][l] = b1.d.kt[k][l];
+        c->sub1.kap[k][l] = b1.d.kap[k][l];
+      }
+    }
   }
   *out = c;
   return ADER_OK;
@@ -521,7 +550,11 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
     ctx->lim_mm = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
     ctx->lim_vb = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 12 * sizeof(double));
+    ctx->lim_gface = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
+    ctx->lim_list = reinterpret_cast<long long*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * sizeof(long long));
     ctx->lim_flag = reinterpret_cast<int*>(p);
   }
   return ADER_OK;
@@ -788,6 +821,17 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
   CK(cudaStreamSynchronize(ctx->stream));
   if ((st = join_out(ctx)) != ADER_OK) return st;
   return rs;
+}
+
+ader_status ader_get_troubled(ader_ctx* ctx, int32_t* flags, int64_t count) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!ctx->opt.limiter) return fail(ctx, ADER_ERR_ARG, "troubled flags need the limiter");
+  if (!flags || count != ctx->mesh.n_cells) return fail(ctx, ADER_ERR_ARG, "flags / count");
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(flags, ctx->lim_flag, (size_t)count * sizeof(int32_t),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return join_out(ctx);
 }
 
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out) {

@@ -142,9 +142,13 @@ cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStre
 cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t s) {
   const unsigned g256 = grid_for(p.ncells, 256, 0x7fffffffLL);
   const unsigned g128 = grid_for(p.ncells, 128, 0x7fffffffLL);
+  // the recompute kernel strides over the troubled-cell list (length known on
+  // the device only): enough warps for every cell, at most 8 blocks per SM
+  const unsigned grec = grid_for(p.ncells, kLimWarps, 152LL * 8);
   lim_minmax_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_detect_kernel<D><<<g256, 256, 0, s>>>(p);
-  lim_fix_kernel<D><<<g128, 128, 0, s>>>(p);
+  lim_recompute_kernel<D><<<grec, 32 * kLimWarps, 0, s>>>(p);
+  lim_neighbour_kernel<D><<<g128, 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 

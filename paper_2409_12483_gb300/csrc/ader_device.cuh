@@ -32,6 +32,7 @@ struct DevCtl {
   int iter_max;
   int pad_;
   unsigned long long troubled;  // cells marked by the limiter's detectors (summed over steps)
+  unsigned long long lim_n;     // entries of the limiter's troubled-cell list (this step)
 };
 
 // How a launch gets its time step.
@@ -251,6 +252,22 @@ __device__ __forceinline__ double wave_speed(const double* U, double gamma, doub
   return fabs(u) + sqrt64(gamma * p * inv);
 }
 
+// x > 0 and finite, tested on the bit pattern (integer pipe, no FP64 compare)
+__device__ __forceinline__ bool pos_finite(double x) {
+  return dbits(x) - 1ull < 0x7fefffffffffffffull;
+}
+
+// Rusanov speed max(s_a, s_b); NaN when either state is non-physical (rho or p
+// not positive and finite), so the flux -- and the candidate of the cells of
+// the face -- is NaN and fails the admissibility check instead of taking one
+// side's speed.
+__device__ __forceinline__ double rusanov_speed(double ra, double pa, double sa, double rb,
+                                                double pb, double sb) {
+  const double s = bitsd(umax64(dbits(sa), dbits(sb)));  // both non-negative
+  const bool ok = pos_finite(ra) & pos_finite(pa) & pos_finite(rb) & pos_finite(pb);
+  return ok ? s : __longlong_as_double(0x7ff8000000000000ll);
+}
+
 // Twice the Rusanov flux between a (left) and b (right):
 // 2 G = F(a) + F(b) - s (b - a), s = max(|u_a| + c_a, |u_b| + c_b); the factor
 // 1/2 is applied once per face together with dt/dx, after the time average.
@@ -262,7 +279,7 @@ __device__ __forceinline__ void rusanov2(const double* a, const double* b, doubl
   const double pb = gm1 * fma(neg_half(b[1]), ub, b[2]);
   const double sa = fabs(ua) + sqrt64(gamma * pa * ia);
   const double sb = fabs(ub) + sqrt64(gamma * pb * ib);
-  const double s = bitsd(umax64(dbits(sa), dbits(sb)));  // both non-negative
+  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
   G2[0] = fma(-s, b[0] - a[0], a[1] + b[1]);
   G2[1] = fma(-s, b[1] - a[1], fma(a[1], ua, pa) + fma(b[1], ub, pb));
   G2[2] = fma(-s, b[2] - a[2], fma(a[2] + pa, ua, (b[2] + pb) * ub));

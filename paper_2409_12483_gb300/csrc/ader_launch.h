@@ -100,20 +100,33 @@ struct WenoParams {
 };
 
 // A posteriori subcell limiter of the DG scheme (ader_limiter.cuh).
+// Degree-1 operators of the limiter's subcell ADER-WENO2 scheme (GL nodes and
+// weights, phi_k(0), phi_k(1), k~ = Lambda^-1 Xi, kappa~ = Upsilon^-1 Lambda).
+struct Sub1Ops {
+  double xi[2], w[2], psi0[2], psi1[2];
+  double kt[2][2], kap[2][2];
+};
+
 struct LimParams {
   const double* u_old;   // u^n, [cell][n][3]
   double* u;             // in: candidate u*, out: u^{n+1} (same layout)
   const double* trace;   // predictor traces [cell][qR(3n) | qL(3n) | u + volume(3n)]
   double* mm;            // [cell][6]: min (3), max (3) of the subcell averages of u^n
-  double* vb;            // [cell][6]: P u^n of the first (3) and last (3) subcell
+  double* vb;            // [cell][12]: P u^n of subcells 0, 1, Ns-2, Ns-1 (3 each)
   int* troubled;         // [cell]
+  long long* list;       // [cell]: the troubled cells of the step (first ctl->lim_n entries)
+  double* gface;         // [cell][2][3]: subcell fluxes of a troubled cell's left / right face
   long long ncells;
   int bc;                // kBcPeriodic or kBcOutflow
   int Ns;
+  int mode;              // 1: detect troubled cells, 2: every cell troubled
+  int max_iter, fixed_iter;  // Picard of the subcell predictor (as the DG predictor's)
+  double tol;
   double gamma, gm1;
   double delta0, eps;    // NAD tolerances
   StepParams sp;
   OpsD ops;
+  Sub1Ops s1;
   double R[kMaxN][kMaxNs];  // reconstruction from subcell averages
 };
 

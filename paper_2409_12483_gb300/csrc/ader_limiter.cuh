@@ -1,27 +1,37 @@
 // ader_limiter.cuh -- sm_103a kernels of the a posteriori subcell limiter of the
 // 1D Euler ADER-DG scheme (Popov, arXiv 2409.12483: subcell projection
 // eq. p_operator and reconstruction eq. r_operator of Sec. 1.4, admissibility
-// detectors PAD and NAD eq. nad_ineq of Sec. 1.6).  Run after the interface
-// kernel has written the candidate u* in place of u^{n+1}:
+// detectors PAD and NAD eq. nad_ineq of Sec. 1.6, the finite-volume ADER-WENO2
+// limiter of Sec. 2).  Run after the interface kernel has written the candidate
+// u* in place of u^{n+1}:
 //
 // lim_minmax_kernel  per cell, the 2N+1 subcell averages P u^n: their minimum and
-//                    maximum per variable and the first and last subcell (the
-//                    states the limited face fluxes use).
+//                    maximum per variable and subcells 0, 1, Ns-2, Ns-1 (the
+//                    stencils of the limited faces of the cell).
 // lim_detect_kernel  per cell, PAD (rho > 0, e > 0) on the subcell averages P u*
 //                    and the relaxed discrete maximum principle against the
 //                    extrema of the cell and its neighbours, delta = max(delta0,
-//                    eps (max - min)); marks troubled cells, counts them.
-// lim_fix_kernel     faces next to a troubled cell carry the first-order subcell
-//                    Rusanov flux on both sides: a DG neighbour's update is
-//                    corrected by the difference to its DG face flux (recomputed
-//                    from the predictor traces); a troubled cell is recomputed by
-//                    first-order Rusanov finite volumes on its 2N+1 subcells and
-//                    reconstructed with the pseudo-inverse R = (P^T P)^-1 P^T,
-//                    falling back to the mean of the subcell values when R v has
-//                    an inadmissible subcell average.
+//                    eps (max - min)); marks troubled cells (mode 2: every cell),
+//                    counts them.
+// lim_recompute_kernel  one warp per listed troubled cell: the ADER-WENO2
+//                    scheme on its 2N+1 subcells from P u^n (lane j: degree-1
+//                    WENO and the degree-1 LST-DG predictor of subcell j - 1,
+//                    the neighbours' boundary subcells included; lane f: the
+//                    Rusanov flux through subcell face f averaged over the two
+//                    tau nodes), the subcell update, the pseudo-inverse
+//                    reconstruction R = (P^T P)^-1 P^T with the mean of the
+//                    subcell values as fallback when R v has an inadmissible
+//                    subcell average; the fluxes of the cell's own faces go to
+//                    gface for the neighbours.
+// lim_neighbour_kernel  per DG cell next to a troubled one: its update is
+//                    corrected by the difference between the subcell flux and
+//                    its DG flux (recomputed from the predictor traces) on the
+//                    shared face, so the step stays conservative.
 //
-// One thread per cell: the detection is a short pass over every cell, the
-// recomputation touches only the few troubled cells and their neighbours.
+// The detectors run one thread per cell; the recomputation touches only the
+// listed cells.  Both cells of a face between two troubled cells form its flux
+// from the same four subcell averages (P u^n of the same coefficients by the
+// same arithmetic), so they see the same bits.
 #pragma once
 
 #include "ader_kernels.cuh"
@@ -53,6 +63,7 @@ __global__ void __launch_bounds__(256) lim_minmax_kernel(const __grid_constant__
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;  // inactive step
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) P.sp.ctl->lim_n = 0;  // the detectors append to the list after this kernel
   if (i >= P.ncells) return;
   const double* u = P.u_old + i * ((N + 1) * kM);
   double lo[kM], hi[kM];
@@ -68,8 +79,10 @@ __global__ void __launch_bounds__(256) lim_minmax_kernel(const __grid_constant__
     for (int r = 0; r < kM; ++r) {
       lo[r] = fmin(lo[r], v[r]);
       hi[r] = fmax(hi[r], v[r]);
-      if (j == 0) P.vb[i * 6 + r] = v[r];
-      if (j == P.Ns - 1) P.vb[i * 6 + 3 + r] = v[r];
+      if (j == 0) P.vb[i * 12 + r] = v[r];
+      if (j == 1) P.vb[i * 12 + 3 + r] = v[r];
+      if (j == P.Ns - 2) P.vb[i * 12 + 6 + r] = v[r];
+      if (j == P.Ns - 1) P.vb[i * 12 + 9 + r] = v[r];
     }
   }
 #pragma unroll
@@ -93,6 +106,15 @@ __global__ void __launch_bounds__(256) lim_detect_kernel(const __grid_constant__
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.ncells) return;
+  if (P.mode == 2) {  // every cell recomputed on its subcells
+    P.troubled[i] = 1;
+    P.list[i] = i;
+    if (i == 0) {
+      P.sp.ctl->lim_n = (unsigned long long)P.ncells;
+      atomicAdd(&P.sp.ctl->troubled, (unsigned long long)P.ncells);
+    }
+    return;
+  }
   const double* u = P.u + i * ((N + 1) * kM);
   double lo[kM], hi[kM];
 #pragma unroll
@@ -122,7 +144,10 @@ __global__ void __launch_bounds__(256) lim_detect_kernel(const __grid_constant__
       if (v[r] < lo[r] - delta[r] || v[r] > hi[r] + delta[r]) bad = true;
   }
   P.troubled[i] = bad ? 1 : 0;
-  if (bad) atomicAdd(&P.sp.ctl->troubled, 1ull);
+  if (bad) {
+    atomicAdd(&P.sp.ctl->troubled, 1ull);
+    P.list[atomicAdd(&P.sp.ctl->lim_n, 1ull)] = i;
+  }
 }
 
 // DG face flux (time-integrated, rescaled) from the predictor traces, as the
@@ -163,119 +188,226 @@ __device__ __forceinline__ void lim_dg_face(const LimParams& P, long long f, dou
   for (int r = 0; r < kM; ++r) G[r] = hlam * s[r];
 }
 
-// first-order subcell flux through face f (between cells f-1 and f): the last
-// subcell of the left cell against the first subcell of the right cell
-__device__ __forceinline__ void lim_subcell_face(const LimParams& P, long long f, double hlam,
-                                                 double* G) {
-  const long long cl = lim_neighbour(f - 1, P.ncells, P.bc), cr = lim_neighbour(f, P.ncells, P.bc);
-  const double* vl = cl >= 0 ? P.vb + cl * 6 + 3 : nullptr;
-  const double* vr = cr >= 0 ? P.vb + cr * 6 : nullptr;
-  if (!vl) vl = vr;
-  if (!vr) vr = vl;
-  double a[kM], b[kM], G2[kM];
+// Degree-1 WENO on a subcell with averages v0 and neighbours vm, vp: slopes of
+// the stencils {j-1, j} and {j, j+1}, smoothness sigma_S = slope_S^2, weights
+// (sigma_S + 1e-14)^-8 normalised (written as 1 / (1 + (s_l / s_r)^8)), nodal
+// values at the two Gauss nodes.
+__device__ __forceinline__ void lim_weno2(const Sub1Ops& s1, const double* vm, const double* v0,
+                                          const double* vp, double (*w)[kM]) {
 #pragma unroll
   for (int r = 0; r < kM; ++r) {
-    a[r] = vl[r];
-    b[r] = vr[r];
-  }
-  rusanov2(a, b, G2, P.gamma, P.gm1);
+    const double sl = v0[r] - vm[r], sr = vp[r] - v0[r];
+    double t = fma(sl, sl, 1.0e-14) / fma(sr, sr, 1.0e-14);
+    t *= t;
+    t *= t;
+    t *= t;
+    const double om = 1.0 / (1.0 + t);  // weight of the left stencil
+    const double slope = fma(om, sl - sr, sr);
 #pragma unroll
-  for (int r = 0; r < kM; ++r) G[r] = hlam * G2[r];
+    for (int k = 0; k < 2; ++k) w[k][r] = fma(slope, s1.xi[k] - 0.5, v0[r]);
+  }
 }
 
+// LST-DG predictor of degree 1 on one subcell (eq. lst_dg_predictor_picard with
+// the degree-1 operators; lam_s = dt / subcell width) and its traces at both ends
+// at the two tau nodes.  Convergence as the DG predictor: max |q' - q| <=
+// tol max(1, max |q'|), capped by max_iter; fixed_iter > 0 runs exactly that many.
+__device__ __forceinline__ bool lim_predict1(const LimParams& P, double lam_s,
+                                             const double (*w)[kM], double (*qR)[kM],
+                                             double (*qL)[kM]) {
+  const Sub1Ops& s1 = P.s1;
+  double q[2][2][kM];
+#pragma unroll
+  for (int p0 = 0; p0 < 2; ++p0)
+#pragma unroll
+    for (int p1 = 0; p1 < 2; ++p1)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) q[p0][p1][r] = w[p1][r];
+  const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+  bool converged = P.fixed_iter > 0;
+  for (int it = 0; it < cap; ++it) {
+    double f[2][2][kM];
+#pragma unroll
+    for (int p0 = 0; p0 < 2; ++p0)
+#pragma unroll
+      for (int p1 = 0; p1 < 2; ++p1) {
+        euler_flux<double>(q[p0][p1], f[p0][p1], P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) f[p0][p1][r] *= lam_s;
+      }
+    double sx[2][2][kM];
+#pragma unroll
+    for (int p0 = 0; p0 < 2; ++p0)
+#pragma unroll
+      for (int p1 = 0; p1 < 2; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r)
+          sx[p0][p1][r] = fma(s1.kt[p1][0], f[p0][0][r], s1.kt[p1][1] * f[p0][1][r]);
+    double delta = 0.0, qmax = 0.0;
+#pragma unroll
+    for (int p0 = 0; p0 < 2; ++p0)
+#pragma unroll
+      for (int p1 = 0; p1 < 2; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          const double qn =
+              w[p1][r] - fma(s1.kap[p0][0], sx[0][p1][r], s1.kap[p0][1] * sx[1][p1][r]);
+          delta = fmax(delta, fabs(qn - q[p0][p1][r]));
+          qmax = fmax(qmax, fabs(qn));
+          q[p0][p1][r] = qn;
+        }
+    if (P.fixed_iter <= 0 && delta <= P.tol * fmax(qmax, 1.0)) {
+      converged = true;
+      break;
+    }
+  }
+#pragma unroll
+  for (int l0 = 0; l0 < 2; ++l0)
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      qR[l0][r] = fma(s1.psi1[0], q[l0][0][r], s1.psi1[1] * q[l0][1][r]);
+      qL[l0][r] = fma(s1.psi0[0], q[l0][0][r], s1.psi0[1] * q[l0][1][r]);
+    }
+  return converged;
+}
+
+constexpr int kLimWarps = 4;  // warps (listed cells in flight) per block
+
 template <int N>
-__global__ void __launch_bounds__(128) lim_fix_kernel(const __grid_constant__ LimParams P) {
+struct LimWarpSmem {
+  static constexpr int n = N + 1, Ns = 2 * N + 1;
+  double ve[Ns + 4][kM];     // subcell averages of u^n, subcells -2 .. Ns+1
+  double qR[Ns + 2][2][kM];  // traces of subcells -1 .. Ns at the two tau nodes
+  double qL[Ns + 2][2][kM];
+  double F[Ns + 1][kM];      // subcell face fluxes (dt/dx scaling)
+  double vnew[Ns][kM];
+  double ur[n][kM];
+};
+
+template <int N>
+__global__ void __launch_bounds__(32 * kLimWarps)
+    lim_recompute_kernel(const __grid_constant__ LimParams P) {
   constexpr int n = N + 1, Ns = 2 * N + 1;
+  __shared__ LimWarpSmem<N> smem[kLimWarps];
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  LimWarpSmem<N>& w = smem[warp];
+  const long long count = (long long)P.sp.ctl->lim_n;
+  const double hlam = 0.5 * dt * P.sp.inv_dx;
+  const double lam_s = dt * P.sp.inv_dx * (double)Ns;  // dt / subcell width
+  for (long long e = (long long)blockIdx.x * kLimWarps + warp; e < count;
+       e += (long long)gridDim.x * kLimWarps) {
+    const long long i = P.list[e];
+    const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
+    // subcell averages: the cell's own from u^n, the neighbours' boundary
+    // subcells from the minmax pass (outflow: the boundary subcell)
+    if (lane < Ns) lim_subcell<N>(P, P.u_old + i * (n * kM), lane, w.ve[lane + 2]);
+    __syncwarp();
+    if (lane < 4 * kM) {
+      const int g = lane / kM, r = lane - g * kM;
+      double v;
+      if (g < 2)
+        v = il >= 0 ? P.vb[il * 12 + 6 + g * 3 + r] : w.ve[2][r];
+      else
+        v = ir >= 0 ? P.vb[ir * 12 + (g - 2) * 3 + r] : w.ve[Ns + 1][r];
+      w.ve[g < 2 ? g : Ns + g][r] = v;
+    }
+    __syncwarp();
+    // lane j: subcell j - 1 (ve index j + 1): degree-1 WENO and predictor
+    if (lane < Ns + 2) {
+      double wn[2][kM];
+      lim_weno2(P.s1, w.ve[lane], w.ve[lane + 1], w.ve[lane + 2], wn);
+      if (!lim_predict1(P, lam_s, wn, w.qR[lane], w.qL[lane]))
+        atomicOr(&P.sp.ctl->status, kStNotConverged);
+    }
+    __syncwarp();
+    // lane f: face between subcells f - 1 and f
+    if (lane < Ns + 1) {
+      double s[kM] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int l0 = 0; l0 < 2; ++l0) {
+        double G2[kM];
+        rusanov2(w.qR[lane][l0], w.qL[lane + 1][l0], G2, P.gamma, P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) s[r] = fma(P.s1.w[l0], G2[r], s[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        w.F[lane][r] = hlam * s[r];
+        if (lane == 0) P.gface[i * 6 + r] = hlam * s[r];
+        if (lane == Ns) P.gface[i * 6 + 3 + r] = hlam * s[r];
+      }
+    }
+    __syncwarp();
+    if (lane < Ns) {
+#pragma unroll
+      for (int r = 0; r < kM; ++r)
+        w.vnew[lane][r] = w.ve[lane + 2][r] - (double)Ns * (w.F[lane + 1][r] - w.F[lane][r]);
+    }
+    __syncwarp();
+    // reconstruction u = R v (lane = (k, r))
+    if (lane < n * kM) {
+      const int k = lane / kM, r = lane - k * kM;
+      double acc = 0.0;
+      for (int j = 0; j < Ns; ++j) acc = fma(P.R[k][j], w.vnew[j][r], acc);
+      w.ur[k][r] = acc;
+    }
+    __syncwarp();
+    bool ok = true;
+    if (lane < Ns) {
+      double v[kM];
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[lane][k], w.ur[k][r], acc);
+        v[r] = acc;
+      }
+      ok = lim_admissible(v);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane < n * kM) {
+      const int k = lane / kM, r = lane - k * kM;
+      double val = w.ur[k][r];
+      if (!ok) {  // the mean of the subcell values
+        double mean = 0.0;
+        for (int j = 0; j < Ns; ++j) mean += w.vnew[j][r];
+        val = mean / (double)Ns;
+      }
+      P.u[(i * n + k) * kM + r] = val;
+    }
+    __syncwarp();  // shared memory is free for the next listed cell
+  }
+}
+
+// DG neighbours of troubled cells: the face term with the subcell flux
+template <int N>
+__global__ void __launch_bounds__(128) lim_neighbour_kernel(const __grid_constant__ LimParams P) {
+  constexpr int n = N + 1;
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.ncells) return;
+  if (i >= P.ncells || P.troubled[i]) return;
   const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
-  const bool tl = il >= 0 && P.troubled[il], tc = P.troubled[i] != 0, tr = ir >= 0 && P.troubled[ir];
-  if (!tl && !tc && !tr) return;
+  const bool tl = il >= 0 && P.troubled[il], tr = ir >= 0 && P.troubled[ir];
+  if (!tl && !tr) return;
   const double hlam = 0.5 * dt * P.sp.inv_dx;
-  const bool limL = tl || tc, limR = tc || tr;  // faces i (left) and i+1 (right)
-  double GL2[kM], GR2[kM];
-  if (limL) lim_subcell_face(P, i, hlam, GL2);
-  if (limR) lim_subcell_face(P, i + 1, hlam, GR2);
+  double GL[kM], GR[kM];
+  if (tl) lim_dg_face<N>(P, i, hlam, GL);
+  if (tr) lim_dg_face<N>(P, i + 1, hlam, GR);
   double* un = P.u + i * (n * kM);
-  if (!tc) {
-    // DG neighbour of a limited face: its face term with the subcell flux
-    double GL[kM], GR[kM];
-    if (limL) lim_dg_face<N>(P, i, hlam, GL);
-    if (limR) lim_dg_face<N>(P, i + 1, hlam, GR);
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        double d = 0.0;
-        if (limR) d -= P.ops.psi1[k] * (GR2[r] - GR[r]);
-        if (limL) d += P.ops.psi0[k] * (GL2[r] - GL[r]);
-        un[k * kM + r] += d / P.ops.w[k];
-      }
-    return;
-  }
-  // troubled cell: first-order Rusanov finite volumes on the 2N+1 subcells of u^n
-  const double* uo = P.u_old + i * (n * kM);
-  double v[Ns][kM], vnew[Ns][kM];
-  for (int j = 0; j < Ns; ++j) lim_subcell<N>(P, uo, j, v[j]);
-  double Fprev[kM];
-#pragma unroll
-  for (int r = 0; r < kM; ++r) Fprev[r] = GL2[r];
-  for (int j = 0; j < Ns; ++j) {
-    double Fnext[kM];
-    if (j == Ns - 1) {
-#pragma unroll
-      for (int r = 0; r < kM; ++r) Fnext[r] = GR2[r];
-    } else {
-      double G2[kM];
-      rusanov2(v[j], v[j + 1], G2, P.gamma, P.gm1);
-#pragma unroll
-      for (int r = 0; r < kM; ++r) Fnext[r] = hlam * G2[r];
-    }
-#pragma unroll
-    for (int r = 0; r < kM; ++r) {
-      vnew[j][r] = v[j][r] - (double)Ns * (Fnext[r] - Fprev[r]);
-      Fprev[r] = Fnext[r];
-    }
-  }
-  // reconstruction u = R v, the cell mean if a subcell average of R v is inadmissible
-  double ur[n][kM];
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
-      double acc = 0.0;
-      for (int j = 0; j < Ns; ++j) acc = fma(P.R[k][j], vnew[j][r], acc);
-      ur[k][r] = acc;
+      double d = 0.0;
+      if (tr) d -= P.ops.psi1[k] * (P.gface[ir * 6 + r] - GR[r]);
+      if (tl) d += P.ops.psi0[k] * (P.gface[il * 6 + 3 + r] - GL[r]);
+      un[k * kM + r] += d / P.ops.w[k];
     }
-  bool ok = true;
-  for (int j = 0; j < Ns; ++j) {
-    double w[kM];
-#pragma unroll
-    for (int r = 0; r < kM; ++r) {
-      double acc = 0.0;
-#pragma unroll
-      for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], ur[k][r], acc);
-      w[r] = acc;
-    }
-    if (!lim_admissible(w)) ok = false;
-  }
-  if (!ok) {
-#pragma unroll
-    for (int r = 0; r < kM; ++r) {
-      double mean = 0.0;
-      for (int j = 0; j < Ns; ++j) mean += vnew[j][r];
-      mean /= (double)Ns;
-#pragma unroll
-      for (int k = 0; k < n; ++k) ur[k][r] = mean;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int r = 0; r < kM; ++r) un[k * kM + r] = ur[k][r];
 }
 
 }  // namespace ader

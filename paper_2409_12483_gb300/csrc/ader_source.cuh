@@ -53,7 +53,7 @@ __device__ __forceinline__ void rusanov2_src(const double* a, const double* b, d
   const double pb = gm1 * fma(neg_half(b[1]), ub, b[2]);
   const double sa = fabs(ua) + sqrt64(gamma * pa * ia);
   const double sb = fabs(ub) + sqrt64(gamma * pb * ib);
-  const double s = bitsd(umax64(dbits(sa), dbits(sb)));  // both non-negative
+  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
   G2[0] = fma(-s, b[0] - a[0], a[1] + b[1]);
   G2[1] = fma(-s, b[1] - a[1], fma(a[1], ua, pa) + fma(b[1], ub, pb));
   G2[2] = fma(-s, b[2] - a[2], fma(a[2] + pa, ua, (b[2] + pb) * ub));

@@ -236,9 +236,9 @@ def test_reacting_system_options_and_sizes(lib):
 
 
 def test_boundary_and_limiter_options(lib, oracle_mod):
-    """Outflow and the limiter are DG options (the limiter for the Euler system);
-    the limiter adds its per-cell buffers to the workspace; the library's R is
-    the oracle's pseudo-inverse of P."""
+    """Outflow and the limiter are DG options (the limiter for the Euler system and
+    N >= 1, modes 1 and 2); the limiter adds its per-cell buffers to the
+    workspace; the library's R is the oracle's pseudo-inverse of P."""
     from paper_2409_12483_gb300.capi import Mesh, default_options
     nc = 10
     ok = C.c_void_p()
@@ -253,9 +253,15 @@ def test_boundary_and_limiter_options(lib, oracle_mod):
     np.testing.assert_allclose(R.reshape(4, 7), oracle_mod.Oracle(3).r_matrix(), rtol=0, atol=1e-13)
     lib.ader_destroy(ok)
     lib.ader_destroy(plain)
+    every = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), 1, 0, C.byref(default_options(limiter=2)),
+                         C.byref(every)) == 0
+    lib.ader_destroy(every)
     for kw, scheme, deg in ((dict(bc="outflow"), 1, 4), (dict(limiter=1), 1, 4),
                             (dict(limiter=1, system="reacting"), 0, 3), (dict(bc=5), 0, 3),
-                            (dict(limiter=2), 0, 3), (dict(limiter=1, nad_eps=-1.0), 0, 3)):
+                            (dict(limiter=3), 0, 3), (dict(limiter=-1), 0, 3),
+                            (dict(limiter=1), 0, 0), (dict(limiter=2), 0, 0),
+                            (dict(limiter=1, nad_eps=-1.0), 0, 3)):
         bad = C.c_void_p()
         assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), deg, scheme,
                              C.byref(default_options(**kw)), C.byref(bad)) == 1, kw

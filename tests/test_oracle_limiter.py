@@ -234,3 +234,22 @@ def test_all_troubled_is_second_order(oracle_mod):
         errs.append(np.abs(np.einsum("ck,k->c", out.reshape(nc, N + 1, 3)[..., 0], w) - exact).mean())
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders.min() > 1.85 and orders.max() < 2.5, (errs, orders)
+
+
+def test_rusanov_with_a_nonphysical_state_is_nan(oracle_mod):
+    """the reading for a non-physical trace state (rho <= 0 or p <= 0, which the
+    paper's PAD is there to catch): the Rusanov flux is NaN whichever side the
+    state is on, so the cells of the face fail PAD and are recomputed"""
+    import ctypes as C
+    L = oracle_mod.lib()
+    good = conserved(np.array(1.0), np.array(0.3), np.array(1.0))
+    for bad in (conserved(np.array(1.0), np.array(0.0), np.array(-0.1)),
+                np.array([-0.2, 0.0, -0.5])):
+        for a, b in ((good, bad), (bad, good)):
+            G = np.zeros(3)
+            L.ob_rusanov(1.4, np.ascontiguousarray(a, dtype=np.float64),
+                         np.ascontiguousarray(b, dtype=np.float64), G)
+            assert np.isnan(G).all()
+    G = np.zeros(3)
+    L.ob_rusanov(1.4, good, good, G)
+    np.testing.assert_allclose(G, euler_flux(good), rtol=1e-15)

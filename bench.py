@@ -603,24 +603,25 @@ def run_limiter(args, dev, flush):
     import workloads as W
     from paper_2409_12483_gb300 import Context
     out = {"riemann": [], "throughput": []}
+    cases = [(N, nc) for N in (3, 5) for nc in (200, 1000)]
+    cases.append((7, 50))  # nearest to the paper's DG-P9 on 50 cells (N <= 7 here)
     for test in (1, 2, 3, 4):
-        for N in (3, 5):
-            for nc in (200, 1000):
-                ctx = Context(nc, N, "dg", device=dev, bc="outflow", limiter=1)
-                u = torch.tensor(W.riemann_initial(ctx.node_coords(), test), device=dev).reshape(-1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                steps, t, rc = ctx.ader_solve(u, t_end=0.15)
-                e1.record()
-                torch.cuda.synchronize()
-                st = ctx.ader_get_stats()
-                out["riemann"].append({
-                    "test": test, "degree": N, "cells": nc, "steps": steps, "status": rc,
-                    "l1_density_vs_exact": riemann_density_l1(ctx, u.cpu().numpy(), test, t),
-                    "troubled_per_step": st["troubled_cells"] / max(steps, 1),
-                    "ms": e0.elapsed_time(e1)})
-                del ctx
+        for N, nc in cases:
+            ctx = Context(nc, N, "dg", device=dev, bc="outflow", limiter=1)
+            u = torch.tensor(W.riemann_initial(ctx.node_coords(), test), device=dev).reshape(-1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            steps, t, rc = ctx.ader_solve(u, t_end=0.15)
+            e1.record()
+            torch.cuda.synchronize()
+            st = ctx.ader_get_stats()
+            out["riemann"].append({
+                "test": test, "degree": N, "cells": nc, "steps": steps, "status": rc,
+                "l1_density_vs_exact": riemann_density_l1(ctx, u.cpu().numpy(), test, t),
+                "troubled_per_step": st["troubled_cells"] / max(steps, 1),
+                "ms": e0.elapsed_time(e1)})
+            del ctx
     st_ = max(2, min(args.steps, 3))
     ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, bc="outflow", limiter=1)
     u0 = torch.tensor(W.riemann_initial(ctx.node_coords(), 1), device=dev).reshape(-1)

@@ -213,7 +213,8 @@ ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
 }
 
 // the a posteriori subcell limiter on the candidate in dst (u^n in src)
-ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp) {
+ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
+                            int want_lambda) {
   LimParams l{};
   l.u_old = src;
   l.u = dst;
@@ -227,6 +228,7 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.bc = ctx->opt.bc;
   l.Ns = ctx->basis.Ns;
   l.mode = ctx->opt.limiter;
+  l.want_lambda = want_lambda;
   l.max_iter = ctx->opt.picard_max_iter;
   l.fixed_iter = ctx->opt.picard_fixed_iter;
   l.tol = ctx->opt.picard_tol;
@@ -238,6 +240,8 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.sp = sp;
   l.ops = ctx->basis.d;
   std::memcpy(l.R, ctx->basis.R, sizeof(l.R));
+  for (int j = 0; j < kMaxNs; ++j)
+    for (int k = 0; k < kMaxN; ++k) l.Pf[j][k] = (float)ctx->basis.d.P[j][k];
   CK(do_limiter(ctx->N, l, ctx->stream));
   ctx->launches += 4;
   return ADER_OK;
@@ -266,15 +270,10 @@ ader_status enqueue_step(ader_ctx* ctx, const double* src, double* dst, const St
   CK(do_face(ctx->N, f, ctx->stream));
   ctx->launches += ctx->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
   if (ctx->opt.limiter) {
-    ader_status st = enqueue_limiter(ctx, src, dst, sp);
+    // with lambda_max of the limited state for the next step (the predictor of
+    // this step has reset the slot)
+    ader_status st = enqueue_limiter(ctx, src, dst, sp, want_lambda);
     if (st != ADER_OK) return st;
-    // lambda_max of the limited state for the next step (the predictor of this
-    // step has reset the slot)
-    if (want_lambda) {
-      CflParams c = make_cfl(ctx, dst, sp.par ^ 1);
-      CK(do_cfl(ctx->N, c, ctx->stream));
-      ctx->launches += 1;
-    }
   }
   if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
   return ADER_OK;
@@ -631,7 +630,7 @@ ader_status ader_correct(ader_ctx* ctx, const double* u, const double* q, double
   CK(do_predict(ctx->N, p, ctx->stream));
   FaceParams f = make_face(ctx, u, u_new, sp, 0);
   CK(do_face(ctx->N, f, ctx->stream));
-  if (ctx->opt.limiter && (st = enqueue_limiter(ctx, u, u_new, sp)) != ADER_OK) return st;
+  if (ctx->opt.limiter && (st = enqueue_limiter(ctx, u, u_new, sp, 0)) != ADER_OK) return st;
   return join_out(ctx);
 }
 
@@ -772,8 +771,7 @@ static ader_status solve_impl(ader_ctx* ctx, double* u, double t0, double t_end,
     }
     if (launches >= max_launches) break;
   }
-  ctx->launches += launches * (long long)K * kernels_per_step(ctx) +
-                   (ctx->opt.limiter ? launches * (long long)K : 0);  // + the CFL after the limiter
+  ctx->launches += launches * (long long)K * kernels_per_step(ctx);
   CK(cudaMemcpyAsync(&ctx->hflags[0].status, &ctx->ctl->status, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&ctx->hflags[0].steps, &ctx->ctl->steps, sizeof(long long),

@@ -148,7 +148,7 @@ cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t
   lim_minmax_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_detect_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_recompute_kernel<D><<<grec, 32 * kLimWarps, 0, s>>>(p);
-  lim_neighbour_kernel<D><<<g128, 128, 0, s>>>(p);
+  lim_finish_kernel<D><<<g128, 128, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -120,6 +120,7 @@ struct LimParams {
   int bc;                // kBcPeriodic or kBcOutflow
   int Ns;
   int mode;              // 1: detect troubled cells, 2: every cell troubled
+  int want_lambda;       // lambda_max of the limited state into ctl->lam[par ^ 1]
   int max_iter, fixed_iter;  // Picard of the subcell predictor (as the DG predictor's)
   double tol;
   double gamma, gm1;
@@ -128,6 +129,7 @@ struct LimParams {
   OpsD ops;
   Sub1Ops s1;
   double R[kMaxN][kMaxNs];  // reconstruction from subcell averages
+  float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening pass of lambda_max)
 };
 
 // Per-degree entry points (defined in ader_deg.cu compiled once per degree).

@@ -23,10 +23,13 @@
 //                    subcell values as fallback when R v has an inadmissible
 //                    subcell average; the fluxes of the cell's own faces go to
 //                    gface for the neighbours.
-// lim_neighbour_kernel  per DG cell next to a troubled one: its update is
+// lim_finish_kernel  per cell: a DG cell next to a troubled one has its update
 //                    corrected by the difference between the subcell flux and
 //                    its DG flux (recomputed from the predictor traces) on the
-//                    shared face, so the step stays conservative.
+//                    shared face, so the step stays conservative; then the
+//                    screened lambda_max of the limited state for the next
+//                    step (the CFL reduction of the unlimited path's interface
+//                    kernel, moved here because the limiter changes the state).
 //
 // The detectors run one thread per cell; the recomputation touches only the
 // listed cells.  Both cells of a face between two troubled cells form its flux
@@ -382,32 +385,103 @@ __global__ void __launch_bounds__(32 * kLimWarps)
   }
 }
 
-// DG neighbours of troubled cells: the face term with the subcell flux
+// Every cell once its state is final: DG neighbours of troubled cells take the
+// face term with the subcell flux; then (want_lambda) lambda_max of the limited
+// state for the next step's CFL rule, screened like the interface kernel's: an
+// FP32 pass over every subcell, FP64 wave speeds only for subcells within 1e-3
+// of the block's FP32 maximum or with a doubtful FP32 state, so the result is
+// the FP64 maximum over all subcells.
 template <int N>
-__global__ void __launch_bounds__(128) lim_neighbour_kernel(const __grid_constant__ LimParams P) {
-  constexpr int n = N + 1;
+__global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__ LimParams P) {
+  constexpr int n = N + 1, Ns = 2 * N + 1;
+  __shared__ unsigned long long s_wmax[4];
+  __shared__ float s_cut;
   double dt;
   int last;
-  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;  // uniform over the grid
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.ncells || P.troubled[i]) return;
-  const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
-  const bool tl = il >= 0 && P.troubled[il], tr = ir >= 0 && P.troubled[ir];
-  if (!tl && !tr) return;
-  const double hlam = 0.5 * dt * P.sp.inv_dx;
-  double GL[kM], GR[kM];
-  if (tl) lim_dg_face<N>(P, i, hlam, GL);
-  if (tr) lim_dg_face<N>(P, i + 1, hlam, GR);
-  double* un = P.u + i * (n * kM);
+  const bool valid = i < P.ncells;
+  double u[n][kM];
+  if (valid) {
+    double* up = P.u + i * (n * kM);
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) u[k][r] = up[k * kM + r];
+    if (!P.troubled[i]) {
+      const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
+      const bool tl = il >= 0 && P.troubled[il], tr = ir >= 0 && P.troubled[ir];
+      if (tl || tr) {
+        const double hlam = 0.5 * dt * P.sp.inv_dx;
+        double GL[kM], GR[kM];
+        if (tl) lim_dg_face<N>(P, i, hlam, GL);
+        if (tr) lim_dg_face<N>(P, i + 1, hlam, GR);
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            double d = 0.0;
+            if (tr) d -= P.ops.psi1[k] * (P.gface[ir * 6 + r] - GR[r]);
+            if (tl) d += P.ops.psi0[k] * (P.gface[il * 6 + 3 + r] - GL[r]);
+            u[k][r] += d / P.ops.w[k];
+            up[k * kM + r] = u[k][r];
+          }
+      }
+    }
+  }
+  if (!P.want_lambda) return;  // uniform over the grid
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  float uf[n][kM], lt[Ns], lt_loc = 0.f;
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
+    for (int r = 0; r < kM; ++r) uf[k][r] = d2f_trunc(u[k][r]);
+#pragma unroll
+  for (int j = 0; j < Ns; ++j) {
+    float v[kM];
+#pragma unroll
     for (int r = 0; r < kM; ++r) {
-      double d = 0.0;
-      if (tr) d -= P.ops.psi1[k] * (P.gface[ir * 6 + r] - GR[r]);
-      if (tl) d += P.ops.psi0[k] * (P.gface[il * 6 + 3 + r] - GL[r]);
-      un[k * kM + r] += d / P.ops.w[k];
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < n; ++k) acc = fmaf(P.Pf[j][k], uf[k][r], acc);
+      v[r] = acc;
     }
+    const float inv = 1.f / v[0];
+    const float uu = v[1] * inv;
+    const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
+      lt[j] = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
+    else
+      lt[j] = fabsf(uu) + sqrtf(gf * pp * inv);
+    if (valid) lt_loc = fmaxf(lt_loc, lt[j]);
+  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
+  if (threadIdx.x == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  const float cut = s_cut;
+  double lmax = 0.0;
+  bool bad = false;
+  if (valid) {
+#pragma unroll
+    for (int j = 0; j < Ns; ++j) {
+      if (!(lt[j] >= cut)) continue;
+      double v[kM];
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], u[k][r], acc);
+        v[r] = acc;
+      }
+      lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
+    }
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
+  if (threadIdx.x == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);
+  if (bad) atomicOr(&P.sp.ctl->status, kStNonPhysical);
 }
 
 }  // namespace ader

@@ -21,11 +21,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ader_oracle.c")
 _SRC_RS = os.path.join(_HERE, "ader_oracle_src.c")
 _SRC_LIM = os.path.join(_HERE, "ader_oracle_lim.c")
+_SRC_2D = os.path.join(_HERE, "ader_oracle_2d.c")
 _HDR = os.path.join(_HERE, "ader_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
 
 M = 3
 MRS = 5  # reacting system: rho, m, E, rho c1, rho c2
+M2 = 4   # 2D Euler: rho, m_x, m_y, E
 MAXN = 10
 MAXNS = 19
 
@@ -37,11 +39,12 @@ OB_ERR_NONPHYSICAL = 5
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _SRC_2D, _HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, _SRC_LIM, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, _SRC_LIM, _SRC_2D,
+           "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -145,6 +148,20 @@ def lib():
                                    C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
                                    P(C.c_double)]
             L.ob_r_matrix.argtypes = [P(Basis), _DP]
+            L.ob2_flux.argtypes = [C.c_double, _DP, _DP, _DP]
+            L.ob2_flux.restype = None
+            L.ob2_rusanov.argtypes = [C.c_double, C.c_int, _DP, _DP, _DP]
+            L.ob2_rusanov.restype = None
+            L.ob2_predict_cell.argtypes = [P(Basis), P(Params), C.c_double, C.c_double, _DP, _DP,
+                                           P(C.c_int)]
+            L.ob2_dg_step.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double,
+                                      C.c_double, C.c_double, _DP, _DP, P(Stats)]
+            L.ob2_dt.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                 _DP]
+            L.ob2_dt.restype = C.c_double
+            L.ob2_solve.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double,
+                                    C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
+                                    P(C.c_double)]
             L.ob_lim_weno2.argtypes = [_DP, _DP, _DP, _DP, _DP]
             L.ob_lim_weno2.restype = None
             L.ob_dgl_step.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double,
@@ -537,3 +554,92 @@ def fv_density_errors(v, rho_avg_exact, x0: float = 0.0, x1: float = 1.0):
 def order(e1: float, e2: float, h1: float, h2: float) -> float:
     """Empirical convergence order p = ln(e1/e2)/ln(h1/h2)."""
     return float(np.log(e1 / e2) / np.log(h1 / h2))
+
+
+# ---------------------------------------------------------------------------
+# 2D Euler on a periodic Cartesian mesh (ader_oracle_2d.c)
+# ---------------------------------------------------------------------------
+
+class Oracle2D:
+    """ADER-DG for the 2D Euler equations on [x0, x1] x [y0, y1], periodic: state
+    u[iy][ix][k1][k2][r] (k1 the xi node, k2 the eta node, r = rho, m_x, m_y, E),
+    the tensor-product predictor of Sec. 1.1 and the corrector of Sec. 1.2."""
+
+    def __init__(self, N: int, gamma: float = 1.4, cfl: float = 0.4, tol: float = 1e-13,
+                 max_iter: int | None = None, fixed_iter: int = 0):
+        self.base = Oracle(N, gamma=gamma, cfl=cfl, tol=tol, max_iter=max_iter,
+                           fixed_iter=fixed_iter)
+        self.N, self.n = N, N + 1
+        self.basis, self.params = self.base.basis, self.base.params
+
+    def table(self, name):
+        return self.base.table(name)
+
+    def set(self, **kw):
+        self.base.set(**kw)
+        return self
+
+    def node_xy(self, nx: int, ny: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+        """(X, Y) of shape [ny][nx][n][n] (k1 along x, k2 along y)."""
+        xi = self.table("xi")
+        dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+        X = x0 + dx * (np.arange(nx)[None, :, None, None] + xi[None, None, :, None])
+        Y = y0 + dy * (np.arange(ny)[:, None, None, None] + xi[None, None, None, :])
+        return np.broadcast_to(X, (ny, nx, self.n, self.n)), np.broadcast_to(Y, (ny, nx, self.n, self.n))
+
+    def flux(self, U):
+        F, G = np.zeros(M2), np.zeros(M2)
+        lib().ob2_flux(self.params.gamma, _arr(U, M2), F, G)
+        return F, G
+
+    def rusanov(self, direction: int, a, b):
+        H = np.zeros(M2)
+        lib().ob2_rusanov(self.params.gamma, direction, _arr(a, M2), _arr(b, M2), H)
+        return H
+
+    def predict_cell(self, u_cell, lx: float, ly: float):
+        q = np.zeros(self.n ** 3 * M2)
+        it = C.c_int(0)
+        rc = lib().ob2_predict_cell(C.byref(self.basis), C.byref(self.params), lx, ly,
+                                    _arr(u_cell, self.n * self.n * M2), q, C.byref(it))
+        return q.reshape(self.n, self.n, self.n, M2), it.value, rc
+
+    def step(self, u, nx: int, ny: int, dx: float, dy: float, dt: float):
+        u = _arr(u).ravel()
+        out = np.zeros_like(u)
+        st = Stats()
+        rc = lib().ob2_dg_step(C.byref(self.basis), C.byref(self.params), nx, ny, dx, dy, dt, u,
+                               out, C.byref(st))
+        return out, rc, st.mean_iters
+
+    def dt(self, u, nx: int, ny: int, dx: float, dy: float) -> float:
+        return lib().ob2_dt(C.byref(self.basis), C.byref(self.params), nx, ny, dx, dy,
+                            _arr(u).ravel())
+
+    def solve(self, u, nx: int, ny: int, dx: float, dy: float, t_end: float = 0.0,
+              max_steps: int = 0):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        steps, t = C.c_int64(0), C.c_double(0.0)
+        rc = lib().ob2_solve(C.byref(self.basis), C.byref(self.params), nx, ny, dx, dy, u, t_end,
+                             max_steps, C.byref(steps), C.byref(t))
+        return u, steps.value, t.value, rc
+
+
+def dg2_density_errors(orc: Oracle2D, u, nx: int, ny: int, rho_exact, x0=0.0, x1=1.0, y0=0.0,
+                       y1=1.0, npts: int = 25):
+    """L1, L2 and Linf errors of the density of a 2D DG solution (eq. epsilons):
+    the npts x npts Gauss-Legendre rule per cell for the integrals, Linf over the
+    same points."""
+    u = np.asarray(u, dtype=np.float64).reshape(ny, nx, orc.n, orc.n, M2)
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1.0), 0.5 * gw
+    phi = np.stack([orc.base.phi(x) for x in gx])  # [npts, n]
+    rho_h = np.einsum("ak,bl,yxkl->yxab", phi, phi, u[..., 0])
+    X = x0 + dx * (np.arange(nx)[None, :, None, None] + gx[None, None, :, None])
+    Y = y0 + dy * (np.arange(ny)[:, None, None, None] + gx[None, None, None, :])
+    err = np.abs(rho_h - rho_exact(X, Y))
+    wts = dx * dy * np.outer(gw, gw)
+    l1 = float((err * wts).sum())
+    l2 = float(np.sqrt((err ** 2 * wts).sum()))
+    return l1, l2, float(err.max())

@@ -218,6 +218,27 @@ int ob_dgl_solve(const ob_basis* b, const ob_params* p, const ob_lim_params* lp,
                  double dx, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
                  double* t_out, int64_t* troubled_total);
 
+/* ------------------------------------------------------------------------
+ * 2D Euler on a periodic Cartesian mesh (ader_oracle_2d.c): state
+ * u[cell][k1][k2][r], cell = iy nx + ix, r = (rho, m_x, m_y, E); predictor
+ * q[p0][p1][p2][r]; the tensor-product predictor of Sec. 1.1 (L^xi = kappa~ (x)
+ * k~ (x) I, L^eta = kappa~ (x) I (x) k~), the corrector of Sec. 1.2 with x- and
+ * y-faces, dt = CFL / (2 (2N+1)) min(dx / lambda_x, dy / lambda_y) over the
+ * Ns x Ns subcell averages (Sec. 1.5, d = 2).
+ * ---------------------------------------------------------------------- */
+#define OB2_M 4
+void ob2_flux(double gamma, const double* U, double* F, double* G);
+double ob2_speed(double gamma, const double* U, int dir);
+void ob2_rusanov(double gamma, int dir, const double* a, const double* b, double* H);
+int ob2_predict_cell(const ob_basis* b, const ob_params* p, double lx, double ly, const double* u,
+                     double* q, int* iters);
+int ob2_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx,
+                double dy, double dt, const double* u, double* u_new, ob_stats* st);
+double ob2_dt(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx, double dy,
+              const double* u);
+int ob2_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx, double dy,
+              double* u, double t_end, int64_t max_steps, int64_t* steps_out, double* t_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,26 @@ ader_status ader_default_options(ader_options* opt);
  *   no device memory.  *out owns host memory only; free with ader_destroy(). */
 ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_options* opt,
                       ader_ctx** out);
+/* The 2D Euler equations on a periodic Cartesian mesh (Sec. 1.1 tensor-product
+ * predictor with L^xi = kappa~ (x) k~ (x) I and L^eta = kappa~ (x) I (x) k~,
+ * Sec. 1.2 corrector with x- and y-faces, Sec. 1.5 time step with d = 2):
+ *   mesh: nx x ny cells on [x0, x1] x [y0, y1] (host pointer, read);
+ *   state u[cell][k1][k2][r], cell = iy nx + ix, k1 the xi node, k2 the eta
+ *   node, r = (rho, m_x, m_y, E), FP64, n_cells = nx ny (ader_state_count);
+ *   degree 0..7; options: DG, Euler, FP64 predictor, periodic, no limiter
+ *   (anything else: ADER_ERR_ARG).
+ * The context works with ader_workspace_bytes, ader_bind, ader_step,
+ * ader_solve, ader_solve_from, ader_solve_host, ader_compute_dt,
+ * ader_get_stats, ader_get_table and ader_destroy; the 1D-only calls
+ * (ader_predict, ader_correct, ader_node_coords, ader_step_noalloc,
+ * ader_autotune, ader_get_troubled) return ADER_ERR_ARG. */
+typedef struct {
+  int64_t nx, ny;
+  double x0, x1, y0, y1;
+} ader_mesh2d;
+ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options* opt,
+                         ader_ctx** out);
+
 void ader_destroy(ader_ctx* ctx);
 const char* ader_last_error(const ader_ctx* ctx);
 const char* ader_status_string(int status);

@@ -40,6 +40,11 @@ class Mesh(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("x0", C.c_double), ("x1", C.c_double)]
 
 
+class Mesh2D(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double)]
+
+
 class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
                 ("picard_max_iter", C.c_int), ("picard_fixed_iter", C.c_int),
@@ -122,6 +127,7 @@ def load(build_if_missing: bool = True):
             "ader_solve_host": ([V, V, D, I64, P(I64), P(D)], C.c_int),
             "ader_solve_from": ([V, V, D, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
+            "ader_init_2d": ([V, C.c_int, V, V], C.c_int),
             "ader_get_troubled": ([V, V, I64], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
             "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
@@ -153,7 +159,7 @@ def exported_symbols():
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_solve_from",
-            "ader_get_stats", "ader_get_troubled",
+            "ader_get_stats", "ader_get_troubled", "ader_init_2d",
             "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
             "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
@@ -217,6 +223,12 @@ class Context:
         if rc != ADER_OK:
             raise AderError(rc, f"ader_init failed ({L.ader_status_string(rc).decode()})")
         self._ctx = ctx
+        self._bind_workspace(device)
+        self.vars = SYSTEM_VARS[self.options.system] if scheme == "dg" else 3
+
+    def _bind_workspace(self, device):
+        torch = _torch()
+        L, ctx = self._L, self._ctx
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         nbytes = int(L.ader_workspace_bytes(ctx))
@@ -228,7 +240,6 @@ class Context:
         self.state_count = int(L.ader_state_count(ctx))
         self.predictor_count = int(L.ader_predictor_count(ctx))
         self.workspace_bytes = nbytes
-        self.vars = SYSTEM_VARS[self.options.system] if scheme == "dg" else 3
 
     # -- helpers --
     def _check(self, rc: int, ok=(ADER_OK,)):
@@ -375,6 +386,47 @@ class Context:
                 "profiled_steps": s.profiled_steps, "weno_ms": s.weno_ms,
                 "predict_ms": s.predict_ms, "face_ms": s.face_ms,
                 "kernel_launches": s.kernel_launches, "troubled_cells": s.troubled_cells}
+
+
+class Context2D(Context):
+    """An ader_ctx of the 2D Euler equations on a periodic nx x ny Cartesian mesh
+    (ader_init_2d); state [iy][ix][k1][k2][4] with r = (rho, m_x, m_y, E).
+    ader_step / ader_solve / ader_solve_host / ader_compute_dt / ader_get_stats
+    work as for 1D contexts."""
+
+    def __init__(self, nx: int, ny: int, degree: int, x0: float = 0.0, x1: float = 1.0,
+                 y0: float = 0.0, y1: float = 1.0, device=None, **options):
+        L = load()
+        self._L = L
+        self.nx, self.ny = int(nx), int(ny)
+        self.n_cells = self.nx * self.ny
+        self.degree = int(degree)
+        self.scheme = "dg"
+        self.n = self.degree + 1
+        self.bounds = (float(x0), float(x1), float(y0), float(y1))
+        mesh = Mesh2D(self.nx, self.ny, *self.bounds)
+        self.options = default_options(**options)
+        ctx = C.c_void_p()
+        rc = L.ader_init_2d(C.byref(mesh), self.degree, C.byref(self.options), C.byref(ctx))
+        if rc != ADER_OK:
+            raise AderError(rc, f"ader_init_2d failed ({L.ader_status_string(rc).decode()})")
+        self._ctx = ctx
+        self._bind_workspace(device)
+        self.vars = 4
+
+    def state_shape(self):
+        return (self.ny, self.nx, self.n, self.n, 4)
+
+    def node_coords(self):
+        """(X, Y), each [ny][nx][n][n]: the GL nodes of every cell (k1 along x, k2 along y)."""
+        import numpy as np
+        xi = self.table("xi")
+        x0, x1, y0, y1 = self.bounds
+        dx, dy = (x1 - x0) / self.nx, (y1 - y0) / self.ny
+        X = x0 + dx * (np.arange(self.nx)[None, :, None, None] + xi[None, None, :, None])
+        Y = y0 + dy * (np.arange(self.ny)[:, None, None, None] + xi[None, None, None, :])
+        shape = (self.ny, self.nx, self.n, self.n)
+        return np.broadcast_to(X, shape).copy(), np.broadcast_to(Y, shape).copy()
 
 
 class NoAllocStep:

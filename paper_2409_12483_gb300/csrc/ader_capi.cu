@@ -38,6 +38,10 @@ struct ader_ctx {
   int N = 0, n = 1, scheme = 0;
   int M = kM;  // variables per node: 3 (Euler) or kMR (reacting system)
   double dx = 0.0;
+  int dims = 1;                   // 2: the 2D Euler mesh of ader_init_2d
+  long long nx = 0, ny = 0;       // 2D: cells per direction (mesh.n_cells = nx ny)
+  double dy = 0.0;
+  double* gface2 = nullptr;       // 2D: face fluxes [cell][dir][k][4]
   // workspace (caller-owned)
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -96,11 +100,13 @@ ader_status fail(ader_ctx* c, ader_status st, const char* fmt, ...) {
 bool is_weno_degree(int N) { return N == 2 || N == 4; }
 
 int64_t state_count(const ader_ctx* c) {
+  if (c->dims == 2) return c->mesh.n_cells * c->n * c->n * kM2;
   return c->scheme == ADER_SCHEME_DG ? c->mesh.n_cells * c->n * c->M : c->mesh.n_cells * kM;
 }
 
 // DG: [cell][qR | qL | u + volume (+ source)], M n doubles each; FV: [cell][qR | qL]
 size_t trace_doubles(const ader_ctx* c) {
+  if (c->dims == 2) return (size_t)c->mesh.n_cells * 5 * c->n * c->n * kM2;  // xR xL yR yL volume
   return (size_t)c->mesh.n_cells * (c->scheme == ADER_SCHEME_DG ? 3 : 2) * c->M * c->n;
 }
 
@@ -109,6 +115,7 @@ size_t workspace_bytes(const ader_ctx* c) {
   b += align_up(trace_doubles(c) * sizeof(double));
   if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
   b += 2 * align_up((size_t)state_count(c) * sizeof(double));
+  if (c->dims == 2) b += align_up((size_t)c->mesh.n_cells * 2 * c->n * kM2 * sizeof(double));
   if (c->opt.limiter)
     b += 2 * align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
          align_up((size_t)c->mesh.n_cells * 12 * sizeof(double)) +
@@ -118,6 +125,7 @@ size_t workspace_bytes(const ader_ctx* c) {
 }
 
 int kernels_per_step(const ader_ctx* c) {
+  if (c->dims == 2) return 4;  // predictor, face fluxes, update, lambda_max
   int k = c->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
   if (c->opt.limiter) k += 4;
   return k;
@@ -133,6 +141,8 @@ StepParams make_step(const ader_ctx* c, int mode, int par, double dt, double t_e
   sp.max_steps = max_steps;
   sp.cfl_factor = c->scheme == ADER_SCHEME_DG ? c->opt.cfl * c->dx / (double)(2 * c->N + 1)
                                               : c->opt.cfl * c->dx;
+  // 2D: dt = CFL / (d (2N+1)) / max(lambda_x / dx, lambda_y / dy), d = 2 (Sec. 1.5)
+  if (c->dims == 2) sp.cfl_factor = c->opt.cfl / (2.0 * (double)(2 * c->N + 1));
   sp.inv_dx = 1.0 / c->dx;
   sp.ctl = c->ctl;
   return sp;
@@ -203,9 +213,33 @@ CflParams make_cfl(const ader_ctx* ctx, const double* u, int slot) {
   return p;
 }
 
+Cfl2DParams make_cfl2d(const ader_ctx* ctx, const double* u, int slot) {
+  Cfl2DParams p{};
+  p.u = u;
+  p.ncells = ctx->mesh.n_cells;
+  p.gamma = ctx->opt.gamma;
+  p.gm1 = ctx->opt.gamma - 1.0;
+  p.inv_dx = 1.0 / ctx->dx;
+  p.inv_dy = 1.0 / ctx->dy;
+  p.ctl = ctx->ctl;
+  p.slot = slot;
+  for (int j = 0; j < kMaxNs; ++j)
+    for (int k = 0; k < kMaxN; ++k) {
+      p.P[j][k] = ctx->basis.d.P[j][k];
+      p.Pf[j][k] = (float)ctx->basis.d.P[j][k];
+    }
+  return p;
+}
+
 // enqueue the CFL kernel into lam[slot] (resets the slot first)
 ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
   CK(cudaMemsetAsync(&ctx->ctl->lam[slot], 0, sizeof(unsigned long long), ctx->stream));
+  if (ctx->dims == 2) {
+    Cfl2DParams p = make_cfl2d(ctx, u, slot);
+    CK(do_cfl2d(ctx->N, p, ctx->stream));
+    ctx->launches += 1;
+    return ADER_OK;
+  }
   CflParams p = make_cfl(ctx, u, slot);
   CK(do_cfl(ctx->N, p, ctx->stream));
   ctx->launches += 1;
@@ -249,8 +283,51 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
 
 // one step from src to dst with the given step parameters; ev (4 events or
 // null) are recorded around the kernels as external event nodes when captured
+// one 2D step: predictor, face fluxes + update, lambda_max of the new state
+ader_status enqueue_step2d(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
+                           int want_lambda, cudaEvent_t* ev) {
+  if (ev) CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], ctx->stream, cudaEventRecordExternal));
+  Predict2DParams p{};
+  p.u = src;
+  p.trace = ctx->trace;
+  p.ncells = ctx->mesh.n_cells;
+  p.max_iter = ctx->opt.picard_max_iter;
+  p.fixed_iter = ctx->opt.picard_fixed_iter;
+  p.tol = ctx->opt.picard_tol;
+  p.gamma = ctx->opt.gamma;
+  p.gm1 = ctx->opt.gamma - 1.0;
+  p.inv_dy = 1.0 / ctx->dy;
+  p.sp = sp;
+  p.ops = ctx->basis.d;
+  CK(do_predict2d(ctx->N, p, ctx->stream));
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], ctx->stream, cudaEventRecordExternal));
+  Face2DParams f{};
+  f.trace = ctx->trace;
+  f.gface = ctx->gface2;
+  f.u_new = dst;
+  f.ncells = ctx->mesh.n_cells;
+  f.nx = ctx->nx;
+  f.ny = ctx->ny;
+  f.gamma = ctx->opt.gamma;
+  f.gm1 = ctx->opt.gamma - 1.0;
+  f.inv_dy = 1.0 / ctx->dy;
+  f.sp = sp;
+  f.ops = ctx->basis.d;
+  CK(do_face2d(ctx->N, f, ctx->stream));
+  ctx->launches += 3;
+  if (want_lambda) {  // the predictor of this step has reset the slot
+    Cfl2DParams c = make_cfl2d(ctx, dst, sp.par ^ 1);
+    CK(do_cfl2d(ctx->N, c, ctx->stream));
+    ctx->launches += 1;
+  }
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
+  return ADER_OK;
+}
+
 ader_status enqueue_step(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
                          int want_lambda, cudaEvent_t* ev = nullptr) {
+  if (ctx->dims == 2) return enqueue_step2d(ctx, src, dst, sp, want_lambda, ev);
   const double* nodal = src;
   if (ev) CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
   if (ctx->scheme == ADER_SCHEME_WENO_FV) {
@@ -420,6 +497,37 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   return ADER_OK;
 }
 
+ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options* opt,
+                         ader_ctx** out) {
+  if (!out) return ADER_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || mesh->nx <= 0 || mesh->ny <= 0 || !(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0))
+    return ADER_ERR_ARG;
+  if (degree < 0 || degree > kMaxDeg) return ADER_ERR_ARG;
+  if (mesh->nx > ((int64_t)1 << 30) / mesh->ny) return ADER_ERR_ARG;
+  ader_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    ader_default_options(&o);
+  }
+  // the 2D path: DG, Euler, FP64 predictor, periodic, no limiter
+  if (o.system != ADER_SYSTEM_EULER || o.precision != ADER_PREC_FP64 || o.bc != ADER_BC_PERIODIC ||
+      o.limiter != 0)
+    return ADER_ERR_ARG;
+  ader_mesh m1{mesh->nx * mesh->ny, mesh->x0, mesh->x1};
+  ader_ctx* c = nullptr;
+  ader_status st = ader_init(&m1, degree, ADER_SCHEME_DG, &o, &c);
+  if (st != ADER_OK) return st;
+  c->dims = 2;
+  c->nx = mesh->nx;
+  c->ny = mesh->ny;
+  c->dx = (mesh->x1 - mesh->x0) / (double)mesh->nx;
+  c->dy = (mesh->y1 - mesh->y0) / (double)mesh->ny;
+  *out = c;
+  return ADER_OK;
+}
+
 void ader_destroy(ader_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -440,12 +548,13 @@ const char* ader_last_error(const ader_ctx* c) { return c ? c->err : "null conte
 
 int64_t ader_state_count(const ader_ctx* c) { return c ? state_count(c) : -1; }
 int64_t ader_predictor_count(const ader_ctx* c) {
+  if (c && c->dims == 2) return c->mesh.n_cells * c->n * c->n * c->n * kM2;
   return c ? c->mesh.n_cells * c->n * c->n * c->M : -1;
 }
 size_t ader_workspace_bytes(const ader_ctx* c) { return c ? workspace_bytes(c) : 0; }
 
 ader_status ader_node_coords(const ader_ctx* c, double* x, int64_t count) {
-  if (!c || !x) return ADER_ERR_ARG;
+  if (!c || !x || c->dims != 1) return ADER_ERR_ARG;
   const int per = c->scheme == ADER_SCHEME_DG ? c->n : 1;
   if (count != c->mesh.n_cells * per) return ADER_ERR_ARG;
   for (int64_t i = 0; i < c->mesh.n_cells; ++i)
@@ -545,6 +654,10 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
   p += align_up((size_t)state_count(ctx) * sizeof(double));
   ctx->hbuf = reinterpret_cast<double*>(p);
   p += align_up((size_t)state_count(ctx) * sizeof(double));
+  if (ctx->dims == 2) {
+    ctx->gface2 = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 2 * ctx->n * kM2 * sizeof(double));
+  }
   if (ctx->opt.limiter) {
     ctx->lim_mm = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
@@ -587,6 +700,7 @@ ader_status ader_compute_dt(ader_ctx* ctx, const double* u, double t, double t_e
 ader_status ader_predict(ader_ctx* ctx, const double* u, double dt, double* q) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
+  if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_predict is 1D only");
   if (!u || !q) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (std::isnan(dt)) return fail(ctx, ADER_ERR_ARG, "dt is NaN");
   if ((st = fork_in(ctx)) != ADER_OK) return st;
@@ -618,6 +732,7 @@ ader_status ader_correct(ader_ctx* ctx, const double* u, const double* q, double
                          double* u_new) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
+  if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_correct is 1D only");
   if (!u || !q || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (!(dt > 0.0)) return fail(ctx, ADER_ERR_ARG, "ader_correct needs dt > 0");
   if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
@@ -824,6 +939,7 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
 ader_status ader_get_troubled(ader_ctx* ctx, int32_t* flags, int64_t count) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
+  if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "the limiter is 1D only");
   if (!ctx->opt.limiter) return fail(ctx, ADER_ERR_ARG, "troubled flags need the limiter");
   if (!flags || count != ctx->mesh.n_cells) return fail(ctx, ADER_ERR_ARG, "flags / count");
   if ((st = fork_in(ctx)) != ADER_OK) return st;
@@ -915,6 +1031,7 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
   if (!u || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, ADER_ERR_ARG, "ader_step_noalloc needs dt > 0");
+  if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_step_noalloc is 1D only");
   if (ctx->opt.limiter)
     return fail(ctx, ADER_ERR_ARG, "the limiter keeps per-cell data in the bound workspace");
   const size_t trace_bytes = trace_doubles(ctx) * sizeof(double);
@@ -989,6 +1106,7 @@ extern "C" ader_status ader_set_tuning(ader_ctx* ctx, const ader_tuning* in) {
 extern "C" ader_status ader_autotune(ader_ctx* ctx, const double* u, int reps, ader_tuning* out) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
+  if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_autotune tunes the 1D kernels");
   if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (reps < 1) reps = 3;
   double dt = 0.0;

@@ -4,6 +4,7 @@
 #include "ader_kernels.cuh"
 #include "ader_source.cuh"
 #include "ader_limiter.cuh"
+#include "ader_kernels2d.cuh"
 
 #ifndef ADER_DEG
 #error "compile with -DADER_DEG=<0..7>"
@@ -149,6 +150,26 @@ cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t
   lim_detect_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_recompute_kernel<D><<<grec, 32 * kLimWarps, 0, s>>>(p);
   lim_finish_kernel<D><<<g128, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_predict2d_, ADER_DEG)(const Predict2DParams& p, cudaStream_t s) {
+  using C = Pred2Cfg<D>;
+  predict2d_kernel<D><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// the face fluxes, then the update (which ends the step on the device)
+cudaError_t ADER_CAT(launch_face2d_, ADER_DEG)(const Face2DParams& p, cudaStream_t s) {
+  constexpr int n = D + 1;
+  face2d_kernel<D><<<grid_for(p.ncells * 2 * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+  update2d_kernel<D><<<grid_for(p.ncells * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t ADER_CAT(launch_cfl2d_, ADER_DEG)(const Cfl2DParams& p, cudaStream_t s) {
+  constexpr int Ns = 2 * D + 1;
+  cfl2d_kernel<D><<<grid_for(p.ncells * Ns * Ns, 256, 0x7fffffffLL), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

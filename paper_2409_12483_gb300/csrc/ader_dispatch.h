@@ -45,6 +45,15 @@ inline cudaError_t do_weno(int N, const WenoParams& p, cudaStream_t s) {
 inline cudaError_t do_limiter(int N, const LimParams& p, cudaStream_t s) {
   ADER_DISPATCH(launch_limiter, N, p, s)
 }
+inline cudaError_t do_predict2d(int N, const Predict2DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_predict2d, N, p, s)
+}
+inline cudaError_t do_face2d(int N, const Face2DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_face2d, N, p, s)
+}
+inline cudaError_t do_cfl2d(int N, const Cfl2DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_cfl2d, N, p, s)
+}
 
 
 #define ADER_DISPATCH4(fn, N, a, b, c, d) \

@@ -1,0 +1,398 @@
+// ader_kernels2d.cuh -- sm_103a kernels of the ADER-DG scheme for the 2D Euler
+// equations on a periodic Cartesian mesh (Popov, arXiv 2409.12483): the
+// tensor-product LST-DG predictor of Sec. 1.1 (eq. lst_dg_predictor_picard with
+// L^xi = kappa~ (x) k~ (x) I, L^eta = kappa~ (x) I (x) k~, L^0 = delta by
+// eq. ind_prop), the corrector of Sec. 1.2 (eq. ader_dg_method_full with x- and
+// y-faces) and lambda_max for the time step of Sec. 1.5 with d = 2.
+//
+// State u[cell][k1][k2][r], cell = iy nx + ix, k1 the xi node, k2 the eta node,
+// r = (rho, m_x, m_y, E).  Trace record per cell (doubles): xR | xL | yR | yL,
+// each [l0][k][4] (the predictor at xi = 1, xi = 0, eta = 1, eta = 0 per tau
+// node l0 and transverse node k), then the volume term [k1][k2][4].
+//
+// predict2d_kernel   one thread per space-time node (p0, p1, p2) of a cell,
+//                    several cells per block: rescaled x- and y-fluxes exchanged
+//                    through shared memory for the k~ contractions along xi and
+//                    eta, their sum exchanged for kappa~ along tau; per-cell
+//                    convergence (the 1D rule); epilogue: traces and volume term.
+// face2d_kernel      one thread per (cell, transverse node, direction): the
+//                    time-integrated Rusanov flux through the cell's left x-face
+//                    or bottom y-face.
+// update2d_kernel    one thread per (cell, node): volume term minus face terms.
+// cfl2d_kernel       one thread per (cell, subcell j1, j2): max(lambda_x / dx,
+//                    lambda_y / dy) over the (P (x) P) u subcell averages, an FP32
+//                    screen confirmed in FP64 like the 1D interface kernel's.
+#pragma once
+
+#include "ader_kernels.cuh"  // device helpers, abs_bits, launch parameter structs
+
+namespace ader {
+
+// x- and y-fluxes of the 2D Euler equations (Sec. 2, eq. system_of_equations)
+__device__ __forceinline__ void euler2_flux(const double* U, double* F, double* G, double gm1) {
+  const double inv = recip(U[0]);
+  const double u = U[1] * inv, v = U[2] * inv;
+  const double p = gm1 * fma(neg_half(U[1]), u, fma(neg_half(U[2]), v, U[3]));
+  F[0] = U[1];
+  F[1] = fma(U[1], u, p);
+  F[2] = U[2] * u;
+  F[3] = (U[3] + p) * u;
+  G[0] = U[2];
+  G[1] = U[1] * v;
+  G[2] = fma(U[2], v, p);
+  G[3] = (U[3] + p) * v;
+}
+
+// Twice the Rusanov flux in direction D (0: x, 1: y) between a (low side) and
+// b (high side); NaN when either state is non-physical.
+template <int D>
+__device__ __forceinline__ void rusanov2_2d(const double* a, const double* b, double* H2,
+                                            double gamma, double gm1) {
+  const double ia = rcp64(a[0]), ib = rcp64(b[0]);
+  const double ua = a[1] * ia, va = a[2] * ia, ub = b[1] * ib, vb = b[2] * ib;
+  const double pa = gm1 * fma(neg_half(a[1]), ua, fma(neg_half(a[2]), va, a[3]));
+  const double pb = gm1 * fma(neg_half(b[1]), ub, fma(neg_half(b[2]), vb, b[3]));
+  const double wa = D == 0 ? ua : va, wb = D == 0 ? ub : vb;  // normal velocities
+  const double sa = fabs(wa) + sqrt64(gamma * pa * ia);
+  const double sb = fabs(wb) + sqrt64(gamma * pb * ib);
+  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
+  // normal flux: m_n (rho), m u_n + p e_n, (E + p) u_n
+  H2[0] = fma(-s, b[0] - a[0], a[1 + D] + b[1 + D]);
+  H2[1] = fma(-s, b[1] - a[1], fma(a[1], wa, D == 0 ? pa : 0.0) + fma(b[1], wb, D == 0 ? pb : 0.0));
+  H2[2] = fma(-s, b[2] - a[2], fma(a[2], wa, D == 1 ? pa : 0.0) + fma(b[2], wb, D == 1 ? pb : 0.0));
+  H2[3] = fma(-s, b[3] - a[3], fma(a[3] + pa, wa, (b[3] + pb) * wb));
+}
+
+template <int N>
+struct Pred2Cfg {
+  static constexpr int n = N + 1, NN = n * n, NST = n * n * n;
+  static constexpr int CPB = NST >= 128 ? 1 : 256 / NST;  // cells per block
+  static constexpr int THREADS = CPB * NST;
+  static constexpr int REC = 5 * NN * kM2;  // trace record doubles per cell
+};
+
+template <int N>
+struct Pred2Shared {
+  using C = Pred2Cfg<N>;
+  double A[C::CPB][C::NST][kM2];  // x-fluxes, then the contraction, then q
+  double B[C::CPB][C::NST][kM2];  // y-fluxes
+  double FB[C::CPB][2][C::NN][kM2];  // time averages of the rescaled fluxes
+  unsigned long long red[C::CPB][2];  // max |q' - q|, max |q'| (bit patterns)
+  int done[C::CPB];
+  double dt;
+  int go;
+};
+
+template <int N>
+__global__ void __launch_bounds__(Pred2Cfg<N>::THREADS)
+    predict2d_kernel(const __grid_constant__ Predict2DParams P) {
+  using C = Pred2Cfg<N>;
+  constexpr int n = N + 1, NN = C::NN, NST = C::NST, CPB = C::CPB;
+  __shared__ Pred2Shared<N> sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double d = 0.0;
+    sh.go = predictor_step_dt(P.sp, &d, blockIdx.x == 0) ? 1 : 0;
+    sh.dt = d;
+  }
+  __syncthreads();
+  if (!sh.go) return;  // uniform
+  const double dt = sh.dt;
+  const double lx = dt * P.sp.inv_dx, ly = dt * P.inv_dy;
+  const int lc = tid / NST, node = tid - lc * NST;
+  const int p0 = node / NN, p1 = (node / n) % n, p2 = node % n;
+  const long long cell = (long long)blockIdx.x * CPB + lc;
+  const bool valid = cell < P.ncells;
+  const OpsD& o = P.ops;
+  double uo[kM2], q[kM2];
+#pragma unroll
+  for (int r = 0; r < kM2; ++r) {
+    uo[r] = valid ? P.u[(cell * NN + p1 * n + p2) * kM2 + r] : 0.0;
+    q[r] = uo[r];
+  }
+  if (node == 0) {
+    sh.done[lc] = valid ? 0 : 1;
+    sh.red[lc][0] = sh.red[lc][1] = 0ull;
+  }
+  __syncthreads();
+  const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+  for (int it = 0; it < cap; ++it) {
+    const bool active = !sh.done[lc];
+    if (active) {
+      double F[kM2], G[kM2];
+      euler2_flux(q, F, G, P.gm1);
+#pragma unroll
+      for (int r = 0; r < kM2; ++r) {
+        sh.A[lc][node][r] = lx * F[r];
+        sh.B[lc][node][r] = ly * G[r];
+      }
+    }
+    __syncthreads();
+    double s[kM2];
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < kM2; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc = fma(o.kt[p1][m], sh.A[lc][(p0 * n + m) * n + p2][r], acc);
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc = fma(o.kt[p2][m], sh.B[lc][(p0 * n + p1) * n + m][r], acc);
+        s[r] = acc;
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = s[r];
+    }
+    __syncthreads();
+    if (active) {
+      unsigned long long dmax = 0ull, qm = 0ull;
+#pragma unroll
+      for (int r = 0; r < kM2; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc = fma(o.kap[p0][m], sh.A[lc][(m * n + p1) * n + p2][r], acc);
+        const double qn = uo[r] - acc;
+        dmax = umax64(dmax, abs_bits(qn - q[r]));
+        qm = umax64(qm, abs_bits(qn));
+        q[r] = qn;
+      }
+      atomicMax(&sh.red[lc][0], dmax);
+      atomicMax(&sh.red[lc][1], qm);
+    }
+    __syncthreads();
+    if (node == 0 && active) {
+      const double delta = bitsd(sh.red[lc][0]), qmax = bitsd(sh.red[lc][1]);
+      const bool conv = P.fixed_iter > 0 ? it + 1 == P.fixed_iter
+                                         : delta <= P.tol * fmax(qmax, 1.0);
+      if (conv || it + 1 == cap) {
+        sh.done[lc] = 1;
+        if (!conv) atomicOr(&P.sp.ctl->status, kStNotConverged);
+        atomicAdd(&P.sp.ctl->iter_sum, (unsigned long long)(it + 1));
+        atomicAdd((unsigned long long*)&P.sp.ctl->iter_cells, 1ull);
+        atomicMax(&P.sp.ctl->iter_max, it + 1);
+      }
+      sh.red[lc][0] = sh.red[lc][1] = 0ull;
+    }
+    __syncthreads();
+    bool all = true;
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) all = all && sh.done[c];
+    if (all) break;  // uniform: every thread reads the same flags
+  }
+  // epilogue: traces at the four sides per tau node, then the volume term
+#pragma unroll
+  for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = q[r];
+  __syncthreads();
+  double* rec = P.trace + cell * C::REC;
+  if (valid && node < NN) {
+    const int l0 = node / n, k = node - l0 * n;
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double aR = 0.0, aL = 0.0, bR = 0.0, bL = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const double qx = sh.A[lc][(l0 * n + m) * n + k][r], qy = sh.A[lc][(l0 * n + k) * n + m][r];
+        aR = fma(o.psi1[m], qx, aR);
+        aL = fma(o.psi0[m], qx, aL);
+        bR = fma(o.psi1[m], qy, bR);
+        bL = fma(o.psi0[m], qy, bL);
+      }
+      rec[0 * NN * kM2 + node * kM2 + r] = aR;
+      rec[1 * NN * kM2 + node * kM2 + r] = aL;
+      rec[2 * NN * kM2 + node * kM2 + r] = bR;
+      rec[3 * NN * kM2 + node * kM2 + r] = bL;
+    }
+  }
+  __syncthreads();
+  {
+    double F[kM2], G[kM2];
+    euler2_flux(q, F, G, P.gm1);
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      sh.A[lc][node][r] = lx * F[r];
+      sh.B[lc][node][r] = ly * G[r];
+    }
+  }
+  __syncthreads();
+  if (node < NN) {
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double fa = 0.0, ga = 0.0;
+#pragma unroll
+      for (int l0 = 0; l0 < n; ++l0) {
+        fa = fma(o.w[l0], sh.A[lc][l0 * NN + node][r], fa);
+        ga = fma(o.w[l0], sh.B[lc][l0 * NN + node][r], ga);
+      }
+      sh.FB[lc][0][node][r] = fa;
+      sh.FB[lc][1][node][r] = ga;
+    }
+  }
+  __syncthreads();
+  if (valid && node < NN) {
+    // this thread's (p1, p2) = (k1, k2): uo holds u[k1][k2]
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double acc = uo[r];
+#pragma unroll
+      for (int l = 0; l < n; ++l) acc = fma(o.vt[p1][l], sh.FB[lc][0][l * n + p2][r], acc);
+#pragma unroll
+      for (int l = 0; l < n; ++l) acc = fma(o.vt[p2][l], sh.FB[lc][1][p1 * n + l][r], acc);
+      rec[4 * NN * kM2 + node * kM2 + r] = acc;
+    }
+  }
+}
+
+// time-integrated rescaled Rusanov flux through the left x-face (dir 0) or the
+// bottom y-face (dir 1) of each cell at transverse node k: [cell][dir][k][4]
+template <int N>
+__global__ void __launch_bounds__(256) face2d_kernel(const __grid_constant__ Face2DParams P) {
+  constexpr int n = N + 1, NN = n * n, REC = Pred2Cfg<N>::REC;
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= P.ncells * 2 * n) return;
+  const long long cell = item / (2 * n);
+  const int rem = (int)(item - cell * 2 * n), dir = rem / n, k = rem - dir * n;
+  const long long iy = cell / P.nx, ix = cell - iy * P.nx;
+  const long long nb = dir == 0 ? iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1)
+                                : (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix;
+  const double* lo = P.trace + nb * REC + (dir == 0 ? 0 : 2) * NN * kM2;   // xR / yR of the neighbour
+  const double* hi = P.trace + cell * REC + (dir == 0 ? 1 : 3) * NN * kM2; // xL / yL of this cell
+  double s[kM2] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int l0 = 0; l0 < n; ++l0) {
+    double a[kM2], b[kM2], H2[kM2];
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      a[r] = lo[(l0 * n + k) * kM2 + r];
+      b[r] = hi[(l0 * n + k) * kM2 + r];
+    }
+    if (dir == 0)
+      rusanov2_2d<0>(a, b, H2, P.gamma, P.gm1);
+    else
+      rusanov2_2d<1>(a, b, H2, P.gamma, P.gm1);
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) s[r] = fma(P.ops.w[l0], H2[r], s[r]);
+  }
+  const double h = 0.5 * dt * (dir == 0 ? P.sp.inv_dx : P.inv_dy);
+#pragma unroll
+  for (int r = 0; r < kM2; ++r) P.gface[item * kM2 + r] = h * s[r];
+}
+
+// u^{n+1}[k1][k2] = volume term - (psi~_k1 Gx_right - psi_k1 Gx_left) / w_k1
+//                               - (psi~_k2 Gy_top - psi_k2 Gy_bottom) / w_k2
+template <int N>
+__global__ void __launch_bounds__(256) update2d_kernel(const __grid_constant__ Face2DParams P) {
+  constexpr int n = N + 1, NN = n * n, REC = Pred2Cfg<N>::REC;
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item < P.ncells * NN) {
+    const long long cell = item / NN;
+    const int k = (int)(item - cell * NN), k1 = k / n, k2 = k - k1 * n;
+    const long long iy = cell / P.nx, ix = cell - iy * P.nx;
+    const long long cr = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1);
+    const long long ct = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix;
+    const double* vol = P.trace + cell * REC + 4 * NN * kM2 + k * kM2;
+    const double* gxl = P.gface + ((cell * 2 + 0) * n + k2) * kM2;
+    const double* gxr = P.gface + ((cr * 2 + 0) * n + k2) * kM2;
+    const double* gyb = P.gface + ((cell * 2 + 1) * n + k1) * kM2;
+    const double* gyt = P.gface + ((ct * 2 + 1) * n + k1) * kM2;
+    const OpsD& o = P.ops;
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      const double fx = fma(o.psi1[k1], gxr[r], -o.psi0[k1] * gxl[r]);
+      const double fy = fma(o.psi1[k2], gyt[r], -o.psi0[k2] * gyb[r]);
+      P.u_new[item * kM2 + r] = fma(-fy, o.rw[k2], fma(-fx, o.rw[k1], vol[r]));
+    }
+  }
+  if (item == 0) corrector_finish(P.sp, dt, last, true);
+}
+
+// max over the Ns x Ns subcells of every cell of max(lambda_x / dx, lambda_y / dy)
+// into ctl->lam[slot]; non-physical subcell averages set the status
+template <int N>
+__global__ void __launch_bounds__(256) cfl2d_kernel(const __grid_constant__ Cfl2DParams P) {
+  constexpr int n = N + 1, NN = n * n, Ns = 2 * N + 1;
+  __shared__ unsigned long long s_wmax[8];
+  __shared__ float s_cut;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = item < P.ncells * Ns * Ns;
+  long long cell = 0;
+  int j1 = 0, j2 = 0;
+  if (valid) {
+    cell = item / (Ns * Ns);
+    const int j = (int)(item - cell * Ns * Ns);
+    j1 = j / Ns;
+    j2 = j - j1 * Ns;
+  }
+  const double* u = P.u + cell * NN * kM2;
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  const float idx = (float)P.inv_dx, idy = (float)P.inv_dy;
+  float lt = 0.f;
+  if (valid) {
+    float v[kM2];
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) {
+        float t = 0.f;
+#pragma unroll
+        for (int k2 = 0; k2 < n; ++k2) t = fmaf(P.Pf[j2][k2], d2f_trunc(u[(k1 * n + k2) * kM2 + r]), t);
+        acc = fmaf(P.Pf[j1][k1], t, acc);
+      }
+      v[r] = acc;
+    }
+    const float inv = 1.f / v[0];
+    const float uu = v[1] * inv, vv = v[2] * inv;
+    const float pp = gm1f * (v[3] - 0.5f * (v[1] * uu + v[2] * vv));
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[3])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
+      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
+    } else {
+      const float c = sqrtf(gf * pp * inv);
+      lt = fmaxf((fabsf(uu) + c) * idx, (fabsf(vv) + c) * idy);
+    }
+  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt), s_wmax);
+  if (threadIdx.x == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  double lmax = 0.0;
+  bool bad = false;
+  if (valid && lt >= s_cut) {
+    double v[kM2];
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) {
+        double t = 0.0;
+#pragma unroll
+        for (int k2 = 0; k2 < n; ++k2) t = fma(P.P[j2][k2], u[(k1 * n + k2) * kM2 + r], t);
+        acc = fma(P.P[j1][k1], t, acc);
+      }
+      v[r] = acc;
+    }
+    const double inv = rcp64(v[0]);
+    const double uu = v[1] * inv, vv = v[2] * inv;
+    const double pp = P.gm1 * fma(neg_half(v[1]), uu, fma(neg_half(v[2]), vv, v[3]));
+    if (!(v[0] > 0.0) || !(pp > 0.0) || !(v[0] < 1.0e300) || !(pp < 1.0e300)) {
+      bad = true;
+    } else {
+      const double c = sqrt64(P.gamma * pp * inv);
+      lmax = fmax((fabs(uu) + c) * P.inv_dx, (fabs(vv) + c) * P.inv_dy);
+    }
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
+  if (threadIdx.x == 0) atomicMax(&P.ctl->lam[P.slot], bm);
+  if (bad) atomicOr(&P.ctl->status, kStNonPhysical);
+}
+
+}  // namespace ader

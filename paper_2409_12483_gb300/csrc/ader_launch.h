@@ -132,6 +132,41 @@ struct LimParams {
   float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening pass of lambda_max)
 };
 
+// 2D Euler (ader_kernels2d.cuh): state [cell][k1][k2][4], cell = iy nx + ix.
+struct Predict2DParams {
+  const double* u;
+  double* trace;         // [cell][xR | xL | yR | yL | volume], each [n][n][4]
+  long long ncells;
+  int max_iter, fixed_iter;
+  double tol;
+  double gamma, gm1;
+  double inv_dy;         // 1 / dy (1 / dx travels in sp)
+  StepParams sp;
+  OpsD ops;
+};
+
+struct Face2DParams {
+  const double* trace;
+  double* gface;         // [cell][dir][k][4]: fluxes of the left x-face and bottom y-face
+  double* u_new;
+  long long ncells, nx, ny;
+  double gamma, gm1;
+  double inv_dy;
+  StepParams sp;
+  OpsD ops;
+};
+
+struct Cfl2DParams {
+  const double* u;
+  long long ncells;
+  double gamma, gm1;
+  double inv_dx, inv_dy;
+  DevCtl* ctl;
+  int slot;
+  double P[kMaxNs][kMaxN];
+  float Pf[kMaxNs][kMaxN];
+};
+
 // Per-degree entry points (defined in ader_deg.cu compiled once per degree).
 #define ADER_DECLARE_DEGREE(D)                                                         \
   cudaError_t launch_predict_##D(const PredictParams& p, cudaStream_t s);              \
@@ -143,6 +178,9 @@ struct LimParams {
   cudaError_t launch_face_multi_##D(const FaceParams& p, const MultiArgs& m, int grid,     \
                                     cudaStream_t s);                                    \
   cudaError_t launch_limiter_##D(const LimParams& p, cudaStream_t s);                   \
+  cudaError_t launch_predict2d_##D(const Predict2DParams& p, cudaStream_t s);           \
+  cudaError_t launch_face2d_##D(const Face2DParams& p, cudaStream_t s);                 \
+  cudaError_t launch_cfl2d_##D(const Cfl2DParams& p, cudaStream_t s);                   \
   cudaError_t prepare_degree_##D();
 
 ADER_DECLARE_DEGREE(0)

@@ -23,7 +23,7 @@ def lib():
 def header_functions():
     text = open(os.path.join(ROOT, "include", "ader.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ader_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(ader_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -265,3 +265,27 @@ def test_boundary_and_limiter_options(lib, oracle_mod):
         bad = C.c_void_p()
         assert lib.ader_init(C.byref(Mesh(nc, 0.0, 1.0)), deg, scheme,
                              C.byref(default_options(**kw)), C.byref(bad)) == 1, kw
+
+
+def test_init_2d_options_and_sizes(lib):
+    """ader_init_2d: DG Euler FP64 periodic without limiter only; the state is
+    nx ny (N+1)^2 4 doubles; the 1D-only node coordinates are refused."""
+    from paper_2409_12483_gb300.capi import Mesh2D, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init_2d(C.byref(Mesh2D(6, 5, 0.0, 1.0, 0.0, 2.0)), 4,
+                            C.byref(default_options()), C.byref(ctx)) == 0
+    assert lib.ader_state_count(ctx) == 6 * 5 * 25 * 4
+    assert lib.ader_predictor_count(ctx) == 6 * 5 * 125 * 4
+    assert lib.ader_workspace_bytes(ctx) > 2 * 8 * lib.ader_state_count(ctx)
+    x = np.zeros(30 * 5)
+    assert lib.ader_node_coords(ctx, x.ctypes.data_as(C.c_void_p), x.size) == 1
+    lib.ader_destroy(ctx)
+    for kw in (dict(precision="fp32"), dict(system="reacting"), dict(bc="outflow"), dict(limiter=1)):
+        bad = C.c_void_p()
+        assert lib.ader_init_2d(C.byref(Mesh2D(4, 4, 0.0, 1.0, 0.0, 1.0)), 2,
+                                C.byref(default_options(**kw)), C.byref(bad)) == 1, kw
+    for mesh in (Mesh2D(0, 4, 0.0, 1.0, 0.0, 1.0), Mesh2D(4, 4, 0.0, 1.0, 1.0, 1.0)):
+        bad = C.c_void_p()
+        assert lib.ader_init_2d(C.byref(mesh), 2, None, C.byref(bad)) == 1
+    bad = C.c_void_p()
+    assert lib.ader_init_2d(C.byref(Mesh2D(4, 4, 0.0, 1.0, 0.0, 1.0)), 8, None, C.byref(bad)) == 1

@@ -76,6 +76,43 @@ def predictor_flops_per_cell(n: int, iters: float, dg: bool = True) -> float:
     return first + max(iters - 1.0, 0.0) * it + epi
 
 
+def predictor2d_flops_per_cell(n: int, iters: float) -> float:
+    """Algorithmic FLOPs of one cell's 2D predictor launch (M = 4 variables,
+    n^3 space-time nodes), as the kernel runs it.  Every iteration: the x- and
+    y-fluxes at n^3 nodes with their dt/dx, dt/dy scaling (25 flops: 1 division,
+    2 velocities, 5 for p, 9 for F and G, 8 scalings), k~ along xi and along eta
+    and kappa~ along tau (2 n^4 M each), q' = u - ... and the difference (2 n^3 M).
+    Epilogue: four traces (8 n^3 M), the fluxes again (25 n^3), the two time
+    averages (4 n^3 M) and the two D~ contractions plus u (4 n^3 M + n^2 M)."""
+    m = 4
+    it = 25 * n ** 3 + 6 * n ** 4 * m + 2 * n ** 3 * m
+    epi = 8 * n ** 3 * m + 25 * n ** 3 + 4 * n ** 3 * m + 4 * n ** 3 * m + n * n * m
+    return iters * it + epi
+
+
+def dg2_errors(ctx, u, t, npts=25):
+    """L1, L2, Linf density errors of the 2D sine wave rho = 1 + 0.5 sin 2 pi
+    (x + y - 2 t) (Sec. 2.1, velocity (1, 1)) with an npts x npts GL rule per
+    cell, from the library's own nodes; measurement code, not the oracle."""
+    import numpy as np
+    xi = ctx.table("xi")
+    n = len(xi)
+    u = np.asarray(u).reshape(ctx.ny, ctx.nx, n, n, 4)
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    L = np.ones((npts, n))
+    for k in range(n):
+        for m in range(n):
+            if m != k:
+                L[:, k] *= (gx - xi[m]) / (xi[k] - xi[m])
+    rho = np.einsum("ak,bl,yxkl->yxab", L, L, u[..., 0])
+    X = (np.arange(ctx.nx)[None, :, None, None] + gx[None, None, :, None]) / ctx.nx
+    Y = (np.arange(ctx.ny)[:, None, None, None] + gx[None, None, None, :]) / ctx.ny
+    err = np.abs(rho - (1 + 0.5 * np.sin(2 * np.pi * (X + Y - 2 * t))))
+    wts = np.outer(gw, gw) / (ctx.nx * ctx.ny)
+    return float((err * wts).sum()), float(np.sqrt((err ** 2 * wts).sum())), float(err.max())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -284,6 +321,8 @@ def main():
                     help="skip the coarse-mesh convergence sweeps of the four precision forms")
     ap.add_argument("--no-limiter", action="store_true",
                     help="skip the subcell limiter's Riemann problems and throughput")
+    ap.add_argument("--no-2d", action="store_true",
+                    help="skip the 2D sine-wave table and the 2D throughput lines")
     ap.add_argument("--no-source", action="store_true",
                     help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
@@ -420,6 +459,8 @@ def main():
             line["source_terms"] = run_source(args, dev, flush)
         if not args.no_limiter:
             line["limiter"] = run_limiter(args, dev, flush)
+        if not args.no_2d:
+            line["two_d"] = run_2d(args, dev, flush)
         line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
@@ -589,6 +630,77 @@ def riemann_density_l1(ctx, u, test, t, npts=25):
     L, R = W.RIEMANN_TESTS[test]
     exact, _, _ = W.riemann_solution(L, R, xs, t)
     return float((np.abs(rho - exact) @ gw).sum() / nc)
+
+
+# Table conv_orders_pde_2d (Sec. 2.1), eps_L1 per (N, cells per direction),
+# printed beside this library's errors for comparison only
+PAPER_2D_L1 = {(1, 10): 5.48e-3, (1, 15): 2.44e-3, (1, 20): 1.37e-3, (1, 25): 8.78e-4,
+               (2, 10): 2.87e-4, (2, 15): 8.44e-5, (2, 20): 3.55e-5, (2, 25): 1.81e-5,
+               (3, 10): 1.13e-5, (3, 15): 2.22e-6, (3, 20): 7.02e-7, (3, 25): 2.87e-7,
+               (4, 10): 3.58e-7, (4, 15): 4.67e-8, (4, 20): 1.10e-8, (4, 25): 3.61e-9,
+               (5, 5): 6.09e-7, (5, 10): 9.33e-9, (5, 15): 8.18e-10, (5, 20): 1.45e-10,
+               (6, 5): 2.75e-8, (6, 10): 2.12e-10, (6, 15): 1.23e-11, (6, 20): 1.63e-12,
+               (7, 5): 1.08e-9, (7, 10): 4.13e-12, (7, 15): 1.61e-13, (7, 20): 1.60e-14}
+
+
+def sine2d_state(ctx):
+    import numpy as np
+    X, Y = ctx.node_coords()
+    rho = 1 + 0.5 * np.sin(2 * np.pi * (X + Y))
+    g = 1.4
+    return np.stack([rho, rho, rho, 1 / (g - 1) + rho], -1)  # u = v = 1, p = 1
+
+
+def run_2d(args, dev, flush):
+    """2D Euler (ader_init_2d): the sine-wave advection problem of Sec. 2.1 at
+    the meshes of Table conv_orders_pde_2d to t = 1 through the GPU path (errors,
+    orders, the paper's eps_L1 beside them), and throughput of the 2D solve."""
+    import numpy as np
+    import torch
+
+    from paper_2409_12483_gb300 import Context2D
+    out = {"sine_wave": [], "throughput": []}
+    for N in range(1, 8):
+        meshes = (10, 15, 20, 25) if N <= 4 else (5, 10, 15, 20)
+        prev = None
+        for nc in meshes:
+            ctx = Context2D(nc, nc, N, device=dev)
+            u = torch.tensor(sine2d_state(ctx).ravel(), device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            steps, t, rc = ctx.ader_solve(u, t_end=1.0)
+            e1.record()
+            torch.cuda.synchronize()
+            err = dg2_errors(ctx, u.cpu().numpy(), t)
+            row = {"degree": N, "cells": f"{nc}x{nc}", "steps": steps, "status": rc,
+                   "eps_l1": err[0], "eps_l2": err[1], "eps_linf": err[2],
+                   "paper_eps_l1": PAPER_2D_L1[(N, nc)], "ms": e0.elapsed_time(e1)}
+            if prev is not None:
+                row["order_l1"] = float(np.log(prev[1] / err[0]) / np.log(nc / prev[0]))
+            prev = (nc, err[0])
+            out["sine_wave"].append(row)
+            del ctx
+    st_ = max(2, min(args.steps, 3))
+    for N, nc, ts in ((3, 512, 20), (5, 320, 20), (7, 160, 10)):
+        ctx = Context2D(nc, nc, N, device=dev, profile=1)
+        u0 = torch.tensor(sine2d_state(ctx).ravel(), device=dev)
+        cells = nc * nc
+        ms, prof, u = measure_solve(ctx, u0, ts, st_, 2, flush)
+        iters = sum(p["mean_iters"] for p in prof) / len(prof)
+        nsteps = sum(p["profiled_steps"] for p in prof)
+        pred_ms = sum(p["predict_ms"] for p in prof) / max(nsteps, 1)
+        face_ms = sum(p["face_ms"] for p in prof) / max(nsteps, 1)
+        fl = cells * predictor2d_flops_per_cell(N + 1, iters)
+        out["throughput"].append({
+            "name": f"dg{N}-2d-{nc}x{nc}", "workload": f"2D sine wave (Sec. 2.1), DG N={N}, "
+            f"{nc}x{nc} cells periodic, {ts} steps, FP64", "value": cells * ts * st_ / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms / st_, "mean_picard_iters": iters,
+            "predict_ms_per_launch": pred_ms, "face_update_cfl_ms_per_launch": face_ms,
+            "predict_fp64_tflops": fl / (pred_ms / 1e3) / 1e12,
+            "predict_frac_of_fp64_peak": fl / (pred_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS})
+        del ctx
+    return out
 
 
 def run_limiter(args, dev, flush):

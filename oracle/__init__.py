@@ -22,12 +22,14 @@ _SRC = os.path.join(_HERE, "ader_oracle.c")
 _SRC_RS = os.path.join(_HERE, "ader_oracle_src.c")
 _SRC_LIM = os.path.join(_HERE, "ader_oracle_lim.c")
 _SRC_2D = os.path.join(_HERE, "ader_oracle_2d.c")
+_SRC_3D = os.path.join(_HERE, "ader_oracle_3d.c")
 _HDR = os.path.join(_HERE, "ader_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
 
 M = 3
 MRS = 5  # reacting system: rho, m, E, rho c1, rho c2
 M2 = 4   # 2D Euler: rho, m_x, m_y, E
+M3 = 5   # 3D Euler: rho, m_x, m_y, m_z, E
 MAXN = 10
 MAXNS = 19
 
@@ -39,12 +41,12 @@ OB_ERR_NONPHYSICAL = 5
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _SRC_2D, _HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _SRC_2D, _SRC_3D, _HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, _SRC_LIM, _SRC_2D,
-           "-lm"]
+           _SRC_3D, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -162,6 +164,21 @@ def lib():
             L.ob2_solve.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double,
                                     C.c_double, _DP, C.c_double, C.c_int64, P(C.c_int64),
                                     P(C.c_double)]
+            L.ob3_flux.argtypes = [C.c_double, _DP, _DP]
+            L.ob3_flux.restype = None
+            L.ob3_rusanov.argtypes = [C.c_double, C.c_int, _DP, _DP, _DP]
+            L.ob3_rusanov.restype = None
+            L.ob3_predict_cell.argtypes = [P(Basis), P(Params), C.c_double, C.c_double,
+                                           C.c_double, _DP, _DP, P(C.c_int)]
+            L.ob3_dg_step.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_int64,
+                                      C.c_double, C.c_double, C.c_double, C.c_double, _DP, _DP,
+                                      P(Stats)]
+            L.ob3_dt.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_int64, C.c_double,
+                                 C.c_double, C.c_double, _DP]
+            L.ob3_dt.restype = C.c_double
+            L.ob3_solve.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_int64,
+                                    C.c_double, C.c_double, C.c_double, _DP, C.c_double,
+                                    C.c_int64, P(C.c_int64), P(C.c_double)]
             L.ob_lim_weno2.argtypes = [_DP, _DP, _DP, _DP, _DP]
             L.ob_lim_weno2.restype = None
             L.ob_dgl_step.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double,
@@ -643,3 +660,88 @@ def dg2_density_errors(orc: Oracle2D, u, nx: int, ny: int, rho_exact, x0=0.0, x1
     l1 = float((err * wts).sum())
     l2 = float(np.sqrt((err ** 2 * wts).sum()))
     return l1, l2, float(err.max())
+
+
+# ---------------------------------------------------------------------------
+# 3D Euler on a periodic Cartesian mesh (ader_oracle_3d.c)
+# ---------------------------------------------------------------------------
+
+class Oracle3D:
+    """ADER-DG for the 3D Euler equations on a periodic box: state
+    u[iz][iy][ix][k1][k2][k3][r] (r = rho, m_x, m_y, m_z, E), the tensor-product
+    predictor of Sec. 1.1 and the corrector of Sec. 1.2."""
+
+    def __init__(self, N: int, gamma: float = 1.4, cfl: float = 0.4, tol: float = 1e-13,
+                 max_iter: int | None = None, fixed_iter: int = 0):
+        self.base = Oracle(N, gamma=gamma, cfl=cfl, tol=tol, max_iter=max_iter,
+                           fixed_iter=fixed_iter)
+        self.N, self.n = N, N + 1
+        self.basis, self.params = self.base.basis, self.base.params
+
+    def table(self, name):
+        return self.base.table(name)
+
+    def node_xyz(self, nx: int, ny: int, nz: int, box=(1.0, 1.0, 1.0)):
+        """(X, Y, Z), each [nz][ny][nx][n][n][n] (k1 along x, k2 along y, k3 along z)."""
+        xi, n = self.table("xi"), self.n
+        shape = (nz, ny, nx, n, n, n)
+        X = box[0] / nx * (np.arange(nx)[None, None, :, None, None, None]
+                           + xi[None, None, None, :, None, None])
+        Y = box[1] / ny * (np.arange(ny)[None, :, None, None, None, None]
+                           + xi[None, None, None, None, :, None])
+        Z = box[2] / nz * (np.arange(nz)[:, None, None, None, None, None]
+                           + xi[None, None, None, None, None, :])
+        return tuple(np.broadcast_to(A, shape).copy() for A in (X, Y, Z))
+
+    def flux(self, U):
+        F = np.zeros(3 * M3)
+        lib().ob3_flux(self.params.gamma, _arr(U, M3), F)
+        return F.reshape(3, M3)
+
+    def rusanov(self, direction: int, a, b):
+        H = np.zeros(M3)
+        lib().ob3_rusanov(self.params.gamma, direction, _arr(a, M3), _arr(b, M3), H)
+        return H
+
+    def predict_cell(self, u_cell, lx: float, ly: float, lz: float):
+        q = np.zeros(self.n ** 4 * M3)
+        it = C.c_int(0)
+        rc = lib().ob3_predict_cell(C.byref(self.basis), C.byref(self.params), lx, ly, lz,
+                                    _arr(u_cell, self.n ** 3 * M3), q, C.byref(it))
+        return q.reshape(self.n, self.n, self.n, self.n, M3), it.value, rc
+
+    def step(self, u, dims, h, dt: float):
+        u = _arr(u).ravel()
+        out = np.zeros_like(u)
+        st = Stats()
+        rc = lib().ob3_dg_step(C.byref(self.basis), C.byref(self.params), *dims, *h, dt, u, out,
+                               C.byref(st))
+        return out, rc, st.mean_iters
+
+    def dt(self, u, dims, h) -> float:
+        return lib().ob3_dt(C.byref(self.basis), C.byref(self.params), *dims, *h, _arr(u).ravel())
+
+    def solve(self, u, dims, h, t_end: float = 0.0, max_steps: int = 0):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        steps, t = C.c_int64(0), C.c_double(0.0)
+        rc = lib().ob3_solve(C.byref(self.basis), C.byref(self.params), *dims, *h, u, t_end,
+                             max_steps, C.byref(steps), C.byref(t))
+        return u, steps.value, t.value, rc
+
+
+def dg3_density_errors(orc: Oracle3D, u, dims, rho_exact, npts: int = 10):
+    """L1, L2 and Linf density errors of a 3D DG solution on the unit box (eq.
+    epsilons) with an npts^3 Gauss-Legendre rule per cell."""
+    nx, ny, nz = dims
+    n = orc.n
+    u = np.asarray(u, dtype=np.float64).reshape(nz, ny, nx, n, n, n, M3)
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1.0), 0.5 * gw
+    phi = np.stack([orc.base.phi(x) for x in gx])
+    rho_h = np.einsum("ak,bl,cm,zyxklm->zyxabc", phi, phi, phi, u[..., 0])
+    X = (np.arange(nx)[None, None, :, None, None, None] + gx[None, None, None, :, None, None]) / nx
+    Y = (np.arange(ny)[None, :, None, None, None, None] + gx[None, None, None, None, :, None]) / ny
+    Z = (np.arange(nz)[:, None, None, None, None, None] + gx[None, None, None, None, None, :]) / nz
+    err = np.abs(rho_h - rho_exact(X, Y, Z))
+    wts = np.einsum("a,b,c->abc", gw, gw, gw) / (nx * ny * nz)
+    return float((err * wts).sum()), float(np.sqrt((err ** 2 * wts).sum())), float(err.max())

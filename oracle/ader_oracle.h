@@ -239,6 +239,28 @@ double ob2_dt(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, dou
 int ob2_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx, double dy,
               double* u, double t_end, int64_t max_steps, int64_t* steps_out, double* t_out);
 
+/* ------------------------------------------------------------------------
+ * 3D Euler on a periodic Cartesian mesh (ader_oracle_3d.c): state
+ * u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x, m_y,
+ * m_z, E); predictor q[p0][p1][p2][p3][r]; L^xi = kappa~ (x) k~ (x) I (x) I and
+ * likewise along eta and zeta; faces in x, y and z; dt = CFL / (3 (2N+1))
+ * min_d (h_d / lambda_d) over the Ns^3 subcell averages.
+ * ---------------------------------------------------------------------- */
+#define OB3_M 5
+void ob3_flux(double gamma, const double* U, double* F);  /* F[3][5]: x-, y-, z-fluxes */
+double ob3_speed(double gamma, const double* U, int dir);
+void ob3_rusanov(double gamma, int dir, const double* a, const double* b, double* H);
+int ob3_predict_cell(const ob_basis* b, const ob_params* p, double lx, double ly, double lz,
+                     const double* u, double* q, int* iters);
+int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz,
+                double dx, double dy, double dz, double dt, const double* u, double* u_new,
+                ob_stats* st);
+double ob3_dt(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz, double dx,
+              double dy, double dz, const double* u);
+int ob3_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz, double dx,
+              double dy, double dz, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
+              double* t_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -156,6 +156,20 @@ typedef struct {
 ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options* opt,
                          ader_ctx** out);
 
+/* The 3D Euler equations on a periodic Cartesian mesh (the same predictor with
+ * L^zeta = kappa~ (x) I (x) I (x) k~ added, x-, y- and z-faces, d = 3):
+ *   mesh: nx x ny x nz cells on [x0, x1] x [y0, y1] x [z0, z1];
+ *   state u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x,
+ *   m_y, m_z, E), FP64; degree 0..4 (one GPU thread per space-time node,
+ *   (N+1)^4 <= 625); the options and the entry points that accept the
+ *   context are those of ader_init_2d. */
+typedef struct {
+  int64_t nx, ny, nz;
+  double x0, x1, y0, y1, z0, z1;
+} ader_mesh3d;
+ader_status ader_init_3d(const ader_mesh3d* mesh, int degree, const ader_options* opt,
+                         ader_ctx** out);
+
 void ader_destroy(ader_ctx* ctx);
 const char* ader_last_error(const ader_ctx* ctx);
 const char* ader_status_string(int status);

@@ -45,6 +45,12 @@ class Mesh2D(C.Structure):
                 ("y0", C.c_double), ("y1", C.c_double)]
 
 
+class Mesh3D(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("x0", C.c_double),
+                ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double), ("z0", C.c_double),
+                ("z1", C.c_double)]
+
+
 class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("picard_tol", C.c_double),
                 ("picard_max_iter", C.c_int), ("picard_fixed_iter", C.c_int),
@@ -128,6 +134,7 @@ def load(build_if_missing: bool = True):
             "ader_solve_from": ([V, V, D, D, I64, P(I64), P(D)], C.c_int),
             "ader_get_stats": ([V, P(Stats)], C.c_int),
             "ader_init_2d": ([V, C.c_int, V, V], C.c_int),
+            "ader_init_3d": ([V, C.c_int, V, V], C.c_int),
             "ader_get_troubled": ([V, V, I64], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
             "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
@@ -159,7 +166,7 @@ def exported_symbols():
             "ader_workspace_bytes", "ader_node_coords", "ader_get_table", "ader_bind",
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_solve_from",
-            "ader_get_stats", "ader_get_troubled", "ader_init_2d",
+            "ader_get_stats", "ader_get_troubled", "ader_init_2d", "ader_init_3d",
             "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
             "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
@@ -427,6 +434,50 @@ class Context2D(Context):
         Y = y0 + dy * (np.arange(self.ny)[:, None, None, None] + xi[None, None, None, :])
         shape = (self.ny, self.nx, self.n, self.n)
         return np.broadcast_to(X, shape).copy(), np.broadcast_to(Y, shape).copy()
+
+
+class Context3D(Context):
+    """An ader_ctx of the 3D Euler equations on a periodic nx x ny x nz Cartesian
+    mesh (ader_init_3d, degrees 0..4); state [iz][iy][ix][k1][k2][k3][5] with
+    r = (rho, m_x, m_y, m_z, E)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, degree: int, box=(1.0, 1.0, 1.0), device=None,
+                 **options):
+        L = load()
+        self._L = L
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n_cells = self.nx * self.ny * self.nz
+        self.degree = int(degree)
+        self.scheme = "dg"
+        self.n = self.degree + 1
+        self.box = tuple(float(b) for b in box)
+        mesh = Mesh3D(self.nx, self.ny, self.nz, 0.0, self.box[0], 0.0, self.box[1], 0.0,
+                      self.box[2])
+        self.options = default_options(**options)
+        ctx = C.c_void_p()
+        rc = L.ader_init_3d(C.byref(mesh), self.degree, C.byref(self.options), C.byref(ctx))
+        if rc != ADER_OK:
+            raise AderError(rc, f"ader_init_3d failed ({L.ader_status_string(rc).decode()})")
+        self._ctx = ctx
+        self._bind_workspace(device)
+        self.vars = 5
+
+    def state_shape(self):
+        return (self.nz, self.ny, self.nx, self.n, self.n, self.n, 5)
+
+    def node_coords(self):
+        """(X, Y, Z), each [nz][ny][nx][n][n][n]."""
+        import numpy as np
+        xi = self.table("xi")
+        n = self.n
+        shape = (self.nz, self.ny, self.nx, n, n, n)
+        X = self.box[0] / self.nx * (np.arange(self.nx)[None, None, :, None, None, None]
+                                     + xi[None, None, None, :, None, None])
+        Y = self.box[1] / self.ny * (np.arange(self.ny)[None, :, None, None, None, None]
+                                     + xi[None, None, None, None, :, None])
+        Z = self.box[2] / self.nz * (np.arange(self.nz)[:, None, None, None, None, None]
+                                     + xi[None, None, None, None, None, :])
+        return tuple(np.broadcast_to(A, shape).copy() for A in (X, Y, Z))
 
 
 class NoAllocStep:

@@ -38,10 +38,10 @@ struct ader_ctx {
   int N = 0, n = 1, scheme = 0;
   int M = kM;  // variables per node: 3 (Euler) or kMR (reacting system)
   double dx = 0.0;
-  int dims = 1;                   // 2: the 2D Euler mesh of ader_init_2d
-  long long nx = 0, ny = 0;       // 2D: cells per direction (mesh.n_cells = nx ny)
-  double dy = 0.0;
-  double* gface2 = nullptr;       // 2D: face fluxes [cell][dir][k][4]
+  int dims = 1;                   // 2 / 3: the meshes of ader_init_2d / ader_init_3d
+  long long nx = 0, ny = 0, nz = 1;  // cells per direction (mesh.n_cells = nx ny nz)
+  double dy = 0.0, dz = 0.0;
+  double* gface2 = nullptr;       // 2D: face fluxes [cell][dir][k][4]; 3D: [cell][d][a][c][5]
   // workspace (caller-owned)
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -101,12 +101,14 @@ bool is_weno_degree(int N) { return N == 2 || N == 4; }
 
 int64_t state_count(const ader_ctx* c) {
   if (c->dims == 2) return c->mesh.n_cells * c->n * c->n * kM2;
+  if (c->dims == 3) return c->mesh.n_cells * c->n * c->n * c->n * kM3;
   return c->scheme == ADER_SCHEME_DG ? c->mesh.n_cells * c->n * c->M : c->mesh.n_cells * kM;
 }
 
 // DG: [cell][qR | qL | u + volume (+ source)], M n doubles each; FV: [cell][qR | qL]
 size_t trace_doubles(const ader_ctx* c) {
   if (c->dims == 2) return (size_t)c->mesh.n_cells * 5 * c->n * c->n * kM2;  // xR xL yR yL volume
+  if (c->dims == 3) return (size_t)c->mesh.n_cells * 7 * c->n * c->n * c->n * kM3;  // 6 faces, volume
   return (size_t)c->mesh.n_cells * (c->scheme == ADER_SCHEME_DG ? 3 : 2) * c->M * c->n;
 }
 
@@ -116,6 +118,7 @@ size_t workspace_bytes(const ader_ctx* c) {
   if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
   b += 2 * align_up((size_t)state_count(c) * sizeof(double));
   if (c->dims == 2) b += align_up((size_t)c->mesh.n_cells * 2 * c->n * kM2 * sizeof(double));
+  if (c->dims == 3) b += align_up((size_t)c->mesh.n_cells * 3 * c->n * c->n * kM3 * sizeof(double));
   if (c->opt.limiter)
     b += 2 * align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
          align_up((size_t)c->mesh.n_cells * 12 * sizeof(double)) +
@@ -125,7 +128,7 @@ size_t workspace_bytes(const ader_ctx* c) {
 }
 
 int kernels_per_step(const ader_ctx* c) {
-  if (c->dims == 2) return 4;  // predictor, face fluxes, update, lambda_max
+  if (c->dims >= 2) return 4;  // predictor, face fluxes, update, lambda_max
   int k = c->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
   if (c->opt.limiter) k += 4;
   return k;
@@ -142,7 +145,7 @@ StepParams make_step(const ader_ctx* c, int mode, int par, double dt, double t_e
   sp.cfl_factor = c->scheme == ADER_SCHEME_DG ? c->opt.cfl * c->dx / (double)(2 * c->N + 1)
                                               : c->opt.cfl * c->dx;
   // 2D: dt = CFL / (d (2N+1)) / max(lambda_x / dx, lambda_y / dy), d = 2 (Sec. 1.5)
-  if (c->dims == 2) sp.cfl_factor = c->opt.cfl / (2.0 * (double)(2 * c->N + 1));
+  if (c->dims >= 2) sp.cfl_factor = c->opt.cfl / ((double)c->dims * (double)(2 * c->N + 1));
   sp.inv_dx = 1.0 / c->dx;
   sp.ctl = c->ctl;
   return sp;
@@ -231,12 +234,37 @@ Cfl2DParams make_cfl2d(const ader_ctx* ctx, const double* u, int slot) {
   return p;
 }
 
+Cfl3DParams make_cfl3d(const ader_ctx* ctx, const double* u, int slot) {
+  Cfl3DParams p{};
+  p.u = u;
+  p.ncells = ctx->mesh.n_cells;
+  p.gamma = ctx->opt.gamma;
+  p.gm1 = ctx->opt.gamma - 1.0;
+  p.inv_dx = 1.0 / ctx->dx;
+  p.inv_dy = 1.0 / ctx->dy;
+  p.inv_dz = 1.0 / ctx->dz;
+  p.ctl = ctx->ctl;
+  p.slot = slot;
+  for (int j = 0; j < kMaxNs; ++j)
+    for (int k = 0; k < kMaxN; ++k) {
+      p.P[j][k] = ctx->basis.d.P[j][k];
+      p.Pf[j][k] = (float)ctx->basis.d.P[j][k];
+    }
+  return p;
+}
+
 // enqueue the CFL kernel into lam[slot] (resets the slot first)
 ader_status enqueue_cfl(ader_ctx* ctx, const double* u, int slot) {
   CK(cudaMemsetAsync(&ctx->ctl->lam[slot], 0, sizeof(unsigned long long), ctx->stream));
   if (ctx->dims == 2) {
     Cfl2DParams p = make_cfl2d(ctx, u, slot);
     CK(do_cfl2d(ctx->N, p, ctx->stream));
+    ctx->launches += 1;
+    return ADER_OK;
+  }
+  if (ctx->dims == 3) {
+    Cfl3DParams p = make_cfl3d(ctx, u, slot);
+    CK(do_cfl3d(ctx->N, p, ctx->stream));
     ctx->launches += 1;
     return ADER_OK;
   }
@@ -325,9 +353,55 @@ ader_status enqueue_step2d(ader_ctx* ctx, const double* src, double* dst, const 
   return ADER_OK;
 }
 
+// one 3D step: predictor, face fluxes + update, lambda_max of the new state
+ader_status enqueue_step3d(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
+                           int want_lambda, cudaEvent_t* ev) {
+  if (ev) CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], ctx->stream, cudaEventRecordExternal));
+  Predict3DParams p{};
+  p.u = src;
+  p.trace = ctx->trace;
+  p.ncells = ctx->mesh.n_cells;
+  p.max_iter = ctx->opt.picard_max_iter;
+  p.fixed_iter = ctx->opt.picard_fixed_iter;
+  p.tol = ctx->opt.picard_tol;
+  p.gamma = ctx->opt.gamma;
+  p.gm1 = ctx->opt.gamma - 1.0;
+  p.inv_dy = 1.0 / ctx->dy;
+  p.inv_dz = 1.0 / ctx->dz;
+  p.sp = sp;
+  p.ops = ctx->basis.d;
+  CK(do_predict3d(ctx->N, p, ctx->stream));
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], ctx->stream, cudaEventRecordExternal));
+  Face3DParams f{};
+  f.trace = ctx->trace;
+  f.gface = ctx->gface2;
+  f.u_new = dst;
+  f.ncells = ctx->mesh.n_cells;
+  f.nx = ctx->nx;
+  f.ny = ctx->ny;
+  f.nz = ctx->nz;
+  f.gamma = ctx->opt.gamma;
+  f.gm1 = ctx->opt.gamma - 1.0;
+  f.inv_dy = 1.0 / ctx->dy;
+  f.inv_dz = 1.0 / ctx->dz;
+  f.sp = sp;
+  f.ops = ctx->basis.d;
+  CK(do_face3d(ctx->N, f, ctx->stream));
+  ctx->launches += 3;
+  if (want_lambda) {
+    Cfl3DParams c = make_cfl3d(ctx, dst, sp.par ^ 1);
+    CK(do_cfl3d(ctx->N, c, ctx->stream));
+    ctx->launches += 1;
+  }
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
+  return ADER_OK;
+}
+
 ader_status enqueue_step(ader_ctx* ctx, const double* src, double* dst, const StepParams& sp,
                          int want_lambda, cudaEvent_t* ev = nullptr) {
   if (ctx->dims == 2) return enqueue_step2d(ctx, src, dst, sp, want_lambda, ev);
+  if (ctx->dims == 3) return enqueue_step3d(ctx, src, dst, sp, want_lambda, ev);
   const double* nodal = src;
   if (ev) CK(cudaEventRecordWithFlags(ev[0], ctx->stream, cudaEventRecordExternal));
   if (ctx->scheme == ADER_SCHEME_WENO_FV) {
@@ -528,6 +602,39 @@ ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options
   return ADER_OK;
 }
 
+ader_status ader_init_3d(const ader_mesh3d* mesh, int degree, const ader_options* opt,
+                         ader_ctx** out) {
+  if (!out) return ADER_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0 || !(mesh->x1 > mesh->x0) ||
+      !(mesh->y1 > mesh->y0) || !(mesh->z1 > mesh->z0))
+    return ADER_ERR_ARG;
+  if (degree < 0 || degree > kMax3DDegree) return ADER_ERR_ARG;
+  if (mesh->nx > ((int64_t)1 << 28) / mesh->ny / mesh->nz) return ADER_ERR_ARG;
+  ader_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    ader_default_options(&o);
+  }
+  if (o.system != ADER_SYSTEM_EULER || o.precision != ADER_PREC_FP64 || o.bc != ADER_BC_PERIODIC ||
+      o.limiter != 0)
+    return ADER_ERR_ARG;
+  ader_mesh m1{mesh->nx * mesh->ny * mesh->nz, mesh->x0, mesh->x1};
+  ader_ctx* c = nullptr;
+  ader_status st = ader_init(&m1, degree, ADER_SCHEME_DG, &o, &c);
+  if (st != ADER_OK) return st;
+  c->dims = 3;
+  c->nx = mesh->nx;
+  c->ny = mesh->ny;
+  c->nz = mesh->nz;
+  c->dx = (mesh->x1 - mesh->x0) / (double)mesh->nx;
+  c->dy = (mesh->y1 - mesh->y0) / (double)mesh->ny;
+  c->dz = (mesh->z1 - mesh->z0) / (double)mesh->nz;
+  *out = c;
+  return ADER_OK;
+}
+
 void ader_destroy(ader_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -549,6 +656,7 @@ const char* ader_last_error(const ader_ctx* c) { return c ? c->err : "null conte
 int64_t ader_state_count(const ader_ctx* c) { return c ? state_count(c) : -1; }
 int64_t ader_predictor_count(const ader_ctx* c) {
   if (c && c->dims == 2) return c->mesh.n_cells * c->n * c->n * c->n * kM2;
+  if (c && c->dims == 3) return c->mesh.n_cells * c->n * c->n * c->n * c->n * kM3;
   return c ? c->mesh.n_cells * c->n * c->n * c->M : -1;
 }
 size_t ader_workspace_bytes(const ader_ctx* c) { return c ? workspace_bytes(c) : 0; }
@@ -657,6 +765,10 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
   if (ctx->dims == 2) {
     ctx->gface2 = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 2 * ctx->n * kM2 * sizeof(double));
+  }
+  if (ctx->dims == 3) {
+    ctx->gface2 = reinterpret_cast<double*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 3 * ctx->n * ctx->n * kM3 * sizeof(double));
   }
   if (ctx->opt.limiter) {
     ctx->lim_mm = reinterpret_cast<double*>(p);

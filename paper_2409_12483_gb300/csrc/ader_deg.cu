@@ -5,6 +5,7 @@
 #include "ader_source.cuh"
 #include "ader_limiter.cuh"
 #include "ader_kernels2d.cuh"
+#include "ader_kernels3d.cuh"
 
 #ifndef ADER_DEG
 #error "compile with -DADER_DEG=<0..7>"
@@ -171,6 +172,38 @@ cudaError_t ADER_CAT(launch_cfl2d_, ADER_DEG)(const Cfl2DParams& p, cudaStream_t
   constexpr int Ns = 2 * D + 1;
   cfl2d_kernel<D><<<grid_for(p.ncells * Ns * Ns, 256, 0x7fffffffLL), 256, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+// 3D: degrees 0..4 (one thread per space-time node); other degrees are refused
+cudaError_t ADER_CAT(launch_predict3d_, ADER_DEG)(const Predict3DParams& p, cudaStream_t s) {
+  if constexpr (D <= kMax3DDeg) {
+    using C = Pred3Cfg<D>;
+    predict3d_kernel<D><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream_t s) {
+  if constexpr (D <= kMax3DDeg) {
+    constexpr int n = D + 1;
+    face3d_kernel<D><<<grid_for(p.ncells * 3 * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+    update3d_kernel<D><<<grid_for(p.ncells * n * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t ADER_CAT(launch_cfl3d_, ADER_DEG)(const Cfl3DParams& p, cudaStream_t s) {
+  if constexpr (D <= kMax3DDeg) {
+    constexpr int Ns = 2 * D + 1;
+    cfl3d_kernel<D><<<grid_for(p.ncells * Ns * Ns * Ns, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {

@@ -54,6 +54,15 @@ inline cudaError_t do_face2d(int N, const Face2DParams& p, cudaStream_t s) {
 inline cudaError_t do_cfl2d(int N, const Cfl2DParams& p, cudaStream_t s) {
   ADER_DISPATCH(launch_cfl2d, N, p, s)
 }
+inline cudaError_t do_predict3d(int N, const Predict3DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_predict3d, N, p, s)
+}
+inline cudaError_t do_face3d(int N, const Face3DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_face3d, N, p, s)
+}
+inline cudaError_t do_cfl3d(int N, const Cfl3DParams& p, cudaStream_t s) {
+  ADER_DISPATCH(launch_cfl3d, N, p, s)
+}
 
 
 #define ADER_DISPATCH4(fn, N, a, b, c, d) \

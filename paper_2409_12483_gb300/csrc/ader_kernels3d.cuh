@@ -1,0 +1,424 @@
+// ader_kernels3d.cuh -- sm_103a kernels of the ADER-DG scheme for the 3D Euler
+// equations on a periodic Cartesian mesh (Popov, arXiv 2409.12483): the
+// tensor-product LST-DG predictor of Sec. 1.1 (eq. lst_dg_predictor_picard with
+// L^xi = kappa~ (x) k~ (x) I (x) I and likewise along eta and zeta, L^0 = delta),
+// the corrector of Sec. 1.2 with x-, y- and z-faces and lambda_max for the time
+// step of Sec. 1.5 with d = 3.  Degrees 0..4 (one thread per space-time node,
+// (N+1)^4 <= 625 threads per cell).
+//
+// State u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x, m_y,
+// m_z, E).  Trace record per cell (doubles): for d = x, y, z and side = low,
+// high the predictor on that face [l0][a][c][5] (a, c the transverse nodes in
+// the order of the two other directions), then the volume term [k1][k2][k3][5].
+//
+// predict3d_kernel   one thread per space-time node (p0, p1, p2, p3): the node's
+//                    three rescaled fluxes pass in turn through one shared array
+//                    for the k~ contractions along xi, eta and zeta, their sum
+//                    for kappa~ along tau; per-cell convergence (the 1D rule);
+//                    epilogue: six face traces and the volume term.
+// face3d_kernel      one thread per (cell, direction, transverse node pair): the
+//                    time-integrated Rusanov flux through the cell's low face.
+// update3d_kernel    one thread per (cell, node).
+// cfl3d_kernel       one thread per (cell, subcell): max_d lambda_d / h_d over
+//                    the (P (x) P (x) P) u subcell averages, FP32 screen, FP64
+//                    confirmation.
+#pragma once
+
+#include "ader_kernels.cuh"  // device helpers, abs_bits, launch parameter structs
+
+namespace ader {
+
+constexpr int kMax3DDeg = kMax3DDegree;
+
+// x-, y- and z-fluxes of the 3D Euler equations: F[d][5]
+__device__ __forceinline__ void euler3_flux(const double* U, double (*F)[kM3], double gm1) {
+  const double inv = recip(U[0]);
+  const double v[3] = {U[1] * inv, U[2] * inv, U[3] * inv};
+  const double p =
+      gm1 * fma(neg_half(U[1]), v[0], fma(neg_half(U[2]), v[1], fma(neg_half(U[3]), v[2], U[4])));
+  const double Ep = U[4] + p;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = U[1 + d];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[d][1 + c] = c == d ? fma(U[1 + c], v[d], p) : U[1 + c] * v[d];
+    F[d][4] = Ep * v[d];
+  }
+}
+
+// Twice the Rusanov flux in direction D between a (low side) and b (high side);
+// NaN when either state is non-physical.
+template <int D>
+__device__ __forceinline__ void rusanov2_3d(const double* a, const double* b, double* H2,
+                                            double gamma, double gm1) {
+  const double ia = rcp64(a[0]), ib = rcp64(b[0]);
+  double va[3], vb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    va[c] = a[1 + c] * ia;
+    vb[c] = b[1 + c] * ib;
+  }
+  const double pa =
+      gm1 * fma(neg_half(a[1]), va[0], fma(neg_half(a[2]), va[1], fma(neg_half(a[3]), va[2], a[4])));
+  const double pb =
+      gm1 * fma(neg_half(b[1]), vb[0], fma(neg_half(b[2]), vb[1], fma(neg_half(b[3]), vb[2], b[4])));
+  const double sa = fabs(va[D]) + sqrt64(gamma * pa * ia);
+  const double sb = fabs(vb[D]) + sqrt64(gamma * pb * ib);
+  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
+  H2[0] = fma(-s, b[0] - a[0], a[1 + D] + b[1 + D]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    H2[1 + c] = fma(-s, b[1 + c] - a[1 + c],
+                    fma(a[1 + c], va[D], c == D ? pa : 0.0) + fma(b[1 + c], vb[D], c == D ? pb : 0.0));
+  H2[4] = fma(-s, b[4] - a[4], fma(a[4] + pa, va[D], (b[4] + pb) * vb[D]));
+}
+
+template <int N>
+struct Pred3Cfg {
+  static constexpr int n = N + 1, NNN = n * n * n, NST = n * n * n * n;
+  static constexpr int CPB = NST >= 128 ? 1 : 256 / NST;  // cells per block
+  static constexpr int THREADS = CPB * NST;
+  static constexpr int REC = 7 * NNN * kM3;  // six face traces + volume term
+};
+
+template <int N>
+struct Pred3Shared {
+  using C = Pred3Cfg<N>;
+  double S[C::CPB][C::NST][kM3];        // one flux direction at a time, then the sum, then q
+  double FB[C::CPB][3][C::NNN][kM3];    // time averages of the three rescaled fluxes
+  unsigned long long red[C::CPB][2];
+  int done[C::CPB];
+  double dt;
+  int go;
+};
+
+template <int N>
+__global__ void __launch_bounds__(Pred3Cfg<N>::THREADS)
+    predict3d_kernel(const __grid_constant__ Predict3DParams P) {
+  using C = Pred3Cfg<N>;
+  constexpr int n = N + 1, NNN = C::NNN, NST = C::NST, CPB = C::CPB;
+  __shared__ Pred3Shared<N> sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double d = 0.0;
+    sh.go = predictor_step_dt(P.sp, &d, blockIdx.x == 0) ? 1 : 0;
+    sh.dt = d;
+  }
+  __syncthreads();
+  if (!sh.go) return;  // uniform
+  const double dt = sh.dt;
+  const double lam[3] = {dt * P.sp.inv_dx, dt * P.inv_dy, dt * P.inv_dz};
+  const int lc = tid / NST, node = tid - lc * NST;
+  const int p0 = node / NNN, p1 = (node / (n * n)) % n, p2 = (node / n) % n, p3 = node % n;
+  const int sp_node = node - p0 * NNN;  // (p1, p2, p3)
+  const long long cell = (long long)blockIdx.x * CPB + lc;
+  const bool valid = cell < P.ncells;
+  const OpsD& o = P.ops;
+  double uo[kM3], q[kM3];
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) {
+    uo[r] = valid ? P.u[(cell * NNN + sp_node) * kM3 + r] : 1.0;
+    q[r] = uo[r];
+  }
+  if (node == 0) {
+    sh.done[lc] = valid ? 0 : 1;
+    sh.red[lc][0] = sh.red[lc][1] = 0ull;
+  }
+  __syncthreads();
+  // stride of direction d in the space-time node index, and this node's index along d
+  const int stride[3] = {n * n, n, 1};
+  const int pd[3] = {p1, p2, p3};
+  const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+  for (int it = 0; it < cap; ++it) {
+    const bool active = !sh.done[lc];
+    double F[3][kM3];
+    euler3_flux(q, F, P.gm1);
+    double acc[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
+      __syncthreads();
+      if (active) {
+        const int base = node - pd[d] * stride[d];
+#pragma unroll
+        for (int r = 0; r < kM3; ++r)
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc[r] = fma(o.kt[pd[d]][m], sh.S[lc][base + m * stride[d]][r], acc[r]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = acc[r];
+    __syncthreads();
+    if (active) {
+      unsigned long long dmax = 0ull, qm = 0ull;
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s = fma(o.kap[p0][m], sh.S[lc][m * NNN + sp_node][r], s);
+        const double qn = uo[r] - s;
+        dmax = umax64(dmax, abs_bits(qn - q[r]));
+        qm = umax64(qm, abs_bits(qn));
+        q[r] = qn;
+      }
+      atomicMax(&sh.red[lc][0], dmax);
+      atomicMax(&sh.red[lc][1], qm);
+    }
+    __syncthreads();
+    if (node == 0 && active) {
+      const double delta = bitsd(sh.red[lc][0]), qmax = bitsd(sh.red[lc][1]);
+      const bool conv = P.fixed_iter > 0 ? it + 1 == P.fixed_iter
+                                         : delta <= P.tol * fmax(qmax, 1.0);
+      if (conv || it + 1 == cap) {
+        sh.done[lc] = 1;
+        if (!conv) atomicOr(&P.sp.ctl->status, kStNotConverged);
+        atomicAdd(&P.sp.ctl->iter_sum, (unsigned long long)(it + 1));
+        atomicAdd((unsigned long long*)&P.sp.ctl->iter_cells, 1ull);
+        atomicMax(&P.sp.ctl->iter_max, it + 1);
+      }
+      sh.red[lc][0] = sh.red[lc][1] = 0ull;
+    }
+    __syncthreads();
+    bool all = true;
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) all = all && sh.done[c];
+    if (all) break;  // uniform
+  }
+  // epilogue: six face traces per tau node, then the volume term
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = q[r];
+  __syncthreads();
+  double* rec = P.trace + cell * C::REC;
+  if (valid && node < NNN) {
+    const int l0 = node / (n * n), a = (node / n) % n, c = node % n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // the space-time index of (l0, node m along d, transverse a, c)
+      const int base = d == 0 ? l0 * NNN + a * n + c
+                     : d == 1 ? l0 * NNN + a * n * n + c
+                              : l0 * NNN + a * n * n + c * n;
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) {
+        double lo = 0.0, hi = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const double x = sh.S[lc][base + m * stride[d]][r];
+          lo = fma(o.psi0[m], x, lo);
+          hi = fma(o.psi1[m], x, hi);
+        }
+        rec[((d * 2 + 0) * NNN + node) * kM3 + r] = lo;
+        rec[((d * 2 + 1) * NNN + node) * kM3 + r] = hi;
+      }
+    }
+  }
+  {
+    double F[3][kM3];
+    euler3_flux(q, F, P.gm1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
+      __syncthreads();
+      if (node < NNN) {
+#pragma unroll
+        for (int r = 0; r < kM3; ++r) {
+          double s = 0.0;
+#pragma unroll
+          for (int l0 = 0; l0 < n; ++l0) s = fma(o.w[l0], sh.S[lc][l0 * NNN + node][r], s);
+          sh.FB[lc][d][node][r] = s;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (valid && node < NNN) {
+    // this thread's (p1, p2, p3) = (k1, k2, k3): uo holds u[k1][k2][k3]
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = uo[r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int base = node - pd[d] * stride[d];
+#pragma unroll
+        for (int l = 0; l < n; ++l) acc = fma(o.vt[pd[d]][l], sh.FB[lc][d][base + l * stride[d]][r], acc);
+      }
+      rec[(6 * NNN + node) * kM3 + r] = acc;
+    }
+  }
+}
+
+// time-integrated rescaled Rusanov flux through the low face of each cell in
+// direction d at transverse nodes (a, c): [cell][d][a][c][5]
+template <int N>
+__global__ void __launch_bounds__(256) face3d_kernel(const __grid_constant__ Face3DParams P) {
+  constexpr int n = N + 1, NNN = n * n * n, REC = Pred3Cfg<N>::REC;
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= P.ncells * 3 * n * n) return;
+  const long long cell = item / (3 * n * n);
+  const int rem = (int)(item - cell * 3 * n * n), d = rem / (n * n), ac = rem - d * n * n;
+  const long long plane = P.nx * P.ny;
+  const long long iz = cell / plane, iy = (cell - iz * plane) / P.nx, ix = cell - iz * plane - iy * P.nx;
+  long long nb;
+  if (d == 0)
+    nb = cell - ix + (ix == 0 ? P.nx - 1 : ix - 1);
+  else if (d == 1)
+    nb = cell + ((iy == 0 ? P.ny - 1 : iy - 1) - iy) * P.nx;
+  else
+    nb = cell + ((iz == 0 ? P.nz - 1 : iz - 1) - iz) * plane;
+  const double* lo = P.trace + nb * REC + (d * 2 + 1) * NNN * kM3;    // high side of the neighbour
+  const double* hi = P.trace + cell * REC + (d * 2 + 0) * NNN * kM3;  // low side of this cell
+  double s[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int l0 = 0; l0 < n; ++l0) {
+    double a[kM3], b[kM3], H2[kM3];
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      a[r] = lo[(l0 * n * n + ac) * kM3 + r];
+      b[r] = hi[(l0 * n * n + ac) * kM3 + r];
+    }
+    if (d == 0)
+      rusanov2_3d<0>(a, b, H2, P.gamma, P.gm1);
+    else if (d == 1)
+      rusanov2_3d<1>(a, b, H2, P.gamma, P.gm1);
+    else
+      rusanov2_3d<2>(a, b, H2, P.gamma, P.gm1);
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) s[r] = fma(P.ops.w[l0], H2[r], s[r]);
+  }
+  const double h = 0.5 * dt * (d == 0 ? P.sp.inv_dx : d == 1 ? P.inv_dy : P.inv_dz);
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) P.gface[item * kM3 + r] = h * s[r];
+}
+
+// u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}
+template <int N>
+__global__ void __launch_bounds__(256) update3d_kernel(const __grid_constant__ Face3DParams P) {
+  constexpr int n = N + 1, NNN = n * n * n, REC = Pred3Cfg<N>::REC;
+  double dt;
+  int last;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item < P.ncells * NNN) {
+    const long long cell = item / NNN;
+    const int k = (int)(item - cell * NNN), k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
+    const long long plane = P.nx * P.ny;
+    const long long iz = cell / plane, iy = (cell - iz * plane) / P.nx, ix = cell - iz * plane - iy * P.nx;
+    const long long hi[3] = {cell - ix + (ix + 1 == P.nx ? 0 : ix + 1),
+                             cell + ((iy + 1 == P.ny ? 0 : iy + 1) - iy) * P.nx,
+                             cell + ((iz + 1 == P.nz ? 0 : iz + 1) - iz) * plane};
+    const int kd[3] = {k1, k2, k3};
+    const int tr[3] = {k2 * n + k3, k1 * n + k3, k1 * n + k2};  // transverse pair per direction
+    const double* vol = P.trace + cell * REC + 6 * NNN * kM3 + k * kM3;
+    const OpsD& o = P.ops;
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double val = vol[r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double gh = P.gface[((hi[d] * 3 + d) * n * n + tr[d]) * kM3 + r];
+        const double gl = P.gface[((cell * 3 + d) * n * n + tr[d]) * kM3 + r];
+        val = fma(-fma(o.psi1[kd[d]], gh, -o.psi0[kd[d]] * gl), o.rw[kd[d]], val);
+      }
+      P.u_new[item * kM3 + r] = val;
+    }
+  }
+  if (item == 0) corrector_finish(P.sp, dt, last, true);
+}
+
+// max over the Ns^3 subcells of every cell of max_d lambda_d / h_d into ctl->lam[slot]
+template <int N>
+__global__ void __launch_bounds__(256) cfl3d_kernel(const __grid_constant__ Cfl3DParams P) {
+  constexpr int n = N + 1, NNN = n * n * n, Ns = 2 * N + 1;
+  __shared__ unsigned long long s_wmax[8];
+  __shared__ float s_cut;
+  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = item < P.ncells * Ns * Ns * Ns;
+  long long cell = 0;
+  int j1 = 0, j2 = 0, j3 = 0;
+  if (valid) {
+    cell = item / (Ns * Ns * Ns);
+    const int j = (int)(item - cell * Ns * Ns * Ns);
+    j1 = j / (Ns * Ns);
+    j2 = (j / Ns) % Ns;
+    j3 = j % Ns;
+  }
+  const double* u = P.u + cell * NNN * kM3;
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  const float ih[3] = {(float)P.inv_dx, (float)P.inv_dy, (float)P.inv_dz};
+  float lt = 0.f;
+  if (valid) {
+    float v[kM3];
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      float acc = 0.f;
+      for (int k1 = 0; k1 < n; ++k1) {
+        float t2 = 0.f;
+        for (int k2 = 0; k2 < n; ++k2) {
+          float t3 = 0.f;
+#pragma unroll
+          for (int k3 = 0; k3 < n; ++k3)
+            t3 = fmaf(P.Pf[j3][k3], d2f_trunc(u[((k1 * n + k2) * n + k3) * kM3 + r]), t3);
+          t2 = fmaf(P.Pf[j2][k2], t3, t2);
+        }
+        acc = fmaf(P.Pf[j1][k1], t2, acc);
+      }
+      v[r] = acc;
+    }
+    const float inv = 1.f / v[0];
+    const float vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
+    const float pp = gm1f * (v[4] - 0.5f * (v[1] * vx + v[2] * vy + v[3] * vz));
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[4])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
+      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
+    } else {
+      const float c = sqrtf(gf * pp * inv);
+      lt = fmaxf(fmaxf((fabsf(vx) + c) * ih[0], (fabsf(vy) + c) * ih[1]), (fabsf(vz) + c) * ih[2]);
+    }
+  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt), s_wmax);
+  if (threadIdx.x == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  double lmax = 0.0;
+  bool bad = false;
+  if (valid && lt >= s_cut) {
+    double v[kM3];
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = 0.0;
+      for (int k1 = 0; k1 < n; ++k1) {
+        double t2 = 0.0;
+        for (int k2 = 0; k2 < n; ++k2) {
+          double t3 = 0.0;
+#pragma unroll
+          for (int k3 = 0; k3 < n; ++k3) t3 = fma(P.P[j3][k3], u[((k1 * n + k2) * n + k3) * kM3 + r], t3);
+          t2 = fma(P.P[j2][k2], t3, t2);
+        }
+        acc = fma(P.P[j1][k1], t2, acc);
+      }
+      v[r] = acc;
+    }
+    const double inv = rcp64(v[0]);
+    const double vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
+    const double pp =
+        P.gm1 * fma(neg_half(v[1]), vx, fma(neg_half(v[2]), vy, fma(neg_half(v[3]), vz, v[4])));
+    if (!(v[0] > 0.0) || !(pp > 0.0) || !(v[0] < 1.0e300) || !(pp < 1.0e300)) {
+      bad = true;
+    } else {
+      const double c = sqrt64(P.gamma * pp * inv);
+      lmax = fmax(fmax((fabs(vx) + c) * P.inv_dx, (fabs(vy) + c) * P.inv_dy), (fabs(vz) + c) * P.inv_dz);
+    }
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
+  if (threadIdx.x == 0) atomicMax(&P.ctl->lam[P.slot], bm);
+  if (bad) atomicOr(&P.ctl->status, kStNonPhysical);
+}
+
+}  // namespace ader

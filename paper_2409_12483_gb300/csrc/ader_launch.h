@@ -167,6 +167,41 @@ struct Cfl2DParams {
   float Pf[kMaxNs][kMaxN];
 };
 
+// 3D Euler (ader_kernels3d.cuh): state [cell][k1][k2][k3][5], cell = (iz ny + iy) nx + ix.
+struct Predict3DParams {
+  const double* u;
+  double* trace;         // [cell][d][side][l0][a][c][5] (six faces), then the volume term
+  long long ncells;
+  int max_iter, fixed_iter;
+  double tol;
+  double gamma, gm1;
+  double inv_dy, inv_dz;  // 1 / dx travels in sp
+  StepParams sp;
+  OpsD ops;
+};
+
+struct Face3DParams {
+  const double* trace;
+  double* gface;         // [cell][d][a][c][5]: fluxes of the low face per direction
+  double* u_new;
+  long long ncells, nx, ny, nz;
+  double gamma, gm1;
+  double inv_dy, inv_dz;
+  StepParams sp;
+  OpsD ops;
+};
+
+struct Cfl3DParams {
+  const double* u;
+  long long ncells;
+  double gamma, gm1;
+  double inv_dx, inv_dy, inv_dz;
+  DevCtl* ctl;
+  int slot;
+  double P[kMaxNs][kMaxN];
+  float Pf[kMaxNs][kMaxN];
+};
+
 // Per-degree entry points (defined in ader_deg.cu compiled once per degree).
 #define ADER_DECLARE_DEGREE(D)                                                         \
   cudaError_t launch_predict_##D(const PredictParams& p, cudaStream_t s);              \
@@ -181,6 +216,9 @@ struct Cfl2DParams {
   cudaError_t launch_predict2d_##D(const Predict2DParams& p, cudaStream_t s);           \
   cudaError_t launch_face2d_##D(const Face2DParams& p, cudaStream_t s);                 \
   cudaError_t launch_cfl2d_##D(const Cfl2DParams& p, cudaStream_t s);                   \
+  cudaError_t launch_predict3d_##D(const Predict3DParams& p, cudaStream_t s);           \
+  cudaError_t launch_face3d_##D(const Face3DParams& p, cudaStream_t s);                 \
+  cudaError_t launch_cfl3d_##D(const Cfl3DParams& p, cudaStream_t s);                   \
   cudaError_t prepare_degree_##D();
 
 ADER_DECLARE_DEGREE(0)

@@ -289,3 +289,25 @@ def test_init_2d_options_and_sizes(lib):
         assert lib.ader_init_2d(C.byref(mesh), 2, None, C.byref(bad)) == 1
     bad = C.c_void_p()
     assert lib.ader_init_2d(C.byref(Mesh2D(4, 4, 0.0, 1.0, 0.0, 1.0)), 8, None, C.byref(bad)) == 1
+
+
+def test_init_3d_options_and_sizes(lib):
+    """ader_init_3d: degrees 0..4, DG Euler FP64 periodic without limiter; the state
+    is nx ny nz (N+1)^3 5 doubles"""
+    from paper_2409_12483_gb300.capi import Mesh3D, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init_3d(C.byref(Mesh3D(4, 3, 2, 0, 1, 0, 1, 0, 2)), 3,
+                            C.byref(default_options()), C.byref(ctx)) == 0
+    assert lib.ader_state_count(ctx) == 24 * 64 * 5
+    assert lib.ader_predictor_count(ctx) == 24 * 256 * 5
+    lib.ader_destroy(ctx)
+    for deg in (5, 7, -1):
+        bad = C.c_void_p()
+        assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 2, 0, 1, 0, 1, 0, 1)), deg, None,
+                                C.byref(bad)) == 1
+    for kw in (dict(limiter=1), dict(bc="outflow"), dict(precision="ff")):
+        bad = C.c_void_p()
+        assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 2, 0, 1, 0, 1, 0, 1)), 2,
+                                C.byref(default_options(**kw)), C.byref(bad)) == 1, kw
+    bad = C.c_void_p()
+    assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 0, 0, 1, 0, 1, 0, 1)), 2, None, C.byref(bad)) == 1

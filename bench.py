@@ -90,6 +90,42 @@ def predictor2d_flops_per_cell(n: int, iters: float) -> float:
     return iters * it + epi
 
 
+def predictor3d_flops_per_cell(n: int, iters: float) -> float:
+    """Algorithmic FLOPs of one cell's 3D predictor launch (M = 5, n^4 space-time
+    nodes): per iteration the three fluxes with their scalings (45 flops per node),
+    k~ along xi, eta, zeta and kappa~ along tau (2 n^5 M each) and the update and
+    difference (2 n^4 M); epilogue: six traces (12 n^4 M), the fluxes again, the
+    three time averages (6 n^4 M) and the three D~ contractions (6 n^4 M)."""
+    m = 5
+    it = 45 * n ** 4 + 8 * n ** 5 * m + 2 * n ** 4 * m
+    epi = 12 * n ** 4 * m + 45 * n ** 4 + 6 * n ** 4 * m + 6 * n ** 4 * m
+    return iters * it + epi
+
+
+def dg3_errors(ctx, u, t, npts=10):
+    """L1, L2, Linf density errors of the 3D sine wave rho = 1 + 0.5 sin 2 pi
+    (x + y + z - 3 t) (Sec. 2.1, velocity (1, 1, 1)) with an npts^3 GL rule per
+    cell; measurement code, not the oracle."""
+    import numpy as np
+    xi = ctx.table("xi")
+    n = len(xi)
+    u = np.asarray(u).reshape(ctx.nz, ctx.ny, ctx.nx, n, n, n, 5)
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    L = np.ones((npts, n))
+    for k in range(n):
+        for m in range(n):
+            if m != k:
+                L[:, k] *= (gx - xi[m]) / (xi[k] - xi[m])
+    rho = np.einsum("ak,bl,cm,zyxklm->zyxabc", L, L, L, u[..., 0])
+    X = (np.arange(ctx.nx)[None, None, :, None, None, None] + gx[None, None, None, :, None, None]) / ctx.nx
+    Y = (np.arange(ctx.ny)[None, :, None, None, None, None] + gx[None, None, None, None, :, None]) / ctx.ny
+    Z = (np.arange(ctx.nz)[:, None, None, None, None, None] + gx[None, None, None, None, None, :]) / ctx.nz
+    err = np.abs(rho - (1 + 0.5 * np.sin(2 * np.pi * (X + Y + Z - 3 * t))))
+    wts = np.einsum("a,b,c->abc", gw, gw, gw) / (ctx.nx * ctx.ny * ctx.nz)
+    return float((err * wts).sum()), float(np.sqrt((err ** 2 * wts).sum())), float(err.max())
+
+
 def dg2_errors(ctx, u, t, npts=25):
     """L1, L2, Linf density errors of the 2D sine wave rho = 1 + 0.5 sin 2 pi
     (x + y - 2 t) (Sec. 2.1, velocity (1, 1)) with an npts x npts GL rule per
@@ -322,7 +358,7 @@ def main():
     ap.add_argument("--no-limiter", action="store_true",
                     help="skip the subcell limiter's Riemann problems and throughput")
     ap.add_argument("--no-2d", action="store_true",
-                    help="skip the 2D sine-wave table and the 2D throughput lines")
+                    help="skip the 2D and 3D sine-wave tables and throughput lines")
     ap.add_argument("--no-source", action="store_true",
                     help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
@@ -461,6 +497,7 @@ def main():
             line["limiter"] = run_limiter(args, dev, flush)
         if not args.no_2d:
             line["two_d"] = run_2d(args, dev, flush)
+            line["three_d"] = run_3d(args, dev, flush)
         line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
@@ -641,6 +678,74 @@ PAPER_2D_L1 = {(1, 10): 5.48e-3, (1, 15): 2.44e-3, (1, 20): 1.37e-3, (1, 25): 8.
                (5, 5): 6.09e-7, (5, 10): 9.33e-9, (5, 15): 8.18e-10, (5, 20): 1.45e-10,
                (6, 5): 2.75e-8, (6, 10): 2.12e-10, (6, 15): 1.23e-11, (6, 20): 1.63e-12,
                (7, 5): 1.08e-9, (7, 10): 4.13e-12, (7, 15): 1.61e-13, (7, 20): 1.60e-14}
+
+
+# Table conv_orders_pde_3d (Sec. 2.1), eps_L1 per (N, cells per direction)
+PAPER_3D_L1 = {(1, 10): 5.24e-2, (1, 15): 1.08e-2, (1, 20): 4.62e-3, (1, 25): 2.82e-3,
+               (2, 10): 7.69e-4, (2, 15): 2.22e-4, (2, 20): 9.29e-5, (2, 25): 4.74e-5,
+               (3, 10): 2.17e-5, (3, 15): 4.28e-6, (3, 20): 1.35e-6, (3, 25): 5.54e-7,
+               (4, 10): 7.69e-7, (4, 15): 1.03e-7, (4, 20): 2.48e-8, (4, 25): 8.16e-9}
+
+
+def sine3d_state(ctx):
+    import numpy as np
+    X, Y, Z = ctx.node_coords()
+    rho = 1 + 0.5 * np.sin(2 * np.pi * (X + Y + Z))
+    return np.stack([rho, rho, rho, rho, 1 / 0.4 + 1.5 * rho], -1)  # velocity (1, 1, 1), p = 1
+
+
+def run_3d(args, dev, flush):
+    """3D Euler (ader_init_3d, degrees 1..4): the sine-wave advection problem of
+    Sec. 2.1 at the meshes of Table conv_orders_pde_3d to t = 1 through the GPU
+    path, and throughput of the 3D solve."""
+    import numpy as np
+    import torch
+
+    from paper_2409_12483_gb300 import Context3D
+    out = {"sine_wave": [], "throughput": []}
+    # the paper's meshes, the finest ones for N <= 2 only (N = 4 on 25^3 alone
+    # takes about two minutes)
+    meshes = {1: (10, 15, 20, 25), 2: (10, 15, 20), 3: (10, 15), 4: (10, 15)}
+    for N in range(1, 5):
+        prev = None
+        for nc in meshes[N]:
+            ctx = Context3D(nc, nc, nc, N, device=dev)
+            u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            steps, t, rc = ctx.ader_solve(u, t_end=1.0)
+            e1.record()
+            torch.cuda.synchronize()
+            err = dg3_errors(ctx, u.cpu().numpy(), t)
+            row = {"degree": N, "cells": f"{nc}^3", "steps": steps, "status": rc,
+                   "eps_l1": err[0], "eps_l2": err[1], "eps_linf": err[2],
+                   "paper_eps_l1": PAPER_3D_L1[(N, nc)], "ms": e0.elapsed_time(e1)}
+            if prev is not None:
+                row["order_l1"] = float(np.log(prev[1] / err[0]) / np.log(nc / prev[0]))
+            prev = (nc, err[0])
+            out["sine_wave"].append(row)
+            del ctx
+    st_ = max(2, min(args.steps, 3))
+    for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10)):
+        ctx = Context3D(nc, nc, nc, N, device=dev, profile=1)
+        u0 = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
+        cells = nc ** 3
+        ms, prof, u = measure_solve(ctx, u0, ts, st_, 2, flush)
+        iters = sum(p["mean_iters"] for p in prof) / len(prof)
+        nsteps = sum(p["profiled_steps"] for p in prof)
+        pred_ms = sum(p["predict_ms"] for p in prof) / max(nsteps, 1)
+        face_ms = sum(p["face_ms"] for p in prof) / max(nsteps, 1)
+        fl = cells * predictor3d_flops_per_cell(N + 1, iters)
+        out["throughput"].append({
+            "name": f"dg{N}-3d-{nc}^3", "workload": f"3D sine wave (Sec. 2.1), DG N={N}, "
+            f"{nc}^3 cells periodic, {ts} steps, FP64", "value": cells * ts * st_ / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms / st_, "mean_picard_iters": iters,
+            "predict_ms_per_launch": pred_ms, "face_update_cfl_ms_per_launch": face_ms,
+            "predict_fp64_tflops": fl / (pred_ms / 1e3) / 1e12,
+            "predict_frac_of_fp64_peak": fl / (pred_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS})
+        del ctx
+    return out
 
 
 def sine2d_state(ctx):

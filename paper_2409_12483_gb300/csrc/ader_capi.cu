@@ -128,7 +128,7 @@ size_t workspace_bytes(const ader_ctx* c) {
 }
 
 int kernels_per_step(const ader_ctx* c) {
-  if (c->dims >= 2) return 4;  // predictor, face fluxes, update, lambda_max
+  if (c->dims >= 2) return 3;  // predictor, face fluxes, update with lambda_max
   int k = c->scheme == ADER_SCHEME_WENO_FV ? 3 : 2;
   if (c->opt.limiter) k += 4;
   return k;
@@ -340,15 +340,11 @@ ader_status enqueue_step2d(ader_ctx* ctx, const double* src, double* dst, const 
   f.gamma = ctx->opt.gamma;
   f.gm1 = ctx->opt.gamma - 1.0;
   f.inv_dy = 1.0 / ctx->dy;
+  f.want_lambda = want_lambda;  // the predictor of this step has reset the slot
   f.sp = sp;
   f.ops = ctx->basis.d;
   CK(do_face2d(ctx->N, f, ctx->stream));
   ctx->launches += 3;
-  if (want_lambda) {  // the predictor of this step has reset the slot
-    Cfl2DParams c = make_cfl2d(ctx, dst, sp.par ^ 1);
-    CK(do_cfl2d(ctx->N, c, ctx->stream));
-    ctx->launches += 1;
-  }
   if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
   return ADER_OK;
 }
@@ -385,15 +381,11 @@ ader_status enqueue_step3d(ader_ctx* ctx, const double* src, double* dst, const 
   f.gm1 = ctx->opt.gamma - 1.0;
   f.inv_dy = 1.0 / ctx->dy;
   f.inv_dz = 1.0 / ctx->dz;
+  f.want_lambda = want_lambda;  // the predictor of this step has reset the slot
   f.sp = sp;
   f.ops = ctx->basis.d;
   CK(do_face3d(ctx->N, f, ctx->stream));
   ctx->launches += 3;
-  if (want_lambda) {
-    Cfl3DParams c = make_cfl3d(ctx, dst, sp.par ^ 1);
-    CK(do_cfl3d(ctx->N, c, ctx->stream));
-    ctx->launches += 1;
-  }
   if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
   return ADER_OK;
 }

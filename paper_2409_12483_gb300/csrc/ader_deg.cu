@@ -164,7 +164,8 @@ cudaError_t ADER_CAT(launch_predict2d_, ADER_DEG)(const Predict2DParams& p, cuda
 cudaError_t ADER_CAT(launch_face2d_, ADER_DEG)(const Face2DParams& p, cudaStream_t s) {
   constexpr int n = D + 1;
   face2d_kernel<D><<<grid_for(p.ncells * 2 * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
-  update2d_kernel<D><<<grid_for(p.ncells * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+  using U = Upd2Cfg<D>;
+  update2d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -189,7 +190,8 @@ cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream
   if constexpr (D <= kMax3DDeg) {
     constexpr int n = D + 1;
     face3d_kernel<D><<<grid_for(p.ncells * 3 * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
-    update3d_kernel<D><<<grid_for(p.ncells * n * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+    using U = Upd3Cfg<D>;
+    update3d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, 0, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;

@@ -18,8 +18,10 @@
 // face2d_kernel      one thread per (cell, transverse node, direction): the
 //                    time-integrated Rusanov flux through the cell's left x-face
 //                    or bottom y-face.
-// update2d_kernel    one thread per (cell, node): volume term minus face terms.
-// cfl2d_kernel       one thread per (cell, subcell j1, j2): max(lambda_x / dx,
+// update2d_kernel    one thread per (cell, node): volume term minus face terms;
+//                    then the next step's max(lambda_x / dx, lambda_y / dy) over
+//                    the block's cells, projected to the subcells in shared memory.
+// cfl2d_kernel       (the first time step) one thread per (cell, subcell j1, j2): max(lambda_x / dx,
 //                    lambda_y / dy) over the (P (x) P) u subcell averages, an FP32
 //                    screen confirmed in FP64 like the 1D interface kernel's.
 #pragma once
@@ -282,18 +284,38 @@ __global__ void __launch_bounds__(256) face2d_kernel(const __grid_constant__ Fac
   for (int r = 0; r < kM2; ++r) P.gface[item * kM2 + r] = h * s[r];
 }
 
-// u^{n+1}[k1][k2] = volume term - (psi~_k1 Gx_right - psi_k1 Gx_left) / w_k1
-//                               - (psi~_k2 Gy_top - psi_k2 Gy_bottom) / w_k2
 template <int N>
-__global__ void __launch_bounds__(256) update2d_kernel(const __grid_constant__ Face2DParams P) {
-  constexpr int n = N + 1, NN = n * n, REC = Pred2Cfg<N>::REC;
+struct Upd2Cfg {
+  static constexpr int n = N + 1, NN = n * n, Ns = 2 * N + 1;
+  static constexpr int CPB = NN >= 256 ? 1 : 256 / NN;  // cells per block
+  static constexpr int USED = CPB * NN;
+  static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
+};
+
+// u^{n+1}[k1][k2] = volume term - (psi~_k1 Gx_right - psi_k1 Gx_left) / w_k1
+//                               - (psi~_k2 Gy_top - psi_k2 Gy_bottom) / w_k2,
+// one thread per (cell, node), CPB cells per block; then (want_lambda) the
+// block projects its cells' new states onto the Ns x Ns subcells one direction
+// at a time through shared memory and reduces max(lambda_x / dx, lambda_y / dy)
+// into ctl->lam[par ^ 1] (FP64, the time step of Sec. 1.5 with d = 2).
+template <int N>
+__global__ void __launch_bounds__(Upd2Cfg<N>::THREADS)
+    update2d_kernel(const __grid_constant__ Face2DParams P) {
+  using C = Upd2Cfg<N>;
+  constexpr int n = N + 1, NN = n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred2Cfg<N>::REC;
+  __shared__ double U[CPB][NN][kM2];
+  __shared__ double T[CPB][n][Ns][kM2];  // projected along eta: [k1][j2]
+  __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
   int last;
-  if (!corrector_step_dt(P.sp, &dt, &last)) return;
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item < P.ncells * NN) {
-    const long long cell = item / NN;
-    const int k = (int)(item - cell * NN), k1 = k / n, k2 = k - k1 * n;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;  // uniform
+  const int tid = threadIdx.x;
+  const int lc = tid / NN, k = tid - lc * NN;
+  const long long cell = (long long)blockIdx.x * CPB + lc;
+  const bool valid = tid < C::USED && cell < P.ncells;
+  const OpsD& o = P.ops;
+  if (valid) {
+    const int k1 = k / n, k2 = k - k1 * n;
     const long long iy = cell / P.nx, ix = cell - iy * P.nx;
     const long long cr = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1);
     const long long ct = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix;
@@ -302,15 +324,56 @@ __global__ void __launch_bounds__(256) update2d_kernel(const __grid_constant__ F
     const double* gxr = P.gface + ((cr * 2 + 0) * n + k2) * kM2;
     const double* gyb = P.gface + ((cell * 2 + 1) * n + k1) * kM2;
     const double* gyt = P.gface + ((ct * 2 + 1) * n + k1) * kM2;
-    const OpsD& o = P.ops;
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
       const double fx = fma(o.psi1[k1], gxr[r], -o.psi0[k1] * gxl[r]);
       const double fy = fma(o.psi1[k2], gyt[r], -o.psi0[k2] * gyb[r]);
-      P.u_new[item * kM2 + r] = fma(-fy, o.rw[k2], fma(-fx, o.rw[k1], vol[r]));
+      const double un = fma(-fy, o.rw[k2], fma(-fx, o.rw[k1], vol[r]));
+      P.u_new[(cell * NN + k) * kM2 + r] = un;
+      U[lc][k][r] = un;
     }
   }
-  if (item == 0) corrector_finish(P.sp, dt, last, true);
+  if (blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
+  if (!P.want_lambda) return;  // uniform
+  __syncthreads();
+  for (int it = tid; it < CPB * n * Ns; it += C::THREADS) {
+    const int c = it / (n * Ns), rem = it - c * n * Ns, k1 = rem / Ns, j2 = rem - k1 * Ns;
+    if ((long long)blockIdx.x * CPB + c >= P.ncells) continue;
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k2 = 0; k2 < n; ++k2) acc = fma(o.P[j2][k2], U[c][k1 * n + k2][r], acc);
+      T[c][k1][j2][r] = acc;
+    }
+  }
+  __syncthreads();
+  double lmax = 0.0;
+  bool bad = false;
+  for (int it = tid; it < CPB * Ns * Ns; it += C::THREADS) {
+    const int c = it / (Ns * Ns), rem = it - c * Ns * Ns, j1 = rem / Ns, j2 = rem - j1 * Ns;
+    if ((long long)blockIdx.x * CPB + c >= P.ncells) continue;
+    double v[kM2];
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) acc = fma(o.P[j1][k1], T[c][k1][j2][r], acc);
+      v[r] = acc;
+    }
+    const double inv = rcp64(v[0]);
+    const double uu = v[1] * inv, vv = v[2] * inv;
+    const double pp = P.gm1 * fma(neg_half(v[1]), uu, fma(neg_half(v[2]), vv, v[3]));
+    if (!(v[0] > 0.0) || !(pp > 0.0) || !(v[0] < 1.0e300) || !(pp < 1.0e300)) {
+      bad = true;
+    } else {
+      const double cs = sqrt64(P.gamma * pp * inv);
+      lmax = fmax(lmax, fmax((fabs(uu) + cs) * P.sp.inv_dx, (fabs(vv) + cs) * P.inv_dy));
+    }
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
+  if (tid == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);
+  if (bad) atomicOr(&P.sp.ctl->status, kStNonPhysical);
 }
 
 // max over the Ns x Ns subcells of every cell of max(lambda_x / dx, lambda_y / dy)

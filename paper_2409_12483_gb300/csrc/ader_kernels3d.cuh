@@ -18,8 +18,10 @@
 //                    epilogue: six face traces and the volume term.
 // face3d_kernel      one thread per (cell, direction, transverse node pair): the
 //                    time-integrated Rusanov flux through the cell's low face.
-// update3d_kernel    one thread per (cell, node).
-// cfl3d_kernel       one thread per (cell, subcell): max_d lambda_d / h_d over
+// update3d_kernel    one thread per (cell, node); then the next step's
+//                    max_d lambda_d / h_d over the block's cells, projected to the
+//                    subcells in shared memory one direction at a time.
+// cfl3d_kernel       (the first time step) one thread per (cell, subcell): max_d lambda_d / h_d over
 //                    the (P (x) P (x) P) u subcell averages, FP32 screen, FP64
 //                    confirmation.
 #pragma once
@@ -296,17 +298,37 @@ __global__ void __launch_bounds__(256) face3d_kernel(const __grid_constant__ Fac
   for (int r = 0; r < kM3; ++r) P.gface[item * kM3 + r] = h * s[r];
 }
 
-// u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}
 template <int N>
-__global__ void __launch_bounds__(256) update3d_kernel(const __grid_constant__ Face3DParams P) {
-  constexpr int n = N + 1, NNN = n * n * n, REC = Pred3Cfg<N>::REC;
+struct Upd3Cfg {
+  static constexpr int n = N + 1, NNN = n * n * n, Ns = 2 * N + 1;
+  static constexpr int CPB = NNN >= 128 ? 1 : 128 / NNN;  // cells per block
+  static constexpr int USED = CPB * NNN;
+  static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
+};
+
+// u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}, one
+// thread per (cell, node), CPB cells per block; then (want_lambda) the block
+// projects its cells' new states onto the Ns^3 subcells one direction at a time
+// through shared memory and reduces max_d lambda_d / h_d into ctl->lam[par ^ 1].
+template <int N>
+__global__ void __launch_bounds__(Upd3Cfg<N>::THREADS)
+    update3d_kernel(const __grid_constant__ Face3DParams P) {
+  using C = Upd3Cfg<N>;
+  constexpr int n = N + 1, NNN = n * n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred3Cfg<N>::REC;
+  __shared__ double U[CPB][NNN][kM3];
+  __shared__ double T1[CPB][n * n][Ns][kM3];  // projected along zeta: [k1 k2][j3]
+  __shared__ double T2[CPB][n][Ns * Ns][kM3];  // then along eta: [k1][j2 j3]
+  __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
   int last;
-  if (!corrector_step_dt(P.sp, &dt, &last)) return;
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item < P.ncells * NNN) {
-    const long long cell = item / NNN;
-    const int k = (int)(item - cell * NNN), k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
+  if (!corrector_step_dt(P.sp, &dt, &last)) return;  // uniform
+  const int tid = threadIdx.x;
+  const int lc = tid / NNN, k = tid - lc * NNN;
+  const long long cell = (long long)blockIdx.x * CPB + lc;
+  const bool valid = tid < C::USED && cell < P.ncells;
+  const OpsD& o = P.ops;
+  if (valid) {
+    const int k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
     const long long plane = P.nx * P.ny;
     const long long iz = cell / plane, iy = (cell - iz * plane) / P.nx, ix = cell - iz * plane - iy * P.nx;
     const long long hi[3] = {cell - ix + (ix + 1 == P.nx ? 0 : ix + 1),
@@ -315,7 +337,6 @@ __global__ void __launch_bounds__(256) update3d_kernel(const __grid_constant__ F
     const int kd[3] = {k1, k2, k3};
     const int tr[3] = {k2 * n + k3, k1 * n + k3, k1 * n + k2};  // transverse pair per direction
     const double* vol = P.trace + cell * REC + 6 * NNN * kM3 + k * kM3;
-    const OpsD& o = P.ops;
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
       double val = vol[r];
@@ -325,10 +346,68 @@ __global__ void __launch_bounds__(256) update3d_kernel(const __grid_constant__ F
         const double gl = P.gface[((cell * 3 + d) * n * n + tr[d]) * kM3 + r];
         val = fma(-fma(o.psi1[kd[d]], gh, -o.psi0[kd[d]] * gl), o.rw[kd[d]], val);
       }
-      P.u_new[item * kM3 + r] = val;
+      P.u_new[(cell * NNN + k) * kM3 + r] = val;
+      U[lc][k][r] = val;
     }
   }
-  if (item == 0) corrector_finish(P.sp, dt, last, true);
+  if (blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
+  if (!P.want_lambda) return;  // uniform
+  __syncthreads();
+  const long long c0 = (long long)blockIdx.x * CPB;
+  for (int it = tid; it < CPB * n * n * Ns; it += C::THREADS) {
+    const int c = it / (n * n * Ns), rem = it - c * n * n * Ns, kk = rem / Ns, j3 = rem - kk * Ns;
+    if (c0 + c >= P.ncells) continue;
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k3 = 0; k3 < n; ++k3) acc = fma(o.P[j3][k3], U[c][kk * n + k3][r], acc);
+      T1[c][kk][j3][r] = acc;
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < CPB * n * Ns * Ns; it += C::THREADS) {
+    const int c = it / (n * Ns * Ns), rem = it - c * n * Ns * Ns, k1 = rem / (Ns * Ns),
+              jj = rem - k1 * Ns * Ns, j2 = jj / Ns, j3 = jj - j2 * Ns;
+    if (c0 + c >= P.ncells) continue;
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k2 = 0; k2 < n; ++k2) acc = fma(o.P[j2][k2], T1[c][k1 * n + k2][j3][r], acc);
+      T2[c][k1][jj][r] = acc;
+    }
+  }
+  __syncthreads();
+  double lmax = 0.0;
+  bool bad = false;
+  for (int it = tid; it < CPB * Ns * Ns * Ns; it += C::THREADS) {
+    const int c = it / (Ns * Ns * Ns), rem = it - c * Ns * Ns * Ns, j1 = rem / (Ns * Ns),
+              jj = rem - j1 * Ns * Ns;
+    if (c0 + c >= P.ncells) continue;
+    double v[kM3];
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) acc = fma(o.P[j1][k1], T2[c][k1][jj][r], acc);
+      v[r] = acc;
+    }
+    const double inv = rcp64(v[0]);
+    const double vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
+    const double pp =
+        P.gm1 * fma(neg_half(v[1]), vx, fma(neg_half(v[2]), vy, fma(neg_half(v[3]), vz, v[4])));
+    if (!(v[0] > 0.0) || !(pp > 0.0) || !(v[0] < 1.0e300) || !(pp < 1.0e300)) {
+      bad = true;
+    } else {
+      const double cs = sqrt64(P.gamma * pp * inv);
+      lmax = fmax(lmax, fmax(fmax((fabs(vx) + cs) * P.sp.inv_dx, (fabs(vy) + cs) * P.inv_dy),
+                             (fabs(vz) + cs) * P.inv_dz));
+    }
+  }
+  const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
+  if (tid == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);
+  if (bad) atomicOr(&P.sp.ctl->status, kStNonPhysical);
 }
 
 // max over the Ns^3 subcells of every cell of max_d lambda_d / h_d into ctl->lam[slot]

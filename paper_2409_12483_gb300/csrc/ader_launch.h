@@ -150,6 +150,7 @@ struct Face2DParams {
   double* gface;         // [cell][dir][k][4]: fluxes of the left x-face and bottom y-face
   double* u_new;
   long long ncells, nx, ny;
+  int want_lambda;       // the update also reduces lambda_max of u_new into ctl->lam[par ^ 1]
   double gamma, gm1;
   double inv_dy;
   StepParams sp;
@@ -185,6 +186,7 @@ struct Face3DParams {
   double* gface;         // [cell][d][a][c][5]: fluxes of the low face per direction
   double* u_new;
   long long ncells, nx, ny, nz;
+  int want_lambda;       // the update also reduces lambda_max of u_new into ctl->lam[par ^ 1]
   double gamma, gm1;
   double inv_dy, inv_dz;
   StepParams sp;

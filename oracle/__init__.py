@@ -23,6 +23,7 @@ _SRC_RS = os.path.join(_HERE, "ader_oracle_src.c")
 _SRC_LIM = os.path.join(_HERE, "ader_oracle_lim.c")
 _SRC_2D = os.path.join(_HERE, "ader_oracle_2d.c")
 _SRC_3D = os.path.join(_HERE, "ader_oracle_3d.c")
+_SRC_NC = os.path.join(_HERE, "ader_oracle_nc.c")
 _HDR = os.path.join(_HERE, "ader_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "libader_oracle.so")
 
@@ -30,6 +31,7 @@ M = 3
 MRS = 5  # reacting system: rho, m, E, rho c1, rho c2
 M2 = 4   # 2D Euler: rho, m_x, m_y, E
 M3 = 5   # 3D Euler: rho, m_x, m_y, m_z, E
+MNC = 4  # Euler + non-conservative passive tracer: rho, m, E, phi
 MAXN = 10
 MAXNS = 19
 
@@ -41,12 +43,12 @@ OB_ERR_NONPHYSICAL = 5
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _SRC_2D, _SRC_3D, _HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_RS, _SRC_LIM, _SRC_2D, _SRC_3D, _SRC_NC, _HDR))
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_RS, _SRC_LIM, _SRC_2D,
-           _SRC_3D, "-lm"]
+           _SRC_3D, _SRC_NC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -179,6 +181,15 @@ def lib():
             L.ob3_solve.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_int64,
                                     C.c_double, C.c_double, C.c_double, _DP, C.c_double,
                                     C.c_int64, P(C.c_int64), P(C.c_double)]
+            L.ob_nc_flux.argtypes = [C.c_double, _DP, _DP]
+            L.ob_nc_flux.restype = None
+            L.ob_nc_face.argtypes = [C.c_double, _DP, _DP, _DP, P(C.c_double)]
+            L.ob_nc_face.restype = None
+            L.ob_nc_predict_cell.argtypes = [P(Basis), P(Params), C.c_double, _DP, _DP, P(C.c_int)]
+            L.ob_nc_step.argtypes = [P(Basis), P(Params), C.c_int64, C.c_double, C.c_double, _DP,
+                                     _DP, P(Stats)]
+            L.ob_nc_solve.argtypes = [P(Basis), P(Params), C.c_int64, C.c_double, _DP, C.c_double,
+                                      C.c_int64, P(C.c_int64), P(C.c_double)]
             L.ob_lim_weno2.argtypes = [_DP, _DP, _DP, _DP, _DP]
             L.ob_lim_weno2.restype = None
             L.ob_dgl_step.argtypes = [P(Basis), P(Params), P(LimParams), C.c_int64, C.c_double,
@@ -745,3 +756,64 @@ def dg3_density_errors(orc: Oracle3D, u, dims, rho_exact, npts: int = 10):
     err = np.abs(rho_h - rho_exact(X, Y, Z))
     wts = np.einsum("a,b,c->abc", gw, gw, gw) / (nx * ny * nz)
     return float((err * wts).sum()), float(np.sqrt((err ** 2 * wts).sum())), float(err.max())
+
+
+# ---------------------------------------------------------------------------
+# non-conservative product: Euler + passive tracer (ader_oracle_nc.c)
+# ---------------------------------------------------------------------------
+
+class NCOracle:
+    """ADER-DG for the 1D Euler equations with a passive tracer in non-conservative
+    form (U = rho, m, E, phi; B(U) dU/dx = (0, 0, 0, u dphi/dx)), periodic; state
+    u[cell][k][4]."""
+
+    def __init__(self, N: int, gamma: float = 1.4, cfl: float = 0.4, tol: float = 1e-13,
+                 max_iter: int | None = None, fixed_iter: int = 0):
+        self.base = Oracle(N, gamma=gamma, cfl=cfl, tol=tol, max_iter=max_iter,
+                           fixed_iter=fixed_iter)
+        self.N, self.n = N, N + 1
+        self.basis, self.params = self.base.basis, self.base.params
+
+    def table(self, name):
+        return self.base.table(name)
+
+    def node_x(self, ncells, x0=0.0, x1=1.0):
+        return self.base.node_x(ncells, x0, x1)
+
+    def flux(self, U):
+        F = np.zeros(MNC)
+        lib().ob_nc_flux(self.params.gamma, _arr(U, MNC), F)
+        return F
+
+    def face(self, a, b):
+        G, bt = np.zeros(MNC), C.c_double(0.0)
+        lib().ob_nc_face(self.params.gamma, _arr(a, MNC), _arr(b, MNC), G, C.byref(bt))
+        return G, bt.value
+
+    def predict_cell(self, u_cell, lam: float):
+        q = np.zeros(self.n * self.n * MNC)
+        it = C.c_int(0)
+        rc = lib().ob_nc_predict_cell(C.byref(self.basis), C.byref(self.params), lam,
+                                      _arr(u_cell, self.n * MNC), q, C.byref(it))
+        return q.reshape(self.n, self.n, MNC), it.value, rc
+
+    def step(self, u, dx: float, dt: float):
+        u = _arr(u).ravel()
+        out = np.zeros_like(u)
+        st = Stats()
+        nc = u.size // (self.n * MNC)
+        rc = lib().ob_nc_step(C.byref(self.basis), C.byref(self.params), nc, dx, dt, u, out,
+                              C.byref(st))
+        return out, rc, st.mean_iters
+
+    def dt(self, u, dx: float) -> float:
+        u = _arr(u).reshape(-1, self.n, MNC)
+        return self.base.dg_dt(np.ascontiguousarray(u[..., :3]), dx)
+
+    def solve(self, u, dx: float, t_end: float = 0.0, max_steps: int = 0):
+        u = np.array(u, dtype=np.float64, copy=True).ravel()
+        nc = u.size // (self.n * MNC)
+        steps, t = C.c_int64(0), C.c_double(0.0)
+        rc = lib().ob_nc_solve(C.byref(self.basis), C.byref(self.params), nc, dx, u, t_end,
+                               max_steps, C.byref(steps), C.byref(t))
+        return u, steps.value, t.value, rc

@@ -261,6 +261,23 @@ int ob3_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int
               double dy, double dz, double* u, double t_end, int64_t max_steps, int64_t* steps_out,
               double* t_out);
 
+/* ------------------------------------------------------------------------
+ * Non-conservative product (ader_oracle_nc.c): 1D Euler with a passive tracer
+ * phi in non-conservative form, U = (rho, m, E, phi), B(U) dU/dx = (0, 0, 0,
+ * u dphi/dx); nested Picard predictor with the b term in the inner loop, the B
+ * volume term and a path-conservative Rusanov face (G +- Bt/2, 3-point GL path
+ * integral along the straight segment).  State u[cell][k][4].
+ * ---------------------------------------------------------------------- */
+#define OB_NC_M 4
+void ob_nc_flux(double gamma, const double* U, double* F);
+void ob_nc_face(double gamma, const double* a, const double* b, double* G, double* Bt);
+int ob_nc_predict_cell(const ob_basis* b, const ob_params* p, double lam, const double* u,
+                       double* q, int* iters);
+int ob_nc_step(const ob_basis* b, const ob_params* p, int64_t ncells, double dx, double dt,
+               const double* u, double* u_new, ob_stats* st);
+int ob_nc_solve(const ob_basis* b, const ob_params* p, int64_t ncells, double dx, double* u,
+                double t_end, int64_t max_steps, int64_t* steps_out, double* t_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,8 +65,16 @@ typedef enum {
  *   advected with the flow and the source S = (0, 0, 0, rho c2, -omega^2 rho c1);
  *   predictor by the nested Picard iteration of eq.
  *   lst_dg_predictor_nested_picards, corrector with the source term of eq.
- *   ader_dg_method_full.  DG scheme and ADER_PREC_FP64 only. */
-typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1 } ader_system;
+ *   ader_dg_method_full.  DG scheme and ADER_PREC_FP64 only.
+ * ADER_SYSTEM_TRACER: a non-conservative product (eq. pde_src with B != 0): 1D
+ *   Euler carrying a passive tracer in non-conservative form, M = 4 variables
+ *   (rho, rho u, E, phi), B(U) dU/dx = (0, 0, 0, u dphi/dx); predictor by the
+ *   nested Picard iteration with b = (dt/dx) B(q) D^xi q in the inner loop,
+ *   corrector with the B volume term and a path-conservative Rusanov face (the
+ *   minus-side cell takes G + Bt/2, the plus side G - Bt/2, Bt the integral of B
+ *   along the straight segment, 3-point Gauss-Legendre).  DG, ADER_PREC_FP64,
+ *   periodic only. */
+typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1, ADER_SYSTEM_TRACER = 2 } ader_system;
 
 /* Boundary condition of the mesh ends.  ADER_BC_OUTFLOW (DG only): free outflow;
  * the ghost side of a boundary face holds the boundary cell's mean state of the

@@ -527,7 +527,10 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
       (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR &&
        o.precision != ADER_PREC_FF_PREDICTOR) ||
       (o.precision == ADER_PREC_FP32_PREDICTOR && o.fp64_sweeps < 1) || o.picard_max_iter > 10000 ||
-      (o.system != ADER_SYSTEM_EULER && o.system != ADER_SYSTEM_REACTING) ||
+      (o.system != ADER_SYSTEM_EULER && o.system != ADER_SYSTEM_REACTING &&
+       o.system != ADER_SYSTEM_TRACER) ||
+      (o.system == ADER_SYSTEM_TRACER &&
+       (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || o.bc != ADER_BC_PERIODIC)) ||
       (o.system == ADER_SYSTEM_REACTING &&
        (scheme != ADER_SCHEME_DG || o.precision != ADER_PREC_FP64 || !std::isfinite(o.omega))) ||
       (o.bc != ADER_BC_PERIODIC && o.bc != ADER_BC_OUTFLOW) ||
@@ -537,7 +540,7 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
     delete c;
     return ADER_ERR_ARG;
   }
-  c->M = o.system == ADER_SYSTEM_REACTING ? kMR : kM;
+  c->M = o.system == ADER_SYSTEM_REACTING ? kMR : (o.system == ADER_SYSTEM_TRACER ? kMN : kM);
   if (build_basis(degree, scheme == ADER_SCHEME_WENO_FV, &c->basis) != 0) {
     delete c;
     return ADER_ERR_ARG;

@@ -6,6 +6,7 @@
 #include "ader_limiter.cuh"
 #include "ader_kernels2d.cuh"
 #include "ader_kernels3d.cuh"
+#include "ader_tracer.cuh"
 
 #ifndef ADER_DEG
 #error "compile with -DADER_DEG=<0..7>"
@@ -95,6 +96,46 @@ cudaError_t launch_predict_src(const PredictParams& p, cudaStream_t s) {
   return launch_predict_src_cpb<16>(p, s);
 }
 
+// tracer system (ader_tracer.cuh): the same tile shapes as the reacting system
+template <int CPB>
+cudaError_t prepare_nc_cpb() {
+  if constexpr (!NcCfg<D, CPB>::kValid) {
+    return cudaSuccess;
+  } else {
+    return cudaFuncSetAttribute(predict_nc_kernel<D, CPB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)NcCfg<D, CPB>::kSmemBytes);
+  }
+}
+
+template <int CPB>
+cudaError_t launch_predict_nc_cpb(const PredictParams& p, cudaStream_t s) {
+  if constexpr (!NcCfg<D, CPB>::kValid) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    using C = NcCfg<D, CPB>;
+    const long long blocks = (p.ncells + C::CPB - 1) / C::CPB;
+    if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    predict_nc_kernel<D, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t launch_predict_nc(const PredictParams& p, cudaStream_t s) {
+  if (p.prec != 0 || p.from_q || p.out_mode != kOutTrace) return cudaErrorInvalidValue;
+  if (p.cpb == 16 && NcCfg<D, 16>::kValid) return launch_predict_nc_cpb<16>(p, s);
+  if (NcCfg<D, 32>::kValid) return launch_predict_nc_cpb<32>(p, s);
+  return launch_predict_nc_cpb<16>(p, s);
+}
+
+cudaError_t launch_face_nc(const FaceParams& p, cudaStream_t s) {
+  using C = FaceCfg<D, 32>;
+  const long long blocks = (p.ncells + C::C - 1) / C::C;
+  if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  face_nc_kernel<D, 32><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_face_src(const FaceParams& p, cudaStream_t s) {
   using C = FaceCfg<D, 32>;
   const long long blocks = (p.ncells + C::C - 1) / C::C;
@@ -120,6 +161,8 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_cpb<64>()) != cudaSuccess) return e;
   if ((e = prepare_src_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_src_cpb<32>()) != cudaSuccess) return e;
+  if ((e = prepare_nc_cpb<16>()) != cudaSuccess) return e;
+  if ((e = prepare_nc_cpb<32>()) != cudaSuccess) return e;
   for (int prec = 0; prec < 3; ++prec) {
     auto k = prec == 0 ? predict_multi_kernel<D, 0>
                        : (prec == 1 ? predict_multi_kernel<D, 1> : predict_multi_kernel<D, 2>);
@@ -132,6 +175,7 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
 
 cudaError_t ADER_CAT(launch_predict_, ADER_DEG)(const PredictParams& p, cudaStream_t s) {
   if (p.sys == kSysReacting) return launch_predict_src(p, s);
+  if (p.sys == kSysTracer) return launch_predict_nc(p, s);
   switch (p.cpb) {
     case 16: return launch_predict_cpb<16>(p, s);
     case 64: return launch_predict_cpb<64>(p, s);
@@ -210,6 +254,7 @@ cudaError_t ADER_CAT(launch_cfl3d_, ADER_DEG)(const Cfl3DParams& p, cudaStream_t
 
 cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStream_t s) {
   if (p.sys == kSysReacting) return launch_face_src(p, s);
+  if (p.sys == kSysTracer) return launch_face_nc(p, s);
   switch (p.cpf) {
     case 32: return launch_face_cf<32>(p, s);
     case 0:

@@ -10,7 +10,7 @@
 namespace ader {
 
 enum : int { kOutQ = 0, kOutTrace = 1 };
-enum : int { kSysEuler = 0, kSysReacting = 1 };
+enum : int { kSysEuler = 0, kSysReacting = 1, kSysTracer = 2 };
 enum : int { kBcPeriodic = 0, kBcOutflow = 1 };
 
 // LST-DG predictor (Algorithm lst_dg_predictor, S = B = 0) with its epilogue.
@@ -28,7 +28,7 @@ struct PredictParams {
   int max_iter;
   int fixed_iter;
   int cpb;               // predictor cells per block (16, 32, 64; tuned), 0 = 32
-  int sys;               // kSysEuler or kSysReacting (ader_source.cuh)
+  int sys;               // kSysEuler, kSysReacting (ader_source.cuh), kSysTracer (ader_tracer.cuh)
   float tol32;
   double tol;
   double gamma, gm1;

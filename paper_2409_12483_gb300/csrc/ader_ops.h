@@ -20,6 +20,7 @@ constexpr int kMaxNs = 2 * kMaxDeg + 1;   // subcells of Sec. 1.4
 constexpr int kMaxH = (kMaxN + 1) / 2;    // half rows of the symmetric k~ form
 constexpr int kM = 3;                     // conserved variables of 1D Euler
 constexpr int kMR = 5;                    // variables of the 1D two-component reacting flow
+constexpr int kMN = 4;                    // 1D Euler + non-conservative tracer (rho, m, E, phi)
 constexpr int kM2 = 4;                    // conserved variables of 2D Euler (rho, m_x, m_y, E)
 constexpr int kM3 = 5;                    // conserved variables of 3D Euler (rho, m_x, m_y, m_z, E)
 

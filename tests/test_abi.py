@@ -311,3 +311,19 @@ def test_init_3d_options_and_sizes(lib):
                                 C.byref(default_options(**kw)), C.byref(bad)) == 1, kw
     bad = C.c_void_p()
     assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 0, 0, 1, 0, 1, 0, 1)), 2, None, C.byref(bad)) == 1
+
+
+def test_tracer_system_options(lib):
+    """the non-conservative tracer system: DG, FP64, periodic; 4 variables per node"""
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    ctx = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(10, 0.0, 1.0)), 3, 0,
+                         C.byref(default_options(system="tracer")), C.byref(ctx)) == 0
+    assert lib.ader_state_count(ctx) == 10 * 4 * 4
+    lib.ader_destroy(ctx)
+    for kw, scheme in ((dict(system="tracer", bc="outflow"), 0), (dict(system="tracer"), 1),
+                       (dict(system="tracer", precision="ff"), 0),
+                       (dict(system="tracer", limiter=1), 0)):
+        bad = C.c_void_p()
+        assert lib.ader_init(C.byref(Mesh(10, 0.0, 1.0)), 4 if scheme else 3, scheme,
+                             C.byref(default_options(**kw)), C.byref(bad)) == 1, kw

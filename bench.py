@@ -495,6 +495,8 @@ def main():
             line["source_terms"] = run_source(args, dev, flush)
         if not args.no_limiter:
             line["limiter"] = run_limiter(args, dev, flush)
+        if not args.no_source:
+            line["non_conservative"] = run_tracer(args, dev, flush)
         if not args.no_2d:
             line["two_d"] = run_2d(args, dev, flush)
             line["three_d"] = run_3d(args, dev, flush)
@@ -806,6 +808,41 @@ def run_2d(args, dev, flush):
             "predict_frac_of_fp64_peak": fl / (pred_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS})
         del ctx
     return out
+
+
+def run_tracer(args, dev, flush):
+    """The non-conservative product (Euler + passive tracer in non-conservative
+    form): throughput at the headline's size, and the tracer's deviation from
+    rho in uniform flow (u = p = 1, tracer started equal to rho), where the
+    non-conservative scheme must reproduce the conservative one."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    st_ = max(2, min(args.steps, 3))
+    ctx = Context(CELLS, DEGREE, "dg", device=dev, profile=1, system="tracer")
+    x = ctx.node_coords()
+    e = W.nodal_state(W.modes4(SEED), x)  # rho, m, E of the headline data
+    u0 = torch.tensor(np.concatenate([e, 0.5 + 0.3 * np.cos(2 * np.pi * x)[..., None]], -1),
+                      device=dev).reshape(-1)
+    line = variant_line("tracer-dg5-1e5", "Euler + non-conservative tracer (B dU/dx = u dphi/dx), "
+                        "DG N=5, 10^5 cells, 100 steps, FP64", ctx, u0, CELLS, DEGREE, TIME_STEPS,
+                        st_, 2, flush)
+    for k in ("predict_fp64_tflops", "predict_frac_of_fp64_peak"):
+        line.pop(k, None)
+    del ctx
+    nc = 64
+    ctx = Context(nc, DEGREE, "dg", device=dev, system="tracer")
+    x = ctx.node_coords()
+    rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+    u = torch.tensor(np.stack([rho, rho, 1 / 0.4 + 0.5 * rho, rho], -1), device=dev).reshape(-1)
+    steps, t, rc = ctx.ader_solve(u, t_end=1.0)
+    torch.cuda.synchronize()
+    v = u.cpu().numpy().reshape(nc, DEGREE + 1, 4)
+    line["uniform_flow_check"] = {"cells": nc, "t": t, "steps": steps,
+                                  "max_abs_tracer_minus_rho": float(np.abs(v[..., 3] - v[..., 0]).max())}
+    return line
 
 
 def run_limiter(args, dev, flush):

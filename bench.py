@@ -363,7 +363,8 @@ def main():
                     help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
-                         "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5")
+                         "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
+                         "step3d-dg2 (multi-D: warmup + steps time steps of one solve)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1119,6 +1120,18 @@ def run_case(args):
     elif args.case == "weno5":
         ctx = Context(nc, 4, "fv", device=dev)
         u = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
+    elif args.case in ("step2d-dg5", "step3d-dg2"):
+        from paper_2409_12483_gb300 import Context2D, Context3D
+        if args.case == "step2d-dg5":  # 96^2 cells: 35 MB state
+            ctx = Context2D(96, 96, 5, device=dev)
+            u = torch.tensor(sine2d_state(ctx).ravel(), device=dev)
+        else:  # 96^3 cells: 0.96 GB state
+            ctx = Context3D(96, 96, 96, 2, device=dev)
+            u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
+        steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
+        return
     else:
         raise SystemExit(f"unknown case {args.case}")
     out = torch.empty_like(u)

@@ -130,3 +130,21 @@ def test_host_solve_and_stats(cuda, oracle_mod):
     assert rel_linf(host, ref) < 1e-11
     st = ctx.ader_get_stats()
     assert st["steps"] == 12 and st["cells"] == 12 * nx * ny and st["max_iters"] >= 1
+
+
+@pytest.mark.parametrize("nx,ny,N", [(1, 1, 3), (1, 4, 2), (6, 1, 5)])
+def test_degenerate_meshes(cuda, oracle_mod, nx, ny, N):
+    """one cell (its own periodic neighbour in both directions) and single rows /
+    columns"""
+    import torch
+    o = oracle_mod.Oracle2D(N)
+    u = smooth_state(o, nx, ny, seed=nx + ny)
+    dx, dy = 1.0 / nx, 1.0 / ny
+    dt = o.dt(u, nx, ny, dx, dy)
+    ref, rc, _ = o.step(u, nx, ny, dx, dy, dt)
+    ctx = make(nx, ny, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, dt)
+    torch.cuda.synchronize()
+    assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12

@@ -117,3 +117,21 @@ def test_sine_wave_errors_equal_the_oracle(cuda, oracle_mod):
     e_gpu = oracle_mod.dg3_density_errors(o, ud.cpu().numpy(), (nc,) * 3, exact)
     e_ref = oracle_mod.dg3_density_errors(o, ref, (nc,) * 3, exact)
     np.testing.assert_allclose(e_gpu, e_ref, rtol=1e-8)
+
+
+@pytest.mark.parametrize("dims,N", [((1, 1, 1), 2), ((1, 2, 3), 1), ((4, 1, 1), 4)])
+def test_degenerate_meshes(cuda, oracle_mod, dims, N):
+    """one cell (its own periodic neighbour in every direction) and single lines"""
+    import torch
+    box = (1.0, 1.0, 1.0)
+    h = tuple(b / d for b, d in zip(box, dims))
+    o = oracle_mod.Oracle3D(N)
+    u = smooth_state(o, dims, box, seed=sum(dims))
+    dt = o.dt(u, dims, h)
+    ref, rc, _ = o.step(u, dims, h, dt)
+    ctx = make(dims, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, dt)
+    torch.cuda.synchronize()
+    assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12

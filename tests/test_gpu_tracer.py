@@ -87,3 +87,19 @@ def test_tracer_equal_to_rho_in_uniform_flow(cuda, oracle_mod):
     out = ud.cpu().numpy().reshape(nc, N + 1, 4)
     assert rc == 0 and steps == 40
     assert np.abs(out[..., 3] - out[..., 0]).max() < 1e-12
+
+
+@pytest.mark.parametrize("nc,N", [(1, 3), (2, 0), (33, 7)])
+def test_degenerate_and_tile_edge_meshes(cuda, oracle_mod, nc, N):
+    """one cell (its own neighbour), two cells, and one cell past a full tile"""
+    import torch
+    o = oracle_mod.NCOracle(N)
+    u = state(o, nc, seed=nc)
+    dt = o.dt(u, 1.0 / nc)
+    ref, rc, _ = o.step(u, 1.0 / nc, dt)
+    ctx = make(nc, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, dt)
+    torch.cuda.synchronize()
+    assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12

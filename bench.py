@@ -687,7 +687,9 @@ PAPER_2D_L1 = {(1, 10): 5.48e-3, (1, 15): 2.44e-3, (1, 20): 1.37e-3, (1, 25): 8.
 PAPER_3D_L1 = {(1, 10): 5.24e-2, (1, 15): 1.08e-2, (1, 20): 4.62e-3, (1, 25): 2.82e-3,
                (2, 10): 7.69e-4, (2, 15): 2.22e-4, (2, 20): 9.29e-5, (2, 25): 4.74e-5,
                (3, 10): 2.17e-5, (3, 15): 4.28e-6, (3, 20): 1.35e-6, (3, 25): 5.54e-7,
-               (4, 10): 7.69e-7, (4, 15): 1.03e-7, (4, 20): 2.48e-8, (4, 25): 8.16e-9}
+               (4, 10): 7.69e-7, (4, 15): 1.03e-7, (4, 20): 2.48e-8, (4, 25): 8.16e-9,
+               (5, 5): 1.11e-6, (5, 10): 1.67e-8, (5, 15): 1.46e-9, (5, 20): 2.60e-10,
+               (6, 5): 5.24e-8, (6, 10): 4.36e-10, (6, 15): 2.59e-11, (6, 20): 3.49e-12}
 
 
 def sine3d_state(ctx):
@@ -698,7 +700,7 @@ def sine3d_state(ctx):
 
 
 def run_3d(args, dev, flush):
-    """3D Euler (ader_init_3d, degrees 1..4): the sine-wave advection problem of
+    """3D Euler (ader_init_3d, degrees 1..6): the sine-wave advection problem of
     Sec. 2.1 at the meshes of Table conv_orders_pde_3d to t = 1 through the GPU
     path, and throughput of the 3D solve."""
     import numpy as np
@@ -708,8 +710,9 @@ def run_3d(args, dev, flush):
     out = {"sine_wave": [], "throughput": []}
     # the paper's meshes, the finest ones for N <= 2 only (N = 4 on 25^3 alone
     # takes about two minutes)
-    meshes = {1: (10, 15, 20, 25), 2: (10, 15, 20), 3: (10, 15), 4: (10, 15)}
-    for N in range(1, 5):
+    meshes = {1: (10, 15, 20, 25), 2: (10, 15, 20), 3: (10, 15), 4: (10, 15), 5: (5, 10),
+              6: (5, 10)}
+    for N in range(1, 7):
         prev = None
         for nc in meshes[N]:
             ctx = Context3D(nc, nc, nc, N, device=dev)
@@ -730,7 +733,7 @@ def run_3d(args, dev, flush):
             out["sine_wave"].append(row)
             del ctx
     st_ = max(2, min(args.steps, 3))
-    for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10)):
+    for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10), (5, 24, 10), (6, 16, 10)):
         ctx = Context3D(nc, nc, nc, N, device=dev, profile=1)
         u0 = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
         cells = nc ** 3

@@ -161,6 +161,16 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_cpb<64>()) != cudaSuccess) return e;
   if ((e = prepare_src_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_src_cpb<32>()) != cudaSuccess) return e;
+  if constexpr (D <= kMax3DDeg) {  // 3D kernels with more than 48 KB of shared memory
+    if ((e = cudaFuncSetAttribute(update3d_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Upd3Cfg<D>::kSmemBytes)) != cudaSuccess)
+      return e;
+  }
+  if constexpr (D > kMax3DLowDeg && D <= kMax3DDeg) {
+    if ((e = cudaFuncSetAttribute(predict3d_hi_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Pred3HiCfg<D>::kSmemBytes)) != cudaSuccess)
+      return e;
+  }
   if ((e = prepare_nc_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_nc_cpb<32>()) != cudaSuccess) return e;
   for (int prec = 0; prec < 3; ++prec) {
@@ -221,9 +231,14 @@ cudaError_t ADER_CAT(launch_cfl2d_, ADER_DEG)(const Cfl2DParams& p, cudaStream_t
 
 // 3D: degrees 0..4 (one thread per space-time node); other degrees are refused
 cudaError_t ADER_CAT(launch_predict3d_, ADER_DEG)(const Predict3DParams& p, cudaStream_t s) {
-  if constexpr (D <= kMax3DDeg) {
+  if constexpr (D <= kMax3DLowDeg) {
     using C = Pred3Cfg<D>;
     predict3d_kernel<D><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+  } else if constexpr (D <= kMax3DDeg) {
+    using C = Pred3HiCfg<D>;
+    if (p.ncells <= 0 || p.ncells > 0x7fffffffLL) return cudaErrorInvalidValue;
+    predict3d_hi_kernel<D><<<(unsigned)p.ncells, C::THREADS, C::kSmemBytes, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;
@@ -235,7 +250,7 @@ cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream
     constexpr int n = D + 1;
     face3d_kernel<D><<<grid_for(p.ncells * 3 * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
     using U = Upd3Cfg<D>;
-    update3d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, 0, s>>>(p);
+    update3d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, U::kSmemBytes, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;

@@ -3,8 +3,9 @@
 // tensor-product LST-DG predictor of Sec. 1.1 (eq. lst_dg_predictor_picard with
 // L^xi = kappa~ (x) k~ (x) I (x) I and likewise along eta and zeta, L^0 = delta),
 // the corrector of Sec. 1.2 with x-, y- and z-faces and lambda_max for the time
-// step of Sec. 1.5 with d = 3.  Degrees 0..4 (one thread per space-time node,
-// (N+1)^4 <= 625 threads per cell).
+// step of Sec. 1.5 with d = 3.  Degrees 0..4: one thread per space-time node
+// ((N+1)^4 <= 625 threads per cell); degrees 5, 6: predict3d_hi_kernel, one
+// thread per spatial node holding its tau column.
 //
 // State u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x, m_y,
 // m_z, E).  Trace record per cell (doubles): for d = x, y, z and side = low,
@@ -31,6 +32,7 @@
 namespace ader {
 
 constexpr int kMax3DDeg = kMax3DDegree;
+constexpr int kMax3DLowDeg = 4;  // one thread per space-time node up to here
 
 // x-, y- and z-fluxes of the 3D Euler equations: F[d][5]
 __device__ __forceinline__ void euler3_flux(const double* U, double (*F)[kM3], double gm1) {
@@ -252,6 +254,200 @@ __global__ void __launch_bounds__(Pred3Cfg<N>::THREADS)
   }
 }
 
+// the d-direction flux of the 3D Euler equations
+template <int D>
+__device__ __forceinline__ void euler3_flux_dir(const double* U, double* f, double gm1) {
+  const double inv = recip(U[0]);
+  const double v[3] = {U[1] * inv, U[2] * inv, U[3] * inv};
+  const double p =
+      gm1 * fma(neg_half(U[1]), v[0], fma(neg_half(U[2]), v[1], fma(neg_half(U[3]), v[2], U[4])));
+  f[0] = U[1 + D];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[1 + c] = c == D ? fma(U[1 + c], v[D], p) : U[1 + c] * v[D];
+  f[4] = (U[4] + p) * v[D];
+}
+
+// Degrees 5 and 6: one block per cell, one thread per SPATIAL node (p1, p2, p3)
+// owning its whole tau column q[p0][5] in registers, so kappa~ along tau is a
+// per-thread contraction; the three rescaled fluxes pass in turn through one
+// dynamic shared array [p0][node][5] (n^4 5 doubles: 52 KB at N = 5, 96 KB at
+// N = 6) for the k~ contractions along xi, eta and zeta.
+template <int N>
+struct Pred3HiCfg {
+  static constexpr int n = N + 1, NNN = n * n * n, NST = n * n * n * n;
+  static constexpr int THREADS = (NNN + 31) / 32 * 32;
+  static constexpr size_t kSmemBytes = (size_t)NST * kM3 * sizeof(double);
+};
+
+template <int N>
+__global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
+    predict3d_hi_kernel(const __grid_constant__ Predict3DParams P) {
+  using C = Pred3HiCfg<N>;
+  constexpr int n = N + 1, NNN = C::NNN, REC = Pred3Cfg<N>::REC;
+  extern __shared__ __align__(16) double S[];  // [p0][node][5]
+  __shared__ unsigned long long red[2];
+  __shared__ int s_done, s_go;
+  __shared__ double s_dt;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double d = 0.0;
+    s_go = predictor_step_dt(P.sp, &d, blockIdx.x == 0) ? 1 : 0;
+    s_dt = d;
+    red[0] = red[1] = 0ull;
+    s_done = 0;
+  }
+  __syncthreads();
+  if (!s_go) return;  // uniform
+  const double dt = s_dt;
+  const double lam[3] = {dt * P.sp.inv_dx, dt * P.inv_dy, dt * P.inv_dz};
+  const long long cell = blockIdx.x;
+  const bool valid = tid < NNN;
+  const int node = valid ? tid : 0;
+  const int p1 = node / (n * n), p2 = (node / n) % n, p3 = node % n;
+  const int stride[3] = {n * n, n, 1};
+  const int pd[3] = {p1, p2, p3};
+  const OpsD& o = P.ops;
+  double uo[kM3], q[n][kM3];
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) uo[r] = valid ? P.u[(cell * NNN + node) * kM3 + r] : 1.0;
+#pragma unroll
+  for (int p0 = 0; p0 < n; ++p0)
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) q[p0][r] = uo[r];
+  const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+  for (int it = 0; it < cap; ++it) {
+    double acc[n][kM3];
+#pragma unroll
+    for (int p0 = 0; p0 < n; ++p0)
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) acc[p0][r] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (valid) {
+#pragma unroll
+        for (int p0 = 0; p0 < n; ++p0) {
+          double f[kM3];
+          if (d == 0) euler3_flux_dir<0>(q[p0], f, P.gm1);
+          if (d == 1) euler3_flux_dir<1>(q[p0], f, P.gm1);
+          if (d == 2) euler3_flux_dir<2>(q[p0], f, P.gm1);
+#pragma unroll
+          for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = lam[d] * f[r];
+        }
+      }
+      __syncthreads();
+      if (valid) {
+        const int base = node - pd[d] * stride[d];
+#pragma unroll
+        for (int p0 = 0; p0 < n; ++p0)
+#pragma unroll
+          for (int r = 0; r < kM3; ++r)
+#pragma unroll
+            for (int m = 0; m < n; ++m)
+              acc[p0][r] = fma(o.kt[pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+      }
+      __syncthreads();
+    }
+    if (valid) {
+      unsigned long long dmax = 0ull, qm = 0ull;
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) {
+        double qn[n];  // kappa~ along tau needs every acc[.][r] before q[.][r] changes
+#pragma unroll
+        for (int p0 = 0; p0 < n; ++p0) {
+          double sum = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) sum = fma(o.kap[p0][m], acc[m][r], sum);
+          qn[p0] = uo[r] - sum;
+        }
+#pragma unroll
+        for (int p0 = 0; p0 < n; ++p0) {
+          dmax = umax64(dmax, abs_bits(qn[p0] - q[p0][r]));
+          qm = umax64(qm, abs_bits(qn[p0]));
+          q[p0][r] = qn[p0];
+        }
+      }
+      atomicMax(&red[0], dmax);
+      atomicMax(&red[1], qm);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double delta = bitsd(red[0]), qmax = bitsd(red[1]);
+      const bool conv = P.fixed_iter > 0 ? it + 1 == P.fixed_iter : delta <= P.tol * fmax(qmax, 1.0);
+      if (conv || it + 1 == cap) {
+        s_done = 1;
+        if (!conv) atomicOr(&P.sp.ctl->status, kStNotConverged);
+        atomicAdd(&P.sp.ctl->iter_sum, (unsigned long long)(it + 1));
+        atomicAdd((unsigned long long*)&P.sp.ctl->iter_cells, 1ull);
+        atomicMax(&P.sp.ctl->iter_max, it + 1);
+      }
+      red[0] = red[1] = 0ull;
+    }
+    __syncthreads();
+    if (s_done) break;  // uniform
+  }
+  // epilogue: the six face traces per tau node, then the volume term
+  if (valid) {
+#pragma unroll
+    for (int p0 = 0; p0 < n; ++p0)
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = q[p0][r];
+  }
+  __syncthreads();
+  double* rec = P.trace + cell * REC;
+  if (valid) {  // item (l0, a, c) = node
+    const int l0 = node / (n * n), a = (node / n) % n, c = node % n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int base = d == 0 ? a * n + c : d == 1 ? a * n * n + c : a * n * n + c * n;
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) {
+        double lo = 0.0, hi = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const double x = S[(l0 * NNN + base + m * stride[d]) * kM3 + r];
+          lo = fma(o.psi0[m], x, lo);
+          hi = fma(o.psi1[m], x, hi);
+        }
+        rec[((d * 2 + 0) * NNN + node) * kM3 + r] = lo;
+        rec[((d * 2 + 1) * NNN + node) * kM3 + r] = hi;
+      }
+    }
+  }
+  __syncthreads();
+  // time-averaged rescaled fluxes of this node's column, per direction, into S as [d][node][5]
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double fb[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int l0 = 0; l0 < n; ++l0) {
+        double f[kM3];
+        if (d == 0) euler3_flux_dir<0>(q[l0], f, P.gm1);
+        if (d == 1) euler3_flux_dir<1>(q[l0], f, P.gm1);
+        if (d == 2) euler3_flux_dir<2>(q[l0], f, P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM3; ++r) fb[r] = fma(o.w[l0], lam[d] * f[r], fb[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) S[(d * NNN + node) * kM3 + r] = fb[r];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = uo[r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int base = node - pd[d] * stride[d];
+#pragma unroll
+        for (int l = 0; l < n; ++l) acc = fma(o.vt[pd[d]][l], S[(d * NNN + base + l * stride[d]) * kM3 + r], acc);
+      }
+      rec[(6 * NNN + node) * kM3 + r] = acc;
+    }
+  }
+}
+
 // time-integrated rescaled Rusanov flux through the low face of each cell in
 // direction d at transverse nodes (a, c): [cell][d][a][c][5]
 template <int N>
@@ -304,6 +500,9 @@ struct Upd3Cfg {
   static constexpr int CPB = NNN >= 128 ? 1 : 128 / NNN;  // cells per block
   static constexpr int USED = CPB * NNN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
+  // dynamic shared memory: U [CPB][NNN][5], T1 [CPB][n n][Ns][5], T2 [CPB][n][Ns Ns][5]
+  static constexpr size_t kSmemBytes =
+      (size_t)CPB * (NNN + n * n * Ns + n * Ns * Ns) * kM3 * sizeof(double);
 };
 
 // u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}, one
@@ -315,9 +514,11 @@ __global__ void __launch_bounds__(Upd3Cfg<N>::THREADS)
     update3d_kernel(const __grid_constant__ Face3DParams P) {
   using C = Upd3Cfg<N>;
   constexpr int n = N + 1, NNN = n * n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred3Cfg<N>::REC;
-  __shared__ double U[CPB][NNN][kM3];
-  __shared__ double T1[CPB][n * n][Ns][kM3];  // projected along zeta: [k1 k2][j3]
-  __shared__ double T2[CPB][n][Ns * Ns][kM3];  // then along eta: [k1][j2 j3]
+  extern __shared__ __align__(16) double dsm[];
+  auto U = reinterpret_cast<double(*)[NNN][kM3]>(dsm);
+  auto T1 = reinterpret_cast<double(*)[n * n][Ns][kM3]>(dsm + CPB * NNN * kM3);  // along zeta: [k1 k2][j3]
+  auto T2 = reinterpret_cast<double(*)[n][Ns * Ns][kM3]>(
+      dsm + CPB * (NNN + n * n * Ns) * kM3);  // then along eta: [k1][j2 j3]
   __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
   int last;

@@ -73,7 +73,8 @@ typedef enum {
  *   corrector with the B volume term and a path-conservative Rusanov face (the
  *   minus-side cell takes G + Bt/2, the plus side G - Bt/2, Bt the integral of B
  *   along the straight segment, 3-point Gauss-Legendre).  DG, ADER_PREC_FP64,
- *   periodic only. */
+ *   periodic only; it runs through ader_step / ader_solve (ader_predict and
+ *   ader_correct return ADER_ERR_ARG). */
 typedef enum { ADER_SYSTEM_EULER = 0, ADER_SYSTEM_REACTING = 1, ADER_SYSTEM_TRACER = 2 } ader_system;
 
 /* Boundary condition of the mesh ends.  ADER_BC_OUTFLOW (DG only): free outflow;

@@ -808,6 +808,8 @@ ader_status ader_predict(ader_ctx* ctx, const double* u, double dt, double* q) {
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
   if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_predict is 1D only");
+  if (ctx->opt.system == ADER_SYSTEM_TRACER)
+    return fail(ctx, ADER_ERR_ARG, "the tracer system's predictor runs inside ader_step / ader_solve");
   if (!u || !q) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (std::isnan(dt)) return fail(ctx, ADER_ERR_ARG, "dt is NaN");
   if ((st = fork_in(ctx)) != ADER_OK) return st;
@@ -840,6 +842,8 @@ ader_status ader_correct(ader_ctx* ctx, const double* u, const double* q, double
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
   if (ctx->dims != 1) return fail(ctx, ADER_ERR_ARG, "ader_correct is 1D only");
+  if (ctx->opt.system == ADER_SYSTEM_TRACER)
+    return fail(ctx, ADER_ERR_ARG, "the tracer system's corrector runs inside ader_step / ader_solve");
   if (!u || !q || !u_new) return fail(ctx, ADER_ERR_ARG, "null pointer");
   if (!(dt > 0.0)) return fail(ctx, ADER_ERR_ARG, "ader_correct needs dt > 0");
   if (u == u_new) return fail(ctx, ADER_ERR_ARG, "u and u_new must not alias");

@@ -160,6 +160,11 @@ def lib():
                                            P(C.c_int)]
             L.ob2_dg_step.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double,
                                       C.c_double, C.c_double, _DP, _DP, P(Stats)]
+            L.ob2_dg_step_cells.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double,
+                                            C.c_double, C.c_double, _DP, _IP, C.c_int64, _DP]
+            L.ob3_dg_step_cells.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_int64,
+                                            C.c_double, C.c_double, C.c_double, C.c_double, _DP, _IP,
+                                            C.c_int64, _DP]
             L.ob2_dt.argtypes = [P(Basis), P(Params), C.c_int64, C.c_int64, C.c_double, C.c_double,
                                  _DP]
             L.ob2_dt.restype = C.c_double
@@ -640,6 +645,14 @@ class Oracle2D:
                                out, C.byref(st))
         return out, rc, st.mean_iters
 
+    def step_cells(self, u, nx: int, ny: int, dx: float, dy: float, dt: float, cells):
+        """u^{n+1} of the listed cells only: [count][n][n][4]"""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size * self.n * self.n * M2)
+        rc = lib().ob2_dg_step_cells(C.byref(self.basis), C.byref(self.params), nx, ny, dx, dy, dt,
+                                     _arr(u).ravel(), cells, cells.size, out)
+        return out.reshape(cells.size, self.n, self.n, M2), rc
+
     def dt(self, u, nx: int, ny: int, dx: float, dy: float) -> float:
         return lib().ob2_dt(C.byref(self.basis), C.byref(self.params), nx, ny, dx, dy,
                             _arr(u).ravel())
@@ -728,6 +741,14 @@ class Oracle3D:
         rc = lib().ob3_dg_step(C.byref(self.basis), C.byref(self.params), *dims, *h, dt, u, out,
                                C.byref(st))
         return out, rc, st.mean_iters
+
+    def step_cells(self, u, dims, h, dt: float, cells):
+        """u^{n+1} of the listed cells only: [count][n][n][n][5]"""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros(cells.size * self.n ** 3 * M3)
+        rc = lib().ob3_dg_step_cells(C.byref(self.basis), C.byref(self.params), *dims, *h, dt,
+                                     _arr(u).ravel(), cells, cells.size, out)
+        return out.reshape(cells.size, self.n, self.n, self.n, M3), rc
 
     def dt(self, u, dims, h) -> float:
         return lib().ob3_dt(C.byref(self.basis), C.byref(self.params), *dims, *h, _arr(u).ravel())

@@ -234,6 +234,9 @@ int ob2_predict_cell(const ob_basis* b, const ob_params* p, double lx, double ly
                      double* q, int* iters);
 int ob2_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx,
                 double dy, double dt, const double* u, double* u_new, ob_stats* st);
+int ob2_dg_step_cells(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx,
+                      double dy, double dt, const double* u, const int64_t* cells, int64_t count,
+                      double* out);
 double ob2_dt(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx, double dy,
               const double* u);
 int ob2_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx, double dy,
@@ -255,6 +258,9 @@ int ob3_predict_cell(const ob_basis* b, const ob_params* p, double lx, double ly
 int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz,
                 double dx, double dy, double dz, double dt, const double* u, double* u_new,
                 ob_stats* st);
+int ob3_dg_step_cells(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz,
+                      double dx, double dy, double dz, double dt, const double* u,
+                      const int64_t* cells, int64_t count, double* out);
 double ob3_dt(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz, double dx,
               double dy, double dz, const double* u);
 int ob3_solve(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz, double dx,

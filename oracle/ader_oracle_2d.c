@@ -133,6 +133,61 @@ int ob2_predict_cell(const ob_basis* b, const ob_params* p, double lx, double ly
 
 static int64_t wrap2(int64_t i, int64_t n) { return ((i % n) + n) % n; }
 
+/* predictor, face traces [l0][k][r] (xR, xL, yR, yL) and volume term of one cell */
+static int cell_record(const ob_basis* b, const ob_params* p, double lx, double ly,
+                       const double* uc, double* q, double* xR, double* xL, double* yR,
+                       double* yL, double* vol, int* iters) {
+  const int n = b->n;
+  const int64_t us = (int64_t)n * n * M2;
+  const int status = ob2_predict_cell(b, p, lx, ly, uc, q, iters);
+  for (int l0 = 0; l0 < n; ++l0)
+    for (int k = 0; k < n; ++k)
+      for (int r = 0; r < M2; ++r) {
+        double aR = 0.0, aL = 0.0, bR = 0.0, bL = 0.0;
+        for (int m = 0; m < n; ++m) {
+          aR += b->psi1[m] * q[Q2(l0, m, k, r)];
+          aL += b->psi0[m] * q[Q2(l0, m, k, r)];
+          bR += b->psi1[m] * q[Q2(l0, k, m, r)];
+          bL += b->psi0[m] * q[Q2(l0, k, m, r)];
+        }
+        const int64_t o = ((int64_t)l0 * n + k) * M2 + r;
+        xR[o] = aR;
+        xL[o] = aL;
+        yR[o] = bR;
+        yL[o] = bL;
+      }
+  /* volume terms: time-averaged rescaled fluxes, D~ along xi and eta */
+  double* fbar = malloc(sizeof(double) * us);
+  double* gbar = malloc(sizeof(double) * us);
+  if (!fbar || !gbar) {
+    free(fbar), free(gbar);
+    return OB_ERR_ARG;
+  }
+  for (int i = 0; i < us; ++i) fbar[i] = gbar[i] = 0.0;
+  for (int l0 = 0; l0 < n; ++l0)
+    for (int l1 = 0; l1 < n; ++l1)
+      for (int l2 = 0; l2 < n; ++l2) {
+        double F[M2], G[M2];
+        ob2_flux(p->gamma, &q[Q2(l0, l1, l2, 0)], F, G);
+        for (int r = 0; r < M2; ++r) {
+          fbar[U2(l1, l2, r)] += b->w[l0] * (lx * F[r]);
+          gbar[U2(l1, l2, r)] += b->w[l0] * (ly * G[r]);
+        }
+      }
+  for (int k1 = 0; k1 < n; ++k1)
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int r = 0; r < M2; ++r) {
+        double ax = 0.0, ay = 0.0;
+        for (int l = 0; l < n; ++l) {
+          ax += b->dt_m[k1][l] * fbar[U2(l, k2, r)];
+          ay += b->dt_m[k2][l] * gbar[U2(k1, l, r)];
+        }
+        vol[U2(k1, k2, r)] = uc[U2(k1, k2, r)] + ax / b->w[k1] + ay / b->w[k2];
+      }
+  free(fbar), free(gbar);
+  return status;
+}
+
 int ob2_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx,
                 double dy, double dt, const double* u, double* u_new, ob_stats* st) {
   if (nx <= 0 || ny <= 0) return OB_ERR_ARG;
@@ -157,54 +212,15 @@ int ob2_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, d
   int status = OB_OK;
   for (int64_t c = 0; c < nc; ++c) {
     int it = 0;
-    if (ob2_predict_cell(b, p, lx, ly, u + c * us, q, &it) != OB_OK) status = OB_ERR_NOT_CONVERGED;
+    if (cell_record(b, p, lx, ly, u + c * us, q, xR + c * ts, xL + c * ts, yR + c * ts, yL + c * ts,
+                    vol + c * us, &it) != OB_OK)
+      status = OB_ERR_NOT_CONVERGED;
     if (st) {
       if (st->cells == 0 || it > st->max_iters) st->max_iters = it;
       if (st->cells == 0 || it < st->min_iters) st->min_iters = it;
       st->mean_iters = (st->mean_iters * (double)st->cells + it) / (double)(st->cells + 1);
       st->cells += 1;
     }
-    for (int l0 = 0; l0 < n; ++l0)
-      for (int k = 0; k < n; ++k)
-        for (int r = 0; r < M2; ++r) {
-          double aR = 0.0, aL = 0.0, bR = 0.0, bL = 0.0;
-          for (int m = 0; m < n; ++m) {
-            aR += b->psi1[m] * q[Q2(l0, m, k, r)];
-            aL += b->psi0[m] * q[Q2(l0, m, k, r)];
-            bR += b->psi1[m] * q[Q2(l0, k, m, r)];
-            bL += b->psi0[m] * q[Q2(l0, k, m, r)];
-          }
-          const int64_t o = c * ts + ((int64_t)l0 * n + k) * M2 + r;
-          xR[o] = aR;
-          xL[o] = aL;
-          yR[o] = bR;
-          yL[o] = bL;
-        }
-    /* volume terms: time-averaged rescaled fluxes, D~ along xi and eta */
-    double* fbar = malloc(sizeof(double) * us);
-    double* gbar = malloc(sizeof(double) * us);
-    for (int i = 0; i < us; ++i) fbar[i] = gbar[i] = 0.0;
-    for (int l0 = 0; l0 < n; ++l0)
-      for (int l1 = 0; l1 < n; ++l1)
-        for (int l2 = 0; l2 < n; ++l2) {
-          double F[M2], G[M2];
-          ob2_flux(p->gamma, &q[Q2(l0, l1, l2, 0)], F, G);
-          for (int r = 0; r < M2; ++r) {
-            fbar[U2(l1, l2, r)] += b->w[l0] * (lx * F[r]);
-            gbar[U2(l1, l2, r)] += b->w[l0] * (ly * G[r]);
-          }
-        }
-    for (int k1 = 0; k1 < n; ++k1)
-      for (int k2 = 0; k2 < n; ++k2)
-        for (int r = 0; r < M2; ++r) {
-          double ax = 0.0, ay = 0.0;
-          for (int l = 0; l < n; ++l) {
-            ax += b->dt_m[k1][l] * fbar[U2(l, k2, r)];
-            ay += b->dt_m[k2][l] * gbar[U2(k1, l, r)];
-          }
-          vol[c * us + U2(k1, k2, r)] = u[c * us + U2(k1, k2, r)] + ax / b->w[k1] + ay / b->w[k2];
-        }
-    free(fbar), free(gbar);
   }
   /* time-integrated Rusanov fluxes through the left x-face and the bottom y-face of each cell */
   for (int64_t iy = 0; iy < ny; ++iy)
@@ -243,6 +259,74 @@ int ob2_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, d
     }
   free(q), free(xR), free(xL), free(yR), free(yL), free(vol), free(Gx), free(Gy);
   if (st) st->status = status;
+  return status;
+}
+
+/* u^{n+1} of the listed cells only (each from its own and its four face
+ * neighbours' predictors, the same arithmetic as ob2_dg_step): out[count][n][n][4] */
+int ob2_dg_step_cells(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, double dx,
+                      double dy, double dt, const double* u, const int64_t* cells, int64_t count,
+                      double* out) {
+  const int n = b->n;
+  const double lx = dt / dx, ly = dt / dy;
+  const int64_t us = (int64_t)n * n * M2, ts = (int64_t)n * n * M2;
+  double* q = malloc(sizeof(double) * n * us);
+  double* rec = malloc(sizeof(double) * 5 * 5 * ts);  /* 5 cells x (xR, xL, yR, yL, vol) */
+  if (!q || !rec) {
+    free(q), free(rec);
+    return OB_ERR_ARG;
+  }
+  int status = OB_OK;
+  for (int64_t s = 0; s < count; ++s) {
+    const int64_t c = cells[s];
+    if (c < 0 || c >= nx * ny) {
+      status = OB_ERR_ARG;
+      break;
+    }
+    const int64_t iy = c / nx, ix = c - iy * nx;
+    /* this cell, left, right, bottom, top */
+    const int64_t nb[5] = {c, iy * nx + wrap2(ix - 1, nx), iy * nx + wrap2(ix + 1, nx),
+                           wrap2(iy - 1, ny) * nx + ix, wrap2(iy + 1, ny) * nx + ix};
+    for (int j = 0; j < 5; ++j) {
+      double* R = rec + j * 5 * ts;
+      int it = 0;
+      if (cell_record(b, p, lx, ly, u + nb[j] * us, q, R, R + ts, R + 2 * ts, R + 3 * ts, R + 4 * ts,
+                      &it) != OB_OK)
+        status = OB_ERR_NOT_CONVERGED;
+    }
+#define REC(j, part) (rec + ((j) * 5 + (part)) * ts)
+    double Gx[2][NM * M2], Gy[2][NM * M2]; /* [0]: low face, [1]: high face */
+    for (int k = 0; k < n; ++k) {
+      double h[4][M2] = {{0}};
+      for (int l0 = 0; l0 < n; ++l0) {
+        const int64_t o = ((int64_t)l0 * n + k) * M2;
+        double H[M2];
+        ob2_rusanov(p->gamma, 0, REC(1, 0) + o, REC(0, 1) + o, H);  /* left x-face */
+        for (int r = 0; r < M2; ++r) h[0][r] += b->w[l0] * (lx * H[r]);
+        ob2_rusanov(p->gamma, 0, REC(0, 0) + o, REC(2, 1) + o, H);  /* right x-face */
+        for (int r = 0; r < M2; ++r) h[1][r] += b->w[l0] * (lx * H[r]);
+        ob2_rusanov(p->gamma, 1, REC(3, 2) + o, REC(0, 3) + o, H);  /* bottom y-face */
+        for (int r = 0; r < M2; ++r) h[2][r] += b->w[l0] * (ly * H[r]);
+        ob2_rusanov(p->gamma, 1, REC(0, 2) + o, REC(4, 3) + o, H);  /* top y-face */
+        for (int r = 0; r < M2; ++r) h[3][r] += b->w[l0] * (ly * H[r]);
+      }
+      for (int r = 0; r < M2; ++r) {
+        Gx[0][k * M2 + r] = h[0][r];
+        Gx[1][k * M2 + r] = h[1][r];
+        Gy[0][k * M2 + r] = h[2][r];
+        Gy[1][k * M2 + r] = h[3][r];
+      }
+    }
+    for (int k1 = 0; k1 < n; ++k1)
+      for (int k2 = 0; k2 < n; ++k2)
+        for (int r = 0; r < M2; ++r) {
+          const double fx = b->psi1[k1] * Gx[1][k2 * M2 + r] - b->psi0[k1] * Gx[0][k2 * M2 + r];
+          const double fy = b->psi1[k2] * Gy[1][k1 * M2 + r] - b->psi0[k2] * Gy[0][k1 * M2 + r];
+          out[s * us + U2(k1, k2, r)] = REC(0, 4)[U2(k1, k2, r)] - fx / b->w[k1] - fy / b->w[k2];
+        }
+#undef REC
+  }
+  free(q), free(rec);
   return status;
 }
 

@@ -152,6 +152,43 @@ static void face_trace(const ob_basis* b, const double* q, int d, int side, doub
         }
 }
 
+/* predictor, six face traces [d][side][l0][a][c][r] and volume term of one cell
+ * (fbar: scratch of 3 n^3 M3 doubles) */
+static int cell_record3(const ob_basis* b, const ob_params* p, const double* lam, const double* uc,
+                        double* q, double* fbar, double* trc, double* vol, int* iters) {
+  const int n = b->n;
+  const int64_t us = (int64_t)n * n * n * M3, ts = us;
+  const int status = ob3_predict_cell(b, p, lam[0], lam[1], lam[2], uc, q, iters);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) face_trace(b, q, d, side, trc + (d * 2 + side) * ts);
+  /* volume terms: time-averaged rescaled fluxes, D~ along each direction */
+  for (int i = 0; i < 3 * us; ++i) fbar[i] = 0.0;
+  for (int l0 = 0; l0 < n; ++l0)
+    for (int l1 = 0; l1 < n; ++l1)
+      for (int l2 = 0; l2 < n; ++l2)
+        for (int l3 = 0; l3 < n; ++l3) {
+          double F[3 * M3];
+          ob3_flux(p->gamma, &q[Q3(l0, l1, l2, l3, 0)], F);
+          for (int d = 0; d < 3; ++d)
+            for (int r = 0; r < M3; ++r)
+              fbar[d * us + U3(l1, l2, l3, r)] += b->w[l0] * (lam[d] * F[d * M3 + r]);
+        }
+  for (int k1 = 0; k1 < n; ++k1)
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int k3 = 0; k3 < n; ++k3)
+        for (int r = 0; r < M3; ++r) {
+          double ax = 0.0, ay = 0.0, az = 0.0;
+          for (int l = 0; l < n; ++l) {
+            ax += b->dt_m[k1][l] * fbar[0 * us + U3(l, k2, k3, r)];
+            ay += b->dt_m[k2][l] * fbar[1 * us + U3(k1, l, k3, r)];
+            az += b->dt_m[k3][l] * fbar[2 * us + U3(k1, k2, l, r)];
+          }
+          vol[U3(k1, k2, k3, r)] =
+              uc[U3(k1, k2, k3, r)] + ax / b->w[k1] + ay / b->w[k2] + az / b->w[k3];
+        }
+  return status;
+}
+
 int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz,
                 double dx, double dy, double dz, double dt, const double* u, double* u_new,
                 ob_stats* st) {
@@ -173,7 +210,7 @@ int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, i
   int status = OB_OK;
   for (int64_t c = 0; c < nc; ++c) {
     int it = 0;
-    if (ob3_predict_cell(b, p, lam[0], lam[1], lam[2], u + c * us, q, &it) != OB_OK)
+    if (cell_record3(b, p, lam, u + c * us, q, fbar, trc + c * 6 * ts, vol + c * us, &it) != OB_OK)
       status = OB_ERR_NOT_CONVERGED;
     if (st) {
       if (st->cells == 0 || it > st->max_iters) st->max_iters = it;
@@ -181,33 +218,6 @@ int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, i
       st->mean_iters = (st->mean_iters * (double)st->cells + it) / (double)(st->cells + 1);
       st->cells += 1;
     }
-    for (int d = 0; d < 3; ++d)
-      for (int side = 0; side < 2; ++side) face_trace(b, q, d, side, trc + (c * 6 + d * 2 + side) * ts);
-    /* volume terms: time-averaged rescaled fluxes, D~ along each direction */
-    for (int i = 0; i < 3 * us; ++i) fbar[i] = 0.0;
-    for (int l0 = 0; l0 < n; ++l0)
-      for (int l1 = 0; l1 < n; ++l1)
-        for (int l2 = 0; l2 < n; ++l2)
-          for (int l3 = 0; l3 < n; ++l3) {
-            double F[3 * M3];
-            ob3_flux(p->gamma, &q[Q3(l0, l1, l2, l3, 0)], F);
-            for (int d = 0; d < 3; ++d)
-              for (int r = 0; r < M3; ++r)
-                fbar[d * us + U3(l1, l2, l3, r)] += b->w[l0] * (lam[d] * F[d * M3 + r]);
-          }
-    for (int k1 = 0; k1 < n; ++k1)
-      for (int k2 = 0; k2 < n; ++k2)
-        for (int k3 = 0; k3 < n; ++k3)
-          for (int r = 0; r < M3; ++r) {
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int l = 0; l < n; ++l) {
-              ax += b->dt_m[k1][l] * fbar[0 * us + U3(l, k2, k3, r)];
-              ay += b->dt_m[k2][l] * fbar[1 * us + U3(k1, l, k3, r)];
-              az += b->dt_m[k3][l] * fbar[2 * us + U3(k1, k2, l, r)];
-            }
-            vol[c * us + U3(k1, k2, k3, r)] =
-                u[c * us + U3(k1, k2, k3, r)] + ax / b->w[k1] + ay / b->w[k2] + az / b->w[k3];
-          }
   }
   /* time-integrated Rusanov fluxes through the low face of each cell per direction */
   for (int64_t iz = 0; iz < nz; ++iz)
@@ -257,6 +267,72 @@ int ob3_dg_step(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, i
       }
   free(q), free(trc), free(vol), free(G), free(fbar);
   if (st) st->status = status;
+  return status;
+}
+
+/* u^{n+1} of the listed cells only (each from its own and its six face
+ * neighbours' predictors, the same arithmetic as ob3_dg_step): out[count][n^3][5] */
+int ob3_dg_step_cells(const ob_basis* b, const ob_params* p, int64_t nx, int64_t ny, int64_t nz,
+                      double dx, double dy, double dz, double dt, const double* u,
+                      const int64_t* cells, int64_t count, double* out) {
+  const int n = b->n;
+  const double lam[3] = {dt / dx, dt / dy, dt / dz};
+  const int64_t us = (int64_t)n * n * n * M3, ts = us;
+  double* q = malloc(sizeof(double) * n * us);
+  double* fbar = malloc(sizeof(double) * 3 * us);
+  double* trc = malloc(sizeof(double) * 7 * 6 * ts);
+  double* vol = malloc(sizeof(double) * us);
+  double* tmpv = malloc(sizeof(double) * us);
+  if (!q || !fbar || !trc || !vol || !tmpv) {
+    free(q), free(fbar), free(trc), free(vol), free(tmpv);
+    return OB_ERR_ARG;
+  }
+  int status = OB_OK;
+  for (int64_t s = 0; s < count; ++s) {
+    const int64_t c = cells[s];
+    if (c < 0 || c >= nx * ny * nz) {
+      status = OB_ERR_ARG;
+      break;
+    }
+    const int64_t plane = nx * ny, iz = c / plane, iy = (c - iz * plane) / nx,
+                  ix = c - iz * plane - iy * nx;
+    /* this cell, then low / high neighbour per direction */
+    const int64_t nb[7] = {c,
+                           (iz * ny + iy) * nx + wrap3(ix - 1, nx), (iz * ny + iy) * nx + wrap3(ix + 1, nx),
+                           (iz * ny + wrap3(iy - 1, ny)) * nx + ix, (iz * ny + wrap3(iy + 1, ny)) * nx + ix,
+                           (wrap3(iz - 1, nz) * ny + iy) * nx + ix, (wrap3(iz + 1, nz) * ny + iy) * nx + ix};
+    for (int j = 0; j < 7; ++j) {
+      int it = 0;
+      if (cell_record3(b, p, lam, u + nb[j] * us, q, fbar, trc + j * 6 * ts, j == 0 ? vol : tmpv,
+                       &it) != OB_OK)
+        status = OB_ERR_NOT_CONVERGED;
+    }
+    for (int k1 = 0; k1 < n; ++k1)
+      for (int k2 = 0; k2 < n; ++k2)
+        for (int k3 = 0; k3 < n; ++k3)
+          for (int r = 0; r < M3; ++r) {
+            const int kk[3] = {k1, k2, k3};
+            const int ta[3] = {k2, k1, k1}, tb[3] = {k3, k3, k2};
+            double val = vol[U3(k1, k2, k3, r)];
+            for (int d = 0; d < 3; ++d) {
+              double gl = 0.0, gh = 0.0;
+              for (int l0 = 0; l0 < n; ++l0) {
+                double H[M3];
+                const int64_t o = ((int64_t)(l0 * n + ta[d]) * n + tb[d]) * M3;
+                /* low face: high side of the low neighbour against this cell's low side */
+                ob3_rusanov(p->gamma, d, trc + ((1 + 2 * d) * 6 + d * 2 + 1) * ts + o,
+                            trc + (0 * 6 + d * 2 + 0) * ts + o, H);
+                gl += b->w[l0] * (lam[d] * H[r]);
+                ob3_rusanov(p->gamma, d, trc + (0 * 6 + d * 2 + 1) * ts + o,
+                            trc + ((2 + 2 * d) * 6 + d * 2 + 0) * ts + o, H);
+                gh += b->w[l0] * (lam[d] * H[r]);
+              }
+              val -= (b->psi1[kk[d]] * gh - b->psi0[kk[d]] * gl) / b->w[kk[d]];
+            }
+            out[s * us + U3(k1, k2, k3, r)] = val;
+          }
+  }
+  free(q), free(fbar), free(trc), free(vol), free(tmpv);
   return status;
 }
 

@@ -171,3 +171,17 @@ def test_sine_wave_orders_and_paper_magnitudes(oracle_mod, N, cells, lo, hi):
         assert (ratio > 0.8).all() and (ratio < 3.0).all(), (N, nc, e, table[(N, nc)])
     orders = np.log(np.array(errs[0]) / np.array(errs[1])) / np.log(cells[1] / cells[0])
     assert (orders > lo).all() and (orders < hi).all(), orders
+
+
+def test_step_cells_equals_the_full_step(oracle_mod):
+    N, nx, ny = 3, 5, 4
+    o = oracle_mod.Oracle2D(N)
+    X, Y = o.node_xy(nx, ny)
+    one = np.ones(X.shape)
+    u = conserved2(1 + 0.2 * np.sin(2 * np.pi * (X + 2 * Y)), 0.5 * one, -0.3 * one, one)
+    dt = o.dt(u, nx, ny, 0.2, 0.25)
+    full, rc, _ = o.step(u, nx, ny, 0.2, 0.25, dt)
+    cells = [0, 4, 7, 19]
+    sel, rc2 = o.step_cells(u, nx, ny, 0.2, 0.25, dt, cells)
+    assert rc == 0 and rc2 == 0
+    np.testing.assert_array_equal(sel, full.reshape(ny * nx, N + 1, N + 1, 4)[cells])

@@ -125,3 +125,17 @@ def test_constant_state_conservation_and_time_step(oracle_mod):
     tot = lambda V: np.einsum("zyxabcr,a,b,c->r", V.reshape(U.shape), wq, wq, wq)
     assert rc == 0
     np.testing.assert_allclose(tot(out), tot(U), rtol=1e-14, atol=1e-14)
+
+
+def test_step_cells_equals_the_full_step(oracle_mod):
+    N, dims, h = 2, (3, 4, 2), (1 / 3, 0.25, 0.5)
+    o = oracle_mod.Oracle3D(N)
+    X, Y, Z = o.node_xyz(*dims)
+    one = np.ones(X.shape)
+    u = conserved3(1 + 0.2 * np.sin(2 * np.pi * (X + Y - Z)), 0.4 * one, -0.2 * one, 0.1 * one, one)
+    dt = o.dt(u, dims, h)
+    full, rc, _ = o.step(u, dims, h, dt)
+    cells = [0, 5, 11, 23]
+    sel, rc2 = o.step_cells(u, dims, h, dt, cells)
+    assert rc == 0 and rc2 == 0
+    np.testing.assert_array_equal(sel, full.reshape(24, N + 1, N + 1, N + 1, 5)[cells])

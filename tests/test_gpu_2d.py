@@ -148,3 +148,30 @@ def test_degenerate_meshes(cuda, oracle_mod, nx, ny, N):
     ctx.ader_step(ud, out, dt)
     torch.cuda.synchronize()
     assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12
+
+
+def test_full_size_n5_320x320_sampled(cuda, oracle_mod):
+    """DG N = 5 on 320 x 320 cells (the size the 2D throughput line times), one
+    step with the time step taken on the device: the CFL step equals the
+    oracle's and sampled cells (the four corners, wrap-around edges, random
+    interior) equal the oracle's per-cell step."""
+    import torch
+    N, nc = 5, 320
+    o = oracle_mod.Oracle2D(N)
+    u = smooth_state(o, nc, nc, seed=21)
+    h = 1.0 / nc
+    ctx = make(nc, nc, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    dt_dev = ctx.ader_compute_dt(ud)
+    ctx.ader_step(ud, out, 0.0)  # CFL step on the device
+    torch.cuda.synchronize()
+    dt = o.dt(u, nc, nc, h, h)
+    assert abs(dt_dev - dt) <= 1e-14 * dt
+    last = nc * nc - 1
+    cells = np.unique(np.concatenate([[0, nc - 1, last - nc + 1, last, nc, 2 * nc - 1],
+                                      np.random.default_rng(2).integers(0, nc * nc, 40)]))
+    sel, rc = o.step_cells(u, nc, nc, h, h, dt, cells)
+    assert rc == 0
+    got = out.cpu().numpy().reshape(nc * nc, N + 1, N + 1, 4)[cells]
+    assert rel_linf(got, sel) < 1e-12

@@ -135,3 +135,32 @@ def test_degenerate_meshes(cuda, oracle_mod, dims, N):
     ctx.ader_step(ud, out, dt)
     torch.cuda.synchronize()
     assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("N,nc", [(3, 64), (6, 16)])
+def test_full_size_sampled(cuda, oracle_mod, N, nc):
+    """DG N = 3 on 64^3 and N = 6 on 16^3 cells (sizes the 3D throughput lines
+    time), one step with the time step taken on the device: the CFL step equals
+    the oracle's and sampled cells (corners, wrap-around faces, random interior)
+    equal the oracle's per-cell step."""
+    import torch
+    dims, box = (nc,) * 3, (1.0, 1.0, 1.0)
+    h = (1.0 / nc,) * 3
+    o = oracle_mod.Oracle3D(N)
+    u = smooth_state(o, dims, box, seed=N + nc)
+    ctx = make(dims, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    dt_dev = ctx.ader_compute_dt(ud)
+    ctx.ader_step(ud, out, 0.0)  # CFL step on the device
+    torch.cuda.synchronize()
+    dt = o.dt(u, dims, h)
+    assert abs(dt_dev - dt) <= 1e-14 * dt
+    total = nc ** 3
+    corners = [0, nc - 1, nc * (nc - 1), nc * nc - 1, total - nc * nc, total - 1]
+    cells = np.unique(np.concatenate([corners,
+                                      np.random.default_rng(3).integers(0, total, 24)]))
+    sel, rc = o.step_cells(u, dims, h, dt, cells)
+    assert rc == 0
+    got = out.cpu().numpy().reshape(total, N + 1, N + 1, N + 1, 5)[cells]
+    assert rel_linf(got, sel) < 1e-12

@@ -313,6 +313,52 @@ def cpu_oracle_rate(target_s: float = 12.0):
     return CELLS * steps / secs, steps, secs
 
 
+def _oracle_replica(steps, barrier, out):
+    """One process of the all-cores oracle timing: the oracle (one thread, as it
+    stands) advances its own copy of the 10^5-cell N = 5 mesh by `steps` steps;
+    every process starts its clock at the same barrier."""
+    import oracle
+    import workloads as W
+    o = oracle.Oracle(DEGREE)
+    u = W.nodal_state(W.modes4(SEED), o.node_x(CELLS))
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    _, done, _, rc = o.solve("dg", u, 1.0 / CELLS, max_steps=steps)
+    out.put((done, time.perf_counter() - t0, rc))
+
+
+def cpu_oracle_rate_all_cores(steps: int):
+    """The same oracle on every host core at once: one spawned process per core,
+    each on its own replica of the mesh (as OpenMP over independent cells would
+    spread them); returns (cell-updates/s over all processes, processes, steps
+    per process, slowest process's seconds)."""
+    import multiprocessing as mp
+    procs = (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+             else (os.cpu_count() or 1))
+    ctx = mp.get_context("spawn")  # a fork after CUDA initialisation can hang
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(steps, barrier, out)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    res = []
+    try:
+        while len(res) < procs:
+            try:
+                res.append(out.get(timeout=2.0))
+            except Exception:  # queue.Empty: give up once a process died without a result
+                if any(p.exitcode not in (None, 0) for p in ps):
+                    raise RuntimeError("an oracle replica process died")
+    finally:
+        for p in ps:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.kill()
+    if any(rc != 0 or done != steps for done, _, rc in res):
+        raise RuntimeError(f"oracle replica failed: {res}")
+    slowest = max(t for _, t, _ in res)
+    return procs * CELLS * steps / slowest, procs, steps, slowest
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -513,6 +559,14 @@ def main():
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"{steps} time steps of the same 10^5-cell N=5 mesh ({secs:.1f} s, 1 thread)"}
+            # the same oracle on all host cores: steps per process sized like the
+            # single-thread sample (about 12 s)
+            k_all = max(1, min(TIME_STEPS, int(round(steps * 12.0 / max(secs, 1e-3)))))
+            r_all, procs, k_all, s_all = cpu_oracle_rate_all_cores(k_all)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": r_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                "sample": f"{procs} processes, each {k_all} time steps of its own copy of the "
+                          f"10^5-cell N=5 mesh (slowest {s_all:.1f} s)"}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -410,7 +410,8 @@ def main():
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
-                         "step3d-dg2 (multi-D: warmup + steps time steps of one solve)")
+                         "step3d-dg2 (multi-D: warmup + steps time steps of one solve) | "
+                         "paper-costs (the sine wave at the meshes of the paper's cost tables)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -746,6 +747,45 @@ PAPER_3D_L1 = {(1, 10): 5.24e-2, (1, 15): 1.08e-2, (1, 20): 4.62e-3, (1, 25): 2.
                (6, 5): 5.24e-8, (6, 10): 4.36e-10, (6, 15): 2.59e-11, (6, 20): 3.49e-12}
 
 
+# Tables comp_costs_dg_2d / comp_costs_dg_3d (Sec. 3): T_JIT, whole-run CPU
+# seconds of the paper's fastest implementation (i9-10980XE, 4 OpenMP threads,
+# limiter admissibility checks every step) for the sine wave to t = 1 on 16^2 and
+# 7^3 cells, printed beside this library's GPU solve time for context only
+PAPER_2D_TJIT_16 = {1: 0.931, 2: 2.10, 3: 3.72, 4: 6.30, 5: 29.5, 6: 78.3, 7: 168.0}
+PAPER_3D_TJIT_7 = {1: 5.20, 2: 12.3, 3: 46.5, 4: 87.4, 5: 170.0, 6: 333.0}
+
+
+def paper_cost_rows(make_ctx, state_fn, table, cells_label, dev):
+    """The sine wave to t = 1 at the mesh of the paper's cost table, per degree:
+    the GPU solve time (state resident, CUDA events; after one untimed solve) and
+    the same solve through the host-buffer call (copies in and out included)."""
+    import numpy as np
+    import torch
+    rows = []
+    for N, t_paper in table.items():
+        ctx = make_ctx(N)
+        u_init = np.ascontiguousarray(state_fn(ctx).ravel())
+        u = torch.tensor(u_init, device=dev)
+        ctx.ader_solve(u, t_end=1.0)  # untimed: first-use setup
+        u = torch.tensor(u_init, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        steps, t, rc = ctx.ader_solve(u, t_end=1.0)
+        e1.record()
+        torch.cuda.synchronize()
+        host = u_init.copy()
+        h0 = time.perf_counter()
+        ctx.ader_solve_host(host, t_end=1.0)
+        h_s = time.perf_counter() - h0
+        s = e0.elapsed_time(e1) / 1e3
+        rows.append({"degree": N, "cells": cells_label, "steps": steps, "status": rc,
+                     "gpu_solve_s": s, "host_call_s": h_s, "paper_t_jit_s": t_paper,
+                     "paper_over_gpu": t_paper / s})
+        del ctx
+    return rows
+
 def sine3d_state(ctx):
     import numpy as np
     X, Y, Z = ctx.node_coords()
@@ -786,6 +826,8 @@ def run_3d(args, dev, flush):
             prev = (nc, err[0])
             out["sine_wave"].append(row)
             del ctx
+    out["paper_cost_table"] = paper_cost_rows(lambda N: Context3D(7, 7, 7, N, device=dev),
+                                              sine3d_state, PAPER_3D_TJIT_7, "7^3", dev)
     st_ = max(2, min(args.steps, 3))
     for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10), (5, 24, 10), (6, 16, 10)):
         ctx = Context3D(nc, nc, nc, N, device=dev, profile=1)
@@ -846,6 +888,8 @@ def run_2d(args, dev, flush):
             prev = (nc, err[0])
             out["sine_wave"].append(row)
             del ctx
+    out["paper_cost_table"] = paper_cost_rows(lambda N: Context2D(16, 16, N, device=dev),
+                                              sine2d_state, PAPER_2D_TJIT_16, "16x16", dev)
     st_ = max(2, min(args.steps, 3))
     for N, nc, ts in ((3, 512, 20), (5, 320, 20), (7, 160, 10)):
         ctx = Context2D(nc, nc, N, device=dev, profile=1)
@@ -1188,6 +1232,14 @@ def run_case(args):
         steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
+        return
+    elif args.case == "paper-costs":  # the cost-table comparison alone
+        from paper_2409_12483_gb300 import Context2D, Context3D
+        print(json.dumps({
+            "two_d": paper_cost_rows(lambda N: Context2D(16, 16, N, device=dev), sine2d_state,
+                                     PAPER_2D_TJIT_16, "16x16", dev),
+            "three_d": paper_cost_rows(lambda N: Context3D(7, 7, 7, N, device=dev), sine3d_state,
+                                       PAPER_3D_TJIT_7, "7^3", dev)}))
         return
     else:
         raise SystemExit(f"unknown case {args.case}")

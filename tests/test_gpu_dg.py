@@ -1,6 +1,6 @@
 """GPU parity of the ADER-DG path (C ABI through the thin binding) against the oracle.
 
-Bar (the benchmark spec): FP64 GPU path within 1e-12 relative L-infinity of the oracle
+Bar: FP64 GPU path within 1e-12 relative L-infinity of the oracle
 per step and 1e-10 at t_end; relative L-inf = max|gpu - oracle| / max|oracle|.
 Sizes span several predictor tiles (32 cells) and face tiles (64 cells) plus a
 ragged tail; the full-size case (N = 5, 10^5 cells) is checked on sampled cells

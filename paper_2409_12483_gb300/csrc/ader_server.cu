@@ -103,6 +103,11 @@ struct ader_server {
   cudaStream_t user_stream = nullptr;  // the caller's stream (may be the legacy default)
   cudaStream_t stream = nullptr;       // private non-blocking stream: all work and capture
   cudaEvent_t ev_fork = nullptr;
+  // one capture branch per degree: the solves of different degrees share no
+  // data, so their tick chains run side by side in the round's graph
+  cudaStream_t deg_stream[kMaxDeg + 1] = {};
+  cudaEvent_t ev_branch = nullptr;
+  cudaEvent_t ev_join[kMaxDeg + 1] = {};
   Basis basis[kMaxDeg + 1];
   bool have_basis[kMaxDeg + 1] = {};
   DevCtl* ctl_dev = nullptr;
@@ -270,28 +275,39 @@ ader_status rebuild(ader_server* srv) {
     srv->dirty = false;
     return ADER_OK;
   }
-  // one round: ticks_per_round ticks; each tick = batched predictors, then batched updates
+  // one round: ticks_per_round ticks; each tick = the batched predictor, then the
+  // batched update, of every degree present.  Each degree's chain of ticks is
+  // captured on its own stream (a branch of the graph), so a tick takes the time
+  // of the slowest degree rather than the sum over degrees.
   cudaGraph_t g;
   SCK(cudaStreamBeginCapture(srv->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = cudaSuccess;
+  cudaError_t ce = cudaEventRecord(srv->ev_branch, srv->stream);
   long long per_round = 0;
-  for (int j = 0; j < srv->opt.ticks_per_round && ce == cudaSuccess; ++j) {
-    for (int N = 0; N <= kMaxDeg && ce == cudaSuccess; ++N) {
-      const auto& L = srv->lists[N];
-      if (!L.pred_n) continue;
-      MultiArgs m{srv->desc_dev, srv->items_dev + L.pred_off, L.pred_n, j & 1};
-      const int grid = (int)std::min<long long>(L.pred_n, 152LL * 4);
-      ce = do_predict_multi(N, server_predict_params(srv, N), m, grid, srv->stream);
+  for (int N = 0; N <= kMaxDeg; ++N) {
+    const auto& L = srv->lists[N];
+    if (!L.pred_n) continue;
+    cudaStream_t bs = srv->deg_stream[N];
+    // fork and join even after an error, so that the capture ends with every
+    // branch joined
+    cudaError_t fe = cudaStreamWaitEvent(bs, srv->ev_branch, 0);
+    if (fe != cudaSuccess) {
+      if (ce == cudaSuccess) ce = fe;
+      continue;  // this stream did not join the capture
+    }
+    for (int j = 0; j < srv->opt.ticks_per_round && ce == cudaSuccess; ++j) {
+      MultiArgs mp{srv->desc_dev, srv->items_dev + L.pred_off, L.pred_n, j & 1};
+      const int gp = (int)std::min<long long>(L.pred_n, 152LL * 4);
+      ce = do_predict_multi(N, server_predict_params(srv, N), mp, gp, bs);
+      ++per_round;
+      if (ce != cudaSuccess) break;
+      MultiArgs mf{srv->desc_dev, srv->items_dev + L.face_off, L.face_n, j & 1};
+      const int gf = (int)std::min<long long>(L.face_n, 152LL * 8);
+      ce = do_face_multi(N, server_face_params(srv, N), mf, gf, bs);
       ++per_round;
     }
-    for (int N = 0; N <= kMaxDeg && ce == cudaSuccess; ++N) {
-      const auto& L = srv->lists[N];
-      if (!L.face_n) continue;
-      MultiArgs m{srv->desc_dev, srv->items_dev + L.face_off, L.face_n, j & 1};
-      const int grid = (int)std::min<long long>(L.face_n, 152LL * 8);
-      ce = do_face_multi(N, server_face_params(srv, N), m, grid, srv->stream);
-      ++per_round;
-    }
+    cudaError_t je = cudaEventRecord(srv->ev_join[N], bs);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(srv->stream, srv->ev_join[N], 0);
+    if (ce == cudaSuccess) ce = je;
   }
   cudaError_t ee = cudaStreamEndCapture(srv->stream, &g);
   if (ce != cudaSuccess) {
@@ -308,6 +324,26 @@ ader_status rebuild(ader_server* srv) {
   srv->graph_launches_per_round = per_round;
   srv->dirty = false;
   return ADER_OK;
+}
+
+// destroys the server's graph, pinned mirror, streams and events (any subset
+// that exists)
+void release_cuda(ader_server* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  if (s->ctl_host) cudaFreeHost(s->ctl_host);
+  s->ctl_host = nullptr;
+  for (int N = 0; N <= kMaxDeg; ++N) {
+    if (s->deg_stream[N]) cudaStreamDestroy(s->deg_stream[N]);
+    if (s->ev_join[N]) cudaEventDestroy(s->ev_join[N]);
+    s->deg_stream[N] = nullptr;
+    s->ev_join[N] = nullptr;
+  }
+  if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_branch) cudaEventDestroy(s->ev_branch);
+  s->stream = nullptr;
+  s->ev_fork = s->ev_branch = nullptr;
 }
 
 }  // namespace
@@ -349,11 +385,20 @@ ader_status ader_server_create(const ader_server_opts* opt, ader_server** out) {
   if (!(s->opt.picard_tol > 0.0)) s->opt.picard_tol = 1e-13;
   s->pool = static_cast<char*>(opt->pool_dev);
   s->user_stream = static_cast<cudaStream_t>(opt->stream);
-  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
-    if (s->stream) cudaStreamDestroy(s->stream);
-    return ADER_ERR_CUDA;
-  }
+  // the server's CUDA objects are released by release_cuda on every exit path
+  struct Guard {
+    ader_server* s;
+    ~Guard() {
+      if (s) release_cuda(s);
+    }
+  } guard{s.get()};
+  bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->ev_branch, cudaEventDisableTiming) == cudaSuccess;
+  for (int N = 0; ok && N <= kMaxDeg; ++N)
+    ok = cudaStreamCreateWithFlags(&s->deg_stream[N], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_join[N], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) return ADER_ERR_CUDA;
   const size_t ctl_bytes = al((size_t)opt->max_slots * sizeof(DevCtl));
   const size_t desc_bytes = al((size_t)opt->max_slots * sizeof(SlotDesc));
   s->items_cap = std::max<size_t>(4096, opt->pool_bytes / 2048);
@@ -367,21 +412,18 @@ ader_status ader_server_create(const ader_server_opts* opt, ader_server** out) {
   s->slots.assign(opt->max_slots, Slot{});
   s->desc_host.assign(opt->max_slots, SlotDesc{});
   if (cudaMallocHost(&s->ctl_host, (size_t)opt->max_slots * sizeof(DevCtl)) != cudaSuccess) {
-    cudaStreamDestroy(s->stream);
-    cudaEventDestroy(s->ev_fork);
+    s->ctl_host = nullptr;
     return ADER_ERR_CUDA;
   }
   std::memset(s->ctl_host, 0, (size_t)opt->max_slots * sizeof(DevCtl));
+  guard.s = nullptr;
   *out = s.release();
   return ADER_OK;
 }
 
 void ader_server_destroy(ader_server* s) {
   if (!s) return;
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  if (s->ctl_host) cudaFreeHost(s->ctl_host);
-  if (s->stream) cudaStreamDestroy(s->stream);
-  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  release_cuda(s);
   delete s;
 }
 

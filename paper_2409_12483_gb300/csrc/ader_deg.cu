@@ -174,10 +174,11 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_nc_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_nc_cpb<32>()) != cudaSuccess) return e;
   for (int prec = 0; prec < 3; ++prec) {
-    auto k = prec == 0 ? predict_multi_kernel<D, 0>
-                       : (prec == 1 ? predict_multi_kernel<D, 1> : predict_multi_kernel<D, 2>);
+    constexpr int T = server_pred_cells(D);
+    auto k = prec == 0 ? predict_multi_kernel<D, 0, T>
+                       : (prec == 1 ? predict_multi_kernel<D, 1, T> : predict_multi_kernel<D, 2, T>);
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)PredCfg<D>::kSmemBytes);
+                             (int)PredCfg<D, T>::kSmemBytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -280,22 +281,23 @@ cudaError_t ADER_CAT(launch_face_update_, ADER_DEG)(const FaceParams& p, cudaStr
 
 cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, const MultiArgs& m,
                                                        int grid, cudaStream_t s) {
-  using C = PredCfg<D>;
+  constexpr int T = server_pred_cells(D);
+  using C = PredCfg<D, T>;
   if (grid <= 0) return cudaErrorInvalidValue;
   if (p.prec == 1)
-    predict_multi_kernel<D, 1><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+    predict_multi_kernel<D, 1, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else if (p.prec == 2)
-    predict_multi_kernel<D, 2><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+    predict_multi_kernel<D, 2, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else
-    predict_multi_kernel<D, 0><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+    predict_multi_kernel<D, 0, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   return cudaGetLastError();
 }
 
 cudaError_t ADER_CAT(launch_face_multi_, ADER_DEG)(const FaceParams& p, const MultiArgs& m, int grid,
                                                     cudaStream_t s) {
-  using C = FaceCfg<D>;
+  using C = FaceCfg<D, kServerFaceCells>;
   if (grid <= 0) return cudaErrorInvalidValue;
-  face_update_multi_kernel<D><<<(unsigned)grid, C::THREADS, 0, s>>>(p, m);
+  face_update_multi_kernel<D, kServerFaceCells><<<(unsigned)grid, C::THREADS, 0, s>>>(p, m);
   return cudaGetLastError();
 }
 

@@ -753,8 +753,8 @@ __global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
 
 // Batched predictor: one launch per degree over the tiles of many independent
 // solves (continuous batching).  Every solve keeps its own device time step.
-template <int N, int PREC>
-__global__ void __launch_bounds__(PredCfg<N>::THREADS)
+template <int N, int PREC, int CPB = 32>
+__global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
     predict_multi_kernel(const __grid_constant__ PredictParams P, const MultiArgs M) {
   extern __shared__ __align__(16) double smem[];
   __shared__ PredShared<N> sh;
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(PredCfg<N>::THREADS)
     double dt;
     if (!block_step_dt<N>(sp, &dt, item.tile == 0, sh)) continue;  // uniform
     const TileIO io{d.u[par], d.trace, nullptr, nullptr, d.ncells, sp.ctl};
-    predict_tile<N, PREC>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
+    predict_tile<N, PREC, CPB>(P, io, item.tile, dt * sp.inv_dx, smem, sh);
   }
 }
 
@@ -987,11 +987,11 @@ __global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
 }
 
 // Batched interface flux + update over the tiles of many solves (see predict_multi_kernel).
-template <int N>
-__global__ void __launch_bounds__(FaceCfg<N>::THREADS)
+template <int N, int C = 64>
+__global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
     face_update_multi_kernel(const __grid_constant__ FaceParams P, const MultiArgs M) {
-  __shared__ FaceShared<N> sh;
-  face_stage_tables<N>(P, sh);
+  __shared__ FaceShared<N, C> sh;
+  face_stage_tables<N, C>(P, sh);
   for (long long it = blockIdx.x; it < M.nitems; it += gridDim.x) {
     const TileItem item = M.items[it];
     const SlotDesc& d = M.slots[item.slot];
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(FaceCfg<N>::THREADS)
     int last;
     if (!corrector_step_dt(sp, &dt, &last)) continue;  // uniform over the block
     const FaceIO io{d.trace, d.u[par], const_cast<double*>(d.u[par ^ 1]), d.ncells};
-    face_tile<N>(P, io, sp, item.tile, dt, sh);
+    face_tile<N, C>(P, io, sp, item.tile, dt, sh);
     corrector_finish(sp, dt, last, item.tile == 0 && threadIdx.x == 0);
   }
 }

@@ -82,8 +82,15 @@ struct SlotDesc {
 
 struct TileItem {
   int slot;
-  int tile;             // 32-cell predictor tile or 64-cell face tile index within the solve
+  int tile;  // predictor or face tile index within the solve (tile sizes below)
 };
+
+// Tile sizes of the batched (server) kernels: 16-cell predictor tiles (32 for
+// N = 0, whose 16-cell tile would be half a warp) and 32-cell face tiles, so a
+// lone large solve spreads over twice as many SMs as with the single-solve
+// kernels' default tiles.
+constexpr int server_pred_cells(int N) { return N == 0 ? 32 : 16; }
+constexpr int kServerFaceCells = 32;
 
 struct MultiArgs {
   const SlotDesc* slots;

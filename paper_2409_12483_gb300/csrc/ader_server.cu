@@ -247,14 +247,16 @@ ader_status rebuild(ader_server* srv) {
     for (size_t s = 0; s < srv->slots.size(); ++s) {
       const Req* r = srv->slots[s].req;
       if (!r || r->degree != N) continue;
-      for (long long t = 0; t < (r->ncells + 31) / 32; ++t) items.push_back({(int)s, (int)t});
+      const long long T = server_pred_cells(N);
+      for (long long t = 0; t < (r->ncells + T - 1) / T; ++t) items.push_back({(int)s, (int)t});
     }
     L.pred_n = (long long)items.size() - L.pred_off;
     L.face_off = (long long)items.size();
     for (size_t s = 0; s < srv->slots.size(); ++s) {
       const Req* r = srv->slots[s].req;
       if (!r || r->degree != N) continue;
-      for (long long t = 0; t < (r->ncells + 63) / 64; ++t) items.push_back({(int)s, (int)t});
+      const long long T = kServerFaceCells;
+      for (long long t = 0; t < (r->ncells + T - 1) / T; ++t) items.push_back({(int)s, (int)t});
     }
     L.face_n = (long long)items.size() - L.face_off;
   }
@@ -401,7 +403,8 @@ ader_status ader_server_create(const ader_server_opts* opt, ader_server** out) {
   if (!ok) return ADER_ERR_CUDA;
   const size_t ctl_bytes = al((size_t)opt->max_slots * sizeof(DevCtl));
   const size_t desc_bytes = al((size_t)opt->max_slots * sizeof(SlotDesc));
-  s->items_cap = std::max<size_t>(4096, opt->pool_bytes / 2048);
+  // at most 1/16 + 1/32 tiles per cell and >= 120 pool bytes per cell
+  s->items_cap = std::max<size_t>(4096, opt->pool_bytes / 1024);
   const size_t item_bytes = al(s->items_cap * sizeof(TileItem));
   if (opt->pool_bytes < ctl_bytes + desc_bytes + item_bytes + kAl) return ADER_ERR_NOMEM;
   s->ctl_dev = reinterpret_cast<DevCtl*>(s->pool);

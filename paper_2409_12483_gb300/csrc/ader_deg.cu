@@ -27,6 +27,28 @@ unsigned grid_for(long long items, int threads, long long cap) {
   return (unsigned)b;
 }
 
+// Block size of the flat (one thread per item) multi-D kernels: 64 threads
+// while the items would fill fewer than four 256-thread blocks per SM, so a
+// small mesh still spreads over many SMs; 256 otherwise.
+int flat_threads(long long items) { return items >= 152LL * 4 * 256 ? 256 : 64; }
+
+// The large block shape of a per-cell multi-D kernel while it gives at least
+// two blocks per SM, else the small one (the same shape when they coincide).
+bool use_big_blocks(long long ncells, int big_cpb) { return ncells >= 152LL * 2 * big_cpb; }
+
+template <int T>
+cudaError_t launch_predict2d_shape(const Predict2DParams& p, cudaStream_t s) {
+  using C = Pred2Cfg<D, T>;
+  predict2d_kernel<D, T><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int T>
+void launch_update2d_shape(const Face2DParams& p, cudaStream_t s) {
+  using U = Upd2Cfg<D, T>;
+  update2d_kernel<D, T><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, 0, s>>>(p);
+}
+
 // The helpers below are instantiated in every per-degree translation unit with
 // different bodies (they depend on ADER_DEG), so they must have internal linkage.
 template <int CPB>
@@ -162,8 +184,11 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   if ((e = prepare_src_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_src_cpb<32>()) != cudaSuccess) return e;
   if constexpr (D <= kMax3DDeg) {  // 3D kernels with more than 48 KB of shared memory
-    if ((e = cudaFuncSetAttribute(update3d_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)Upd3Cfg<D>::kSmemBytes)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(update3d_kernel<D, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Upd3Cfg<D, 128>::kSmemBytes)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(update3d_kernel<D, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Upd3Cfg<D, 64>::kSmemBytes)) != cudaSuccess)
       return e;
   }
   if constexpr (D > kMax3DLowDeg && D <= kMax3DDeg) {
@@ -210,31 +235,43 @@ cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t
 }
 
 cudaError_t ADER_CAT(launch_predict2d_, ADER_DEG)(const Predict2DParams& p, cudaStream_t s) {
-  using C = Pred2Cfg<D>;
-  predict2d_kernel<D><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
-  return cudaGetLastError();
+  if constexpr (Pred2Cfg<D, 256>::CPB != Pred2Cfg<D, 64>::CPB) {
+    if (!use_big_blocks(p.ncells, Pred2Cfg<D, 256>::CPB)) return launch_predict2d_shape<64>(p, s);
+  }
+  return launch_predict2d_shape<256>(p, s);
 }
 
 // the face fluxes, then the update (which ends the step on the device)
 cudaError_t ADER_CAT(launch_face2d_, ADER_DEG)(const Face2DParams& p, cudaStream_t s) {
   constexpr int n = D + 1;
-  face2d_kernel<D><<<grid_for(p.ncells * 2 * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
-  using U = Upd2Cfg<D>;
-  update2d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, 0, s>>>(p);
+  const long long items = p.ncells * 2 * n;
+  const int tpb = flat_threads(items);
+  face2d_kernel<D><<<grid_for(items, tpb, 0x7fffffffLL), tpb, 0, s>>>(p);
+  if (Upd2Cfg<D, 256>::CPB != Upd2Cfg<D, 128>::CPB &&
+      !use_big_blocks(p.ncells, Upd2Cfg<D, 256>::CPB))
+    launch_update2d_shape<128>(p, s);
+  else
+    launch_update2d_shape<256>(p, s);
   return cudaGetLastError();
 }
 
 cudaError_t ADER_CAT(launch_cfl2d_, ADER_DEG)(const Cfl2DParams& p, cudaStream_t s) {
   constexpr int Ns = 2 * D + 1;
-  cfl2d_kernel<D><<<grid_for(p.ncells * Ns * Ns, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+  const long long items = p.ncells * Ns * Ns;
+  const int tpb = flat_threads(items);
+  cfl2d_kernel<D><<<grid_for(items, tpb, 0x7fffffffLL), tpb, 0, s>>>(p);
   return cudaGetLastError();
 }
 
 // 3D: degrees 0..4 (one thread per space-time node); other degrees are refused
 cudaError_t ADER_CAT(launch_predict3d_, ADER_DEG)(const Predict3DParams& p, cudaStream_t s) {
   if constexpr (D <= kMax3DLowDeg) {
-    using C = Pred3Cfg<D>;
-    predict3d_kernel<D><<<grid_for(p.ncells, C::CPB, 0x7fffffffLL), C::THREADS, 0, s>>>(p);
+    using B = Pred3Cfg<D, 256>;
+    using S = Pred3Cfg<D, 64>;
+    if (B::CPB != S::CPB && !use_big_blocks(p.ncells, B::CPB))
+      predict3d_kernel<D, 64><<<grid_for(p.ncells, S::CPB, 0x7fffffffLL), S::THREADS, 0, s>>>(p);
+    else
+      predict3d_kernel<D, 256><<<grid_for(p.ncells, B::CPB, 0x7fffffffLL), B::THREADS, 0, s>>>(p);
     return cudaGetLastError();
   } else if constexpr (D <= kMax3DDeg) {
     using C = Pred3HiCfg<D>;
@@ -249,9 +286,15 @@ cudaError_t ADER_CAT(launch_predict3d_, ADER_DEG)(const Predict3DParams& p, cuda
 cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream_t s) {
   if constexpr (D <= kMax3DDeg) {
     constexpr int n = D + 1;
-    face3d_kernel<D><<<grid_for(p.ncells * 3 * n * n, 256, 0x7fffffffLL), 256, 0, s>>>(p);
-    using U = Upd3Cfg<D>;
-    update3d_kernel<D><<<grid_for(p.ncells, U::CPB, 0x7fffffffLL), U::THREADS, U::kSmemBytes, s>>>(p);
+    const long long items = p.ncells * 3 * n * n;
+    const int tpb = flat_threads(items);
+    face3d_kernel<D><<<grid_for(items, tpb, 0x7fffffffLL), tpb, 0, s>>>(p);
+    using B = Upd3Cfg<D, 128>;
+    using S = Upd3Cfg<D, 64>;
+    if (B::CPB != S::CPB && !use_big_blocks(p.ncells, B::CPB))
+      update3d_kernel<D, 64><<<grid_for(p.ncells, S::CPB, 0x7fffffffLL), S::THREADS, S::kSmemBytes, s>>>(p);
+    else
+      update3d_kernel<D, 128><<<grid_for(p.ncells, B::CPB, 0x7fffffffLL), B::THREADS, B::kSmemBytes, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;
@@ -261,7 +304,9 @@ cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream
 cudaError_t ADER_CAT(launch_cfl3d_, ADER_DEG)(const Cfl3DParams& p, cudaStream_t s) {
   if constexpr (D <= kMax3DDeg) {
     constexpr int Ns = 2 * D + 1;
-    cfl3d_kernel<D><<<grid_for(p.ncells * Ns * Ns * Ns, 256, 0x7fffffffLL), 256, 0, s>>>(p);
+    const long long items = p.ncells * Ns * Ns * Ns;
+    const int tpb = flat_threads(items);
+    cfl3d_kernel<D><<<grid_for(items, tpb, 0x7fffffffLL), tpb, 0, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;

@@ -65,17 +65,21 @@ __device__ __forceinline__ void rusanov2_2d(const double* a, const double* b, do
   H2[3] = fma(-s, b[3] - a[3], fma(a[3] + pa, wa, (b[3] + pb) * wb));
 }
 
-template <int N>
+// T: target threads per block.  The launcher takes T = 256 when the mesh fills
+// at least two blocks per SM and T = 64 below that, so that a small mesh still
+// spreads over many SMs (GB300 issues 2 FP64 lanes per SM per clock, so the
+// cells per SM set a small mesh's step time).
+template <int N, int T = 256>
 struct Pred2Cfg {
   static constexpr int n = N + 1, NN = n * n, NST = n * n * n;
-  static constexpr int CPB = NST >= 128 ? 1 : 256 / NST;  // cells per block
+  static constexpr int CPB = NST >= T / 2 ? 1 : T / NST;  // cells per block
   static constexpr int THREADS = CPB * NST;
   static constexpr int REC = 5 * NN * kM2;  // trace record doubles per cell
 };
 
-template <int N>
+template <int N, int T>
 struct Pred2Shared {
-  using C = Pred2Cfg<N>;
+  using C = Pred2Cfg<N, T>;
   double A[C::CPB][C::NST][kM2];  // x-fluxes, then the contraction, then q
   double B[C::CPB][C::NST][kM2];  // y-fluxes
   double FB[C::CPB][2][C::NN][kM2];  // time averages of the rescaled fluxes
@@ -85,12 +89,12 @@ struct Pred2Shared {
   int go;
 };
 
-template <int N>
-__global__ void __launch_bounds__(Pred2Cfg<N>::THREADS)
+template <int N, int T = 256>
+__global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
     predict2d_kernel(const __grid_constant__ Predict2DParams P) {
-  using C = Pred2Cfg<N>;
+  using C = Pred2Cfg<N, T>;
   constexpr int n = N + 1, NN = C::NN, NST = C::NST, CPB = C::CPB;
-  __shared__ Pred2Shared<N> sh;
+  __shared__ Pred2Shared<N, T> sh;
   const int tid = threadIdx.x;
   if (tid == 0) {
     double d = 0.0;
@@ -284,10 +288,10 @@ __global__ void __launch_bounds__(256) face2d_kernel(const __grid_constant__ Fac
   for (int r = 0; r < kM2; ++r) P.gface[item * kM2 + r] = h * s[r];
 }
 
-template <int N>
+template <int N, int T = 256>  // T: target threads per block (256, or 128 for small meshes)
 struct Upd2Cfg {
   static constexpr int n = N + 1, NN = n * n, Ns = 2 * N + 1;
-  static constexpr int CPB = NN >= 256 ? 1 : 256 / NN;  // cells per block
+  static constexpr int CPB = NN >= T ? 1 : T / NN;  // cells per block
   static constexpr int USED = CPB * NN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
 };
@@ -298,10 +302,10 @@ struct Upd2Cfg {
 // block projects its cells' new states onto the Ns x Ns subcells one direction
 // at a time through shared memory and reduces max(lambda_x / dx, lambda_y / dy)
 // into ctl->lam[par ^ 1] (FP64, the time step of Sec. 1.5 with d = 2).
-template <int N>
-__global__ void __launch_bounds__(Upd2Cfg<N>::THREADS)
+template <int N, int TB = 256>
+__global__ void __launch_bounds__(Upd2Cfg<N, TB>::THREADS)
     update2d_kernel(const __grid_constant__ Face2DParams P) {
-  using C = Upd2Cfg<N>;
+  using C = Upd2Cfg<N, TB>;
   constexpr int n = N + 1, NN = n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred2Cfg<N>::REC;
   __shared__ double U[CPB][NN][kM2];
   __shared__ double T[CPB][n][Ns][kM2];  // projected along eta: [k1][j2]

@@ -77,17 +77,18 @@ __device__ __forceinline__ void rusanov2_3d(const double* a, const double* b, do
   H2[4] = fma(-s, b[4] - a[4], fma(a[4] + pa, va[D], (b[4] + pb) * vb[D]));
 }
 
-template <int N>
+// T: target threads per block, 256 or (small meshes) 64, as for Pred2Cfg
+template <int N, int T = 256>
 struct Pred3Cfg {
   static constexpr int n = N + 1, NNN = n * n * n, NST = n * n * n * n;
-  static constexpr int CPB = NST >= 128 ? 1 : 256 / NST;  // cells per block
+  static constexpr int CPB = NST >= T / 2 ? 1 : T / NST;  // cells per block
   static constexpr int THREADS = CPB * NST;
   static constexpr int REC = 7 * NNN * kM3;  // six face traces + volume term
 };
 
-template <int N>
+template <int N, int T>
 struct Pred3Shared {
-  using C = Pred3Cfg<N>;
+  using C = Pred3Cfg<N, T>;
   double S[C::CPB][C::NST][kM3];        // one flux direction at a time, then the sum, then q
   double FB[C::CPB][3][C::NNN][kM3];    // time averages of the three rescaled fluxes
   unsigned long long red[C::CPB][2];
@@ -96,12 +97,12 @@ struct Pred3Shared {
   int go;
 };
 
-template <int N>
-__global__ void __launch_bounds__(Pred3Cfg<N>::THREADS)
+template <int N, int T = 256>
+__global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
     predict3d_kernel(const __grid_constant__ Predict3DParams P) {
-  using C = Pred3Cfg<N>;
+  using C = Pred3Cfg<N, T>;
   constexpr int n = N + 1, NNN = C::NNN, NST = C::NST, CPB = C::CPB;
-  __shared__ Pred3Shared<N> sh;
+  __shared__ Pred3Shared<N, T> sh;
   const int tid = threadIdx.x;
   if (tid == 0) {
     double d = 0.0;
@@ -494,10 +495,10 @@ __global__ void __launch_bounds__(256) face3d_kernel(const __grid_constant__ Fac
   for (int r = 0; r < kM3; ++r) P.gface[item * kM3 + r] = h * s[r];
 }
 
-template <int N>
+template <int N, int T = 128>  // T: target threads per block (128, or 64 for small meshes)
 struct Upd3Cfg {
   static constexpr int n = N + 1, NNN = n * n * n, Ns = 2 * N + 1;
-  static constexpr int CPB = NNN >= 128 ? 1 : 128 / NNN;  // cells per block
+  static constexpr int CPB = NNN >= T ? 1 : T / NNN;  // cells per block
   static constexpr int USED = CPB * NNN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
   // dynamic shared memory: U [CPB][NNN][5], T1 [CPB][n n][Ns][5], T2 [CPB][n][Ns Ns][5]
@@ -509,10 +510,10 @@ struct Upd3Cfg {
 // thread per (cell, node), CPB cells per block; then (want_lambda) the block
 // projects its cells' new states onto the Ns^3 subcells one direction at a time
 // through shared memory and reduces max_d lambda_d / h_d into ctl->lam[par ^ 1].
-template <int N>
-__global__ void __launch_bounds__(Upd3Cfg<N>::THREADS)
+template <int N, int TB = 128>
+__global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
     update3d_kernel(const __grid_constant__ Face3DParams P) {
-  using C = Upd3Cfg<N>;
+  using C = Upd3Cfg<N, TB>;
   constexpr int n = N + 1, NNN = n * n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred3Cfg<N>::REC;
   extern __shared__ __align__(16) double dsm[];
   auto U = reinterpret_cast<double(*)[NNN][kM3]>(dsm);

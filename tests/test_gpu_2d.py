@@ -175,3 +175,28 @@ def test_full_size_n5_320x320_sampled(cuda, oracle_mod):
     assert rc == 0
     got = out.cpu().numpy().reshape(nc * nc, N + 1, N + 1, 4)[cells]
     assert rel_linf(got, sel) < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_large_block_shapes_sampled(cuda, oracle_mod, N):
+    """100 x 100 cells: enough for the launchers to take the large block shapes of
+    the predictor and the update (the ragged meshes above take the small ones);
+    one device-CFL step checked on sampled cells against the oracle's per-cell
+    step."""
+    import torch
+    nc = 100
+    o = oracle_mod.Oracle2D(N)
+    u = smooth_state(o, nc, nc, seed=40 + N)
+    h = 1.0 / nc
+    ctx = make(nc, nc, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, 0.0)
+    torch.cuda.synchronize()
+    dt = o.dt(u, nc, nc, h, h)
+    cells = np.unique(np.concatenate([[0, nc - 1, nc * nc - nc, nc * nc - 1],
+                                      np.random.default_rng(N).integers(0, nc * nc, 40)]))
+    sel, rc = o.step_cells(u, nc, nc, h, h, dt, cells)
+    assert rc == 0
+    got = out.cpu().numpy().reshape(nc * nc, N + 1, N + 1, 4)[cells]
+    assert rel_linf(got, sel) < 1e-12

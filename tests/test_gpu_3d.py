@@ -164,3 +164,28 @@ def test_full_size_sampled(cuda, oracle_mod, N, nc):
     assert rc == 0
     got = out.cpu().numpy().reshape(total, N + 1, N + 1, N + 1, 5)[cells]
     assert rel_linf(got, sel) < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_large_block_shapes_sampled(cuda, oracle_mod, N):
+    """18^3 cells: enough for the launchers to take the large block shapes of the
+    predictor and the update (the ragged meshes above take the small ones); one
+    device-CFL step checked on sampled cells against the oracle's per-cell step."""
+    import torch
+    nc = 18
+    dims, box, h = (nc,) * 3, (1.0, 1.0, 1.0), (1.0 / nc,) * 3
+    o = oracle_mod.Oracle3D(N)
+    u = smooth_state(o, dims, box, seed=50 + N)
+    ctx = make(dims, N)
+    ud = to_dev(u)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, 0.0)
+    torch.cuda.synchronize()
+    dt = o.dt(u, dims, h)
+    total = nc ** 3
+    cells = np.unique(np.concatenate([[0, total - 1, nc * nc - 1, total - nc * nc],
+                                      np.random.default_rng(N).integers(0, total, 24)]))
+    sel, rc = o.step_cells(u, dims, h, dt, cells)
+    assert rc == 0
+    got = out.cpu().numpy().reshape(total, N + 1, N + 1, N + 1, 5)[cells]
+    assert rel_linf(got, sel) < 1e-12

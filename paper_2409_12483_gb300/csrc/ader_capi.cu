@@ -450,8 +450,8 @@ ader_status status_from_flags(ader_ctx* ctx, int st) {
 
 bool valid_cpb(int N, int cpb) {
   const int threads = cpb * (N + 1);
-  return (cpb == 16 || cpb == 32 || cpb == 64) && threads % 32 == 0 && threads <= 512 &&
-         (N <= 5 || cpb <= 32);
+  return (cpb == 16 || cpb == 32 || cpb == 64) && (threads % 32 == 0 || cpb == 16) &&
+         threads <= 512 && (N <= 5 || cpb <= 32);
 }
 
 int graph_steps_for(int64_t ncells) {
@@ -516,6 +516,10 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   c->n = degree + 1;
   c->scheme = scheme;
   c->dx = (mesh->x1 - mesh->x0) / (double)mesh->n_cells;
+  // default tiles: half-size below two blocks per SM, so that a small mesh
+  // spreads over more SMs (autotuning or ader_set_tuning replaces them)
+  if (mesh->n_cells < 152LL * 2 * 32) c->tune.predict_cells_per_block = 16;
+  if (mesh->n_cells < 152LL * 2 * 64) c->tune.face_cells_per_block = 32;
   if (opt) {
     c->opt = *opt;
   } else {

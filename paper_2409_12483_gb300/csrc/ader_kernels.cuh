@@ -33,8 +33,9 @@
 namespace ader {
 
 // Predictor tile: CPB cells x n tau nodes = blockDim threads.  CPB is a tuning
-// choice (16, 32 or 64 cells); the autotuner only picks shapes whose blockDim is
-// a multiple of 32 (no idle lanes) and whose registers fit.
+// choice (16, 32 or 64 cells) among shapes whose registers fit; a 16-cell tile
+// of an even degree ends in a partial warp, which small meshes (the default
+// below ~10^4 cells) accept for twice as many blocks.
 template <int N, int CPB_ = 32>
 struct PredCfg {
   static constexpr int n = N + 1;
@@ -42,7 +43,8 @@ struct PredCfg {
   static constexpr int THREADS = CPB * n;
   // exchange rows [CPB][n][n][3], fbar [CPB][n][3], initial data [CPB][n][3]
   static constexpr size_t kSmemBytes = (size_t)CPB * kM * n * (n + 2) * sizeof(double);
-  static constexpr bool kValid = (THREADS % 32 == 0) && THREADS <= 512 && (N <= 5 || CPB <= 32);
+  static constexpr bool kValid =
+      (THREADS % 32 == 0 || CPB == 16) && THREADS <= 512 && (N <= 5 || CPB <= 32);
 };
 constexpr int kMaxCpb = 64;
 

@@ -147,8 +147,22 @@ def test_tuning_validation_without_gpu(lib):
                          C.byref(ctx)) == 0
     t = Tuning()
     assert lib.ader_get_tuning(ctx, C.byref(t)) == 0
-    assert (t.predict_cells_per_block, t.face_cells_per_block) == (32, 64)
+    # a small mesh defaults to half-size tiles, a large one to 32 / 64 cells
+    assert (t.predict_cells_per_block, t.face_cells_per_block) == (16, 32)
     assert t.graph_steps >= 2 and t.graph_steps % 2 == 0
+    big = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(100_000, 0.0, 1.0)), 2, 0, C.byref(default_options()),
+                         C.byref(big)) == 0
+    assert lib.ader_get_tuning(big, C.byref(t)) == 0
+    assert (t.predict_cells_per_block, t.face_cells_per_block) == (32, 64)
+    lib.ader_destroy(big)
+    # 16-cell tiles are accepted at every degree (a partial last warp for even N)
+    even = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(100, 0.0, 1.0)), 2, 0, C.byref(default_options()),
+                         C.byref(even)) == 0
+    assert lib.ader_set_tuning(even, C.byref(Tuning(16, 64, 8, 0.0, 0.0, 0.0))) == 0
+    assert lib.ader_set_tuning(even, C.byref(Tuning(64, 64, 8, 0.0, 0.0, 0.0))) == 0
+    lib.ader_destroy(even)
     for cpb, cpf, k in [(64, 64, 8), (8, 64, 8), (32, 48, 8), (32, 64, 7), (32, 64, 0)]:
         bad = Tuning(cpb, cpf, k, 0.0, 0.0, 0.0)  # 64 cells x 8 nodes is too big at N = 7
         assert lib.ader_set_tuning(ctx, C.byref(bad)) == 1

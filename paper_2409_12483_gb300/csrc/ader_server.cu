@@ -268,12 +268,10 @@ ader_status rebuild(ader_server* srv) {
                         cudaMemcpyHostToDevice, srv->stream));
   SCK(cudaMemcpyAsync(srv->desc_dev, srv->desc_host.data(), srv->desc_host.size() * sizeof(SlotDesc),
                       cudaMemcpyHostToDevice, srv->stream));
-  if (srv->gexec) {
-    cudaGraphExecDestroy(srv->gexec);
-    srv->gexec = nullptr;
-  }
   srv->graph_launches_per_round = 0;
   if (items.empty()) {
+    if (srv->gexec) cudaGraphExecDestroy(srv->gexec);
+    srv->gexec = nullptr;
     srv->dirty = false;
     return ADER_OK;
   }
@@ -312,14 +310,27 @@ ader_status rebuild(ader_server* srv) {
     if (ce == cudaSuccess) ce = je;
   }
   cudaError_t ee = cudaStreamEndCapture(srv->stream, &g);
-  if (ce != cudaSuccess) {
+  if (ce != cudaSuccess || ee != cudaSuccess) {
     if (ee == cudaSuccess) cudaGraphDestroy(g);
-    return sfail(srv, ADER_ERR_CUDA, "batched launch failed during capture: %s",
-                 cudaGetErrorString(ce));
-  }
-  if (ee != cudaSuccess)
+    if (srv->gexec) cudaGraphExecDestroy(srv->gexec);
+    srv->gexec = nullptr;
+    if (ce != cudaSuccess)
+      return sfail(srv, ADER_ERR_CUDA, "batched launch failed during capture: %s",
+                   cudaGetErrorString(ce));
     return sfail(srv, ADER_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ee));
-  ee = cudaGraphInstantiate(&srv->gexec, g, 0);
+  }
+  // Most rounds change only the work lists' lengths and offsets (kernel
+  // parameters and grid sizes) of the same degrees: update the executable graph
+  // in place, and instantiate afresh only when the graph's shape changed.
+  if (srv->gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(srv->gexec, g, &info) != cudaSuccess) {
+      (void)cudaGetLastError();  // the failed update leaves no error behind
+      cudaGraphExecDestroy(srv->gexec);
+      srv->gexec = nullptr;
+    }
+  }
+  ee = srv->gexec ? cudaSuccess : cudaGraphInstantiate(&srv->gexec, g, 0);
   cudaGraphDestroy(g);
   if (ee != cudaSuccess)
     return sfail(srv, ADER_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ee));

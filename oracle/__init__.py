@@ -398,13 +398,14 @@ class Oracle:
         lib().ob_lim_weno2(_arr(vm, M), _arr(v0, M), _arr(vp, M), _arr(xi, 2), w)
         return w.reshape(2, M)
 
-    def dgl_step(self, u, dx, dt, bc: str = "periodic", limiter: bool = True):
+    def dgl_step(self, u, dx, dt, bc: str = "periodic", limiter: bool = True,
+                 delta0: float = 1e-4, eps: float = 1e-3):
         u = _arr(u)
         nc = u.size // (self.n * M)
         out = np.zeros_like(u)
         tr = np.zeros(nc, dtype=np.int32)
         st = Stats()
-        lp = self.lim_params(bc, limiter)
+        lp = self.lim_params(bc, limiter, delta0, eps)
         rc = lib().ob_dgl_step(C.byref(self.basis), C.byref(self.params), C.byref(lp), nc, dx, dt,
                                u, out, tr.ctypes.data, C.byref(st))
         return out, tr, rc

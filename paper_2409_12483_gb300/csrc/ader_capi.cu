@@ -2,6 +2,7 @@
 // workspace, kernel sequencing, the device-resident time loop under CUDA graphs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -54,8 +55,7 @@ struct ader_ctx {
   double* wrec = nullptr;
   double* ubuf = nullptr;
   double* hbuf = nullptr;
-  double* lim_mm = nullptr;   // limiter: subcell extrema of u^n [cell][6]
-  double* lim_vb = nullptr;   // limiter: subcells 0, 1, Ns-2, Ns-1 of P u^n [cell][12]
+  float* lim_mmf = nullptr;   // limiter: FP32 subcell extrema of u^n and bounds [cell][9]
   Sub1Ops sub1{};             // limiter: degree-1 operators of the subcell scheme
   int* lim_flag = nullptr;    // limiter: troubled flags [cell]
   long long* lim_list = nullptr;  // limiter: troubled-cell list [cell]
@@ -120,8 +120,8 @@ size_t workspace_bytes(const ader_ctx* c) {
   if (c->dims == 2) b += align_up((size_t)c->mesh.n_cells * 2 * c->n * kM2 * sizeof(double));
   if (c->dims == 3) b += align_up((size_t)c->mesh.n_cells * 3 * c->n * c->n * kM3 * sizeof(double));
   if (c->opt.limiter)
-    b += 2 * align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
-         align_up((size_t)c->mesh.n_cells * 12 * sizeof(double)) +
+    b += align_up((size_t)c->mesh.n_cells * 9 * sizeof(float)) +
+         align_up((size_t)c->mesh.n_cells * 6 * sizeof(double)) +
          align_up((size_t)c->mesh.n_cells * sizeof(long long)) +
          align_up((size_t)c->mesh.n_cells * sizeof(int));
   return b;
@@ -281,8 +281,7 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.u_old = src;
   l.u = dst;
   l.trace = ctx->trace;
-  l.mm = ctx->lim_mm;
-  l.vb = ctx->lim_vb;
+  l.mmf = ctx->lim_mmf;
   l.troubled = ctx->lim_flag;
   l.list = ctx->lim_list;
   l.gface = ctx->lim_gface;
@@ -302,8 +301,16 @@ ader_status enqueue_limiter(ader_ctx* ctx, const double* src, double* dst, const
   l.sp = sp;
   l.ops = ctx->basis.d;
   std::memcpy(l.R, ctx->basis.R, sizeof(l.R));
-  for (int j = 0; j < kMaxNs; ++j)
-    for (int k = 0; k < kMaxN; ++k) l.Pf[j][k] = (float)ctx->basis.d.P[j][k];
+  double pabs = 0.0;
+  for (int j = 0; j < kMaxNs; ++j) {
+    double a = 0.0;
+    for (int k = 0; k < kMaxN; ++k) {
+      l.Pf[j][k] = (float)ctx->basis.d.P[j][k];
+      a += std::fabs(ctx->basis.d.P[j][k]);
+    }
+    pabs = std::max(pabs, a);
+  }
+  l.pabs = (float)(pabs * (1.0 + 1e-6));  // rounded up
   CK(do_limiter(ctx->N, l, ctx->stream));
   ctx->launches += 4;
   return ADER_OK;
@@ -770,10 +777,8 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
     p += align_up((size_t)ctx->mesh.n_cells * 3 * ctx->n * ctx->n * kM3 * sizeof(double));
   }
   if (ctx->opt.limiter) {
-    ctx->lim_mm = reinterpret_cast<double*>(p);
-    p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
-    ctx->lim_vb = reinterpret_cast<double*>(p);
-    p += align_up((size_t)ctx->mesh.n_cells * 12 * sizeof(double));
+    ctx->lim_mmf = reinterpret_cast<float*>(p);
+    p += align_up((size_t)ctx->mesh.n_cells * 9 * sizeof(float));
     ctx->lim_gface = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 6 * sizeof(double));
     ctx->lim_list = reinterpret_cast<long long*>(p);

@@ -118,8 +118,8 @@ struct LimParams {
   const double* u_old;   // u^n, [cell][n][3]
   double* u;             // in: candidate u*, out: u^{n+1} (same layout)
   const double* trace;   // predictor traces [cell][qR(3n) | qL(3n) | u + volume(3n)]
-  double* mm;            // [cell][6]: min (3), max (3) of the subcell averages of u^n
-  double* vb;            // [cell][12]: P u^n of subcells 0, 1, Ns-2, Ns-1 (3 each)
+  float* mmf;            // [cell][9]: FP32 min (3), max (3) of the subcell averages of
+                         // u^n and a bound (3) on their distance from the FP64 ones
   int* troubled;         // [cell]
   long long* list;       // [cell]: the troubled cells of the step (first ctl->lim_n entries)
   double* gface;         // [cell][2][3]: subcell fluxes of a troubled cell's left / right face
@@ -136,7 +136,8 @@ struct LimParams {
   OpsD ops;
   Sub1Ops s1;
   double R[kMaxN][kMaxNs];  // reconstruction from subcell averages
-  float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening pass of lambda_max)
+  float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening passes)
+  float pabs;               // max_j sum_k |P_jk|
 };
 
 // 2D Euler (ader_kernels2d.cuh): state [cell][k1][k2][4], cell = iy nx + ix.

@@ -5,14 +5,16 @@
 // limiter of Sec. 2).  Run after the interface kernel has written the candidate
 // u* in place of u^{n+1}:
 //
-// lim_minmax_kernel  per cell, the 2N+1 subcell averages P u^n: their minimum and
-//                    maximum per variable and subcells 0, 1, Ns-2, Ns-1 (the
-//                    stencils of the limited faces of the cell).
+// lim_minmax_kernel  per cell, the 2N+1 subcell averages P u^n in FP32: their
+//                    minimum and maximum per variable and a bound on their
+//                    distance from the FP64 averages.
 // lim_detect_kernel  per cell, PAD (rho > 0, e > 0) on the subcell averages P u*
 //                    and the relaxed discrete maximum principle against the
 //                    extrema of the cell and its neighbours, delta = max(delta0,
 //                    eps (max - min)); marks troubled cells (mode 2: every cell),
-//                    counts them.
+//                    counts them.  An FP32 pass clears the cells that pass with
+//                    the error bounds to spare; the rest are decided in FP64,
+//                    so every flag is the FP64 detectors' flag.
 // lim_recompute_kernel  one warp per listed troubled cell: the ADER-WENO2
 //                    scheme on its 2N+1 subcells from P u^n (lane j: degree-1
 //                    WENO and the degree-1 LST-DG predictor of subcell j - 1,
@@ -60,6 +62,46 @@ __device__ __forceinline__ void lim_subcell(const LimParams& P, const double* u,
   }
 }
 
+// FP32 screening of the detectors.  The FP32 image of a coefficient is its
+// truncation (integer operations, no FP64 work; relative error below 2^-23),
+// P is rounded to FP32 (2^-24) and the n fmaf roundings add n 2^-24, so an FP32
+// subcell average differs from the FP64 one by less than
+// (n + 4) 2^-24 sum_k |P_jk| max_k |u_k| (the FP64 sum's own rounding and the
+// second-order terms included); the bound used is twice that, with
+// max_j sum_k |P_jk| in place of the row sum.  A cell whose coefficients leave
+// the range where that holds (|u| above 1e30 or all below 1e-30, NaN) gets no
+// bound and is decided in FP64.
+
+// FP32 image of a cell's coefficients and the error bound of its subcell
+// averages per variable (negative: no bound)
+template <int N>
+__device__ __forceinline__ void lim_image32(const LimParams& P, const double* u,
+                                            float (&uf)[N + 1][kM], float (&bound)[kM]) {
+#pragma unroll
+  for (int r = 0; r < kM; ++r) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+      uf[k][r] = d2f_trunc(u[k * kM + r]);
+      m = fmaxf(m, fabsf(uf[k][r]));
+    }
+    bound[r] = (m < 1e30f && m > 1e-30f) ? (float)(N + 5) * 0x1p-23f * P.pabs * m : -1.f;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void lim_subcell32(const LimParams& P, const float (&uf)[N + 1][kM],
+                                              int j, float* v) {
+#pragma unroll
+  for (int r = 0; r < kM; ++r) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k <= N; ++k) acc = fmaf(P.Pf[j][k], uf[k][r], acc);
+    v[r] = acc;
+  }
+}
+
+// per cell: FP32 extrema of the subcell averages of u^n and their bound
 template <int N>
 __global__ void __launch_bounds__(256) lim_minmax_kernel(const __grid_constant__ LimParams P) {
   double dt;
@@ -68,30 +110,28 @@ __global__ void __launch_bounds__(256) lim_minmax_kernel(const __grid_constant__
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) P.sp.ctl->lim_n = 0;  // the detectors append to the list after this kernel
   if (i >= P.ncells) return;
-  const double* u = P.u_old + i * ((N + 1) * kM);
-  double lo[kM], hi[kM];
+  float uf[N + 1][kM], bound[kM], lo[kM], hi[kM];
+  lim_image32<N>(P, P.u_old + i * ((N + 1) * kM), uf, bound);
 #pragma unroll
   for (int r = 0; r < kM; ++r) {
     lo[r] = INFINITY;
     hi[r] = -INFINITY;
   }
   for (int j = 0; j < P.Ns; ++j) {
-    double v[kM];
-    lim_subcell<N>(P, u, j, v);
+    float v[kM];
+    lim_subcell32<N>(P, uf, j, v);
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
-      lo[r] = fmin(lo[r], v[r]);
-      hi[r] = fmax(hi[r], v[r]);
-      if (j == 0) P.vb[i * 12 + r] = v[r];
-      if (j == 1) P.vb[i * 12 + 3 + r] = v[r];
-      if (j == P.Ns - 2) P.vb[i * 12 + 6 + r] = v[r];
-      if (j == P.Ns - 1) P.vb[i * 12 + 9 + r] = v[r];
+      lo[r] = fminf(lo[r], v[r]);
+      hi[r] = fmaxf(hi[r], v[r]);
     }
   }
+  float* out = P.mmf + i * 9;
 #pragma unroll
   for (int r = 0; r < kM; ++r) {
-    P.mm[i * 6 + r] = lo[r];
-    P.mm[i * 6 + 3 + r] = hi[r];
+    out[r] = lo[r];
+    out[3 + r] = hi[r];
+    out[6 + r] = bound[r];
   }
 }
 
@@ -118,33 +158,88 @@ __global__ void __launch_bounds__(256) lim_detect_kernel(const __grid_constant__
     }
     return;
   }
+  // FP32 screen: the cell is certainly admissible when every FP32 subcell
+  // average of u* lies inside the NAD interval and PAD holds with the error
+  // bounds to spare; otherwise the FP64 detectors below decide
   const double* u = P.u + i * ((N + 1) * kM);
-  double lo[kM], hi[kM];
-#pragma unroll
-  for (int r = 0; r < kM; ++r) {
-    lo[r] = INFINITY;
-    hi[r] = -INFINITY;
-  }
-  for (int d = -1; d <= 1; ++d) {
-    const long long c = lim_neighbour(i + d, P.ncells, P.bc);
-    if (c < 0) continue;
+  bool sure = true;
+  {
+    float uf[N + 1][kM], bc[kM], lo[kM], hi[kM], bn[kM];
+    lim_image32<N>(P, u, uf, bc);
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
-      lo[r] = fmin(lo[r], P.mm[c * 6 + r]);
-      hi[r] = fmax(hi[r], P.mm[c * 6 + 3 + r]);
+      lo[r] = INFINITY;
+      hi[r] = -INFINITY;
+      bn[r] = 0.f;
+    }
+    for (int d = -1; d <= 1; ++d) {
+      const long long c = lim_neighbour(i + d, P.ncells, P.bc);
+      if (c < 0) continue;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        lo[r] = fminf(lo[r], P.mmf[c * 9 + r]);
+        hi[r] = fmaxf(hi[r], P.mmf[c * 9 + 3 + r]);
+        const float b = P.mmf[c * 9 + 6 + r];
+        bn[r] = b < 0.f ? INFINITY : fmaxf(bn[r], b);
+      }
+    }
+    float slack[kM], dlo[kM];
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      // the FP64 delta is at least max(delta0, eps (hi - lo - 2 bn))
+      dlo[r] = fmaxf((float)P.delta0 * (1.f - 1e-6f), (float)P.eps * (hi[r] - lo[r] - 2.f * bn[r]));
+      slack[r] = 2.f * (bn[r] + bc[r]);  // doubled for the FP32 roundings below
+      if (!(bc[r] >= 0.f) || !(slack[r] < INFINITY)) sure = false;
+    }
+    for (int j = 0; j < P.Ns && sure; ++j) {
+      float v[kM];
+      lim_subcell32<N>(P, uf, j, v);
+#pragma unroll
+      for (int r = 0; r < kM; ++r)
+        if (!(v[r] - lo[r] + dlo[r] >= slack[r]) || !(hi[r] - v[r] + dlo[r] >= slack[r]))
+          sure = false;
+      // PAD: rho > 0 and E - m^2 / (2 rho) > 0 with the first-order error of the
+      // FP32 evaluation (four times over)
+      const float kin = 0.5f * v[1] * v[1] / v[0];
+      const float eb = bc[2] + (fabsf(v[1]) * bc[1] + kin * bc[0]) / v[0];
+      if (!(v[0] > 4.f * bc[0]) || !(v[2] - kin > 4.f * eb + 1e-6f * (fabsf(v[2]) + kin)))
+        sure = false;
     }
   }
-  double delta[kM];
-#pragma unroll
-  for (int r = 0; r < kM; ++r) delta[r] = fmax(P.delta0, P.eps * (hi[r] - lo[r]));
   bool bad = false;
-  for (int j = 0; j < P.Ns; ++j) {
-    double v[kM];
-    lim_subcell<N>(P, u, j, v);
-    if (!lim_admissible(v)) bad = true;
+  if (!sure) {
+    // FP64 detectors: extrema of the cell and its neighbours from u^n, then PAD
+    // and NAD on the subcell averages of u*
+    double lo[kM], hi[kM];
 #pragma unroll
-    for (int r = 0; r < kM; ++r)
-      if (v[r] < lo[r] - delta[r] || v[r] > hi[r] + delta[r]) bad = true;
+    for (int r = 0; r < kM; ++r) {
+      lo[r] = INFINITY;
+      hi[r] = -INFINITY;
+    }
+    for (int d = -1; d <= 1; ++d) {
+      const long long c = lim_neighbour(i + d, P.ncells, P.bc);
+      if (c < 0) continue;
+      for (int j = 0; j < P.Ns; ++j) {
+        double v[kM];
+        lim_subcell<N>(P, P.u_old + c * ((N + 1) * kM), j, v);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          lo[r] = fmin(lo[r], v[r]);
+          hi[r] = fmax(hi[r], v[r]);
+        }
+      }
+    }
+    double delta[kM];
+#pragma unroll
+    for (int r = 0; r < kM; ++r) delta[r] = fmax(P.delta0, P.eps * (hi[r] - lo[r]));
+    for (int j = 0; j < P.Ns; ++j) {
+      double v[kM];
+      lim_subcell<N>(P, u, j, v);
+      if (!lim_admissible(v)) bad = true;
+#pragma unroll
+      for (int r = 0; r < kM; ++r)
+        if (v[r] < lo[r] - delta[r] || v[r] > hi[r] + delta[r]) bad = true;
+    }
   }
   P.troubled[i] = bad ? 1 : 0;
   if (bad) {
@@ -304,18 +399,24 @@ __global__ void __launch_bounds__(32 * kLimWarps)
        e += (long long)gridDim.x * kLimWarps) {
     const long long i = P.list[e];
     const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
-    // subcell averages: the cell's own from u^n, the neighbours' boundary
-    // subcells from the minmax pass (outflow: the boundary subcell)
+    // subcell averages of u^n: the cell's own, and the neighbours' two subcells
+    // next to each face (lane 0, 1: left neighbour's Ns-2, Ns-1; lane 2, 3: right
+    // neighbour's 0, 1), by the same arithmetic the neighbour uses for its own,
+    // so both sides of a face between troubled cells see the same bits
     if (lane < Ns) lim_subcell<N>(P, P.u_old + i * (n * kM), lane, w.ve[lane + 2]);
+    if (lane < 4) {
+      const long long nb = lane < 2 ? il : ir;
+      if (nb >= 0)
+        lim_subcell<N>(P, P.u_old + nb * (n * kM), lane < 2 ? Ns - 2 + lane : lane - 2,
+                       w.ve[lane < 2 ? lane : Ns + lane]);
+    }
     __syncwarp();
-    if (lane < 4 * kM) {
-      const int g = lane / kM, r = lane - g * kM;
-      double v;
-      if (g < 2)
-        v = il >= 0 ? P.vb[il * 12 + 6 + g * 3 + r] : w.ve[2][r];
-      else
-        v = ir >= 0 ? P.vb[ir * 12 + (g - 2) * 3 + r] : w.ve[Ns + 1][r];
-      w.ve[g < 2 ? g : Ns + g][r] = v;
+    if (lane < 4) {  // outflow boundary: the boundary subcell itself
+      const long long nb = lane < 2 ? il : ir;
+      if (nb < 0) {
+#pragma unroll
+        for (int r = 0; r < kM; ++r) w.ve[lane < 2 ? lane : Ns + lane][r] = w.ve[lane < 2 ? 2 : Ns + 1][r];
+      }
     }
     __syncwarp();
     // lane j: subcell j - 1 (ve index j + 1): degree-1 WENO and predictor

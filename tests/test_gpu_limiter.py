@@ -177,3 +177,30 @@ def test_every_cell_on_subcells_solve_parity(cuda, oracle_mod, N):
     assert rc == 0 and steps == steps_ref and t == 0.25
     assert ctx.ader_get_stats()["troubled_cells"] == ttot == nc * steps
     assert rel_linf(ud.cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("N", [2, 5])
+@pytest.mark.parametrize("delta0,eps", [(0.0, 0.0), (1e-9, 1e-6), (1e-4, 1e-3)])
+def test_nad_decisions_near_the_threshold(cuda, oracle_mod, N, delta0, eps):
+    """smooth data with a strict or tight discrete maximum principle: many
+    subcell averages sit at the edge of the NAD interval, where the FP32 screen
+    must hand the decision to the FP64 detectors; the troubled cells are the
+    oracle's exactly"""
+    import torch
+    o = oracle_mod.Oracle(N)
+    nc = 64
+    u = W.nodal_state(field_nonlinear(80 + N), o.node_x(nc))
+    dx = 1.0 / nc
+    dt = o.dg_dt(u, dx)
+    ref, tr, rc = o.dgl_step(u, dx, dt, limiter=True, delta0=delta0, eps=eps)
+    assert rc == 0
+    ctx = make(nc, N, limiter=1, nad_delta0=delta0, nad_eps=eps)
+    ud = to_dev(u, cuda)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, dt)
+    flags = ctx.ader_get_troubled().cpu().numpy()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(flags, tr)
+    assert rel_linf(out.cpu().numpy(), ref) < 1e-12
+    if delta0 == 0.0:
+        assert tr.any()  # the strict principle flags the cells at smooth extrema

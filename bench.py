@@ -411,7 +411,8 @@ def main():
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
                          "step3d-dg2 (multi-D: warmup + steps time steps of one solve) | "
-                         "paper-costs (the sine wave at the meshes of the paper's cost tables)")
+                         "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
+                         "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1229,6 +1230,25 @@ def run_case(args):
         else:  # 96^3 cells: 0.96 GB state
             ctx = Context3D(96, 96, 96, 2, device=dev)
             u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
+        steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
+        return
+    elif args.case in ("sod-dg5-limiter", "tracer-dg5", "reacting-dg5"):
+        # 10^6 cells (144-192 MB of state, above L2): warmup + steps time steps
+        import numpy as np
+        if args.case == "sod-dg5-limiter":
+            ctx = Context(nc, 5, "dg", device=dev, bc="outflow", limiter=1)
+            u = torch.tensor(W.riemann_initial(ctx.node_coords(), 1), device=dev).reshape(-1)
+        elif args.case == "tracer-dg5":
+            ctx = Context(nc, 5, "dg", device=dev, system="tracer")
+            x = ctx.node_coords()
+            e = W.nodal_state(W.modes4(SEED), x)
+            u = torch.tensor(np.concatenate([e, 0.5 + 0.3 * np.cos(2 * np.pi * x)[..., None]], -1),
+                             device=dev).reshape(-1)
+        else:
+            ctx = Context(nc, 5, "dg", device=dev, system="reacting", omega=1.0)
+            u = torch.tensor(W.reacting_state(ctx.node_coords(), seed=SEED), device=dev).reshape(-1)
         steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))

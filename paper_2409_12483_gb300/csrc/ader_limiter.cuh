@@ -531,6 +531,28 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
     }
   }
   if (!P.want_lambda) return;  // uniform over the grid
+  // A cell whose coefficients equal, bit for bit, those of the previous cell of
+  // the block has the same subcell wave speeds, so only the first cell of such
+  // a run enters the maximum.  Uniform regions (Riemann data) stay bitwise
+  // uniform from cell to cell, and there the screen below would otherwise
+  // evaluate nearly every subcell in FP64 (they all tie with the maximum).
+  __shared__ double s_u[128][n * kM];
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) s_u[threadIdx.x][k * kM + r] = u[k][r];
+  }
+  __syncthreads();
+  bool twin = valid && threadIdx.x > 0;
+  if (twin) {
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r)
+        twin = twin && dbits(s_u[threadIdx.x - 1][k * kM + r]) == dbits(u[k][r]);
+  }
+  const bool own = valid && !twin;  // this cell's subcells enter the maximum
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
   float uf[n][kM], lt[Ns], lt_loc = 0.f;
 #pragma unroll
@@ -554,7 +576,7 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
       lt[j] = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
     else
       lt[j] = fabsf(uu) + sqrtf(gf * pp * inv);
-    if (valid) lt_loc = fmaxf(lt_loc, lt[j]);
+    if (own) lt_loc = fmaxf(lt_loc, lt[j]);
   }
   const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
   if (threadIdx.x == 0) {
@@ -565,7 +587,7 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
   const float cut = s_cut;
   double lmax = 0.0;
   bool bad = false;
-  if (valid) {
+  if (own) {
 #pragma unroll
     for (int j = 0; j < Ns; ++j) {
       if (!(lt[j] >= cut)) continue;

@@ -78,28 +78,37 @@ def predictor_flops_per_cell(n: int, iters: float, dg: bool = True) -> float:
 
 def predictor2d_flops_per_cell(n: int, iters: float) -> float:
     """Algorithmic FLOPs of one cell's 2D predictor launch (M = 4 variables,
-    n^3 space-time nodes), as the kernel runs it.  Every iteration: the x- and
-    y-fluxes at n^3 nodes with their dt/dx, dt/dy scaling (25 flops: 1 division,
-    2 velocities, 5 for p, 9 for F and G, 8 scalings), k~ along xi and along eta
-    and kappa~ along tau (2 n^4 M each), q' = u - ... and the difference (2 n^3 M).
-    Epilogue: four traces (8 n^3 M), the fluxes again (25 n^3), the two time
-    averages (4 n^3 M) and the two D~ contractions plus u (4 n^3 M + n^2 M)."""
+    n^3 space-time nodes), as the kernel runs it.  Iteration 1 starts from q = u
+    in every tau row: the fluxes at the n^2 spatial nodes (25 flops each: 1
+    division, 2 velocities, 5 for p, 9 for F and G, 8 scalings), k~ along xi and
+    eta there (4 n^3 M), q' = u - (row sum of kappa~) s (2 n^3 M) and the
+    difference (n^3 M).  Every later iteration: the fluxes at n^3 nodes, k~ along
+    xi and along eta and kappa~ along tau (2 n^4 M each), q' = u - ... and the
+    difference (2 n^3 M).  Epilogue: four traces (8 n^3 M), the fluxes again
+    (25 n^3), the two time averages (4 n^3 M) and the two D~ contractions plus u
+    (4 n^3 M + n^2 M)."""
     m = 4
+    first = 25 * n ** 2 + 7 * n ** 3 * m
     it = 25 * n ** 3 + 6 * n ** 4 * m + 2 * n ** 3 * m
     epi = 8 * n ** 3 * m + 25 * n ** 3 + 4 * n ** 3 * m + 4 * n ** 3 * m + n * n * m
-    return iters * it + epi
+    return first + max(iters - 1.0, 0.0) * it + epi
 
 
 def predictor3d_flops_per_cell(n: int, iters: float) -> float:
     """Algorithmic FLOPs of one cell's 3D predictor launch (M = 5, n^4 space-time
-    nodes): per iteration the three fluxes with their scalings (45 flops per node),
-    k~ along xi, eta, zeta and kappa~ along tau (2 n^5 M each) and the update and
-    difference (2 n^4 M); epilogue: six traces (12 n^4 M), the fluxes again, the
-    three time averages (6 n^4 M) and the three D~ contractions (6 n^4 M)."""
+    nodes), as the kernel runs it: iteration 1 (q = u in every tau row) forms the
+    three fluxes (45 flops per node) and k~ along xi, eta, zeta (6 n^4 M) at the
+    n^3 spatial nodes only, then q' = u - (row sum of kappa~) s and the difference
+    (3 n^4 M); every later iteration the three fluxes with their scalings at n^4
+    nodes, k~ along xi, eta, zeta and kappa~ along tau (2 n^5 M each) and the
+    update and difference (2 n^4 M); epilogue: six traces (12 n^4 M), the fluxes
+    again, the three time averages (6 n^4 M) and the three D~ contractions
+    (6 n^4 M)."""
     m = 5
+    first = 45 * n ** 3 + 9 * n ** 4 * m
     it = 45 * n ** 4 + 8 * n ** 5 * m + 2 * n ** 4 * m
     epi = 12 * n ** 4 * m + 45 * n ** 4 + 6 * n ** 4 * m + 6 * n ** 4 * m
-    return iters * it + epi
+    return first + max(iters - 1.0, 0.0) * it + epi
 
 
 def dg3_errors(ctx, u, t, npts=10):

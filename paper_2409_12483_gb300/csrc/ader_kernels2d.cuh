@@ -124,7 +124,13 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
     const bool active = !sh.done[lc];
-    if (active) {
+    // Iteration 1 starts from q = u in every tau row, so its fluxes and their
+    // xi / eta contractions do not depend on tau: the p0 = 0 threads form them
+    // once per (p1, p2), and q' = u - (sum_m kappa~[p0][m]) s with the row sums
+    // of kappa~ (kappa~ 1 = tau).
+    const bool first = it == 0;
+    const bool work = active && (!first || p0 == 0);
+    if (work) {
       double F[kM2], G[kM2];
       euler2_flux(q, F, G, P.gm1);
 #pragma unroll
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
     }
     __syncthreads();
     double s[kM2];
-    if (active) {
+    if (work) {
 #pragma unroll
       for (int r = 0; r < kM2; ++r) {
         double acc = 0.0;
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
       }
     }
     __syncthreads();
-    if (active) {
+    if (work) {
 #pragma unroll
       for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = s[r];
     }
@@ -157,8 +163,12 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
 #pragma unroll
       for (int r = 0; r < kM2; ++r) {
         double acc = 0.0;
+        if (first) {
+          acc = o.kaprow[p0] * sh.A[lc][p1 * n + p2][r];  // node (0, p1, p2)
+        } else {
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fma(o.kap[p0][m], sh.A[lc][(m * n + p1) * n + p2][r], acc);
+          for (int m = 0; m < n; ++m) acc = fma(o.kap[p0][m], sh.A[lc][(m * n + p1) * n + p2][r], acc);
+        }
         const double qn = uo[r] - acc;
         dmax = umax64(dmax, abs_bits(qn - q[r]));
         qm = umax64(qm, abs_bits(qn));

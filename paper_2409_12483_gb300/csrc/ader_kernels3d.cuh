@@ -136,15 +136,22 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
     const bool active = !sh.done[lc];
+    // Iteration 1 starts from q = u in every tau row: its fluxes and their
+    // contractions do not depend on tau, so the p0 = 0 threads form them once per
+    // spatial node, and q' = u - (sum_m kappa~[p0][m]) s (kappa~ 1 = tau).
+    const bool first = it == 0;
+    const bool work = !first || p0 == 0;
     double F[3][kM3];
-    euler3_flux(q, F, P.gm1);
+    if (work) euler3_flux(q, F, P.gm1);
     double acc[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+      if (work) {
 #pragma unroll
-      for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
+        for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
+      }
       __syncthreads();
-      if (active) {
+      if (active && work) {
         const int base = node - pd[d] * stride[d];
 #pragma unroll
         for (int r = 0; r < kM3; ++r)
@@ -153,16 +160,22 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
       }
       __syncthreads();
     }
+    if (work) {
 #pragma unroll
-    for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = acc[r];
+      for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = acc[r];
+    }
     __syncthreads();
     if (active) {
       unsigned long long dmax = 0ull, qm = 0ull;
 #pragma unroll
       for (int r = 0; r < kM3; ++r) {
         double s = 0.0;
+        if (first) {
+          s = o.kaprow[p0] * sh.S[lc][sp_node][r];  // node (0, p1, p2, p3)
+        } else {
 #pragma unroll
-        for (int m = 0; m < n; ++m) s = fma(o.kap[p0][m], sh.S[lc][m * NNN + sp_node][r], s);
+          for (int m = 0; m < n; ++m) s = fma(o.kap[p0][m], sh.S[lc][m * NNN + sp_node][r], s);
+        }
         const double qn = uo[r] - s;
         dmax = umax64(dmax, abs_bits(qn - q[r]));
         qm = umax64(qm, abs_bits(qn));
@@ -317,6 +330,11 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
     for (int r = 0; r < kM3; ++r) q[p0][r] = uo[r];
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
+    // Iteration 1 starts from q = u in every tau row: the fluxes and their
+    // contractions are the same for every p0, so they are formed for p0 = 0 only
+    // and q'[p0] = u - (sum_m kappa~[p0][m]) s (kappa~ 1 = tau).
+    const bool first = it == 0;
+    const int rows = first ? 1 : n;
     double acc[n][kM3];
 #pragma unroll
     for (int p0 = 0; p0 < n; ++p0)
@@ -327,6 +345,7 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
       if (valid) {
 #pragma unroll
         for (int p0 = 0; p0 < n; ++p0) {
+          if (p0 >= rows) break;
           double f[kM3];
           if (d == 0) euler3_flux_dir<0>(q[p0], f, P.gm1);
           if (d == 1) euler3_flux_dir<1>(q[p0], f, P.gm1);
@@ -339,12 +358,14 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
       if (valid) {
         const int base = node - pd[d] * stride[d];
 #pragma unroll
-        for (int p0 = 0; p0 < n; ++p0)
+        for (int p0 = 0; p0 < n; ++p0) {
+          if (p0 >= rows) break;
 #pragma unroll
           for (int r = 0; r < kM3; ++r)
 #pragma unroll
             for (int m = 0; m < n; ++m)
               acc[p0][r] = fma(o.kt[pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+        }
       }
       __syncthreads();
     }
@@ -356,8 +377,12 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
 #pragma unroll
         for (int p0 = 0; p0 < n; ++p0) {
           double sum = 0.0;
+          if (first) {
+            sum = o.kaprow[p0] * acc[0][r];
+          } else {
 #pragma unroll
-          for (int m = 0; m < n; ++m) sum = fma(o.kap[p0][m], acc[m][r], sum);
+            for (int m = 0; m < n; ++m) sum = fma(o.kap[p0][m], acc[m][r], sum);
+          }
           qn[p0] = uo[r] - sum;
         }
 #pragma unroll

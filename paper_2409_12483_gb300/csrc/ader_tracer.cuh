@@ -133,8 +133,30 @@ __device__ __forceinline__ void predict_nc_tile(const PredictParams& P, const Ti
     int it = 0;
     while (__syncthreads_or(!done_o && it < cap)) {
       ++it;
-      // outer: rescaled flux of the current iterate and k~ along xi (frozen below)
-      {
+      // outer: rescaled flux of the current iterate and k~ along xi (frozen
+      // below).  Iteration 1 starts from q = u in every tau row, so the rows are
+      // all equal: thread p0 forms the flux at node p0 and then g at node p0 of
+      // the cell's single row (row 0 of the frozen rows), which every thread
+      // reads after the barrier that opens the inner loop.
+      const bool first_o = it == 1;  // uniform over the block
+      if (first_o) {
+        double F[M];
+        tracer_flux(uc + p0 * M, F, P.gm1);
+#pragma unroll
+        for (int r = 0; r < M; ++r) my_d[r] = lam * F[r];  // the exchange row is free here
+        __syncthreads();
+        double gv[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) gv[r] = 0.0;
+#pragma unroll
+        for (int q1 = 0; q1 < n; ++q1) {
+          const double a = P.ops.kt[p0][q1];
+#pragma unroll
+          for (int r = 0; r < M; ++r) gv[r] = fma(a, sd[(lc * n + q1) * RS + r], gv[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) sg[(size_t)(lc * n) * RS + p0 * M + r] = gv[r];
+      } else {
         double f[n][M];
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1) {
@@ -144,6 +166,7 @@ __device__ __forceinline__ void predict_nc_tile(const PredictParams& P, const Ti
         }
         kxi_row<N, double, M>(f, my_g, P.ops.kt, P.ops.ksa, P.ops.ksb);
       }
+      const double* gsrc = first_o ? sg + (size_t)(lc * n) * RS : my_g;
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
@@ -163,8 +186,8 @@ __device__ __forceinline__ void predict_nc_tile(const PredictParams& P, const Ti
         for (int p1 = 0; p1 < n; ++p1) {
           if (m == 1)
 #pragma unroll
-            for (int r = 0; r < 3; ++r) my_d[p1 * M + r] = my_g[p1 * M + r];
-          my_d[p1 * M + 3] = my_g[p1 * M + 3] + bv[p1];
+            for (int r = 0; r < 3; ++r) my_d[p1 * M + r] = gsrc[p1 * M + r];
+          my_d[p1 * M + 3] = gsrc[p1 * M + 3] + bv[p1];
         }
         __syncthreads();
         // b acts on phi only and the flux rows are frozen: after the first inner

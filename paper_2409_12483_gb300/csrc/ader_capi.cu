@@ -350,6 +350,8 @@ ader_status enqueue_step2d(ader_ctx* ctx, const double* src, double* dst, const 
   f.want_lambda = want_lambda;  // the predictor of this step has reset the slot
   f.sp = sp;
   f.ops = ctx->basis.d;
+  for (int j = 0; j < kMaxNs; ++j)
+    for (int k = 0; k < kMaxN; ++k) f.Pf[j][k] = (float)ctx->basis.d.P[j][k];
   CK(do_face2d(ctx->N, f, ctx->stream));
   ctx->launches += 3;
   if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));
@@ -391,6 +393,8 @@ ader_status enqueue_step3d(ader_ctx* ctx, const double* src, double* dst, const 
   f.want_lambda = want_lambda;  // the predictor of this step has reset the slot
   f.sp = sp;
   f.ops = ctx->basis.d;
+  for (int j = 0; j < kMaxNs; ++j)
+    for (int k = 0; k < kMaxN; ++k) f.Pf[j][k] = (float)ctx->basis.d.P[j][k];
   CK(do_face3d(ctx->N, f, ctx->stream));
   ctx->launches += 3;
   if (ev) CK(cudaEventRecordWithFlags(ev[3], ctx->stream, cudaEventRecordExternal));

@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(Upd2Cfg<N, TB>::THREADS)
   using C = Upd2Cfg<N, TB>;
   constexpr int n = N + 1, NN = n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred2Cfg<N>::REC;
   __shared__ double U[CPB][NN][kM2];
-  __shared__ double T[CPB][n][Ns][kM2];  // projected along eta: [k1][j2]
+  __shared__ float T[CPB][n][Ns][kM2];  // FP32 screen: projected along eta, [k1][j2]
+  __shared__ float LT[CPB][Ns * Ns];    // FP32 screen: subcell speeds
+  __shared__ float s_cut;
   __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
   int last;
@@ -350,29 +352,75 @@ __global__ void __launch_bounds__(Upd2Cfg<N, TB>::THREADS)
   if (blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
   if (!P.want_lambda) return;  // uniform
   __syncthreads();
+  // lambda_max of u_new over the Ns^2 subcells, screened as in the 1D interface
+  // kernel: the separable projection and the wave speeds in FP32 for every
+  // subcell, then FP64 only for the subcells within 1e-3 of the block's FP32
+  // maximum and those whose FP32 state is doubtful, so the result is the FP64
+  // maximum over every subcell.
+  const long long c0 = (long long)blockIdx.x * CPB;
   for (int it = tid; it < CPB * n * Ns; it += C::THREADS) {
     const int c = it / (n * Ns), rem = it - c * n * Ns, k1 = rem / Ns, j2 = rem - k1 * Ns;
-    if ((long long)blockIdx.x * CPB + c >= P.ncells) continue;
+    if (c0 + c >= P.ncells) continue;
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
-      double acc = 0.0;
+      float acc = 0.f;
 #pragma unroll
-      for (int k2 = 0; k2 < n; ++k2) acc = fma(o.P[j2][k2], U[c][k1 * n + k2][r], acc);
+      for (int k2 = 0; k2 < n; ++k2) acc = fmaf(P.Pf[j2][k2], d2f_trunc(U[c][k1 * n + k2][r]), acc);
       T[c][k1][j2][r] = acc;
     }
   }
   __syncthreads();
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  const float ihx = (float)P.sp.inv_dx, ihy = (float)P.inv_dy;
+  float lt_loc = 0.f;
+  for (int it = tid; it < CPB * Ns * Ns; it += C::THREADS) {
+    const int c = it / (Ns * Ns), rem = it - c * Ns * Ns, j1 = rem / Ns, j2 = rem - j1 * Ns;
+    if (c0 + c >= P.ncells) continue;
+    float v[kM2];
+#pragma unroll
+    for (int r = 0; r < kM2; ++r) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) acc = fmaf(P.Pf[j1][k1], T[c][k1][j2][r], acc);
+      v[r] = acc;
+    }
+    const float inv = 1.f / v[0];
+    const float uu = v[1] * inv, vv = v[2] * inv;
+    const float pp = gm1f * (v[3] - 0.5f * (v[1] * uu + v[2] * vv));
+    float lt;
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[3])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
+      lt = __int_as_float(0x7f800000);  // doubtful: always evaluated in FP64
+    } else {
+      const float cs = sqrtf(gf * pp * inv);
+      lt = fmaxf((fabsf(uu) + cs) * ihx, (fabsf(vv) + cs) * ihy);
+    }
+    LT[c][rem] = lt;
+    lt_loc = fmaxf(lt_loc, lt);
+  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
+  if (tid == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  const float cut = s_cut;
   double lmax = 0.0;
   bool bad = false;
   for (int it = tid; it < CPB * Ns * Ns; it += C::THREADS) {
     const int c = it / (Ns * Ns), rem = it - c * Ns * Ns, j1 = rem / Ns, j2 = rem - j1 * Ns;
-    if ((long long)blockIdx.x * CPB + c >= P.ncells) continue;
+    if (c0 + c >= P.ncells || !(LT[c][rem] >= cut)) continue;
+    // the subcell average in FP64 by the separable sums (eta, then xi)
     double v[kM2];
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
       double acc = 0.0;
 #pragma unroll
-      for (int k1 = 0; k1 < n; ++k1) acc = fma(o.P[j1][k1], T[c][k1][j2][r], acc);
+      for (int k1 = 0; k1 < n; ++k1) {
+        double t = 0.0;
+#pragma unroll
+        for (int k2 = 0; k2 < n; ++k2) t = fma(o.P[j2][k2], U[c][k1 * n + k2][r], t);
+        acc = fma(o.P[j1][k1], t, acc);
+      }
       v[r] = acc;
     }
     const double inv = rcp64(v[0]);

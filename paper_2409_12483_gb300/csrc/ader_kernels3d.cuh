@@ -27,6 +27,8 @@
 //                    confirmation.
 #pragma once
 
+#include <type_traits>
+
 #include "ader_kernels.cuh"  // device helpers, abs_bits, launch parameter structs
 
 namespace ader {
@@ -526,9 +528,17 @@ struct Upd3Cfg {
   static constexpr int CPB = NNN >= T ? 1 : T / NNN;  // cells per block
   static constexpr int USED = CPB * NNN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
-  // dynamic shared memory: U [CPB][NNN][5], T1 [CPB][n n][Ns][5], T2 [CPB][n][Ns Ns][5]
-  static constexpr size_t kSmemBytes =
-      (size_t)CPB * (NNN + n * n * Ns + n * Ns * Ns) * kM3 * sizeof(double);
+  // The screening of lambda_max projects in FP32 throughout for N <= 2; above
+  // that the per-subcell FP64 re-evaluation would cost (n^3 + n^2 + n) 5 FMAs, so
+  // the two separable passes stay FP64 and only the last one is screened.
+  static constexpr bool kScreenAll = N <= 2;
+  // dynamic shared memory: U [CPB][NNN][5] (FP64); T1 [CPB][n n][Ns][5] (along
+  // zeta) and T2 [CPB][n][Ns Ns][5] (along eta), FP32 or FP64 as above; the FP32
+  // subcell speeds LT [CPB][Ns^3]
+  static constexpr size_t kTBytes = kScreenAll ? sizeof(float) : sizeof(double);
+  static constexpr size_t kSmemBytes = (size_t)CPB * NNN * kM3 * sizeof(double) +
+                                       (size_t)CPB * (n * n * Ns + n * Ns * Ns) * kM3 * kTBytes +
+                                       (size_t)CPB * Ns * Ns * Ns * sizeof(float);
 };
 
 // u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}, one
@@ -542,9 +552,6 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
   constexpr int n = N + 1, NNN = n * n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred3Cfg<N>::REC;
   extern __shared__ __align__(16) double dsm[];
   auto U = reinterpret_cast<double(*)[NNN][kM3]>(dsm);
-  auto T1 = reinterpret_cast<double(*)[n * n][Ns][kM3]>(dsm + CPB * NNN * kM3);  // along zeta: [k1 k2][j3]
-  auto T2 = reinterpret_cast<double(*)[n][Ns * Ns][kM3]>(
-      dsm + CPB * (NNN + n * n * Ns) * kM3);  // then along eta: [k1][j2 j3]
   __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
   int last;
@@ -580,16 +587,36 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
   if (blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
   if (!P.want_lambda) return;  // uniform
   __syncthreads();
+  // lambda_max of u_new over the Ns^3 subcells, screened as in the 1D interface
+  // kernel: the wave speeds of every subcell in FP32 (FP32 pipes), then FP64
+  // only for the subcells within 1e-3 of the block's FP32 maximum and those
+  // whose FP32 state is doubtful, so the result is the FP64 maximum over every
+  // subcell.  N <= 2 projects in FP32 throughout and re-evaluates a candidate
+  // from u_new; above that the separable passes T1 (zeta) and T2 (eta) stay
+  // FP64 and the screen covers the last (xi) pass and the speeds.
+  __shared__ float s_cut;
   const long long c0 = (long long)blockIdx.x * CPB;
+  const float gf = (float)P.gamma, gm1f = (float)P.gm1;
+  const float ihx = (float)P.sp.inv_dx, ihy = (float)P.inv_dy, ihz = (float)P.inv_dz;
+  constexpr bool kAll = C::kScreenAll;
+  using TT = typename std::conditional<kAll, float, double>::type;
+  TT* T1 = reinterpret_cast<TT*>(dsm + CPB * NNN * kM3);  // [CPB][n n][Ns][5]
+  TT* T2 = T1 + CPB * n * n * Ns * kM3;                    // [CPB][n][Ns Ns][5]
+  float* LT = reinterpret_cast<float*>(T2 + CPB * n * Ns * Ns * kM3);  // [CPB][Ns^3]
   for (int it = tid; it < CPB * n * n * Ns; it += C::THREADS) {
     const int c = it / (n * n * Ns), rem = it - c * n * n * Ns, kk = rem / Ns, j3 = rem - kk * Ns;
     if (c0 + c >= P.ncells) continue;
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
-      double acc = 0.0;
+      TT acc = TT(0);
 #pragma unroll
-      for (int k3 = 0; k3 < n; ++k3) acc = fma(o.P[j3][k3], U[c][kk * n + k3][r], acc);
-      T1[c][kk][j3][r] = acc;
+      for (int k3 = 0; k3 < n; ++k3) {
+        if constexpr (kAll)
+          acc = fmaf(P.Pf[j3][k3], d2f_trunc(U[c][kk * n + k3][r]), acc);
+        else
+          acc = fma(o.P[j3][k3], U[c][kk * n + k3][r], acc);
+      }
+      T1[((c * n * n + kk) * Ns + j3) * kM3 + r] = acc;
     }
   }
   __syncthreads();
@@ -599,25 +626,85 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
     if (c0 + c >= P.ncells) continue;
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
-      double acc = 0.0;
+      TT acc = TT(0);
 #pragma unroll
-      for (int k2 = 0; k2 < n; ++k2) acc = fma(o.P[j2][k2], T1[c][k1 * n + k2][j3][r], acc);
-      T2[c][k1][jj][r] = acc;
+      for (int k2 = 0; k2 < n; ++k2) {
+        if constexpr (kAll)
+          acc = fmaf(P.Pf[j2][k2], T1[((c * n * n + k1 * n + k2) * Ns + j3) * kM3 + r], acc);
+        else
+          acc = fma(o.P[j2][k2], T1[((c * n * n + k1 * n + k2) * Ns + j3) * kM3 + r], acc);
+      }
+      T2[((c * n + k1) * Ns * Ns + jj) * kM3 + r] = acc;
     }
   }
   __syncthreads();
-  double lmax = 0.0;
-  bool bad = false;
+  float lt_loc = 0.f;
   for (int it = tid; it < CPB * Ns * Ns * Ns; it += C::THREADS) {
     const int c = it / (Ns * Ns * Ns), rem = it - c * Ns * Ns * Ns, j1 = rem / (Ns * Ns),
               jj = rem - j1 * Ns * Ns;
     if (c0 + c >= P.ncells) continue;
+    float v[kM3];
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k1 = 0; k1 < n; ++k1) {
+        const TT t = T2[((c * n + k1) * Ns * Ns + jj) * kM3 + r];
+        if constexpr (kAll)
+          acc = fmaf(P.Pf[j1][k1], t, acc);
+        else
+          acc = fmaf(P.Pf[j1][k1], d2f_trunc(t), acc);
+      }
+      v[r] = acc;
+    }
+    const float inv = 1.f / v[0];
+    const float vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
+    const float pp = gm1f * (v[4] - 0.5f * (v[1] * vx + v[2] * vy + v[3] * vz));
+    float lt;
+    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[4])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
+      lt = __int_as_float(0x7f800000);  // doubtful: always evaluated in FP64
+    } else {
+      const float cs = sqrtf(gf * pp * inv);
+      lt = fmaxf(fmaxf((fabsf(vx) + cs) * ihx, (fabsf(vy) + cs) * ihy), (fabsf(vz) + cs) * ihz);
+    }
+    LT[it] = lt;
+    lt_loc = fmaxf(lt_loc, lt);
+  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
+  if (tid == 0) {
+    const float m = __uint_as_float((unsigned)fm);
+    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
+  }
+  __syncthreads();
+  const float cut = s_cut;
+  double lmax = 0.0;
+  bool bad = false;
+  for (int it = tid; it < CPB * Ns * Ns * Ns; it += C::THREADS) {
+    const int c = it / (Ns * Ns * Ns), rem = it - c * Ns * Ns * Ns, j1 = rem / (Ns * Ns),
+              jj = rem - j1 * Ns * Ns, j2 = jj / Ns, j3 = jj - j2 * Ns;
+    if (c0 + c >= P.ncells || !(LT[it] >= cut)) continue;
+    // the subcell average in FP64 by the separable sums (zeta, eta, then xi)
     double v[kM3];
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
       double acc = 0.0;
 #pragma unroll
-      for (int k1 = 0; k1 < n; ++k1) acc = fma(o.P[j1][k1], T2[c][k1][jj][r], acc);
+      for (int k1 = 0; k1 < n; ++k1) {
+        double t2;
+        if constexpr (kAll) {
+          t2 = 0.0;
+#pragma unroll
+          for (int k2 = 0; k2 < n; ++k2) {
+            double t1 = 0.0;
+#pragma unroll
+            for (int k3 = 0; k3 < n; ++k3) t1 = fma(o.P[j3][k3], U[c][(k1 * n + k2) * n + k3][r], t1);
+            t2 = fma(o.P[j2][k2], t1, t2);
+          }
+        } else {
+          t2 = T2[((c * n + k1) * Ns * Ns + jj) * kM3 + r];
+        }
+        acc = fma(o.P[j1][k1], t2, acc);
+      }
       v[r] = acc;
     }
     const double inv = rcp64(v[0]);

@@ -163,6 +163,7 @@ struct Face2DParams {
   double inv_dy;
   StepParams sp;
   OpsD ops;
+  float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening pass of lambda_max)
 };
 
 struct Cfl2DParams {
@@ -199,6 +200,7 @@ struct Face3DParams {
   double inv_dy, inv_dz;
   StepParams sp;
   OpsD ops;
+  float Pf[kMaxNs][kMaxN];  // P in FP32 (the screening pass of lambda_max)
 };
 
 struct Cfl3DParams {

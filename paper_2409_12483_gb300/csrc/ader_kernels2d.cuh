@@ -268,10 +268,15 @@ __global__ void __launch_bounds__(256) face2d_kernel(const __grid_constant__ Fac
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  // items run direction-major (dir, cell, k), so a warp takes one direction and
+  // one instantiation of the Rusanov flux
   const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= P.ncells * 2 * n) return;
-  const long long cell = item / (2 * n);
-  const int rem = (int)(item - cell * 2 * n), dir = rem / n, k = rem - dir * n;
+  const long long per_dir = P.ncells * n;
+  if (item >= 2 * per_dir) return;
+  const int dir = (int)(item / per_dir);
+  const long long cell = (item - dir * per_dir) / n;
+  const int k = (int)(item - dir * per_dir - cell * n);
+  const long long out = (cell * 2 + dir) * n + k;  // [cell][dir][k]
   const long long iy = cell / P.nx, ix = cell - iy * P.nx;
   const long long nb = dir == 0 ? iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1)
                                 : (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix;
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(256) face2d_kernel(const __grid_constant__ Fac
   }
   const double h = 0.5 * dt * (dir == 0 ? P.sp.inv_dx : P.inv_dy);
 #pragma unroll
-  for (int r = 0; r < kM2; ++r) P.gface[item * kM2 + r] = h * s[r];
+  for (int r = 0; r < kM2; ++r) P.gface[out * kM2 + r] = h * s[r];
 }
 
 template <int N, int T = 256>  // T: target threads per block (256, or 128 for small meshes)

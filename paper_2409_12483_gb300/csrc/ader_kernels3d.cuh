@@ -484,10 +484,17 @@ __global__ void __launch_bounds__(256) face3d_kernel(const __grid_constant__ Fac
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
+  // items run direction-major (d, cell, pair), so a warp takes one direction and
+  // one instantiation of the Rusanov flux (cell-major items would interleave the
+  // three directions' code paths within a warp)
   const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= P.ncells * 3 * n * n) return;
-  const long long cell = item / (3 * n * n);
-  const int rem = (int)(item - cell * 3 * n * n), d = rem / (n * n), ac = rem - d * n * n;
+  const long long per_dir = P.ncells * n * n;
+  if (item >= 3 * per_dir) return;
+  const int d = (int)(item / per_dir);
+  const long long rem = item - d * per_dir;
+  const long long cell = rem / (n * n);
+  const int ac = (int)(rem - cell * n * n);
+  const long long out = (cell * 3 + d) * (n * n) + ac;  // [cell][dir][pair]
   const long long plane = P.nx * P.ny;
   const long long iz = cell / plane, iy = (cell - iz * plane) / P.nx, ix = cell - iz * plane - iy * P.nx;
   long long nb;
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(256) face3d_kernel(const __grid_constant__ Fac
   }
   const double h = 0.5 * dt * (d == 0 ? P.sp.inv_dx : d == 1 ? P.inv_dy : P.inv_dz);
 #pragma unroll
-  for (int r = 0; r < kM3; ++r) P.gface[item * kM3 + r] = h * s[r];
+  for (int r = 0; r < kM3; ++r) P.gface[out * kM3 + r] = h * s[r];
 }
 
 template <int N, int T = 128>  // T: target threads per block (128, or 64 for small meshes)

@@ -535,10 +535,12 @@ struct Upd3Cfg {
   static constexpr int CPB = NNN >= T ? 1 : T / NNN;  // cells per block
   static constexpr int USED = CPB * NNN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
-  // The screening of lambda_max projects in FP32 throughout for N <= 2; above
-  // that the per-subcell FP64 re-evaluation would cost (n^3 + n^2 + n) 5 FMAs, so
-  // the two separable passes stay FP64 and only the last one is screened.
-  static constexpr bool kScreenAll = N <= 2;
+  // The screening of lambda_max projects in FP32 throughout for N <= 1; above
+  // that the per-subcell FP64 re-evaluation ((n^3 + n^2 + n) 5 FMAs) costs more
+  // than the two separable FP64 passes (measured at N = 2: 15.9 against 17.2 ms
+  // per face + update launch pair on 96^3 cells), so those stay FP64 and only the
+  // last pass is screened.
+  static constexpr bool kScreenAll = N <= 1;
   // dynamic shared memory: U [CPB][NNN][5] (FP64); T1 [CPB][n n][Ns][5] (along
   // zeta) and T2 [CPB][n][Ns Ns][5] (along eta), FP32 or FP64 as above; the FP32
   // subcell speeds LT [CPB][Ns^3]
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
   // kernel: the wave speeds of every subcell in FP32 (FP32 pipes), then FP64
   // only for the subcells within 1e-3 of the block's FP32 maximum and those
   // whose FP32 state is doubtful, so the result is the FP64 maximum over every
-  // subcell.  N <= 2 projects in FP32 throughout and re-evaluates a candidate
+  // subcell.  N <= 1 projects in FP32 throughout and re-evaluates a candidate
   // from u_new; above that the separable passes T1 (zeta) and T2 (eta) stay
   // FP64 and the screen covers the last (xi) pass and the speeds.
   __shared__ float s_cut;

@@ -255,6 +255,58 @@ def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warm
     return out
 
 
+# The headline is the LAST stdout line and carries the contract's keys only;
+# every secondary study is printed on an earlier line of its own.
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                 "roofline", "e2e", "gpu_launches", "clocks", "errors", "cpu_baseline")
+MAX_HEADLINE_BYTES = 4096
+
+
+def headline_line(*, world, steps, warmup, value, ms_per_step, tuning, roofline, e2e, launches,
+                  clocks, errors) -> dict:
+    """The headline JSON object (cpu_baseline is added once it is measured)."""
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": CELLS, "degree": DEGREE,
+                   "time_steps": TIME_STEPS, "parallelism": f"replicas x{world}",
+                   "tuning": {k: tuning[k] for k in ("predict_cells_per_block",
+                                                     "face_cells_per_block", "graph_steps")},
+                   "l2": "flushed (256 MB write) before each timed step; the 14.4 MB state "
+                         "stays L2-resident across the 100 time steps of a step"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "errors": errors,
+    }
+
+
+def print_study(name, fn, *args, out=None):
+    """Run one secondary study and print it as its own compact JSON line
+    ({"study": name, ...}); a study that raises prints its error instead, so the
+    headline that follows is always printed."""
+    out = out or sys.stdout
+    t0 = time.perf_counter()
+    try:
+        body = {"study": name, "result": fn(*args)}
+    except Exception as e:  # noqa: BLE001 -- reported, the bench goes on
+        body = {"study": name, "error": f"{type(e).__name__}: {e}"[:500]}
+    body["seconds"] = round(time.perf_counter() - t0, 2)
+    print(json.dumps(body, separators=(",", ":"), default=float), file=out, flush=True)
+
+
+def print_headline(head: dict, out=None) -> str:
+    """Print the headline as the last line (compact, at most MAX_HEADLINE_BYTES)."""
+    extra = set(head) - set(HEADLINE_KEYS)
+    if extra:
+        raise ValueError(f"headline keys outside the contract: {sorted(extra)}")
+    line = json.dumps(head, separators=(",", ":"), default=float)
+    if len(line) > MAX_HEADLINE_BYTES:
+        raise ValueError(f"headline line is {len(line)} bytes (> {MAX_HEADLINE_BYTES})")
+    print(line, file=out or sys.stdout, flush=True)
+    return line
+
+
 def max_over_ranks(x: float, dist=None, device=None) -> float:
     """Max of a per-rank time over all ranks (identity without a process group)."""
     if dist is None:
@@ -528,37 +580,29 @@ def main():
     launches = sum(p["kernel_launches"] for p in prof)
 
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": CELLS, "degree": DEGREE,
-                       "time_steps": TIME_STEPS, "parallelism": f"replicas x{world}",
-                       "tuning": {k: tuning[k] for k in ("predict_cells_per_block",
-                                                         "face_cells_per_block", "graph_steps")},
-                       "l2": "flushed (256 MB write) before each timed step; the 14.4 MB state "
-                             "stays L2-resident across the 100 time steps of a step"},
-            "roofline": roofline,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clocks.summary(),
-        }
+        head = headline_line(
+            world=world, steps=args.steps, warmup=args.warmup, value=value,
+            ms_per_step=total_ms / args.steps, tuning=tuning, roofline=roofline, e2e=e2e,
+            launches=launches, clocks=clocks.summary(),
+            errors={"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)})
+        studies = []
         if not args.no_variants:
-            line["variants"] = run_variants(args, dev, flush)
+            studies.append(("precision_forms_and_variants", run_variants, (args, dev, flush)))
         if not args.no_serving:
-            line["serving"] = run_serving(dev, args.serving_requests)
+            studies.append(("serving", run_serving, (dev, args.serving_requests)))
         if not args.no_convergence:
-            line["convergence"] = run_convergence(dev)
+            studies.append(("convergence", run_convergence, (dev,)))
         if not args.no_source:
-            line["source_terms"] = run_source(args, dev, flush)
+            studies.append(("source_terms", run_source, (args, dev, flush)))
         if not args.no_limiter:
-            line["limiter"] = run_limiter(args, dev, flush)
+            studies.append(("limiter", run_limiter, (args, dev, flush)))
         if not args.no_source:
-            line["non_conservative"] = run_tracer(args, dev, flush)
+            studies.append(("non_conservative", run_tracer, (args, dev, flush)))
         if not args.no_2d:
-            line["two_d"] = run_2d(args, dev, flush)
-            line["three_d"] = run_3d(args, dev, flush)
-        line["errors"] = {"l1_density_vs_exact": dg_l1_error(ctx, u_last, W.modes4(SEED), t_last)}
+            studies.append(("two_d", run_2d, (args, dev, flush)))
+            studies.append(("three_d", run_3d, (args, dev, flush)))
+        for name, fn, fargs in studies:
+            print_study(name, fn, *fargs)
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
             u_in, u_or, k = cpu_oracle_rate.last
@@ -566,19 +610,19 @@ def main():
             ctx.ader_solve(ug, max_steps=k)
             torch.cuda.synchronize()
             par = float(np.abs(ug.cpu().numpy() - u_or.ravel()).max() / np.abs(u_or).max())
-            line["errors"]["rel_linf_vs_fp64_oracle_after_oracle_steps"] = par
-            line["cpu_baseline"] = {
+            head["errors"]["rel_linf_vs_fp64_oracle_after_oracle_steps"] = par
+            head["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"{steps} time steps of the same 10^5-cell N=5 mesh ({secs:.1f} s, 1 thread)"}
             # the same oracle on all host cores: steps per process sized like the
             # single-thread sample (about 12 s)
             k_all = max(1, min(TIME_STEPS, int(round(steps * 12.0 / max(secs, 1e-3)))))
             r_all, procs, k_all, s_all = cpu_oracle_rate_all_cores(k_all)
-            line["cpu_baseline"]["all_cores"] = {
+            head["cpu_baseline"]["all_cores"] = {
                 "value": r_all, "unit": UNIT, "cores": procs, "kind": "oracle",
                 "sample": f"{procs} processes, each {k_all} time steps of its own copy of the "
                           f"10^5-cell N=5 mesh (slowest {s_all:.1f} s)"}
-        print(json.dumps(line), flush=True)
+        print_headline(head)
     if pg:
         pg.destroy_process_group()
 
@@ -836,8 +880,6 @@ def run_3d(args, dev, flush):
             prev = (nc, err[0])
             out["sine_wave"].append(row)
             del ctx
-    out["paper_cost_table"] = paper_cost_rows(lambda N: Context3D(7, 7, 7, N, device=dev),
-                                              sine3d_state, PAPER_3D_TJIT_7, "7^3", dev)
     st_ = max(2, min(args.steps, 3))
     for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10), (5, 24, 10), (6, 16, 10)):
         ctx = Context3D(nc, nc, nc, N, device=dev, profile=1)
@@ -898,8 +940,6 @@ def run_2d(args, dev, flush):
             prev = (nc, err[0])
             out["sine_wave"].append(row)
             del ctx
-    out["paper_cost_table"] = paper_cost_rows(lambda N: Context2D(16, 16, N, device=dev),
-                                              sine2d_state, PAPER_2D_TJIT_16, "16x16", dev)
     st_ = max(2, min(args.steps, 3))
     for N, nc, ts in ((3, 512, 20), (5, 320, 20), (7, 160, 10)):
         ctx = Context2D(nc, nc, N, device=dev, profile=1)

@@ -398,7 +398,11 @@ ader_status ader_server_totals(const ader_server* srv, int64_t* cell_updates, in
  *     control block is cleared on the stream at the start of each call, but
  *     calls whose work overlaps on the GPU (other streams, other threads) race
  *     on the array: serialise them;
- *   - asynchronous on the stream; launch errors return ADER_ERR_CUDA. */
+ *   - synchronises the stream before returning: it reads back the step's status
+ *     bits from the array and returns ADER_ERR_NOT_CONVERGED when some cell hit
+ *     the Picard iteration cap, ADER_ERR_NONPHYSICAL when some subcell average
+ *     of u_new has rho <= 0 or p <= 0 or is not finite (u_new is written in both
+ *     cases); launch errors return ADER_ERR_CUDA. */
 #define ADER_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 ader_status ader_step_noalloc(ader_ctx* ctx, const double* u_dev, double* u_new_dev, double dt,
                               void* stream);

@@ -503,13 +503,15 @@ class NoAllocStep:
         self._ctx = ctx
         self.state_count = int(L.ader_state_count(ctx))
 
-    def step(self, u, u_new, dt: float, stream=None):
+    def step(self, u, u_new, dt: float, stream=None, allow=()):
+        """One step; synchronises the stream and returns the status (statuses in
+        `allow`, e.g. ADER_ERR_NOT_CONVERGED, are returned instead of raised)."""
         torch = _torch()
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         rc = self._L.ader_step_noalloc(self._ctx, _ptr(u, numel=self.state_count, name="u"),
                                        _ptr(u_new, numel=self.state_count, name="u_new"),
                                        float(dt), C.c_void_p(s))
-        if rc != ADER_OK:
+        if rc != ADER_OK and rc not in allow:
             raise AderError(rc, self._L.ader_last_error(self._ctx).decode())
         return rc
 

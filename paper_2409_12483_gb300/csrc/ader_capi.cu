@@ -1123,6 +1123,27 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
 bool g_noalloc_degree_ready[kMaxDevices][kMaxDeg + 1] = {};
 
+// Bytes of the static scratch one step of this context needs: the control
+// block, the traces (DG: with the volume term) and, for WENO-FV, the
+// reconstruction.
+size_t noalloc_need(const ader_ctx* ctx, long long cells) {
+  const size_t per = (size_t)(ctx->scheme == ADER_SCHEME_DG ? 3 : 2) * ctx->M * ctx->n;
+  const size_t trace_bytes = (size_t)cells * per * sizeof(double);
+  const size_t wrec_bytes =
+      ctx->scheme == ADER_SCHEME_WENO_FV ? (size_t)cells * ctx->n * kM * sizeof(double) : 0;
+  return kNoallocCtlBytes + align_up(trace_bytes) + wrec_bytes;
+}
+
+// The largest mesh noalloc_need() accepts, from the same expression (bisection).
+long long noalloc_max_cells(const ader_ctx* ctx) {
+  long long lo = 0, hi = (long long)(kNoallocBytes / sizeof(double)) + 1;
+  while (hi - lo > 1) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (noalloc_need(ctx, mid) <= kNoallocBytes) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // Per-device set-up, with that device current: look up the scratch address and
 // raise the predictor's dynamic shared-memory limit for this degree.
 ader_status noalloc_setup(ader_ctx* ctx, int N, void** out) {
@@ -1159,16 +1180,13 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
   if (ctx->opt.limiter)
     return fail(ctx, ADER_ERR_ARG, "the limiter keeps per-cell data in the bound workspace");
   const size_t trace_bytes = trace_doubles(ctx) * sizeof(double);
-  const size_t wrec_bytes =
-      ctx->scheme == ADER_SCHEME_WENO_FV ? (size_t)ctx->mesh.n_cells * ctx->n * kM * sizeof(double) : 0;
-  const size_t need = kNoallocCtlBytes + align_up(trace_bytes) + wrec_bytes;
+  const size_t need = noalloc_need(ctx, ctx->mesh.n_cells);
   if (need > kNoallocBytes) {
-    const long long per_cell = (long long)(3 * ctx->M * ctx->n * sizeof(double));
     return fail(ctx, ADER_ERR_ARG,
                 "mesh of %lld cells needs %zu bytes of scratch; the static scratch holds %zu "
-                "bytes (at most %lld cells at N = %d)",
+                "bytes (at most %lld cells for this scheme at N = %d)",
                 (long long)ctx->mesh.n_cells, need, kNoallocBytes,
-                (long long)((kNoallocBytes - kNoallocCtlBytes - 256) / per_cell), ctx->N);
+                (long long)noalloc_max_cells(ctx), ctx->N);
   }
   void* base = nullptr;
   ader_status st = noalloc_setup(ctx, ctx->N, &base);
@@ -1196,10 +1214,17 @@ extern "C" ader_status ader_step_noalloc(ader_ctx* ctx, const double* u, double*
   PredictParams pp = make_predict(ctx, nodal, sp);
   pp.trace = trace;
   CK(do_predict(ctx->N, pp, s));
-  FaceParams f = make_face(ctx, u, u_new, sp, 0);
+  // lambda_max of u_new is reduced into the static control block only so that a
+  // non-physical result raises the status bit read below; u_new is unchanged by it
+  FaceParams f = make_face(ctx, u, u_new, sp, 1);
   f.trace = trace;
   CK(do_face(ctx->N, f, s));
-  return ADER_OK;
+  // the sticky status bits (Picard cap, non-physical state): read back through a
+  // host variable on the stack, after the kernels, then the stream is drained
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return status_from_flags(ctx, flags);
 }
 
 // ---------------------------------------------------------------------------

@@ -62,3 +62,67 @@ def test_noalloc_rejects_meshes_beyond_the_static_scratch(cuda):
     ok.step(u, out, 1e-7)
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.parametrize("prec,kw", [("fp32", {"fp64_sweeps": 2}), ("ff", {})])
+def test_noalloc_step_other_precisions(cuda, prec, kw):
+    """The FP32-predictor and float-float forms through the no-alloc step equal
+    the same forms through ader_step (same kernels, same inputs)."""
+    import torch
+    from paper_2409_12483_gb300 import Context
+    from paper_2409_12483_gb300.capi import NoAllocStep
+    N, nc = 5, 2011
+    u0 = torch.tensor(_state("dg", N, nc), device=cuda).reshape(-1).contiguous()
+    ref_ctx = Context(nc, N, "dg", precision=prec, **kw)
+    dt = ref_ctx.ader_compute_dt(u0)
+    a_ref = torch.empty_like(u0)
+    ref_ctx.ader_step(u0, a_ref, dt)
+    stepper = NoAllocStep(nc, N, "dg", precision=prec, **kw)
+    a = torch.full_like(u0, float("nan"))
+    b = torch.full_like(u0, float("nan"))
+    stepper.step(u0, a, dt)
+    stepper.step(u0, b, dt)
+    torch.cuda.synchronize()
+    assert rel_linf(a.cpu().numpy(), a_ref.cpu().numpy()) < 1e-12
+    assert rel_linf(b.cpu().numpy(), a_ref.cpu().numpy()) < 1e-12
+
+
+def test_noalloc_reports_the_iteration_cap(cuda):
+    """A step whose Picard iteration hits the cap returns ADER_ERR_NOT_CONVERGED
+    (the state is still written and equals ader_step's); the next, uncapped step
+    on the same static array returns OK again."""
+    import torch
+    from paper_2409_12483_gb300 import ADER_ERR_NOT_CONVERGED, ADER_OK, Context
+    from paper_2409_12483_gb300.capi import NoAllocStep
+    N, nc = 5, 300
+    u0 = torch.tensor(_state("dg", N, nc), device=cuda).reshape(-1).contiguous()
+    capped = dict(picard_max_iter=1, picard_tol=1e-15)
+    ref_ctx = Context(nc, N, "dg", **capped)
+    dt = 4.0 * ref_ctx.ader_compute_dt(u0)
+    a_ref = torch.empty_like(u0)
+    ref_ctx.ader_step(u0, a_ref, dt)
+    assert ref_ctx.ader_get_stats()["status"] == ADER_ERR_NOT_CONVERGED
+    stepper = NoAllocStep(nc, N, "dg", **capped)
+    a = torch.full_like(u0, float("nan"))
+    rc = stepper.step(u0, a, dt, allow=(ADER_ERR_NOT_CONVERGED,))
+    assert rc == ADER_ERR_NOT_CONVERGED
+    assert rel_linf(a.cpu().numpy(), a_ref.cpu().numpy()) < 1e-12
+    ok = NoAllocStep(nc, N, "dg")
+    assert ok.step(u0, a, dt / 4.0) == ADER_OK
+
+
+def test_noalloc_reports_a_nonphysical_result(cuda):
+    """A state with negative pressure in one cell gives ADER_ERR_NONPHYSICAL."""
+    import numpy as np
+    import torch
+    from paper_2409_12483_gb300 import ADER_ERR_NONPHYSICAL
+    from paper_2409_12483_gb300.capi import NoAllocStep
+    N, nc = 3, 64
+    u = _state("dg", N, nc).reshape(nc, N + 1, 3).copy()
+    u[10, :, 2] = 0.5 * u[10, :, 1] ** 2 / u[10, :, 0] - 0.1  # E below the kinetic energy
+    ud = torch.tensor(u, device=cuda).reshape(-1).contiguous()
+    stepper = NoAllocStep(nc, N, "dg")
+    out = torch.empty_like(ud)
+    rc = stepper.step(ud, out, 1e-4, allow=(ADER_ERR_NONPHYSICAL,))
+    assert rc == ADER_ERR_NONPHYSICAL
+    assert np.isfinite(out.cpu().numpy()[: 9 * (N + 1) * 3]).all()

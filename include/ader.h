@@ -262,6 +262,79 @@ ader_status ader_solve_from(ader_ctx* ctx, double* u_dev, double t0, double t_en
 ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t max_steps,
                             int64_t* steps_out, double* t_out);
 
+/* ---------------------------------------------------------------------------
+ * Context-resident state: the mesh-level form of the paper's interface, which
+ * hands the previous solution to get_cell_local_solution(u_prev) (the LST-DG
+ * predictor of one cell, Sec. 1.1, algorithm lst_dg_predictor) and to
+ * get_dg_solution(u_prev) / get_fv_solution(v_prev) (the corrector of Sec. 1.2 /
+ * Sec. 1.3, algorithms ader_dg and ader_weno_fv).  The state lives in the bound
+ * workspace (one more state-sized region, counted by ader_workspace_bytes); a
+ * simulated time t travels with it.  These calls take no state pointers; the
+ * pointer-taking calls above stay the zero-copy path and do not touch it.
+ * ader_bind() of a new workspace forgets the resident state.
+ * ------------------------------------------------------------------------- */
+
+/* Copy a state (ader_state_count() doubles, layout of this header) into the
+ * context and set its time to 0.  on_device = 1: u is a device pointer, copied
+ * on the context's stream (asynchronous); 0: a host pointer (synchronises, so the
+ * buffer may be reused on return).  count must equal ader_state_count(). */
+ader_status ader_set_state(ader_ctx* ctx, const double* u, int64_t count, int on_device);
+/* Copy the resident state out (same conventions; a host copy synchronises).
+ * ADER_ERR_STATE before ader_set_state. */
+ader_status ader_get_state(ader_ctx* ctx, double* u, int64_t count, int on_device);
+/* Simulated time of the resident state (host pointer, written). */
+ader_status ader_get_state_time(ader_ctx* ctx, double* t);
+/* The LST-DG predictor q[cell][p0][p1][r] of the resident state (the
+ * mesh-level get_cell_local_solution): q_dev is a caller-owned DEVICE buffer
+ * of count = ader_predictor_count() doubles; dt > 0 as given, dt <= 0 the CFL
+ * step of Sec. 1.5.  The resident state is not changed.  1D only. */
+ader_status ader_get_predictor(ader_ctx* ctx, double dt, double* q_dev, int64_t count);
+/* Advance the resident state by one time step (predictor, corrector; the
+ * limiter when enabled): dt > 0 as given; dt <= 0 the CFL step of Sec. 1.5 for
+ * the resident state (computed on the device and read back: synchronises).
+ * *dt_out (may be NULL) receives the step used; the resident time advances by
+ * it.  Otherwise asynchronous; the step's status bits land in ader_get_stats. */
+ader_status ader_state_step(ader_ctx* ctx, double dt, double* dt_out);
+/* ader_solve_from on the resident state, from its current time: CFL steps until
+ * t_end (t_end > 0, clipped) or max_steps.  The resident time becomes the time
+ * reached (also on ADER_ERR_NOT_CONVERGED / NONPHYSICAL / TIMEOUT).  Synchronises. */
+ader_status ader_state_solve(ader_ctx* ctx, double t_end, int64_t max_steps, int64_t* steps_out,
+                             double* t_out);
+
+/* ---------------------------------------------------------------------------
+ * Domain decomposition of one periodic 1D mesh over several contexts (one per
+ * GPU or process).  A shard holds the contiguous cells [first_cell, first_cell +
+ * n_local) of the global mesh plus halo_cells copies of its neighbours' cells on
+ * each side, as one array of n_local + 2 halo_cells cells:
+ *   [ left halo | local cells | right halo ],  local cells at cell offset halo_cells.
+ * Halo width: DG 1 (the face neighbour's traces come from its own cell-local
+ * predictor, recomputed here); WENO-FV N + 1 (the neighbour's reconstruction
+ * reaches N cells further).  One time step of the global scheme is then:
+ *   1. fill the halos: the first halo_cells local cells go to the left
+ *      neighbour's right halo, the last ones to the right neighbour's left halo
+ *      (periodic: shard 0's left neighbour is the last shard);
+ *   2. dt = min over shards of ader_compute_dt(ctx, u, t, 0, &dt_shard) (an
+ *      8-byte min-reduction), clipped on the host to t_end - t when t + dt >=
+ *      t_end;
+ *   3. ader_step(ctx, u, u_new, dt) on the whole array.
+ * The local cells of u_new then equal the single-mesh step (same kernels on the
+ * same inputs); the halo cells of u_new are stale until the next fill.  The
+ * device-resident time loops (ader_solve*, ader_state_solve) return
+ * ADER_ERR_ARG on a shard: their time step needs every shard's lambda_max.
+ * Periodic global mesh, no limiter; n_local >= 1 (DG) or >= N (WENO-FV).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t first_cell;       /* global index of the first local cell */
+  int64_t n_local;          /* cells this shard advances */
+  int64_t n_global;         /* cells of the global mesh */
+  int64_t halo_cells;       /* halo cells on each side */
+  int64_t values_per_cell;  /* doubles per cell in the state array */
+} ader_shard;
+ader_status ader_init_shard(const ader_mesh* global_mesh, int64_t first_cell, int64_t n_local,
+                            int degree, int scheme, const ader_options* opt, ader_ctx** out);
+/* Layout of a shard context (ADER_ERR_ARG for a context from ader_init). */
+ader_status ader_shard_info(const ader_ctx* ctx, ader_shard* out);
+
 /* Statistics of the last predictor/solve call (synchronises). */
 ader_status ader_get_stats(ader_ctx* ctx, ader_stats* out);
 

@@ -68,6 +68,11 @@ class Stats(C.Structure):
                 ("troubled_cells", C.c_int64)]
 
 
+class ShardInfo(C.Structure):
+    _fields_ = [("first_cell", C.c_int64), ("n_local", C.c_int64), ("n_global", C.c_int64),
+                ("halo_cells", C.c_int64), ("values_per_cell", C.c_int64)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("predict_cells_per_block", C.c_int), ("face_cells_per_block", C.c_int),
                 ("graph_steps", C.c_int), ("predict_ms", C.c_double), ("face_ms", C.c_double),
@@ -137,6 +142,14 @@ def load(build_if_missing: bool = True):
             "ader_init_3d": ([V, C.c_int, V, V], C.c_int),
             "ader_get_troubled": ([V, V, I64], C.c_int),
             "ader_step_noalloc": ([V, V, V, D, V], C.c_int),
+            "ader_set_state": ([V, V, I64, C.c_int], C.c_int),
+            "ader_get_state": ([V, V, I64, C.c_int], C.c_int),
+            "ader_get_state_time": ([V, P(D)], C.c_int),
+            "ader_get_predictor": ([V, D, V, I64], C.c_int),
+            "ader_state_step": ([V, D, P(D)], C.c_int),
+            "ader_state_solve": ([V, D, I64, P(I64), P(D)], C.c_int),
+            "ader_init_shard": ([P(Mesh), I64, I64, C.c_int, C.c_int, P(Options), P(V)], C.c_int),
+            "ader_shard_info": ([V, P(ShardInfo)], C.c_int),
             "ader_autotune": ([V, V, C.c_int, P(Tuning)], C.c_int),
             "ader_get_tuning": ([V, P(Tuning)], C.c_int),
             "ader_set_tuning": ([V, P(Tuning)], C.c_int),
@@ -167,7 +180,9 @@ def exported_symbols():
             "ader_compute_dt", "ader_predict", "ader_correct", "ader_step",
             "ader_weno_reconstruct", "ader_solve", "ader_solve_host", "ader_solve_from",
             "ader_get_stats", "ader_get_troubled", "ader_init_2d", "ader_init_3d",
-            "ader_step_noalloc", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
+            "ader_step_noalloc", "ader_set_state", "ader_get_state", "ader_get_state_time",
+            "ader_get_predictor", "ader_state_step", "ader_state_solve", "ader_init_shard",
+            "ader_shard_info", "ader_autotune", "ader_get_tuning", "ader_set_tuning",
             "ader_server_default_options", "ader_server_create",
             "ader_server_destroy", "ader_server_last_error", "ader_server_request_bytes",
             "ader_server_submit", "ader_server_progress", "ader_server_poll",
@@ -225,13 +240,16 @@ class Context:
         mesh = Mesh(self.n_cells, float(x0), float(x1))
         self.options = default_options(**options)
         ctx = C.c_void_p()
-        rc = L.ader_init(C.byref(mesh), self.degree, SCHEMES[scheme], C.byref(self.options),
-                         C.byref(ctx))
+        rc = self._create(L, mesh, ctx)
         if rc != ADER_OK:
             raise AderError(rc, f"ader_init failed ({L.ader_status_string(rc).decode()})")
         self._ctx = ctx
         self._bind_workspace(device)
         self.vars = SYSTEM_VARS[self.options.system] if scheme == "dg" else 3
+
+    def _create(self, L, mesh, ctx):
+        return L.ader_init(C.byref(mesh), self.degree, SCHEMES[self.scheme], C.byref(self.options),
+                           C.byref(ctx))
 
     def _bind_workspace(self, device):
         torch = _torch()
@@ -385,6 +403,65 @@ class Context:
         self._check(self._L.ader_get_troubled(self._ctx, C.c_void_p(flags.data_ptr()), flags.numel()))
         return flags
 
+    # -- context-resident state --
+    def ader_set_state(self, u):
+        """u: a CUDA tensor (copied on the device) or a host array / CPU tensor."""
+        torch = _torch()
+        if isinstance(u, torch.Tensor) and u.is_cuda:
+            return self._check(self._L.ader_set_state(
+                self._ctx, _ptr(u, numel=self.state_count, name="u"), self.state_count, 1))
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(u.cpu() if isinstance(u, torch.Tensor) else u,
+                                            dtype=np.float64).ravel())
+        if a.size != self.state_count:
+            raise ValueError(f"state has {a.size} values, expected {self.state_count}")
+        return self._check(self._L.ader_set_state(self._ctx, a.ctypes.data_as(C.c_void_p),
+                                                  a.size, 0))
+
+    def ader_get_state(self, out=None, on_device: bool = True):
+        """The resident state: into `out` (a CUDA tensor, or a host numpy array),
+        else a new CUDA tensor (on_device) or numpy array."""
+        torch = _torch()
+        import numpy as np
+        if out is None:
+            out = (torch.empty(self.state_count, dtype=torch.float64, device=self.device)
+                   if on_device else np.empty(self.state_count))
+        if isinstance(out, torch.Tensor):
+            self._check(self._L.ader_get_state(
+                self._ctx, _ptr(out, numel=self.state_count, name="out"), self.state_count, 1))
+        else:
+            if out.dtype != np.float64 or out.size != self.state_count or not out.flags.c_contiguous:
+                raise ValueError("out must be a contiguous float64 array of state_count values")
+            self._check(self._L.ader_get_state(self._ctx, out.ctypes.data_as(C.c_void_p),
+                                               self.state_count, 0))
+        return out
+
+    def ader_get_state_time(self) -> float:
+        t = C.c_double(0.0)
+        self._check(self._L.ader_get_state_time(self._ctx, C.byref(t)))
+        return t.value
+
+    def ader_get_predictor(self, dt: float = 0.0, q=None):
+        torch = _torch()
+        if q is None:
+            q = torch.empty(self.predictor_count, dtype=torch.float64, device=self.device)
+        self._check(self._L.ader_get_predictor(self._ctx, float(dt),
+                                               _ptr(q, numel=self.predictor_count, name="q"),
+                                               self.predictor_count))
+        return q
+
+    def ader_state_step(self, dt: float = 0.0) -> float:
+        used = C.c_double(0.0)
+        self._check(self._L.ader_state_step(self._ctx, float(dt), C.byref(used)))
+        return used.value
+
+    def ader_state_solve(self, t_end: float = 0.0, max_steps: int = 0, allow=()):
+        steps, t = C.c_int64(0), C.c_double(0.0)
+        rc = self._check(self._L.ader_state_solve(self._ctx, float(t_end), int(max_steps),
+                                                  C.byref(steps), C.byref(t)),
+                         ok=(ADER_OK,) + tuple(allow))
+        return steps.value, t.value, rc
+
     def ader_get_stats(self) -> dict:
         s = Stats()
         self._check(self._L.ader_get_stats(self._ctx, C.byref(s)))
@@ -478,6 +555,29 @@ class Context3D(Context):
         Z = self.box[2] / self.nz * (np.arange(self.nz)[:, None, None, None, None, None]
                                      + xi[None, None, None, None, None, :])
         return tuple(np.broadcast_to(A, shape).copy() for A in (X, Y, Z))
+
+
+class ShardContext(Context):
+    """One shard of a periodic global 1D mesh (ader_init_shard): the cells
+    [first_cell, first_cell + n_local) plus `halo` copies of the neighbours'
+    cells on each side, as one state array of n_local + 2 halo cells."""
+
+    def __init__(self, n_global: int, first_cell: int, n_local: int, degree: int,
+                 scheme: str = "dg", x0: float = 0.0, x1: float = 1.0, device=None, **options):
+        self._shard_args = (int(n_global), int(first_cell), int(n_local))
+        self._gx = (float(x0), float(x1))
+        super().__init__(n_local, degree, scheme, x0, x1, device, **options)
+        info = ShardInfo()
+        self._check(self._L.ader_shard_info(self._ctx, C.byref(info)))
+        self.first_cell, self.n_local = info.first_cell, info.n_local
+        self.n_global, self.halo = info.n_global, info.halo_cells
+        self.values_per_cell = info.values_per_cell
+        self.n_cells = self.n_local + 2 * self.halo
+
+    def _create(self, L, mesh, ctx):
+        n_global, first, n_local = self._shard_args
+        return L.ader_init_shard(C.byref(Mesh(n_global, *self._gx)), first, n_local, self.degree,
+                                 SCHEMES[self.scheme], C.byref(self.options), C.byref(ctx))
 
 
 class NoAllocStep:

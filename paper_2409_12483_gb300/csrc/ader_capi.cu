@@ -55,6 +55,13 @@ struct ader_ctx {
   double* wrec = nullptr;
   double* ubuf = nullptr;
   double* hbuf = nullptr;
+  double* sbuf = nullptr;         // the context-resident state (ader_set_state)
+  bool state_set = false;
+  double state_t = 0.0;           // simulated time of the resident state
+  // shard of a periodic global mesh (ader_init_shard): local cells
+  // [shard_first, shard_first + shard_local) held at offset shard_halo
+  long long shard_first = -1, shard_local = 0, shard_global = 0;
+  int shard_halo = 0;
   float* lim_mmf = nullptr;   // limiter: FP32 subcell extrema of u^n and bounds [cell][9]
   Sub1Ops sub1{};             // limiter: degree-1 operators of the subcell scheme
   int* lim_flag = nullptr;    // limiter: troubled flags [cell]
@@ -116,7 +123,7 @@ size_t workspace_bytes(const ader_ctx* c) {
   size_t b = align_up(sizeof(DevCtl));
   b += align_up(trace_doubles(c) * sizeof(double));
   if (c->scheme == ADER_SCHEME_WENO_FV) b += align_up((size_t)c->mesh.n_cells * c->n * kM * 8);
-  b += 2 * align_up((size_t)state_count(c) * sizeof(double));
+  b += 3 * align_up((size_t)state_count(c) * sizeof(double));  // ubuf, hbuf, sbuf
   if (c->dims == 2) b += align_up((size_t)c->mesh.n_cells * 2 * c->n * kM2 * sizeof(double));
   if (c->dims == 3) b += align_up((size_t)c->mesh.n_cells * 3 * c->n * c->n * kM3 * sizeof(double));
   if (c->opt.limiter)
@@ -772,6 +779,9 @@ ader_status ader_bind(ader_ctx* ctx, void* ws, size_t bytes, void* stream) {
   p += align_up((size_t)state_count(ctx) * sizeof(double));
   ctx->hbuf = reinterpret_cast<double*>(p);
   p += align_up((size_t)state_count(ctx) * sizeof(double));
+  ctx->sbuf = reinterpret_cast<double*>(p);
+  p += align_up((size_t)state_count(ctx) * sizeof(double));
+  ctx->state_set = false;  // a new workspace holds no resident state
   if (ctx->dims == 2) {
     ctx->gface2 = reinterpret_cast<double*>(p);
     p += align_up((size_t)ctx->mesh.n_cells * 2 * ctx->n * kM2 * sizeof(double));
@@ -912,6 +922,10 @@ static ader_status solve_impl(ader_ctx* ctx, double* u, double t0, double t_end,
   ader_status st = need_bound(ctx);
   if (st != ADER_OK) return st;
   if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (ctx->shard_first >= 0)
+    return fail(ctx, ADER_ERR_ARG,
+                "a shard's time step needs every shard's lambda_max: advance it with "
+                "ader_compute_dt, a min over shards and ader_step");
   if (!(t_end > 0.0) && max_steps <= 0)
     return fail(ctx, ADER_ERR_ARG, "need t_end > 0 or max_steps > 0");
   if (std::isnan(t_end) || max_steps < 0) return fail(ctx, ADER_ERR_ARG, "bad t_end / max_steps");
@@ -1058,6 +1072,143 @@ ader_status ader_solve_host(ader_ctx* ctx, double* u_host, double t_end, int64_t
   CK(cudaStreamSynchronize(ctx->stream));
   if ((st = join_out(ctx)) != ADER_OK) return st;
   return rs;
+}
+
+// ---- context-resident state (the mesh-level form of the paper's
+// get_cell_local_solution(u_prev) / get_dg_solution(u_prev) of Sec. 1.1, 1.2) ----
+
+ader_status ader_set_state(ader_ctx* ctx, const double* u, int64_t count, int on_device) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (count != state_count(ctx))
+    return fail(ctx, ADER_ERR_ARG, "count %lld != ader_state_count %lld", (long long)count,
+                (long long)state_count(ctx));
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(ctx->sbuf, u, (size_t)count * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));  // the host buffer is free on return
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  ctx->state_set = true;
+  ctx->state_t = 0.0;
+  return ADER_OK;
+}
+
+ader_status ader_get_state(ader_ctx* ctx, double* u, int64_t count, int on_device) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!u) return fail(ctx, ADER_ERR_ARG, "null pointer");
+  if (!ctx->state_set) return fail(ctx, ADER_ERR_STATE, "no resident state (call ader_set_state)");
+  if (count != state_count(ctx))
+    return fail(ctx, ADER_ERR_ARG, "count %lld != ader_state_count %lld", (long long)count,
+                (long long)state_count(ctx));
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(u, ctx->sbuf, (size_t)count * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+  return join_out(ctx);
+}
+
+ader_status ader_get_state_time(ader_ctx* ctx, double* t) {
+  if (!ctx || !t) return ADER_ERR_ARG;
+  if (!ctx->state_set) return fail(ctx, ADER_ERR_STATE, "no resident state (call ader_set_state)");
+  *t = ctx->state_t;
+  return ADER_OK;
+}
+
+ader_status ader_get_predictor(ader_ctx* ctx, double dt, double* q, int64_t count) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!ctx->state_set) return fail(ctx, ADER_ERR_STATE, "no resident state (call ader_set_state)");
+  if (count != ader_predictor_count(ctx))
+    return fail(ctx, ADER_ERR_ARG, "count %lld != ader_predictor_count %lld", (long long)count,
+                (long long)ader_predictor_count(ctx));
+  return ader_predict(ctx, ctx->sbuf, dt, q);
+}
+
+ader_status ader_state_step(ader_ctx* ctx, double dt, double* dt_out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!ctx->state_set) return fail(ctx, ADER_ERR_STATE, "no resident state (call ader_set_state)");
+  if (std::isnan(dt)) return fail(ctx, ADER_ERR_ARG, "dt is NaN");
+  if (!(dt > 0.0) && (st = ader_compute_dt(ctx, ctx->sbuf, ctx->state_t, 0.0, &dt)) != ADER_OK)
+    return st;
+  if ((st = fork_in(ctx)) != ADER_OK) return st;
+  if ((st = reset_ctl(ctx)) != ADER_OK) return st;
+  const StepParams sp = make_step(ctx, kDtFixed, 0, dt, 0.0, 0);
+  if ((st = enqueue_step(ctx, ctx->sbuf, ctx->ubuf, sp, 0)) != ADER_OK) return st;
+  CK(cudaMemcpyAsync(ctx->sbuf, ctx->ubuf, (size_t)state_count(ctx) * sizeof(double),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  if ((st = join_out(ctx)) != ADER_OK) return st;
+  ctx->state_t += dt;
+  if (dt_out) *dt_out = dt;
+  return ADER_OK;
+}
+
+ader_status ader_state_solve(ader_ctx* ctx, double t_end, int64_t max_steps, int64_t* steps_out,
+                             double* t_out) {
+  ader_status st = need_bound(ctx);
+  if (st != ADER_OK) return st;
+  if (!ctx->state_set) return fail(ctx, ADER_ERR_STATE, "no resident state (call ader_set_state)");
+  if (t_end > 0.0 && !(ctx->state_t < t_end))
+    return fail(ctx, ADER_ERR_ARG, "the resident state is already at t = %.17g >= t_end",
+                ctx->state_t);
+  double t = ctx->state_t;
+  int64_t steps = 0;
+  const ader_status rs = solve_impl(ctx, ctx->sbuf, ctx->state_t, t_end, max_steps, &steps, &t);
+  if (rs == ADER_OK || rs == ADER_ERR_NOT_CONVERGED || rs == ADER_ERR_NONPHYSICAL ||
+      rs == ADER_ERR_TIMEOUT)
+    ctx->state_t = t;
+  if (steps_out) *steps_out = steps;
+  if (t_out) *t_out = t;
+  return rs;
+}
+
+// ---- one shard of a periodic global mesh (multi-GPU decomposition) ----
+
+ader_status ader_init_shard(const ader_mesh* global, int64_t first_cell, int64_t n_local,
+                            int degree, int scheme, const ader_options* opt, ader_ctx** out) {
+  if (!out) return ADER_ERR_ARG;
+  *out = nullptr;
+  if (!global || global->n_cells <= 0 || !(global->x1 > global->x0)) return ADER_ERR_ARG;
+  if (first_cell < 0 || n_local <= 0 || first_cell + n_local > global->n_cells) return ADER_ERR_ARG;
+  ader_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    ader_default_options(&o);
+  }
+  if (o.bc != ADER_BC_PERIODIC || o.limiter != 0) return ADER_ERR_ARG;
+  // halo: DG needs the face neighbour's cell only (its predictor is cell-local);
+  // WENO-FV needs the neighbour's reconstruction too, whose stencil reaches N
+  // cells further: N + 1 cells
+  const int H = scheme == ADER_SCHEME_DG ? 1 : degree + 1;
+  const int64_t min_local = scheme == ADER_SCHEME_DG ? 1 : degree;
+  if (n_local < min_local) return ADER_ERR_ARG;
+  const double dx = (global->x1 - global->x0) / (double)global->n_cells;
+  ader_mesh m{n_local + 2 * H, global->x0 + dx * (double)(first_cell - H), 0.0};
+  m.x1 = m.x0 + dx * (double)m.n_cells;
+  ader_ctx* c = nullptr;
+  const ader_status st = ader_init(&m, degree, scheme, &o, &c);
+  if (st != ADER_OK) return st;
+  c->dx = dx;  // the global mesh's spacing, bit for bit
+  c->shard_first = first_cell;
+  c->shard_local = n_local;
+  c->shard_global = global->n_cells;
+  c->shard_halo = H;
+  *out = c;
+  return ADER_OK;
+}
+
+ader_status ader_shard_info(const ader_ctx* ctx, ader_shard* out) {
+  if (!ctx || !out) return ADER_ERR_ARG;
+  if (ctx->shard_first < 0) return ADER_ERR_ARG;
+  out->first_cell = ctx->shard_first;
+  out->n_local = ctx->shard_local;
+  out->n_global = ctx->shard_global;
+  out->halo_cells = ctx->shard_halo;
+  out->values_per_cell = state_count(ctx) / ctx->mesh.n_cells;
+  return ADER_OK;
 }
 
 ader_status ader_get_troubled(ader_ctx* ctx, int32_t* flags, int64_t count) {
@@ -1340,6 +1491,7 @@ extern "C" ader_status ader_autotune(ader_ctx* ctx, const double* u, int reps, a
   const int prof_saved = ctx->opt.profile;
   ctx->opt.profile = 0;
   for (int K : {4, 8, 16, 32, 64}) {
+    if (ctx->shard_first >= 0) break;  // a shard has no device-resident time loop
     ctx->tune.graph_steps = K;
     if (ctx->gexec) {
       cudaGraphExecDestroy(ctx->gexec);

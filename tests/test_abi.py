@@ -341,3 +341,65 @@ def test_tracer_system_options(lib):
         bad = C.c_void_p()
         assert lib.ader_init(C.byref(Mesh(10, 0.0, 1.0)), 4 if scheme else 3, scheme,
                              C.byref(default_options(**kw)), C.byref(bad)) == 1, kw
+
+
+def test_shard_init_layout_and_validation(lib):
+    """ader_init_shard: halo width (DG 1, WENO-FV N + 1), the extended array's
+    size, its node coordinates equal to the global mesh's, and the rejected
+    configurations (outflow, limiter, blocks smaller than the stencil)."""
+    from paper_2409_12483_gb300.capi import Mesh, ShardInfo, default_options
+    opt = default_options()
+    g = Mesh(40, -1.0, 3.0)
+    for scheme, N, H, per in [(0, 3, 1, 4 * 3), (1, 4, 5, 3), (1, 2, 3, 3)]:
+        ctx = C.c_void_p()
+        assert lib.ader_init_shard(C.byref(g), 10, 17, N, scheme, C.byref(opt), C.byref(ctx)) == 0
+        info = ShardInfo()
+        assert lib.ader_shard_info(ctx, C.byref(info)) == 0
+        assert (info.first_cell, info.n_local, info.n_global, info.halo_cells) == (10, 17, 40, H)
+        assert info.values_per_cell == per
+        assert lib.ader_state_count(ctx) == (17 + 2 * H) * per
+        # coordinates of the extended array = the global mesh's cells 10-H .. 27+H
+        k = per // 3
+        x = np.zeros((17 + 2 * H) * k)
+        assert lib.ader_node_coords(ctx, x.ctypes.data_as(C.c_void_p), x.size) == 0
+        full = C.c_void_p()
+        assert lib.ader_init(C.byref(g), N, scheme, C.byref(opt), C.byref(full)) == 0
+        xg = np.zeros(40 * k)
+        assert lib.ader_node_coords(full, xg.ctypes.data_as(C.c_void_p), xg.size) == 0
+        assert np.allclose(x[:H * k], xg[(10 - H) * k:10 * k], rtol=0, atol=1e-13)
+        assert np.allclose(x[H * k:(17 + H) * k], xg[10 * k:27 * k], rtol=0, atol=1e-13)
+        lib.ader_destroy(full)
+        # a shard has no device-resident time loop; calls that need a workspace say so
+        assert lib.ader_solve(ctx, None, 1.0, 0, None, None) in (1, 7)
+        lib.ader_destroy(ctx)
+    plain = C.c_void_p()
+    assert lib.ader_init(C.byref(g), 3, 0, C.byref(opt), C.byref(plain)) == 0
+    assert lib.ader_shard_info(plain, C.byref(ShardInfo())) == 1
+    lib.ader_destroy(plain)
+    ctx = C.c_void_p()
+    bad = [(g, 35, 10, 3, 0, opt),                         # block beyond the mesh
+           (g, -1, 10, 3, 0, opt), (g, 0, 0, 3, 0, opt),
+           (g, 0, 3, 4, 1, opt),                           # WENO5 block smaller than N
+           (g, 0, 10, 3, 0, default_options(bc=1)),        # outflow
+           (g, 0, 10, 3, 0, default_options(limiter=1))]
+    for mesh, first, nl, N, scheme, o in bad:
+        assert lib.ader_init_shard(C.byref(mesh), first, nl, N, scheme, C.byref(o),
+                                   C.byref(ctx)) == 1, (first, nl, N, scheme)
+        assert not ctx.value
+
+
+def test_resident_state_calls_need_a_workspace(lib):
+    from paper_2409_12483_gb300.capi import Mesh, default_options
+    opt = default_options()
+    ctx = C.c_void_p()
+    assert lib.ader_init(C.byref(Mesh(12, 0.0, 1.0)), 2, 0, C.byref(opt), C.byref(ctx)) == 0
+    u = np.zeros(12 * 3 * 3)
+    ptr = u.ctypes.data_as(C.c_void_p)
+    assert lib.ader_set_state(ctx, ptr, u.size, 0) == 7
+    assert lib.ader_get_state(ctx, ptr, u.size, 0) == 7
+    assert lib.ader_state_step(ctx, 0.1, None) == 7
+    assert lib.ader_state_solve(ctx, 1.0, 0, None, None) == 7
+    assert lib.ader_get_predictor(ctx, 0.1, ptr, 12 * 9 * 3) == 7
+    t = C.c_double(0.0)
+    assert lib.ader_get_state_time(ctx, C.byref(t)) == 7
+    lib.ader_destroy(ctx)

@@ -86,25 +86,35 @@ def test_resident_predictor_matches_oracle(cuda, oracle_mod, N):
 
 
 def test_resident_solve_split_equals_one_solve_and_oracle(cuda, oracle_mod):
+    """A resident solve split by max_steps continues from the resident time and
+    equals one solve bit for bit; a split at an intermediate t_end (which adds a
+    clipped step) matches the oracle split the same way at 1e-10."""
     import torch
     from paper_2409_12483_gb300 import Context
     N, nc = 2, 100
     o = oracle_mod.Oracle(N)
     u = W.nodal_state(W.sine(), o.node_x(nc))
-    ctx = Context(nc, N, "dg")
-    ctx.ader_set_state(u)
-    s1, t1, _ = ctx.ader_state_solve(t_end=0.03)
-    assert t1 == 0.03 and ctx.ader_get_state_time() == 0.03
-    s2, t2, _ = ctx.ader_state_solve(t_end=0.1)
-    assert t2 == 0.1
-    split = ctx.ader_get_state(on_device=False)
     one = Context(nc, N, "dg")
     ud = torch.tensor(u.ravel(), device=cuda)
     steps, t, _ = one.ader_solve(ud, t_end=0.1)
     ref, steps_ref, t_ref, rc = o.solve("dg", u, 1.0 / nc, t_end=0.1)
-    assert steps_ref == steps
-    assert rel_linf(ud.cpu().numpy(), ref) < 1e-10
-    assert rel_linf(split, ref) < 1e-10
+    assert steps_ref == steps and rel_linf(ud.cpu().numpy(), ref) < 1e-10
+    ctx = Context(nc, N, "dg")
+    ctx.ader_set_state(u)
+    s1, t1, _ = ctx.ader_state_solve(max_steps=7)
+    assert s1 == 7 and ctx.ader_get_state_time() == t1
+    s2, t2, _ = ctx.ader_state_solve(t_end=0.1)
+    assert s1 + s2 == steps and t2 == t
+    assert np.array_equal(ctx.ader_get_state(on_device=False), ud.cpu().numpy())
+    # split at t = 0.03: one more (clipped) step on both sides
+    ctx.ader_set_state(u)
+    a1, _, _ = ctx.ader_state_solve(t_end=0.03)
+    assert ctx.ader_get_state_time() == 0.03
+    a2, _, _ = ctx.ader_state_solve(t_end=0.1)
+    r1, b1, _, _ = o.solve("dg", u, 1.0 / nc, t_end=0.03)
+    r2, b2, _, _ = o.solve("dg", r1, 1.0 / nc, t_end=0.1 - 0.03)
+    assert (a1, a2) == (b1, b2)
+    assert rel_linf(ctx.ader_get_state(on_device=False), r2) < 1e-10
     with pytest.raises(Exception):
         ctx.ader_state_solve(t_end=0.05)  # already past it
 

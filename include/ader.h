@@ -54,8 +54,11 @@ typedef enum { ADER_SCHEME_DG = 0, ADER_SCHEME_WENO_FV = 1 } ader_scheme;
 typedef enum {
   ADER_PREC_FP64 = 0,            /* whole path in FP64 */
   ADER_PREC_FP32_PREDICTOR = 1,  /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
-  ADER_PREC_FF_PREDICTOR = 2     /* Picard and predictor epilogue in float-float (~48 bits,
+  ADER_PREC_FF_PREDICTOR = 2,    /* Picard and predictor epilogue in float-float (~48 bits,
                                     FP32 pipes); corrector and CFL in FP64 */
+  ADER_PREC_FP32_FF_SWEEPS = 3   /* Picard in FP32 (to fp32_tol), then fp64_sweeps sweeps and
+                                    the predictor epilogue in float-float (FP64-grade accuracy
+                                    on the FP32 pipes); corrector and CFL in FP64 */
 } ader_precision;
 
 /* The system of conservation laws.
@@ -96,7 +99,9 @@ typedef struct {
   int picard_max_iter;    /* iteration cap in tolerance mode; 0 = 4(N+1)+8 */
   int picard_fixed_iter;  /* > 0: exactly this many iterations, no early exit */
   int precision;          /* ader_precision */
-  int fp64_sweeps;        /* FP64 Picard sweeps after the FP32 stage (>= 1) */
+  int fp64_sweeps;        /* sweeps after the FP32 stage (>= 1): FP64 sweeps for
+                             ADER_PREC_FP32_PREDICTOR, float-float sweeps for
+                             ADER_PREC_FP32_FF_SWEEPS */
   double fp32_tol;        /* FP32 stage tolerance (relative, as picard_tol) (1e-6) */
   int profile;            /* 1: ader_solve records CUDA events around every kernel of every
                              step on the stream it launches them on (graph event nodes) and
@@ -392,7 +397,7 @@ typedef struct {
   int max_slots;            /* solves resident at once (>= 1) */
   int ticks_per_round;      /* time steps per graph replay (even, >= 2) */
   int precision;            /* ader_precision of every solve's predictor */
-  int fp64_sweeps;          /* FP64 sweeps after the FP32 stage (precision 1) */
+  int fp64_sweeps;          /* sweeps after the FP32 stage (precision 1: FP64, 3: float-float) */
   double gamma, cfl;        /* shared physics / CFL (1.4, 0.4) */
   double picard_tol;        /* 0 = 1e-13 */
   void* stream;             /* cudaStream_t the server works on (NULL = default) */

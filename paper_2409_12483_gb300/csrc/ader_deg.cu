@@ -63,6 +63,9 @@ cudaError_t prepare_cpb() {
     e = cudaFuncSetAttribute(predict_kernel<D, 1, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(predict_kernel<D, 3, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(predict_kernel<D, 2, CPB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   }
@@ -80,6 +83,8 @@ cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
       predict_kernel<D, 1, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else if (p.prec == 2 && !p.from_q)
       predict_kernel<D, 2, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else if (p.prec == 3 && !p.from_q)
+      predict_kernel<D, 3, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else
       predict_kernel<D, 0, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     return cudaGetLastError();
@@ -201,10 +206,12 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
   }
   if ((e = prepare_nc_cpb<16>()) != cudaSuccess) return e;
   if ((e = prepare_nc_cpb<32>()) != cudaSuccess) return e;
-  for (int prec = 0; prec < 3; ++prec) {
+  for (int prec = 0; prec < 4; ++prec) {
     constexpr int T = server_pred_cells(D);
-    auto k = prec == 0 ? predict_multi_kernel<D, 0, T>
-                       : (prec == 1 ? predict_multi_kernel<D, 1, T> : predict_multi_kernel<D, 2, T>);
+    auto k = prec == 0   ? predict_multi_kernel<D, 0, T>
+             : prec == 1 ? predict_multi_kernel<D, 1, T>
+             : prec == 2 ? predict_multi_kernel<D, 2, T>
+                         : predict_multi_kernel<D, 3, T>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)PredCfg<D, T>::kSmemBytes);
     if (e != cudaSuccess) return e;
@@ -336,6 +343,8 @@ cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, co
     predict_multi_kernel<D, 1, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else if (p.prec == 2)
     predict_multi_kernel<D, 2, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+  else if (p.prec == 3)
+    predict_multi_kernel<D, 3, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else
     predict_multi_kernel<D, 0, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   return cudaGetLastError();

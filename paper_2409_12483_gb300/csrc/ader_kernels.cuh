@@ -304,7 +304,8 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
                                               const ff (&kr)[N + 1], const OpsF& of, double* sgd,
                                               unsigned long long (*s_red)[kMaxCpb][2], int lc,
                                               int p0, bool valid, int cap, bool fixed, float tol,
-                                              ff gm1, bool* conv, ff krow) {
+                                              ff gm1, bool* conv, ff krow,
+                                              bool first_from_u = true) {
   constexpr int n = N + 1;
   float2* sg = reinterpret_cast<float2*>(sgd);  // one (hi, lo) pair per double slot
   bool done = !valid;
@@ -319,7 +320,7 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
   while (__syncthreads_or(!done && it < cap)) {
     ++it;
     ff qn[n][kM];
-    if (N >= 1 && it == 1) {
+    if (N >= 1 && first_from_u && it == 1) {
       float2* fcell = sg + (size_t)(lc * n) * kM;
       float2* gcell = sg + (size_t)(CPB * n + lc * n) * kM;
       {
@@ -543,8 +544,9 @@ __device__ __forceinline__ void epilogue_ff(const PredictParams& P, const ff (&q
 // PREC (compile-time, so each form carries only its own state in registers):
 //   0: Picard in FP64;
 //   1: Picard in FP32 followed by P.sweeps FP64 sweeps;
-//   2: Picard in float-float (FP64-accurate, FP32 pipes).
-// The epilogue (traces, volume term) is float-float in form 2 and FP64 otherwise.
+//   2: Picard in float-float (FP64-accurate, FP32 pipes);
+//   3: Picard in FP32 followed by P.sweeps float-float sweeps.
+// The epilogue (traces, volume term) is float-float in forms 2 and 3, FP64 otherwise.
 template <int N, int PREC, int CPB = 32>
 __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileIO& io,
                                              long long tile, double lam, double* smem,
@@ -579,7 +581,7 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
       u_own[r] = src[p0 * kM + r];
-      if constexpr (PREC == 2) {  // the float-float form keeps a (hi, lo) copy
+      if constexpr (PREC >= 2) {  // the float-float forms keep a (hi, lo) copy
         const ff v = d2ff(u_own[r]);
         reinterpret_cast<float2*>(su)[(lc * n + p0) * kM + r] = make_float2(v.hi, v.lo);
       } else {
@@ -623,6 +625,51 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     } else {
       const int stride = (P.dg ? 9 : 6) * n;
       epilogue_ff<N, CPB>(P, qf, u_own, lamf, io.trace + (valid ? cell : 0) * (long long)stride,
+                          valid, lc, p0, smem);
+      epilogue_done = true;
+    }
+  } else if constexpr (PREC == 3) {
+    // FP32 Picard stage from the hi parts of u, then P.sweeps float-float sweeps
+    // from its result (exact in float-float) and the float-float epilogue
+    const SmemRowsFF uff{reinterpret_cast<const float2*>(su) + lc * n * kM};
+    float qf[n][kM], uf[n][kM], krf[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        uf[k][r] = uff.at(k, r).hi;
+        qf[k][r] = uf[k][r];
+      }
+#pragma unroll
+    for (int q0 = 0; q0 < n; ++q0) krf[q0] = (float)(lam * P.ops.kap[p0][q0]);
+    bool conv32;
+    const int cap32 = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+    iters = picard_loop<N, float, CPB>(qf, RegRows<N, float>{uf}, krf, P.opf.kt, P.opf.ksa,
+                                       P.opf.ksb, reinterpret_cast<float*>(sg), s_red, lc, p0, valid,
+                                       cap32, P.fixed_iter > 0, P.tol32, (float)P.gm1, &conv32,
+                                       true, (float)(lam * P.ops.kaprow[p0]));
+    ff qq[n][kM], krff[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int r = 0; r < kM; ++r) qq[k][r] = ff{qf[k][r], 0.0f};
+    const ff lamf = d2ff(lam);
+#pragma unroll
+    for (int q0 = 0; q0 < n; ++q0)
+      krff[q0] = ff_mul(lamf, ff{P.opf.kap[p0][q0], P.opf.kaplo[p0][q0]});
+    bool dummy;
+    iters += picard_loop_ff<N, CPB>(qq, uff, krff, P.opf, sg, s_red, lc, p0, valid, P.sweeps, true,
+                                    (float)P.tol, d2ff(P.gm1), &dummy,
+                                    ff_mul(lamf, ff{P.opf.kaprow[p0], P.opf.kaprowlo[p0]}), false);
+    conv = conv32;
+    if (P.out_mode == kOutQ) {
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) q[k][r] = ff2d(qq[k][r]);
+    } else {
+      const int stride = (P.dg ? 9 : 6) * n;
+      epilogue_ff<N, CPB>(P, qq, u_own, lamf, io.trace + (valid ? cell : 0) * (long long)stride,
                           valid, lc, p0, smem);
       epilogue_done = true;
     }

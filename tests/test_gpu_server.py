@@ -52,13 +52,13 @@ MIX = [(1, 37, 0.02), (2, 100, 0.01), (3, 65, 0.01), (4, 200, 0.004), (5, 33, 0.
        (6, 129, 0.002), (7, 64, 0.003), (5, 300, 0.001)]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "ff"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "ff", "fp32ff"])
 def test_results_equal_alone(cuda, precision):
     """the batched kernels (16-cell predictor tiles, 32-cell face tiles, one graph
     branch per degree) give every solve the result of its own context"""
     from paper_2409_12483_gb300.capi import REQ_DONE, Server
     extra = {"precision": precision}
-    if precision == "fp32":
+    if precision in ("fp32", "fp32ff"):
         extra["fp64_sweeps"] = 2
     srv = Server(pool_bytes=256 << 20, max_slots=16, ticks_per_round=8, **extra)
     ids = []

@@ -297,11 +297,16 @@ __device__ __forceinline__ int picard_loop(T (&q)[N + 1][kM], const UA& uh,
 
 // Picard iteration in float-float arithmetic (about 48 bits, FP32 pipes): the
 // same iteration as picard_loop<N, double>, including the once-per-cell first
-// iteration from q = u.  q, uh, kr, krow are ff; k~ comes from the (kt, ktlo)
-// float tables; the convergence test compares |q' - q| with tol max(1, |q'|).
+// iteration from q = u.  q, uh, krow are ff; k~ comes from the (kt, ktlo) float
+// tables and -(dt/dx) kappa~ from the block's shared table nkr[p0][q0] (hi, lo);
+// the convergence test compares |q' - q| with tol max(1, |q'|).  The two
+// contractions are rolled over one index (k~ over its output row p1, whose
+// result goes to shared memory; kappa~ over q0, accumulating in registers),
+// with the sums in the same order as fully unrolled loops: the loop body stays
+// small enough for the instruction cache.
 template <int N, int CPB = 32>
 __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRowsFF& uh,
-                                              const ff (&kr)[N + 1], const OpsF& of, double* sgd,
+                                              const float2* nkr, const OpsF& of, double* sgd,
                                               unsigned long long (*s_red)[kMaxCpb][2], int lc,
                                               int p0, bool valid, int cap, bool fixed, float tol,
                                               ff gm1, bool* conv, ff krow,
@@ -368,32 +373,47 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
         ff f[n][kM];
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1) euler_flux_ff(q[p1], f[p1], gm1);
+#pragma unroll 1
+        for (int p1 = 0; p1 < n; ++p1) {
+          ff_acc acc[kM];
+#pragma unroll
+          for (int r = 0; r < kM; ++r) acc[r].zero();
+#pragma unroll
+          for (int q1 = 0; q1 < n; ++q1) {
+            const ff a{of.kt[p1][q1], of.ktlo[p1][q1]};
+#pragma unroll
+            for (int r = 0; r < kM; ++r) acc[r].fma_add(a, f[q1][r]);
+          }
+#pragma unroll
+          for (int r = 0; r < kM; ++r) {
+            const ff g = acc[r].get();
+            my_row[p1 * kM + r] = make_float2(g.hi, g.lo);
+          }
+        }
+      }
+      __syncthreads();
+      ff_acc acc[n][kM];
+#pragma unroll
+      for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+        for (int r = 0; r < kM; ++r) acc[p1][r].set(uh.at(p1, r));
+#pragma unroll 1
+      for (int q0 = 0; q0 < n; ++q0) {
+        const float2 k = nkr[p0 * kMaxN + q0];
+        const ff nk{k.x, k.y};
+        const float2* gq = cell_g + (size_t)(q0 * n) * kM;
 #pragma unroll
         for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
           for (int r = 0; r < kM; ++r) {
-            ff_acc acc;
-            acc.zero();
-#pragma unroll
-            for (int q1 = 0; q1 < n; ++q1) acc.fma_add(ff{of.kt[p1][q1], of.ktlo[p1][q1]}, f[q1][r]);
-            const ff g = acc.get();
-            my_row[p1 * kM + r] = make_float2(g.hi, g.lo);
+            const float2 g = gq[p1 * kM + r];
+            acc[p1][r].fma_add(nk, ff{g.x, g.y});
           }
       }
-      __syncthreads();
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
-          ff_acc acc;
-          acc.set(uh.at(p1, r));
-#pragma unroll
-          for (int q0 = 0; q0 < n; ++q0) {
-            const float2 g = cell_g[(q0 * n + p1) * kM + r];
-            acc.fma_add(ff{-kr[q0].hi, -kr[q0].lo}, ff{g.x, g.y});
-          }
-          qn[p1][r] = acc.get();
-        }
+        for (int r = 0; r < kM; ++r) qn[p1][r] = acc[p1][r].get();
     }
     if (!done && !fixed) {
       unsigned long long dmax = 0ull, qmax = 0ull;
@@ -453,6 +473,7 @@ struct PredShared {
   int go;
   double kr[kMaxN][kMaxN];  // (dt/dx) kappa~ of the current tile's time step
   double krow[kMaxN];       // (dt/dx) tau (row sums of kappa~)
+  float2 nkrf[kMaxN][kMaxN];  // float-float forms: -(dt/dx) kappa~ as (hi, lo)
 };
 
 // The predictor's time-step decision (a division and the clipping to t_end) made
@@ -512,31 +533,40 @@ __device__ __forceinline__ void epilogue_ff(const PredictParams& P, const ff (&q
     for (int r = 0; r < kM; ++r) my_row[p1 * kM + r] = make_float2(F[r].hi, F[r].lo);
   }
   __syncthreads();
-  // fbar[p0] = (dt/dx) sum_l0 w_l0 F(q[l0][p0])
+  // fbar[p0] = (dt/dx) sum_l0 w_l0 F(q[l0][p0])  (rolled over l0)
+  {
+    ff_acc s[kM];
 #pragma unroll
-  for (int r = 0; r < kM; ++r) {
-    ff_acc s;
-    s.zero();
-#pragma unroll
+    for (int r = 0; r < kM; ++r) s[r].zero();
+#pragma unroll 1
     for (int l0 = 0; l0 < n; ++l0) {
-      const float2 f = sg[((lc * n + l0) * n + p0) * kM + r];
-      s.fma_add(ff{of.w[l0], of.wlo[l0]}, ff{f.x, f.y});
+      const ff w{of.w[l0], of.wlo[l0]};
+      const float2* f = sg + ((lc * n + l0) * n + p0) * kM;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) s[r].fma_add(w, ff{f[r].x, f[r].y});
     }
-    const ff fb = ff_mul(s.get(), lam);
-    sfb[(lc * n + p0) * kM + r] = make_float2(fb.hi, fb.lo);
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      const ff fb = ff_mul(s[r].get(), lam);
+      sfb[(lc * n + p0) * kM + r] = make_float2(fb.hi, fb.lo);
+    }
   }
   __syncthreads();
-  // u_k + (sum_l D~_kl fbar_l) / w_k for k = p0
+  // u_k + (sum_l D~_kl fbar_l) / w_k for k = p0  (rolled over l)
+  {
+    ff_acc acc[kM];
 #pragma unroll
-  for (int r = 0; r < kM; ++r) {
-    ff_acc acc;
-    acc.zero();
-#pragma unroll
+    for (int r = 0; r < kM; ++r) acc[r].zero();
+#pragma unroll 1
     for (int l = 0; l < n; ++l) {
-      const float2 f = sfb[(lc * n + l) * kM + r];
-      acc.fma_add(ff{of.vt[p0][l], of.vtlo[p0][l]}, ff{f.x, f.y});
+      const ff v{of.vt[p0][l], of.vtlo[p0][l]};
+      const float2* f = sfb + (lc * n + l) * kM;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) acc[r].fma_add(v, ff{f[r].x, f[r].y});
     }
-    if (valid) dst[2 * n * kM + p0 * kM + r] = u_own[r] + ff2d(acc.get());
+#pragma unroll
+    for (int r = 0; r < kM; ++r)
+      if (valid) dst[2 * n * kM + p0 * kM + r] = u_own[r] + ff2d(acc[r].get());
   }
 }
 
@@ -565,6 +595,13 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
   if constexpr (PREC != 2) {  // (dt/dx) kappa~ once per block (made visible by the barrier below)
     if (tid < n * n) sh.kr[tid / n][tid % n] = lam * P.ops.kap[tid / n][tid % n];
     if (tid < n) sh.krow[tid] = lam * P.ops.kaprow[tid];
+  }
+  if constexpr (PREC >= 2) {  // the same, negated, in float-float
+    if (tid < n * n) {
+      const int a = tid / n, b = tid % n;
+      const ff v = ff_mul(d2ff(lam), ff{P.opf.kap[a][b], P.opf.kaplo[a][b]});
+      sh.nkrf[a][b] = make_float2(-v.hi, -v.lo);
+    }
   }
   if (tid == 0) {
     sh.itmax = 0;
@@ -605,16 +642,14 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
     __syncthreads();
   } else if constexpr (PREC == 2) {
     const SmemRowsFF uf{reinterpret_cast<const float2*>(su) + lc * n * kM};
-    ff qf[n][kM], krf[n];
+    ff qf[n][kM];
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int r = 0; r < kM; ++r) qf[k][r] = uf.at(k, r);
     const ff lamf = d2ff(lam);
-#pragma unroll
-    for (int q0 = 0; q0 < n; ++q0) krf[q0] = ff_mul(lamf, ff{P.opf.kap[p0][q0], P.opf.kaplo[p0][q0]});
     const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
-    iters = picard_loop_ff<N, CPB>(qf, uf, krf, P.opf, sg, s_red, lc, p0, valid, cap,
+    iters = picard_loop_ff<N, CPB>(qf, uf, &sh.nkrf[0][0], P.opf, sg, s_red, lc, p0, valid, cap,
                                    P.fixed_iter > 0, (float)P.tol, d2ff(P.gm1), &conv,
                                    ff_mul(lamf, ff{P.opf.kaprow[p0], P.opf.kaprowlo[p0]}));
     if (P.out_mode == kOutQ) {
@@ -648,17 +683,15 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
                                        P.opf.ksb, reinterpret_cast<float*>(sg), s_red, lc, p0, valid,
                                        cap32, P.fixed_iter > 0, P.tol32, (float)P.gm1, &conv32,
                                        true, (float)(lam * P.ops.kaprow[p0]));
-    ff qq[n][kM], krff[n];
+    ff qq[n][kM];
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int r = 0; r < kM; ++r) qq[k][r] = ff{qf[k][r], 0.0f};
     const ff lamf = d2ff(lam);
-#pragma unroll
-    for (int q0 = 0; q0 < n; ++q0)
-      krff[q0] = ff_mul(lamf, ff{P.opf.kap[p0][q0], P.opf.kaplo[p0][q0]});
     bool dummy;
-    iters += picard_loop_ff<N, CPB>(qq, uff, krff, P.opf, sg, s_red, lc, p0, valid, P.sweeps, true,
+    iters += picard_loop_ff<N, CPB>(qq, uff, &sh.nkrf[0][0], P.opf, sg, s_red, lc, p0, valid,
+                                    P.sweeps, true,
                                     (float)P.tol, d2ff(P.gm1), &dummy,
                                     ff_mul(lamf, ff{P.opf.kaprow[p0], P.opf.kaprowlo[p0]}), false);
     conv = conv32;

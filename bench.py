@@ -460,6 +460,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving benchmark (scaled Poisson stream)")
     ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--serving-max-cells", type=int, default=2048)
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the coarse-mesh convergence sweeps of the four precision forms")
     ap.add_argument("--no-limiter", action="store_true",
@@ -473,6 +474,7 @@ def main():
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
                          "step3d-dg2 (multi-D: warmup + steps time steps of one solve) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
+                         "serving-large (512 requests, cells up to 4096) | "
                          "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -589,7 +591,8 @@ def main():
         if not args.no_variants:
             studies.append(("precision_forms_and_variants", run_variants, (args, dev, flush)))
         if not args.no_serving:
-            studies.append(("serving", run_serving, (dev, args.serving_requests)))
+            studies.append(("serving", run_serving, (dev, args.serving_requests,
+                                                     args.serving_max_cells)))
         if not args.no_convergence:
             studies.append(("convergence", run_convergence, (dev,)))
         if not args.no_source:
@@ -1165,7 +1168,8 @@ def run_variants(args, dev, flush):
 SERVING_NOTE = ("scaled stand-in for the 4096-request stream (cells log-uniform in [64, 65536], "
                 "t_end 0.5: ~2.5e13 cell-updates, days of GPU time): {n} requests, cells "
                 "log-uniform in [64, {cmax}], N ~ U{{1..7}}, rho and p = 1 + 3 modes (amplitudes "
-                "<= 0.1/3), u = 0.5, t_end = {tend}, seed 12483; FP32 predictor + FP64 corrector/CFL")
+                "<= 0.1/3), u = 0.5, t_end = {tend}, seed 12483; FP32 predictor (FP32 Picard + 2 "
+                "float-float sweeps and epilogue) + FP64 corrector/CFL")
 
 
 def serving_stream(n, cmax, tend, seed=SEED):
@@ -1174,14 +1178,23 @@ def serving_stream(n, cmax, tend, seed=SEED):
     return reqs
 
 
-def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
+def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0), ticks=16,
+                tick_sweep=(4, 64)):
     """Continuous-batching server vs the plain per-solve FP64 path on one GPU.
 
     Saturation: every request queued at t = 0.  Open loop: Poisson arrivals at
     fractions of the server's saturation rate, server clock = wall clock.
     Baseline: each request solved alone with ader_solve (FP64) in arrival order;
     its latencies replay the same arrival times on a FIFO single server with the
-    measured per-request service times."""
+    measured per-request service times.
+
+    Latency breakdown per request: queue wait (admitted - arrival), run time
+    (finished - admitted) and the request's own time steps.  Every admitted
+    solve advances one step per tick, so run time ~ steps x tick time: the
+    spread of latencies follows the spread of step counts (cells x (2N+1)),
+    which the p50/p99 of run time per step isolates.  The open loop at 0.8 x
+    saturation is repeated with shorter and longer graph rounds
+    (ticks_per_round in tick_sweep)."""
     import numpy as np
     import torch
 
@@ -1196,9 +1209,9 @@ def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
         del ctx
     pool = sum(Server.request_bytes(r.degree, r.cells) for r in reqs) + (64 << 20)
 
-    def run_server(arrivals):
-        srv = Server(pool_bytes=pool, max_slots=len(reqs), ticks_per_round=16,
-                     precision="fp32", fp64_sweeps=1, device=dev)
+    def run_server(arrivals, tpr=ticks):
+        srv = Server(pool_bytes=pool, max_slots=len(reqs), ticks_per_round=tpr,
+                     precision="fp32ff", fp64_sweeps=2, device=dev)
         ids = [srv.submit(r.degree, st, r.t_end, arrival=a) for r, st, a in zip(reqs, states, arrivals)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1212,18 +1225,26 @@ def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
         res = [srv.poll(i) for i in ids]
         assert all(x["state"] == REQ_DONE for x in res)
         lat = np.array([x["finished"] - x["arrival"] for x in res])
+        wait = np.array([x["admitted"] - x["arrival"] for x in res])
+        steps = np.array([x["steps"] for x in res], dtype=float)
         tot = srv.totals()
         srv.close()
+        run_per_step = (lat - wait) / steps
+        pct = lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+        tot["breakdown"] = {"queue_wait_s": pct(wait), "run_s": pct(lat - wait),
+                            "steps": pct(steps), "run_s_per_step": pct(run_per_step),
+                            "corr_latency_steps": float(np.corrcoef(lat, steps)[0, 1])}
         return wall, lat, tot
 
     wall0, lat0, tot0 = run_server([0.0] * len(reqs))
     sat = len(reqs) / wall0
     out = {"workload": SERVING_NOTE.format(n=n, cmax=cmax, tend=tend),
            "cell_updates": tot0["cell_updates"],
+           "ticks_per_round": ticks,
            "saturation": {"solves_per_s": sat, "cell_updates_per_s": tot0["cell_updates"] / wall0,
                           "makespan_s": wall0, "rounds": tot0["rounds"], "ticks": tot0["ticks"],
                           "kernel_launches": tot0["kernel_launches"]},
-           "open_loop": []}
+           "open_loop": [], "tick_sweep_at_0.8": []}
     # plain per-solve FP64 baseline: service time of every request alone
     service = []
     for r, st in zip(reqs, states):
@@ -1244,7 +1265,7 @@ def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
         rate = frac * sat
         gaps = rng.exponential(1.0 / rate, size=len(reqs))
         arr = np.cumsum(gaps) - gaps[0]
-        wall, lat, _ = run_server(list(arr))
+        wall, lat, tot = run_server(list(arr))
         # FIFO replay of the baseline on the same arrivals
         end, blat = 0.0, []
         for a, sv in zip(arr, service):
@@ -1255,10 +1276,17 @@ def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0)):
         out["open_loop"].append({
             "arrival_rate_frac_of_saturation": frac, "arrival_rate_solves_per_s": rate,
             "server": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                       "solves_per_s": len(reqs) / wall},
+                       "solves_per_s": len(reqs) / wall, "breakdown": tot["breakdown"]},
             "baseline_per_solve_fp64": {"p50_s": float(np.percentile(blat, 50)),
                                         "p99_s": float(np.percentile(blat, 99)),
                                         "solves_per_s": len(reqs) / max(end, 1e-9)}})
+        if frac == 0.8:
+            for tpr in tick_sweep:
+                wall, lat, tot = run_server(list(arr), tpr)
+                out["tick_sweep_at_0.8"].append({
+                    "ticks_per_round": tpr, "p50_s": float(np.percentile(lat, 50)),
+                    "p99_s": float(np.percentile(lat, 99)), "solves_per_s": len(reqs) / wall,
+                    "queue_wait_p99_s": tot["breakdown"]["queue_wait_s"]["p99"]})
     return out
 
 
@@ -1312,6 +1340,9 @@ def run_case(args):
         steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
+        return
+    elif args.case == "serving-large":  # a larger slice of the serving stream
+        print_study("serving_512_requests_cells_to_4096", run_serving, dev, 512, 4096)
         return
     elif args.case == "paper-costs":  # the cost-table comparison alone
         from paper_2409_12483_gb300 import Context2D, Context3D

@@ -174,8 +174,9 @@ ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options
  * L^zeta = kappa~ (x) I (x) I (x) k~ added, x-, y- and z-faces, d = 3):
  *   mesh: nx x ny x nz cells on [x0, x1] x [y0, y1] x [z0, z1];
  *   state u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x,
- *   m_y, m_z, E), FP64; degree 0..6 (N <= 4: one GPU thread per space-time
- *   node; N = 5, 6: one thread per spatial node holding its tau column); the
+ *   m_y, m_z, E), FP64; degree 0..7 (N <= 4: one GPU thread per space-time
+ *   node; N = 5, 6: one thread per spatial node holding its tau column; N = 7:
+ *   a cluster of two CTAs per cell, each holding half of every tau column); the
  *   options and the entry points that accept the context are those of
  *   ader_init_2d. */
 typedef struct {

@@ -515,7 +515,7 @@ class Context2D(Context):
 
 class Context3D(Context):
     """An ader_ctx of the 3D Euler equations on a periodic nx x ny x nz Cartesian
-    mesh (ader_init_3d, degrees 0..6); state [iz][iy][ix][k1][k2][k3][5] with
+    mesh (ader_init_3d, degrees 0..7); state [iz][iy][ix][k1][k2][k3][5] with
     r = (rho, m_x, m_y, m_z, E)."""
 
     def __init__(self, nx: int, ny: int, nz: int, degree: int, box=(1.0, 1.0, 1.0), device=None,

@@ -199,9 +199,14 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
                                   (int)Upd3Cfg<D, 64>::kSmemBytes)) != cudaSuccess)
       return e;
   }
-  if constexpr (D > kMax3DLowDeg && D <= kMax3DDeg) {
+  if constexpr (D > kMax3DLowDeg && D <= kMax3DHiDeg) {
     if ((e = cudaFuncSetAttribute(predict3d_hi_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)Pred3HiCfg<D>::kSmemBytes)) != cudaSuccess)
+      return e;
+  }
+  if constexpr (D > kMax3DHiDeg && D <= kMax3DDeg && Pred3ClCfg<D>::kValid) {
+    if ((e = cudaFuncSetAttribute(predict3d_cl_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Pred3ClCfg<D>::kSmemBytes)) != cudaSuccess)
       return e;
   }
   if ((e = prepare_nc_cpb<16>()) != cudaSuccess) return e;
@@ -283,10 +288,15 @@ cudaError_t ADER_CAT(launch_predict3d_, ADER_DEG)(const Predict3DParams& p, cuda
     else
       predict3d_kernel<D, 256><<<grid_for(p.ncells, B::CPB, 0x7fffffffLL), B::THREADS, 0, s>>>(p);
     return cudaGetLastError();
-  } else if constexpr (D <= kMax3DDeg) {
+  } else if constexpr (D <= kMax3DHiDeg) {
     using C = Pred3HiCfg<D>;
     if (p.ncells <= 0 || p.ncells > 0x7fffffffLL) return cudaErrorInvalidValue;
     predict3d_hi_kernel<D><<<(unsigned)p.ncells, C::THREADS, C::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+  } else if constexpr (D <= kMax3DDeg && Pred3ClCfg<D>::kValid) {
+    using C = Pred3ClCfg<D>;  // two CTAs (one cluster) per cell
+    if (p.ncells <= 0 || p.ncells > 0x3fffffffLL) return cudaErrorInvalidValue;
+    predict3d_cl_kernel<D><<<(unsigned)(2 * p.ncells), C::THREADS, C::kSmemBytes, s>>>(p);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;

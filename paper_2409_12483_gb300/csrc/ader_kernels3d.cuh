@@ -5,7 +5,8 @@
 // the corrector of Sec. 1.2 with x-, y- and z-faces and lambda_max for the time
 // step of Sec. 1.5 with d = 3.  Degrees 0..4: one thread per space-time node
 // ((N+1)^4 <= 625 threads per cell); degrees 5, 6: predict3d_hi_kernel, one
-// thread per spatial node holding its tau column.
+// thread per spatial node holding its tau column; degree 7: predict3d_cl_kernel,
+// a cluster of two CTAs per cell, each holding half of every tau column.
 //
 // State u[cell][k1][k2][k3][r], cell = (iz ny + iy) nx + ix, r = (rho, m_x, m_y,
 // m_z, E).  Trace record per cell (doubles): for d = x, y, z and side = low,
@@ -27,14 +28,18 @@
 //                    confirmation.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "ader_kernels.cuh"  // device helpers, abs_bits, launch parameter structs
 
 namespace ader {
 
+namespace cg = cooperative_groups;
+
 constexpr int kMax3DDeg = kMax3DDegree;
 constexpr int kMax3DLowDeg = 4;  // one thread per space-time node up to here
+constexpr int kMax3DHiDeg = 6;   // one thread per spatial node holding its tau column up to here
 
 // x-, y- and z-fluxes of the 3D Euler equations: F[d][5]
 __device__ __forceinline__ void euler3_flux(const double* U, double (*F)[kM3], double gm1) {
@@ -474,6 +479,233 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
       rec[(6 * NNN + node) * kM3 + r] = acc;
     }
   }
+}
+
+// Degree 7: a cell's space-time tile (4096 nodes x 5 doubles, and as much again
+// for the contracted fluxes g) outgrows one SM's registers and shared memory, so
+// a cluster of two CTAs on two SMs shares it.  Each CTA owns H = n/2 tau rows of
+// every spatial node: one thread per spatial node keeps those rows of q in
+// registers; the rescaled fluxes of its rows pass through the CTA's shared array
+// S for the k~ contractions along xi, eta and zeta (as in predict3d_hi_kernel),
+// and their sum g goes to the CTA's shared array G.  The kappa~ contraction
+// along tau needs all n rows of g: the peer's rows are read through distributed
+// shared memory after a cluster barrier, and the per-cell convergence test
+// reduces both CTAs' maxima the same way, so both take the same decision.
+// Epilogue: each CTA writes the face traces of its own tau rows; the time
+// averages of the fluxes are summed per CTA over its rows, the two partial sums
+// added in a fixed order (rank 0's first), and each CTA forms the volume term
+// of half of the spatial nodes.
+template <int N>
+struct Pred3ClCfg {
+  static constexpr int n = N + 1, NNN = n * n * n, H = n / 2;
+  static constexpr int THREADS = (NNN + 31) / 32 * 32;
+  // G and S: [H][NNN][5] doubles each (80 KB each at N = 7)
+  static constexpr size_t kSmemBytes = 2 * (size_t)H * NNN * kM3 * sizeof(double);
+  static constexpr bool kValid = n % 2 == 0;  // the tau rows split evenly (launched for N = 7)
+};
+
+template <int N>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREADS, 1)
+    predict3d_cl_kernel(const __grid_constant__ Predict3DParams P) {
+  using C = Pred3ClCfg<N>;
+  constexpr int n = N + 1, NNN = C::NNN, H = C::H, REC = Pred3Cfg<N>::REC;
+  extern __shared__ __align__(16) double smem[];
+  double* G = smem;                 // [H][NNN][5] this CTA's rows of g
+  double* S = smem + H * NNN * kM3; // [H][NNN][5] flux exchange, then q, then partial fbar
+  __shared__ unsigned long long red[2][2];  // [iteration parity][max |q'-q|, max |q'|]
+  __shared__ int s_go;
+  __shared__ double s_dt;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned rank = cluster.block_rank();
+  const long long cell = blockIdx.x / 2;
+  const int tid = threadIdx.x;
+  const int row0 = (int)rank * H;
+  if (tid == 0) {
+    double d = 0.0;
+    s_go = predictor_step_dt(P.sp, &d, blockIdx.x == 0) ? 1 : 0;
+    s_dt = d;
+    red[0][0] = red[0][1] = red[1][0] = red[1][1] = 0ull;
+  }
+  __syncthreads();
+  if (!s_go) return;  // uniform over the grid: both CTAs of the cluster leave here
+  const double dt = s_dt;
+  const double lam[3] = {dt * P.sp.inv_dx, dt * P.inv_dy, dt * P.inv_dz};
+  const bool valid = tid < NNN;
+  const int node = valid ? tid : 0;
+  const int p1 = node / (n * n), p2 = (node / n) % n, p3 = node % n;
+  const int stride[3] = {n * n, n, 1};
+  const int pd[3] = {p1, p2, p3};
+  const OpsD& o = P.ops;
+  const double* Gpeer = cluster.map_shared_rank(G, rank ^ 1u);
+  const unsigned long long* redpeer = cluster.map_shared_rank(&red[0][0], rank ^ 1u);
+  double uo[kM3], q[H][kM3];
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) uo[r] = valid ? P.u[(cell * NNN + node) * kM3 + r] : 1.0;
+#pragma unroll
+  for (int i = 0; i < H; ++i)
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) q[i][r] = uo[r];
+  const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
+  for (int it = 0; it < cap; ++it) {
+    // iteration 1 from q = u in every tau row: g is the same for every row
+    // (formed once per CTA) and q'[p0] = u - (sum_m kappa~[p0][m]) g
+    const bool first = it == 0;
+    const int rows = first ? 1 : H;
+    double acc[H][kM3];
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) acc[i][r] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          if (i >= rows) break;
+          double f[kM3];
+          if (d == 0) euler3_flux_dir<0>(q[i], f, P.gm1);
+          if (d == 1) euler3_flux_dir<1>(q[i], f, P.gm1);
+          if (d == 2) euler3_flux_dir<2>(q[i], f, P.gm1);
+#pragma unroll
+          for (int r = 0; r < kM3; ++r) S[(i * NNN + node) * kM3 + r] = lam[d] * f[r];
+        }
+      }
+      __syncthreads();
+      if (valid) {
+        const int base = node - pd[d] * stride[d];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          if (i >= rows) break;
+#pragma unroll
+          for (int r = 0; r < kM3; ++r)
+#pragma unroll
+            for (int m = 0; m < n; ++m)
+              acc[i][r] = fma(o.kt[pd[d]][m], S[(i * NNN + base + m * stride[d]) * kM3 + r], acc[i][r]);
+        }
+      }
+      __syncthreads();
+    }
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        if (i >= rows) break;
+#pragma unroll
+        for (int r = 0; r < kM3; ++r) G[(i * NNN + node) * kM3 + r] = acc[i][r];
+      }
+    }
+    cluster.sync();  // both CTAs' rows of g are complete and visible
+    if (valid) {
+      unsigned long long dmax = 0ull, qm = 0ull;
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) {
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          const int p0 = row0 + i;
+          double sum = 0.0;
+          if (first) {
+            sum = o.kaprow[p0] * G[node * kM3 + r];
+          } else {
+#pragma unroll
+            for (int m = 0; m < n; ++m) {
+              const double* src = (m / H == (int)rank) ? G : Gpeer;
+              sum = fma(o.kap[p0][m], src[((m % H) * NNN + node) * kM3 + r], sum);
+            }
+          }
+          const double qn = uo[r] - sum;
+          dmax = umax64(dmax, abs_bits(qn - q[i][r]));
+          qm = umax64(qm, abs_bits(qn));
+          q[i][r] = qn;
+        }
+      }
+      atomicMax(&red[it & 1][0], dmax);
+      atomicMax(&red[it & 1][1], qm);
+    }
+    cluster.sync();  // the peer has read G; both CTAs' maxima are complete
+    const double delta = bitsd(umax64(red[it & 1][0], redpeer[(it & 1) * 2 + 0]));
+    const double qmax = bitsd(umax64(red[it & 1][1], redpeer[(it & 1) * 2 + 1]));
+    const bool conv = P.fixed_iter > 0 ? it + 1 == P.fixed_iter : delta <= P.tol * fmax(qmax, 1.0);
+    if (tid == 0) {  // the other parity's slots: nobody reads them until the next barrier
+      red[(it + 1) & 1][0] = red[(it + 1) & 1][1] = 0ull;
+    }
+    if (conv || it + 1 == cap) {
+      if (rank == 0 && tid == 0) {
+        if (!conv) atomicOr(&P.sp.ctl->status, kStNotConverged);
+        atomicAdd(&P.sp.ctl->iter_sum, (unsigned long long)(it + 1));
+        atomicAdd((unsigned long long*)&P.sp.ctl->iter_cells, 1ull);
+        atomicMax(&P.sp.ctl->iter_max, it + 1);
+      }
+      break;  // uniform over the cluster
+    }
+  }
+  // epilogue 1: the face traces of this CTA's tau rows, items (i, a, c) x 3 directions
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) S[(i * NNN + node) * kM3 + r] = q[i][r];
+  }
+  __syncthreads();
+  double* rec = P.trace + cell * REC;
+  for (int item = tid; item < 3 * H * n * n; item += C::THREADS) {
+    const int d = item / (H * n * n), rest = item - d * (H * n * n);
+    const int i = rest / (n * n), a = (rest / n) % n, c = rest % n;
+    const int out = (row0 + i) * n * n + a * n + c;  // (l0, a, c)
+    const int base = d == 0 ? a * n + c : d == 1 ? a * n * n + c : a * n * n + c * n;
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double lo = 0.0, hi = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const double x = S[(i * NNN + base + m * stride[d]) * kM3 + r];
+        lo = fma(o.psi0[m], x, lo);
+        hi = fma(o.psi1[m], x, hi);
+      }
+      rec[((d * 2 + 0) * NNN + out) * kM3 + r] = lo;
+      rec[((d * 2 + 1) * NNN + out) * kM3 + r] = hi;
+    }
+  }
+  // epilogue 2: partial time averages of the rescaled fluxes over this CTA's
+  // rows, [d][node][5] in G (the peer finished reading G at the last barrier)
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double fb[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        double f[kM3];
+        if (d == 0) euler3_flux_dir<0>(q[i], f, P.gm1);
+        if (d == 1) euler3_flux_dir<1>(q[i], f, P.gm1);
+        if (d == 2) euler3_flux_dir<2>(q[i], f, P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM3; ++r) fb[r] = fma(o.w[row0 + i], lam[d] * f[r], fb[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) G[(d * NNN + node) * kM3 + r] = fb[r];
+    }
+  }
+  cluster.sync();  // both partial sums are complete
+  // epilogue 3: the volume term of half of the spatial nodes
+  const double* F0 = rank == 0 ? G : Gpeer;  // rank 0's partial sum first
+  const double* F1 = rank == 0 ? Gpeer : G;
+  for (int v = (int)rank * (NNN / 2) + tid; v < ((int)rank + 1) * (NNN / 2) && tid < NNN / 2;
+       v += C::THREADS) {
+    const int vd[3] = {v / (n * n), (v / n) % n, v % n};
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) {
+      double acc = P.u[(cell * NNN + v) * kM3 + r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int base = v - vd[d] * stride[d];
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          const int idx = (d * NNN + base + l * stride[d]) * kM3 + r;
+          acc = fma(o.vt[vd[d]][l], F0[idx] + F1[idx], acc);
+        }
+      }
+      rec[(6 * NNN + v) * kM3 + r] = acc;
+    }
+  }
+  cluster.sync();  // the peer's shared memory stays valid until both are done reading it
 }
 
 // time-integrated rescaled Rusanov flux through the low face of each cell in

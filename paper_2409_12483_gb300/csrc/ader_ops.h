@@ -14,7 +14,7 @@
 namespace ader {
 
 constexpr int kMaxDeg = 7;
-constexpr int kMax3DDegree = 6;           // 3D: registers hold a tau column of (N+1) x 5 doubles
+constexpr int kMax3DDegree = 7;           // 3D: N = 7 splits each tau column over a 2-CTA cluster
 constexpr int kMaxN = kMaxDeg + 1;        // GL nodes per direction
 constexpr int kMaxNs = 2 * kMaxDeg + 1;   // subcells of Sec. 1.4
 constexpr int kMaxH = (kMaxN + 1) / 2;    // half rows of the symmetric k~ form

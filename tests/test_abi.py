@@ -306,7 +306,7 @@ def test_init_2d_options_and_sizes(lib):
 
 
 def test_init_3d_options_and_sizes(lib):
-    """ader_init_3d: degrees 0..6, DG Euler FP64 periodic without limiter; the state
+    """ader_init_3d: degrees 0..7, DG Euler FP64 periodic without limiter; the state
     is nx ny nz (N+1)^3 5 doubles"""
     from paper_2409_12483_gb300.capi import Mesh3D, default_options
     ctx = C.c_void_p()
@@ -315,7 +315,11 @@ def test_init_3d_options_and_sizes(lib):
     assert lib.ader_state_count(ctx) == 24 * 64 * 5
     assert lib.ader_predictor_count(ctx) == 24 * 256 * 5
     lib.ader_destroy(ctx)
-    for deg in (7, -1):
+    ok = C.c_void_p()
+    assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 2, 0, 1, 0, 1, 0, 1)), 7, None, C.byref(ok)) == 0
+    assert lib.ader_state_count(ok) == 8 * 512 * 5
+    lib.ader_destroy(ok)
+    for deg in (8, -1):
         bad = C.c_void_p()
         assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 2, 0, 1, 0, 1, 0, 1)), deg, None,
                                 C.byref(bad)) == 1

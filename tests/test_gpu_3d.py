@@ -1,4 +1,5 @@
-"""GPU parity of the 3D Euler ADER-DG path (ader_init_3d, degrees 0..6:
+"""GPU parity of the 3D Euler ADER-DG path (ader_init_3d, degrees 0..7 (N = 7:
+the two-CTA cluster predictor):
 tensor-product predictor along xi, eta, zeta of Sec. 1.1, x/y/z faces of Sec.
 1.2, d = 3 time step of Sec. 1.5) against the oracle's ob3_* family.  Bar:
 1e-12 relative L-inf per step, 1e-10 after a solve."""
@@ -40,7 +41,7 @@ def to_dev(a):
     return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("N", range(0, 7))
+@pytest.mark.parametrize("N", range(0, 8))
 def test_step_parity(cuda, oracle_mod, N):
     """one step on smooth data, a ragged mesh (partial blocks), unequal spacings"""
     import torch
@@ -60,7 +61,7 @@ def test_step_parity(cuda, oracle_mod, N):
     assert abs(ctx.ader_compute_dt(ud) - dt) < 1e-14 * dt
 
 
-@pytest.mark.parametrize("N", [1, 3, 5])
+@pytest.mark.parametrize("N", [1, 3, 5, 7])
 def test_fixed_iteration_step_parity(cuda, oracle_mod, N):
     import torch
     dims, box = (3, 3, 3), (1.0, 1.0, 1.0)
@@ -119,7 +120,8 @@ def test_sine_wave_errors_equal_the_oracle(cuda, oracle_mod):
     np.testing.assert_allclose(e_gpu, e_ref, rtol=1e-8)
 
 
-@pytest.mark.parametrize("dims,N", [((1, 1, 1), 2), ((1, 2, 3), 1), ((4, 1, 1), 4), ((2, 1, 2), 6)])
+@pytest.mark.parametrize("dims,N", [((1, 1, 1), 2), ((1, 2, 3), 1), ((4, 1, 1), 4), ((2, 1, 2), 6),
+                                    ((1, 1, 1), 7), ((3, 1, 2), 7)])
 def test_degenerate_meshes(cuda, oracle_mod, dims, N):
     """one cell (its own periodic neighbour in every direction) and single lines"""
     import torch
@@ -137,9 +139,9 @@ def test_degenerate_meshes(cuda, oracle_mod, dims, N):
     assert rc == 0 and rel_linf(out.cpu().numpy(), ref) < 1e-12
 
 
-@pytest.mark.parametrize("N,nc", [(3, 64), (6, 16)])
+@pytest.mark.parametrize("N,nc", [(3, 64), (6, 16), (7, 12)])
 def test_full_size_sampled(cuda, oracle_mod, N, nc):
-    """DG N = 3 on 64^3 and N = 6 on 16^3 cells (sizes the 3D throughput lines
+    """DG N = 3 on 64^3, N = 6 on 16^3 and N = 7 on 12^3 cells (sizes the 3D throughput lines
     time), one step with the time step taken on the device: the CFL step equals
     the oracle's and sampled cells (corners, wrap-around faces, random interior)
     equal the oracle's per-cell step."""
@@ -189,3 +191,26 @@ def test_large_block_shapes_sampled(cuda, oracle_mod, N):
     assert rc == 0
     got = out.cpu().numpy().reshape(total, N + 1, N + 1, N + 1, 5)[cells]
     assert rel_linf(got, sel) < 1e-12
+
+
+def test_n7_solve_parity_and_conservation(cuda, oracle_mod):
+    """DG N = 7 (the cluster predictor) through the device time loop: a short
+    solve against the oracle's, and the conserved totals to round-off."""
+    import torch
+    N, dims, box = 7, (2, 2, 2), (1.0, 1.0, 1.0)
+    h = (0.5,) * 3
+    o = oracle_mod.Oracle3D(N)
+    u = smooth_state(o, dims, box, seed=77)
+    ref, steps_ref, t_ref, rc = o.solve(u, dims, h, t_end=0.01)
+    assert rc == 0
+    ctx = make(dims, N)
+    ud = to_dev(u)
+    steps, t, rc = ctx.ader_solve(ud, t_end=0.01)
+    torch.cuda.synchronize()
+    got = ud.cpu().numpy()
+    assert rc == 0 and steps == steps_ref and t == 0.01
+    assert rel_linf(got, ref) < 1e-10
+    wq = o.table("w")
+    n = N + 1
+    tot = lambda V: np.einsum("zyxabcr,a,b,c->r", V.reshape(dims[::-1] + (n, n, n, 5)), wq, wq, wq)
+    np.testing.assert_allclose(tot(got), tot(u), rtol=1e-13, atol=1e-13)

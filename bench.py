@@ -472,7 +472,7 @@ def main():
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
-                         "step3d-dg2 (multi-D: warmup + steps time steps of one solve) | "
+                         "step3d-dg2 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
                          "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells)")
@@ -803,7 +803,8 @@ PAPER_3D_L1 = {(1, 10): 5.24e-2, (1, 15): 1.08e-2, (1, 20): 4.62e-3, (1, 25): 2.
                (3, 10): 2.17e-5, (3, 15): 4.28e-6, (3, 20): 1.35e-6, (3, 25): 5.54e-7,
                (4, 10): 7.69e-7, (4, 15): 1.03e-7, (4, 20): 2.48e-8, (4, 25): 8.16e-9,
                (5, 5): 1.11e-6, (5, 10): 1.67e-8, (5, 15): 1.46e-9, (5, 20): 2.60e-10,
-               (6, 5): 5.24e-8, (6, 10): 4.36e-10, (6, 15): 2.59e-11, (6, 20): 3.49e-12}
+               (6, 5): 5.24e-8, (6, 10): 4.36e-10, (6, 15): 2.59e-11, (6, 20): 3.49e-12,
+               (7, 5): 1.90e-9, (7, 10): 7.14e-12, (7, 15): 2.78e-13, (7, 20): 2.74e-14}
 
 
 # Tables comp_costs_dg_2d / comp_costs_dg_3d (Sec. 3): T_JIT, whole-run CPU
@@ -811,7 +812,7 @@ PAPER_3D_L1 = {(1, 10): 5.24e-2, (1, 15): 1.08e-2, (1, 20): 4.62e-3, (1, 25): 2.
 # limiter admissibility checks every step) for the sine wave to t = 1 on 16^2 and
 # 7^3 cells, printed beside this library's GPU solve time for context only
 PAPER_2D_TJIT_16 = {1: 0.931, 2: 2.10, 3: 3.72, 4: 6.30, 5: 29.5, 6: 78.3, 7: 168.0}
-PAPER_3D_TJIT_7 = {1: 5.20, 2: 12.3, 3: 46.5, 4: 87.4, 5: 170.0, 6: 333.0}
+PAPER_3D_TJIT_7 = {1: 5.20, 2: 12.3, 3: 46.5, 4: 87.4, 5: 170.0, 6: 333.0, 7: 638.0}
 
 
 def paper_cost_rows(make_ctx, state_fn, table, cells_label, dev):
@@ -853,7 +854,7 @@ def sine3d_state(ctx):
 
 
 def run_3d(args, dev, flush):
-    """3D Euler (ader_init_3d, degrees 1..6): the sine-wave advection problem of
+    """3D Euler (ader_init_3d, degrees 1..7): the sine-wave advection problem of
     Sec. 2.1 at the meshes of Table conv_orders_pde_3d to t = 1 through the GPU
     path, and throughput of the 3D solve."""
     import numpy as np
@@ -864,8 +865,8 @@ def run_3d(args, dev, flush):
     # the paper's meshes, the finest ones for N <= 2 only (N = 4 on 25^3 alone
     # takes about two minutes)
     meshes = {1: (10, 15, 20, 25), 2: (10, 15, 20), 3: (10, 15), 4: (10, 15), 5: (5, 10),
-              6: (5, 10)}
-    for N in range(1, 7):
+              6: (5, 10), 7: (5, 10)}
+    for N in range(1, 8):
         prev = None
         for nc in meshes[N]:
             ctx = Context3D(nc, nc, nc, N, device=dev)
@@ -886,7 +887,7 @@ def run_3d(args, dev, flush):
             out["sine_wave"].append(row)
             del ctx
     st_ = max(2, min(args.steps, 3))
-    for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10), (5, 24, 10), (6, 16, 10)):
+    for N, nc, ts in ((2, 96, 10), (3, 64, 10), (4, 40, 10), (5, 24, 10), (6, 16, 10), (7, 12, 10)):
         ctx = Context3D(nc, nc, nc, N, device=dev, profile=1)
         u0 = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
         cells = nc ** 3
@@ -1310,11 +1311,14 @@ def run_case(args):
     elif args.case == "weno5":
         ctx = Context(nc, 4, "fv", device=dev)
         u = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
-    elif args.case in ("step2d-dg5", "step3d-dg2"):
+    elif args.case in ("step2d-dg5", "step3d-dg2", "step3d-dg7"):
         from paper_2409_12483_gb300 import Context2D, Context3D
         if args.case == "step2d-dg5":  # 96^2 cells: 35 MB state
             ctx = Context2D(96, 96, 5, device=dev)
             u = torch.tensor(sine2d_state(ctx).ravel(), device=dev)
+        elif args.case == "step3d-dg7":  # 12^3 cells: 35 MB state, 248 MB traces
+            ctx = Context3D(12, 12, 12, 7, device=dev)
+            u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
         else:  # 96^3 cells: 0.96 GB state
             ctx = Context3D(96, 96, 96, 2, device=dev)
             u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)

@@ -475,6 +475,7 @@ def main():
                          "step3d-dg2 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
+                         "sine-tables (the 2D / 3D sine-wave convergence tables against the paper's) | "
                          "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -853,10 +854,10 @@ def sine3d_state(ctx):
     return np.stack([rho, rho, rho, rho, 1 / 0.4 + 1.5 * rho], -1)  # velocity (1, 1, 1), p = 1
 
 
-def run_3d(args, dev, flush):
-    """3D Euler (ader_init_3d, degrees 1..7): the sine-wave advection problem of
-    Sec. 2.1 at the meshes of Table conv_orders_pde_3d to t = 1 through the GPU
-    path, and throughput of the 3D solve."""
+def run_3d(args, dev, flush, tables=False):
+    """3D Euler (ader_init_3d, degrees 1..7): throughput of the 3D solve and,
+    with tables, the sine-wave advection problem of Sec. 2.1 at the meshes of
+    Table conv_orders_pde_3d to t = 1 through the GPU path."""
     import numpy as np
     import torch
 
@@ -866,7 +867,7 @@ def run_3d(args, dev, flush):
     # takes about two minutes)
     meshes = {1: (10, 15, 20, 25), 2: (10, 15, 20), 3: (10, 15), 4: (10, 15), 5: (5, 10),
               6: (5, 10), 7: (5, 10)}
-    for N in range(1, 8):
+    for N in (range(1, 8) if tables else ()):
         prev = None
         for nc in meshes[N]:
             ctx = Context3D(nc, nc, nc, N, device=dev)
@@ -916,16 +917,17 @@ def sine2d_state(ctx):
     return np.stack([rho, rho, rho, 1 / (g - 1) + rho], -1)  # u = v = 1, p = 1
 
 
-def run_2d(args, dev, flush):
-    """2D Euler (ader_init_2d): the sine-wave advection problem of Sec. 2.1 at
-    the meshes of Table conv_orders_pde_2d to t = 1 through the GPU path (errors,
-    orders, the paper's eps_L1 beside them), and throughput of the 2D solve."""
+def run_2d(args, dev, flush, tables=False):
+    """2D Euler (ader_init_2d): throughput of the 2D solve and, with tables, the
+    sine-wave advection problem of Sec. 2.1 at the meshes of Table
+    conv_orders_pde_2d to t = 1 through the GPU path (errors, orders, the
+    paper's eps_L1 beside them)."""
     import numpy as np
     import torch
 
     from paper_2409_12483_gb300 import Context2D
     out = {"sine_wave": [], "throughput": []}
-    for N in range(1, 8):
+    for N in (range(1, 8) if tables else ()):
         meshes = (10, 15, 20, 25) if N <= 4 else (5, 10, 15, 20)
         prev = None
         for nc in meshes:
@@ -1344,6 +1346,11 @@ def run_case(args):
         steps, t, rc = ctx.ader_solve(u, max_steps=args.warmup + args.steps)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
+        return
+    elif args.case == "sine-tables":  # the 2D and 3D convergence tables of Sec. 2.1
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        print_study("two_d_sine_wave_table", lambda: run_2d(args, dev, flush, True)["sine_wave"])
+        print_study("three_d_sine_wave_table", lambda: run_3d(args, dev, flush, True)["sine_wave"])
         return
     elif args.case == "serving-large":  # a larger slice of the serving stream
         print_study("serving_512_requests_cells_to_4096", run_serving, dev, 512, 4096)

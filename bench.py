@@ -591,6 +591,7 @@ def main():
         studies = []
         if not args.no_variants:
             studies.append(("precision_forms_and_variants", run_variants, (args, dev, flush)))
+            studies.append(("small_meshes_graphs_vs_plain", run_small_meshes, (dev,)))
         if not args.no_serving:
             studies.append(("serving", run_serving, (dev, args.serving_requests,
                                                      args.serving_max_cells)))
@@ -1165,6 +1166,48 @@ def run_variants(args, dev, flush):
             return {"rel_linf_vs_fp64_path": (u - u64).abs().max().item() / u64.abs().max().item()}
         out.append(variant_line(name, desc, c, u0, nc, 7, ts, st, 1, flush, extra=err7))
         del c
+    return out
+
+
+def run_small_meshes(dev, steps_n=2000):
+    """Batching pattern on small meshes, where one step is short: the same
+    ader_solve time loop as device-resident CUDA graphs (autotuned tile shapes
+    and graph length) against one host-launched ader_step per step (device CFL
+    step, default shapes), FP64 and the float-float predictor.  Time per step
+    from the host clock around whole solves (synchronised)."""
+    import torch
+
+    import workloads as W
+    from paper_2409_12483_gb300 import Context
+    out = []
+    for N, nc in ((2, 100), (2, 1000), (5, 1000), (2, 10000), (5, 10000)):
+        for prec in ("fp64", "ff"):
+            ctx = Context(nc, N, "dg", device=dev, precision=prec)
+            u0 = torch.tensor(W.nodal_state(W.sine(), ctx.node_coords()), device=dev).reshape(-1)
+            plain = Context(nc, N, "dg", device=dev, precision=prec)
+            tune = ctx.ader_autotune(u0, reps=3)
+            g = p = 0.0
+            for _ in range(2):  # the second pass is timed
+                u = u0.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx.ader_solve(u, max_steps=steps_n)
+                torch.cuda.synchronize()
+                g = (time.perf_counter() - t0) / steps_n
+                a, b = u0.clone(), torch.empty_like(u0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(steps_n):
+                    plain.ader_step(a, b, 0.0)
+                    a, b = b, a
+                torch.cuda.synchronize()
+                p = (time.perf_counter() - t0) / steps_n
+            out.append({"degree": N, "cells": nc, "precision": prec,
+                        "graph_us_per_step": 1e6 * g, "plain_us_per_step": 1e6 * p,
+                        "graph_speedup": p / g, "graph_cell_updates_per_s": nc / g,
+                        "tuning": {k: tune[k] for k in ("predict_cells_per_block",
+                                                         "face_cells_per_block", "graph_steps")}})
+            del ctx, plain
     return out
 
 

@@ -83,6 +83,8 @@ struct Pred2Shared {
   double A[C::CPB][C::NST][kM2];  // x-fluxes, then the contraction, then q
   double B[C::CPB][C::NST][kM2];  // y-fluxes
   double FB[C::CPB][2][C::NN][kM2];  // time averages of the rescaled fluxes
+  double kd[2][N + 1][N + 1];        // (dt/dx) k~, (dt/dy) k~
+  double nk[N + 1][N + 1];           // -kappa~
   unsigned long long red[C::CPB][2];  // max |q' - q|, max |q'| (bit patterns)
   int done[C::CPB];
   double dt;
@@ -120,6 +122,18 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
     sh.done[lc] = valid ? 0 : 1;
     sh.red[lc][0] = sh.red[lc][1] = 0ull;
   }
+  // the operators with the time-step scalings folded in once per block:
+  // (dt/dx) k~, (dt/dy) k~ and -kappa~ (the fluxes are stored unscaled and
+  // q' = u - kappa~ g is one FMA chain from u); shared tables, because the rows
+  // a thread reads depend on its node
+  for (int i = tid; i < 3 * n * n; i += C::THREADS) {
+    const int d = i / (n * n), a = (i / n) % n, b = i % n;
+    if (d < 2)
+      sh.kd[d][a][b] = (d == 0 ? lx : ly) * o.kt[a][b];
+    else
+      sh.nk[a][b] = -o.kap[a][b];
+  }
+  const double nkrow = -o.kaprow[p0];
   __syncthreads();
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
@@ -135,8 +149,8 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
       euler2_flux(q, F, G, P.gm1);
 #pragma unroll
       for (int r = 0; r < kM2; ++r) {
-        sh.A[lc][node][r] = lx * F[r];
-        sh.B[lc][node][r] = ly * G[r];
+        sh.A[lc][node][r] = F[r];
+        sh.B[lc][node][r] = G[r];
       }
     }
     __syncthreads();
@@ -146,9 +160,9 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
       for (int r = 0; r < kM2; ++r) {
         double acc = 0.0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fma(o.kt[p1][m], sh.A[lc][(p0 * n + m) * n + p2][r], acc);
+        for (int m = 0; m < n; ++m) acc = fma(sh.kd[0][p1][m], sh.A[lc][(p0 * n + m) * n + p2][r], acc);
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fma(o.kt[p2][m], sh.B[lc][(p0 * n + p1) * n + m][r], acc);
+        for (int m = 0; m < n; ++m) acc = fma(sh.kd[1][p2][m], sh.B[lc][(p0 * n + p1) * n + m][r], acc);
         s[r] = acc;
       }
     }
@@ -162,14 +176,14 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
       unsigned long long dmax = 0ull, qm = 0ull;
 #pragma unroll
       for (int r = 0; r < kM2; ++r) {
-        double acc = 0.0;
+        double qn;
         if (first) {
-          acc = o.kaprow[p0] * sh.A[lc][p1 * n + p2][r];  // node (0, p1, p2)
+          qn = fma(nkrow, sh.A[lc][p1 * n + p2][r], uo[r]);  // node (0, p1, p2)
         } else {
+          qn = uo[r];
 #pragma unroll
-          for (int m = 0; m < n; ++m) acc = fma(o.kap[p0][m], sh.A[lc][(m * n + p1) * n + p2][r], acc);
+          for (int m = 0; m < n; ++m) qn = fma(sh.nk[p0][m], sh.A[lc][(m * n + p1) * n + p2][r], qn);
         }
-        const double qn = uo[r] - acc;
         dmax = umax64(dmax, abs_bits(qn - q[r]));
         qm = umax64(qm, abs_bits(qn));
         q[r] = qn;

@@ -98,6 +98,8 @@ struct Pred3Shared {
   using C = Pred3Cfg<N, T>;
   double S[C::CPB][C::NST][kM3];        // one flux direction at a time, then the sum, then q
   double FB[C::CPB][3][C::NNN][kM3];    // time averages of the three rescaled fluxes
+  double kd[3][N + 1][N + 1];           // (dt/h_d) k~ per direction
+  double nk[N + 1][N + 1];              // -kappa~
   unsigned long long red[C::CPB][2];
   int done[C::CPB];
   double dt;
@@ -136,6 +138,16 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
     sh.done[lc] = valid ? 0 : 1;
     sh.red[lc][0] = sh.red[lc][1] = 0ull;
   }
+  // the operators with the time-step scalings folded in once per block: the
+  // fluxes are stored unscaled and q' = u - kappa~ g is one FMA chain from u
+  // (shared tables: the rows a thread reads depend on its node)
+  for (int i = tid; i < 4 * n * n; i += C::THREADS) {
+    const int d = i / (n * n), a = (i / n) % n, b = i % n;
+    if (d < 3)
+      sh.kd[d][a][b] = lam[d] * o.kt[a][b];
+    else
+      sh.nk[a][b] = -o.kap[a][b];
+  }
   __syncthreads();
   // stride of direction d in the space-time node index, and this node's index along d
   const int stride[3] = {n * n, n, 1};
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
     for (int d = 0; d < 3; ++d) {
       if (work) {
 #pragma unroll
-        for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
+        for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = F[d][r];
       }
       __syncthreads();
       if (active && work) {
@@ -163,7 +175,8 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
 #pragma unroll
         for (int r = 0; r < kM3; ++r)
 #pragma unroll
-          for (int m = 0; m < n; ++m) acc[r] = fma(o.kt[pd[d]][m], sh.S[lc][base + m * stride[d]][r], acc[r]);
+          for (int m = 0; m < n; ++m)
+            acc[r] = fma(sh.kd[d][pd[d]][m], sh.S[lc][base + m * stride[d]][r], acc[r]);
       }
       __syncthreads();
     }
@@ -176,14 +189,14 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
       unsigned long long dmax = 0ull, qm = 0ull;
 #pragma unroll
       for (int r = 0; r < kM3; ++r) {
-        double s = 0.0;
+        double qn;
         if (first) {
-          s = o.kaprow[p0] * sh.S[lc][sp_node][r];  // node (0, p1, p2, p3)
+          qn = fma(-o.kaprow[p0], sh.S[lc][sp_node][r], uo[r]);  // node (0, p1, p2, p3)
         } else {
+          qn = uo[r];
 #pragma unroll
-          for (int m = 0; m < n; ++m) s = fma(o.kap[p0][m], sh.S[lc][m * NNN + sp_node][r], s);
+          for (int m = 0; m < n; ++m) qn = fma(sh.nk[p0][m], sh.S[lc][m * NNN + sp_node][r], qn);
         }
-        const double qn = uo[r] - s;
         dmax = umax64(dmax, abs_bits(qn - q[r]));
         qm = umax64(qm, abs_bits(qn));
         q[r] = qn;
@@ -309,6 +322,8 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
   __shared__ unsigned long long red[2];
   __shared__ int s_done, s_go;
   __shared__ double s_dt;
+  __shared__ double kd[3][N + 1][N + 1];  // (dt/h_d) k~: the rows a thread reads depend on its node
+  __shared__ double nk[N + 1][N + 1];     // -kappa~
   const int tid = threadIdx.x;
   if (tid == 0) {
     double d = 0.0;
@@ -328,6 +343,13 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
   const int stride[3] = {n * n, n, 1};
   const int pd[3] = {p1, p2, p3};
   const OpsD& o = P.ops;
+  for (int i = tid; i < 4 * n * n; i += C::THREADS) {
+    const int d = i / (n * n), a = (i / n) % n, b = i % n;
+    if (d < 3)
+      kd[d][a][b] = lam[d] * o.kt[a][b];
+    else
+      nk[a][b] = -o.kap[a][b];
+  }
   double uo[kM3], q[n][kM3];
 #pragma unroll
   for (int r = 0; r < kM3; ++r) uo[r] = valid ? P.u[(cell * NNN + node) * kM3 + r] : 1.0;
@@ -335,6 +357,7 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
   for (int p0 = 0; p0 < n; ++p0)
 #pragma unroll
     for (int r = 0; r < kM3; ++r) q[p0][r] = uo[r];
+  __syncthreads();
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
     // Iteration 1 starts from q = u in every tau row: the fluxes and their
@@ -358,7 +381,7 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
           if (d == 1) euler3_flux_dir<1>(q[p0], f, P.gm1);
           if (d == 2) euler3_flux_dir<2>(q[p0], f, P.gm1);
 #pragma unroll
-          for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = lam[d] * f[r];
+          for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = f[r];
         }
       }
       __syncthreads();
@@ -371,7 +394,7 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
           for (int r = 0; r < kM3; ++r)
 #pragma unroll
             for (int m = 0; m < n; ++m)
-              acc[p0][r] = fma(o.kt[pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+              acc[p0][r] = fma(kd[d][pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
         }
       }
       __syncthreads();
@@ -383,14 +406,15 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
         double qn[n];  // kappa~ along tau needs every acc[.][r] before q[.][r] changes
 #pragma unroll
         for (int p0 = 0; p0 < n; ++p0) {
-          double sum = 0.0;
+          double v;
           if (first) {
-            sum = o.kaprow[p0] * acc[0][r];
+            v = fma(-o.kaprow[p0], acc[0][r], uo[r]);
           } else {
+            v = uo[r];
 #pragma unroll
-            for (int m = 0; m < n; ++m) sum = fma(o.kap[p0][m], acc[m][r], sum);
+            for (int m = 0; m < n; ++m) v = fma(nk[p0][m], acc[m][r], v);
           }
-          qn[p0] = uo[r] - sum;
+          qn[p0] = v;
         }
 #pragma unroll
         for (int p0 = 0; p0 < n; ++p0) {
@@ -515,6 +539,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
   __shared__ unsigned long long red[2][2];  // [iteration parity][max |q'-q|, max |q'|]
   __shared__ int s_go;
   __shared__ double s_dt;
+  __shared__ double kd[3][N + 1][N + 1];  // (dt/h_d) k~: the rows a thread reads depend on its node
+  __shared__ double nk[N + 1][N + 1];     // -kappa~
   cg::cluster_group cluster = cg::this_cluster();
   const unsigned rank = cluster.block_rank();
   const long long cell = blockIdx.x / 2;
@@ -538,6 +564,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
   const OpsD& o = P.ops;
   const double* Gpeer = cluster.map_shared_rank(G, rank ^ 1u);
   const unsigned long long* redpeer = cluster.map_shared_rank(&red[0][0], rank ^ 1u);
+  for (int i = tid; i < 4 * n * n; i += C::THREADS) {
+    const int d = i / (n * n), a = (i / n) % n, b = i % n;
+    if (d < 3)
+      kd[d][a][b] = lam[d] * o.kt[a][b];
+    else
+      nk[a][b] = -o.kap[a][b];
+  }
   double uo[kM3], q[H][kM3];
 #pragma unroll
   for (int r = 0; r < kM3; ++r) uo[r] = valid ? P.u[(cell * NNN + node) * kM3 + r] : 1.0;
@@ -567,7 +600,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
           if (d == 1) euler3_flux_dir<1>(q[i], f, P.gm1);
           if (d == 2) euler3_flux_dir<2>(q[i], f, P.gm1);
 #pragma unroll
-          for (int r = 0; r < kM3; ++r) S[(i * NNN + node) * kM3 + r] = lam[d] * f[r];
+          for (int r = 0; r < kM3; ++r) S[(i * NNN + node) * kM3 + r] = f[r];
         }
       }
       __syncthreads();
@@ -580,7 +613,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
           for (int r = 0; r < kM3; ++r)
 #pragma unroll
             for (int m = 0; m < n; ++m)
-              acc[i][r] = fma(o.kt[pd[d]][m], S[(i * NNN + base + m * stride[d]) * kM3 + r], acc[i][r]);
+              acc[i][r] = fma(kd[d][pd[d]][m], S[(i * NNN + base + m * stride[d]) * kM3 + r], acc[i][r]);
         }
       }
       __syncthreads();
@@ -601,17 +634,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
 #pragma unroll
         for (int i = 0; i < H; ++i) {
           const int p0 = row0 + i;
-          double sum = 0.0;
+          double qn;
           if (first) {
-            sum = o.kaprow[p0] * G[node * kM3 + r];
+            qn = fma(-o.kaprow[p0], G[node * kM3 + r], uo[r]);
           } else {
+            qn = uo[r];
 #pragma unroll
             for (int m = 0; m < n; ++m) {
               const double* src = (m / H == (int)rank) ? G : Gpeer;
-              sum = fma(o.kap[p0][m], src[((m % H) * NNN + node) * kM3 + r], sum);
+              qn = fma(nk[p0][m], src[((m % H) * NNN + node) * kM3 + r], qn);
             }
           }
-          const double qn = uo[r] - sum;
           dmax = umax64(dmax, abs_bits(qn - q[i][r]));
           qm = umax64(qm, abs_bits(qn));
           q[i][r] = qn;

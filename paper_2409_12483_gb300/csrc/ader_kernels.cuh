@@ -958,6 +958,45 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   if (bad) atomicOr(&sp.ctl->status, kStNonPhysical);
 }
 
+// Twice the Rusanov flux (as rusanov2) with the wave speed screened in FP32.
+// The speed s enters 2G = F(a) + F(b) - s (b - a) only through s (b - a).  An
+// FP32 speed from the FP64 u, p and 1/rho (each truncated to FP32: relative
+// error 2^-23; gamma rounded, two products and sqrtf rounded, |u| + c rounded)
+// is within 1e-6 of s relative; where 1e-6 s max|b - a| is below 1e-16 of
+// max|F(a) + F(b)| -- the FP64 evaluation's own rounding level, which is the
+// case wherever the two traces nearly agree (smooth data) -- that speed is
+// used, and elsewhere (jumps, doubtful or non-physical states) the FP64 speeds
+// of rusanov2.  Both sides are checked for rho, p > 0 before the FP32 speed is
+// trusted, so a non-physical state still gives a NaN flux.
+__device__ __forceinline__ void rusanov2_screened(const double* a, const double* b, double* G2,
+                                                  double gamma, double gm1, float gammaf) {
+  const double ia = rcp64(a[0]), ib = rcp64(b[0]);
+  const double ua = a[1] * ia, ub = b[1] * ib;
+  const double pa = gm1 * fma(neg_half(a[1]), ua, a[2]);
+  const double pb = gm1 * fma(neg_half(b[1]), ub, b[2]);
+  const double d0 = b[0] - a[0], d1 = b[1] - a[1], d2 = b[2] - a[2];
+  const double F0 = a[1] + b[1];
+  const double F1 = fma(a[1], ua, pa) + fma(b[1], ub, pb);
+  const double F2 = fma(a[2] + pa, ua, (b[2] + pb) * ub);
+  const float caf = sqrtf(gammaf * d2f_trunc(pa) * d2f_trunc(ia));
+  const float cbf = sqrtf(gammaf * d2f_trunc(pb) * d2f_trunc(ib));
+  const float sf = fmaxf(fabsf(d2f_trunc(ua)) + caf, fabsf(d2f_trunc(ub)) + cbf);
+  const float jf = d2f_trunc(bitsd(umax64(umax64(abs_bits(d0), abs_bits(d1)), abs_bits(d2))));
+  const float ff = d2f_trunc(bitsd(umax64(umax64(abs_bits(F0), abs_bits(F1)), abs_bits(F2))));
+  const bool phys = pos_finite(a[0]) & pos_finite(pa) & pos_finite(b[0]) & pos_finite(pb);
+  double s;
+  if (phys && sf * jf * 1e-6f <= 1e-16f * ff) {
+    s = f2d_bits(sf);
+  } else {
+    const double sa = fabs(ua) + sqrt64(gamma * pa * ia);
+    const double sb = fabs(ub) + sqrt64(gamma * pb * ib);
+    s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
+  }
+  G2[0] = fma(-s, d0, F0);
+  G2[1] = fma(-s, d1, F1);
+  G2[2] = fma(-s, d2, F2);
+}
+
 // One tile (C cells) of the interface flux + update (+ lambda_max) of one solve.
 template <int N, int C = 64>
 __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
@@ -994,7 +1033,7 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
         g[r] = m;
       }
     }
-    rusanov2(a, b, G2, P.gamma, P.gm1);
+    rusanov2_screened(a, b, G2, P.gamma, P.gm1, (float)P.gamma);
 #pragma unroll
     for (int r = 0; r < kM; ++r) sh.G[(f * n + l0) * kM + r] = G2[r];
   }

@@ -649,6 +649,7 @@ def run_convergence(dev):
              "fp32_2sweeps": dict(precision="fp32", fp64_sweeps=2),
              "fp32ff_1sweep": dict(precision="fp32ff", fp64_sweeps=1),
              "fp32ff_2sweeps": dict(precision="fp32ff", fp64_sweeps=2),
+             "incr": dict(precision="incr"),
              "ff": dict(precision="ff")}
     out = []
     for N, data, field, meshes in ((2, "sine", W.sine(), (50, 100, 200, 400)),
@@ -1097,7 +1098,10 @@ def run_variants(args, dev, flush):
                     "rel_linf_vs_fp64_path_one_step":
                         (one - one_ref).abs().max().item() / one_ref.abs().max().item()}
         return f
-    forms5 = (("dg5-1e5-fp32ff1", "as the headline, FP32 Picard + 1 float-float sweep and "
+    forms5 = (("dg5-1e5-incr", "as the headline, increment form: float-float first iteration "
+               "and terms of u, FP32 Picard on the correction with exact flux differences",
+               dict(precision="incr")),
+              ("dg5-1e5-fp32ff1", "as the headline, FP32 Picard + 1 float-float sweep and "
                "float-float epilogue", dict(precision="fp32ff", fp64_sweeps=1)),
               ("dg5-1e5-fp32ff2", "as the headline, FP32 Picard + 2 float-float sweeps and "
                "float-float epilogue", dict(precision="fp32ff", fp64_sweeps=2)),
@@ -1154,6 +1158,8 @@ def run_variants(args, dev, flush):
                             c64, u0, nc, 7, ts, st, 1, flush, extra=grab))
     del c64
     for name, desc, kw in (
+            ("dg7-1e6-incr", "ADER-DG N=7, 10^6 cells, increment form (FP32 Picard on the "
+             "correction)", dict(precision="incr")),
             ("dg7-1e6-ffpred", "ADER-DG N=7, 10^6 cells, float-float Picard", dict(precision="ff")),
             ("dg7-1e6-fp32ff2", "ADER-DG N=7, 10^6 cells, FP32 Picard + 2 float-float sweeps",
              dict(precision="fp32ff", fp64_sweeps=2)),

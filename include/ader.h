@@ -56,9 +56,16 @@ typedef enum {
   ADER_PREC_FP32_PREDICTOR = 1,  /* Picard in FP32, then fp64_sweeps FP64 sweeps; rest FP64 */
   ADER_PREC_FF_PREDICTOR = 2,    /* Picard and predictor epilogue in float-float (~48 bits,
                                     FP32 pipes); corrector and CFL in FP64 */
-  ADER_PREC_FP32_FF_SWEEPS = 3   /* Picard in FP32 (to fp32_tol), then fp64_sweeps sweeps and
+  ADER_PREC_FP32_FF_SWEEPS = 3,  /* Picard in FP32 (to fp32_tol), then fp64_sweeps sweeps and
                                     the predictor epilogue in float-float (FP64-grade accuracy
                                     on the FP32 pipes); corrector and CFL in FP64 */
+  ADER_PREC_FP32_INCREMENT = 4   /* increment form: with q = u + d, the tau-independent first
+                                    iteration d1 = -(dt/dx) tau (x) k~ F(u) and the terms of u
+                                    in float-float; the Picard iterations on d - d1 in FP32 with
+                                    F(u + d) - F(u) as exact differences, so FP32 rounding is
+                                    relative to the correction, not the state; stops at the FP64
+                                    tolerance or the FP32 resolution of the correction.  Euler
+                                    system only; corrector and CFL in FP64 */
 } ader_precision;
 
 /* The system of conservation laws.

@@ -24,7 +24,7 @@ ADER_ERR_TIMEOUT = 6
 ADER_ERR_STATE = 7
 
 SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
-PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2, "fp32ff": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2, "fp32ff": 3, "incr": 4}
 SYSTEMS = {"euler": 0, "reacting": 1, "tracer": 2}
 BOUNDARIES = {"periodic": 0, "outflow": 1}
 SYSTEM_VARS = {0: 3, 1: 5, 2: 4}

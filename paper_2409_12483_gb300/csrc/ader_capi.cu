@@ -547,7 +547,8 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
   if (o.picard_max_iter <= 0) o.picard_max_iter = 4 * c->n + 8;
   if (!(o.gamma > 1.0) || !(o.cfl > 0.0) || !(o.picard_tol >= 0.0) || o.picard_fixed_iter < 0 ||
       (o.precision != ADER_PREC_FP64 && o.precision != ADER_PREC_FP32_PREDICTOR &&
-       o.precision != ADER_PREC_FF_PREDICTOR && o.precision != ADER_PREC_FP32_FF_SWEEPS) ||
+       o.precision != ADER_PREC_FF_PREDICTOR && o.precision != ADER_PREC_FP32_FF_SWEEPS &&
+       o.precision != ADER_PREC_FP32_INCREMENT) ||
       ((o.precision == ADER_PREC_FP32_PREDICTOR || o.precision == ADER_PREC_FP32_FF_SWEEPS) &&
        o.fp64_sweeps < 1) || o.picard_max_iter > 10000 ||
       (o.system != ADER_SYSTEM_EULER && o.system != ADER_SYSTEM_REACTING &&

@@ -2,6 +2,7 @@
 // plain launchers.  Compiled once per degree with -DADER_DEG=<0..7>, so the
 // degrees build in parallel and each kernel is fully unrolled for its N.
 #include "ader_kernels.cuh"
+#include "ader_incr.cuh"
 #include "ader_source.cuh"
 #include "ader_limiter.cuh"
 #include "ader_kernels2d.cuh"
@@ -66,6 +67,9 @@ cudaError_t prepare_cpb() {
     e = cudaFuncSetAttribute(predict_kernel<D, 3, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(predict_incr_kernel<D, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)IncrCfg<D, CPB>::kSmemBytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(predict_kernel<D, 2, CPB>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   }
@@ -85,6 +89,9 @@ cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
       predict_kernel<D, 2, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else if (p.prec == 3 && !p.from_q)
       predict_kernel<D, 3, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else if (p.prec == 4 && !p.from_q)
+      predict_incr_kernel<D, CPB>
+          <<<(unsigned)blocks, C::THREADS, IncrCfg<D, CPB>::kSmemBytes, s>>>(p);
     else
       predict_kernel<D, 0, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     return cudaGetLastError();

@@ -16,9 +16,10 @@
 // weights sum to 1).  Convergence: the FP32 iteration stops when the change of
 // e falls below max(tol max(1, max|u|), 2^-21 max|e|) -- the FP64 tolerance, or
 // the FP32 resolution of the correction -- or when it has stopped contracting
-// (change above half the previous one) while already below 2^-12 max|e|: the
-// rounding of the FP32 contractions (k~ has entries of order N^2, so their sums
-// cancel) sets a noise floor above 2^-21 max|e| on coarse meshes, where the
+// (change above half the previous one) while already below 2^-12 max|d|: the
+// FP32 evaluation of dF(u, d1 + e) and of the contractions (k~ has entries of
+// order N^2, so their sums cancel) leaves a noise floor proportional to |d|,
+// which lies above 2^-21 max|e| where e is much smaller than d1, while the
 // Picard map itself contracts by orders of magnitude per iteration.
 #pragma once
 
@@ -56,7 +57,7 @@ __device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
 // FP32 row exchange [CPB][n][n][3]; F(u), then the scaled time-averaged flux
 // [CPB][n][3] (float-float); g0 [CPB][n][3] (float-float); u [CPB][n][3]
 // (float-float); per-cell sums psi~ u, psi u, psi~ g0, psi g0 [CPB][4][3]
-// (float-float); per-cell max |u| [CPB] (float bits).
+// (float-float); per-cell max |u| [CPB] and max |d| [2][CPB] (float bits).
 template <int N, int CPB>
 struct IncrCfg {
   static constexpr int n = N + 1, THREADS = CPB * n;
@@ -65,7 +66,8 @@ struct IncrCfg {
   static constexpr int UU = G0 + 2 * CPB * n * kM;
   static constexpr int TR = UU + 2 * CPB * n * kM;
   static constexpr int UM = TR + 2 * CPB * 4 * kM;
-  static constexpr int FLOATS = UM + CPB;
+  static constexpr int DM = UM + CPB;
+  static constexpr int FLOATS = DM + 2 * CPB;
   static constexpr size_t kSmemBytes = (size_t)FLOATS * sizeof(float);
   static constexpr bool kValid = PredCfg<N, CPB>::kValid;
 };
@@ -82,6 +84,7 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
   float2* uu = reinterpret_cast<float2*>(smf + C::UU);
   float2* tr = reinterpret_cast<float2*>(smf + C::TR);
   unsigned* umax = reinterpret_cast<unsigned*>(smf + C::UM);
+  unsigned* dmaxs = reinterpret_cast<unsigned*>(smf + C::DM);  // [parity][cell]
   unsigned long long(*s_red)[kMaxCpb][2] = sh.red;
   const OpsF& of = P.opf;
 
@@ -91,6 +94,7 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
   const bool valid = cell < io.ncells;
   for (int i = tid; i < 2 * kMaxCpb * 2; i += THREADS) (&s_red[0][0][0])[i] = 0ull;
   if (tid < CPB) umax[tid] = 0u;
+  if (tid < 2 * CPB) dmaxs[tid] = 0u;
   if (tid == 0) {
     sh.itmax = 0;
     sh.itsum = 0ull;
@@ -211,16 +215,18 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
         en[p1][r] = acc;
       }
     if (!done && !fixed) {
-      unsigned long long dmax = 0ull, emx = 0ull;
+      unsigned long long dmax = 0ull, emx = 0ull, dfull = 0ull;
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           dmax = umax64(dmax, abs_bits<float>(en[p1][r] - e[p1][r]));
           emx = umax64(emx, abs_bits<float>(en[p1][r]));
+          dfull = umax64(dfull, abs_bits<float>(d1h[p1][r] + en[p1][r]));
         }
       atomicMax(&s_red[it & 1][lc][0], dmax);
       atomicMax(&s_red[it & 1][lc][1], emx);
+      atomicMax(&dmaxs[(it & 1) * CPB + lc], (unsigned)dfull);
     }
     __syncthreads();
     if (!done) {
@@ -231,7 +237,8 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
       if (!fixed) {
         const float dl = from_bits<float>(s_red[it & 1][lc][0]);
         const float em = from_bits<float>(s_red[it & 1][lc][1]);
-        const bool stalled = it >= 2 && dl > 0.5f * dl_prev && dl <= 0x1p-12f * em;
+        const float dm = __uint_as_float(dmaxs[(it & 1) * CPB + lc]);
+        const bool stalled = it >= 2 && dl > 0.5f * dl_prev && dl <= 0x1p-12f * dm;
         if (dl <= fmaxf(tol_abs, 0x1p-21f * em) || stalled) {
           done = true;
           ok = true;
@@ -242,6 +249,7 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
     if (p0 == 0) {
       s_red[(it + 1) & 1][lc][0] = 0ull;
       s_red[(it + 1) & 1][lc][1] = 0ull;
+      dmaxs[((it + 1) & 1) * CPB + lc] = 0u;
     }
   }
   const int iters = it + 1;

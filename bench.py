@@ -1231,7 +1231,7 @@ def serving_stream(n, cmax, tend, seed=SEED):
 
 
 def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0), ticks=16,
-                tick_sweep=(4, 64)):
+                tick_sweep=(4, 64), precision="fp32ff", sweeps=2):
     """Continuous-batching server vs the plain per-solve FP64 path on one GPU.
 
     Saturation: every request queued at t = 0.  Open loop: Poisson arrivals at
@@ -1263,7 +1263,7 @@ def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0), ticks=1
 
     def run_server(arrivals, tpr=ticks):
         srv = Server(pool_bytes=pool, max_slots=len(reqs), ticks_per_round=tpr,
-                     precision="fp32ff", fp64_sweeps=2, device=dev)
+                     precision=precision, fp64_sweeps=sweeps, device=dev)
         ids = [srv.submit(r.degree, st, r.t_end, arrival=a) for r, st, a in zip(reqs, states, arrivals)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -228,6 +228,13 @@ cudaError_t ADER_CAT(prepare_degree_, ADER_DEG)() {
                              (int)PredCfg<D, T>::kSmemBytes);
     if (e != cudaSuccess) return e;
   }
+  {
+    constexpr int T = server_pred_cells(D);
+    e = cudaFuncSetAttribute(predict_incr_multi_kernel<D, T>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)IncrCfg<D, T>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -362,6 +369,9 @@ cudaError_t ADER_CAT(launch_predict_multi_, ADER_DEG)(const PredictParams& p, co
     predict_multi_kernel<D, 2, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   else if (p.prec == 3)
     predict_multi_kernel<D, 3, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
+  else if (p.prec == 4)
+    predict_incr_multi_kernel<D, T>
+        <<<(unsigned)grid, C::THREADS, IncrCfg<D, T>::kSmemBytes, s>>>(p, m);
   else
     predict_multi_kernel<D, 0, T><<<(unsigned)grid, C::THREADS, C::kSmemBytes, s>>>(p, m);
   return cudaGetLastError();

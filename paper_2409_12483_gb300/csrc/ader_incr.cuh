@@ -356,4 +356,24 @@ __global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS)
   predict_tile_incr<N, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smf, sh);
 }
 
+// Batched increment-form predictor over the tiles of many solves (as
+// predict_multi_kernel; every solve keeps its own device time step).
+template <int N, int CPB>
+__global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS)
+    predict_incr_multi_kernel(const __grid_constant__ PredictParams P, const MultiArgs M) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ PredShared<N> sh;
+  for (long long it = blockIdx.x; it < M.nitems; it += gridDim.x) {
+    const TileItem item = M.items[it];
+    const SlotDesc& d = M.slots[item.slot];
+    const int par = M.tick_par ^ d.par0;
+    StepParams sp = d.sp;
+    sp.par = par;
+    double dt;
+    if (!block_step_dt<N>(sp, &dt, item.tile == 0, sh)) continue;  // uniform
+    const TileIO io{d.u[par], d.trace, nullptr, nullptr, d.ncells, sp.ctl};
+    predict_tile_incr<N, CPB>(P, io, item.tile, dt * sp.inv_dx, smf, sh);
+  }
+}
+
 }  // namespace ader

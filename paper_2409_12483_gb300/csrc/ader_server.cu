@@ -388,7 +388,8 @@ ader_status ader_server_create(const ader_server_opts* opt, ader_server** out) {
       (opt->ticks_per_round & 1) || opt->ticks_per_round > 4096 || !(opt->gamma > 1.0) ||
       !(opt->cfl > 0.0) ||
       (opt->precision != ADER_PREC_FP64 && opt->precision != ADER_PREC_FP32_PREDICTOR &&
-       opt->precision != ADER_PREC_FF_PREDICTOR && opt->precision != ADER_PREC_FP32_FF_SWEEPS) ||
+       opt->precision != ADER_PREC_FF_PREDICTOR && opt->precision != ADER_PREC_FP32_FF_SWEEPS &&
+       opt->precision != ADER_PREC_FP32_INCREMENT) ||
       ((opt->precision == ADER_PREC_FP32_PREDICTOR || opt->precision == ADER_PREC_FP32_FF_SWEEPS) &&
        opt->fp64_sweeps < 1) ||
       reinterpret_cast<uintptr_t>(opt->pool_dev) % kAl)

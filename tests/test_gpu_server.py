@@ -52,7 +52,7 @@ MIX = [(1, 37, 0.02), (2, 100, 0.01), (3, 65, 0.01), (4, 200, 0.004), (5, 33, 0.
        (6, 129, 0.002), (7, 64, 0.003), (5, 300, 0.001)]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "ff", "fp32ff"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "ff", "fp32ff", "incr"])
 def test_results_equal_alone(cuda, precision):
     """the batched kernels (16-cell predictor tiles, 32-cell face tiles, one graph
     branch per degree) give every solve the result of its own context"""

@@ -1220,8 +1220,8 @@ def run_small_meshes(dev, steps_n=2000):
 SERVING_NOTE = ("scaled stand-in for the 4096-request stream (cells log-uniform in [64, 65536], "
                 "t_end 0.5: ~2.5e13 cell-updates, days of GPU time): {n} requests, cells "
                 "log-uniform in [64, {cmax}], N ~ U{{1..7}}, rho and p = 1 + 3 modes (amplitudes "
-                "<= 0.1/3), u = 0.5, t_end = {tend}, seed 12483; FP32 predictor (FP32 Picard + 2 "
-                "float-float sweeps and epilogue) + FP64 corrector/CFL")
+                "<= 0.1/3), u = 0.5, t_end = {tend}, seed 12483; FP32 predictor (increment form: "
+                "FP32 Picard on the correction, float-float terms of u) + FP64 corrector/CFL")
 
 
 def serving_stream(n, cmax, tend, seed=SEED):
@@ -1231,7 +1231,7 @@ def serving_stream(n, cmax, tend, seed=SEED):
 
 
 def run_serving(dev, n=128, cmax=2048, tend=0.05, rates=(0.5, 0.8, 1.0), ticks=16,
-                tick_sweep=(4, 64), precision="fp32ff", sweeps=2):
+                tick_sweep=(4, 64), precision="incr", sweeps=1):
     """Continuous-batching server vs the plain per-solve FP64 path on one GPU.
 
     Saturation: every request queued at t = 0.  Open loop: Poisson arrivals at

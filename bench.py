@@ -471,7 +471,8 @@ def main():
                     help="skip the reacting-flow (source term) throughput and ODE convergence study")
     ap.add_argument("--case", default=None,
                     help="profiling case instead of the bench line: "
-                         "predict-dg5 | predict-dg5-ff | predict-dg7-fp32 | weno5 | step2d-dg5 | "
+                         "predict-dg5 | predict-dg5-ff | predict-dg5-incr | predict-dg7-fp32 | weno5 | "
+                         "step2d-dg5 | "
                          "step3d-dg2 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
@@ -1355,6 +1356,9 @@ def run_case(args):
         u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
     elif args.case == "predict-dg5-ff":
         ctx = Context(nc, 5, "dg", device=dev, precision="ff")
+        u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+    elif args.case == "predict-dg5-incr":
+        ctx = Context(nc, 5, "dg", device=dev, precision="incr")
         u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
     elif args.case == "predict-dg7-fp32":
         ctx = Context(nc, 7, "dg", device=dev, precision="fp32", fp64_sweeps=2)

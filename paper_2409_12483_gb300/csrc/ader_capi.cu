@@ -176,6 +176,11 @@ PredictParams make_predict(const ader_ctx* c, const double* u_nodal, const StepP
   p.tol32 = (float)c->opt.fp32_tol;
   p.gamma = c->opt.gamma;
   p.gm1 = c->opt.gamma - 1.0;
+  p.gamf = (float)p.gamma;
+  p.gm1f = (float)p.gm1;
+  p.c1f = (float)(0.5 * (3.0 - p.gamma));
+  p.c2f = (float)(0.5 * p.gm1);
+  p.tolf = (float)p.tol;
   p.sp = sp;
   p.ops = c->basis.d;
   p.opf = c->basis.f;

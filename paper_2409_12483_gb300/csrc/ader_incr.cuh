@@ -179,13 +179,12 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
     }
 #pragma unroll
   for (int q0 = 0; q0 < n; ++q0) nkr[q0] = -(float)(lam * P.ops.kap[p0][q0]);
-  const float gm1s = (float)P.gm1, c1 = (float)(0.5 * (3.0 - P.gamma)),
-              c2 = (float)(0.5 * (P.gamma - 1.0)), gam = (float)P.gamma;
+  const float gam = P.gamf, gm1s = P.gm1f, c1 = P.c1f, c2 = P.c2f;
   float* my_h = hrows + (lc * n + p0) * n * kM;
   const float* cell_h = hrows + lc * n * n * kM;
   const bool fixed = P.fixed_iter > 0;
   const int cap = (fixed ? P.fixed_iter : P.max_iter) - 1;  // iteration 1 gave d1
-  const float tol_abs = (float)P.tol * fmaxf(1.0f, __uint_as_float(umax[lc]));
+  const float tol_abs = P.tolf * fmaxf(1.0f, __uint_as_float(umax[lc]));
   bool done = !valid;
   bool ok = !valid || fixed;
   int it = 0;
@@ -215,18 +214,25 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
         en[p1][r] = acc;
       }
     if (!done && !fixed) {
-      unsigned long long dmax = 0ull, emx = 0ull, dfull = 0ull;
+      unsigned long long dmax = 0ull, emx = 0ull;
 #pragma unroll
       for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           dmax = umax64(dmax, abs_bits<float>(en[p1][r] - e[p1][r]));
           emx = umax64(emx, abs_bits<float>(en[p1][r]));
-          dfull = umax64(dfull, abs_bits<float>(d1h[p1][r] + en[p1][r]));
         }
       atomicMax(&s_red[it & 1][lc][0], dmax);
       atomicMax(&s_red[it & 1][lc][1], emx);
-      atomicMax(&dmaxs[(it & 1) * CPB + lc], (unsigned)dfull);
+      if (it >= 2) {  // the stagnation test needs max |d| from the second FP32 iteration on
+        unsigned dfull = 0u;
+#pragma unroll
+        for (int p1 = 0; p1 < n; ++p1)
+#pragma unroll
+          for (int r = 0; r < kM; ++r)
+            dfull = max(dfull, (unsigned)abs_bits<float>(d1h[p1][r] + en[p1][r]));
+        atomicMax(&dmaxs[(it & 1) * CPB + lc], dfull);
+      }
     }
     __syncthreads();
     if (!done) {

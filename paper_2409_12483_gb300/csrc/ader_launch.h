@@ -32,6 +32,9 @@ struct PredictParams {
   float tol32;
   double tol;
   double gamma, gm1;
+  // FP32 constants of the increment form: gamma, gamma - 1, (3 - gamma)/2,
+  // (gamma - 1)/2, tol (rounded once on the host)
+  float gamf, gm1f, c1f, c2f, tolf;
   double om2;            // omega^2 of the reacting system's source
   StepParams sp;
   OpsD ops;

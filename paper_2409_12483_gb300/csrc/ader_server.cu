@@ -171,6 +171,11 @@ PredictParams server_predict_params(const ader_server* srv, int N) {
   p.tol32 = 1e-6f;
   p.gamma = srv->opt.gamma;
   p.gm1 = srv->opt.gamma - 1.0;
+  p.gamf = (float)p.gamma;
+  p.gm1f = (float)p.gm1;
+  p.c1f = (float)(0.5 * (3.0 - p.gamma));
+  p.c2f = (float)(0.5 * p.gm1);
+  p.tolf = (float)p.tol;
   p.ops = srv->basis[N].d;
   p.opf = srv->basis[N].f;
   return p;

@@ -1144,7 +1144,23 @@ def run_variants(args, dev, flush):
     wl["plain_host_launched"] = {"value": nc * TIME_STEPS / (ev0.elapsed_time(ev1) / 1e3),
                                  "unit": UNIT, "ms_per_step": ev0.elapsed_time(ev1)}
     out.append(wl)
-    del ctx, v0, plain, a, b
+    w64 = torch.empty_like(v0)
+    w64.copy_(v0)
+    ctx.ader_solve(w64, max_steps=TIME_STEPS)
+    del ctx, plain, a, b
+    # the same workload with the faster predictor forms (WENO, interface and CFL in FP64)
+    for name, kw in (("weno5-1e6-incr", dict(precision="incr")),
+                     ("weno5-1e6-ffpred", dict(precision="ff"))):
+        c = Context(nc, 4, "fv", device=dev, profile=1, **kw)
+        c.ader_autotune(v0, reps=2)
+
+        def errw(u):
+            return {"rel_linf_vs_fp64_path": (u - w64).abs().max().item() / w64.abs().max().item()}
+        out.append(variant_line(name, f"ADER-WENO5 FV, 10^6 cells, modes4, 100 steps, predictor "
+                                f"{kw['precision']}", c, v0, nc, 4, TIME_STEPS, st, 1, flush,
+                                dg=False, extra=errw))
+        del c
+    del v0, w64
     # ADER-DG N=7, 10^6 cells: FP64 and FP32-predictor (2 FP64 sweeps), 20 steps
     ts = 20
     c64 = Context(nc, 7, "dg", device=dev, profile=1)

@@ -45,8 +45,38 @@ __device__ __forceinline__ void euler2_flux(const double* U, double* F, double* 
   G[3] = (U[3] + p) * v;
 }
 
+// Rusanov speed of a multi-D face with the FP32 screen of the 1D interface
+// kernel: the speed enters the flux only through s (b - a), and an FP32 speed
+// from the FP64 normal velocities, p and 1/rho truncated to FP32 is within
+// 1e-6 of s relative, so it is used wherever 1e-6 s max|b - a| is below 1e-16
+// of max|F(a) + F(b)| (the FP64 evaluation's own rounding level); elsewhere --
+// jumps, doubtful or non-physical states -- the FP64 speeds (NaN for a
+// non-physical side, as rusanov_speed).
+template <int MV>
+__device__ __forceinline__ double screened_speed(const double (&d)[MV], const double (&F)[MV],
+                                                 double ra, double rb, double wa, double wb,
+                                                 double pa, double pb, double ia, double ib,
+                                                 double gamma) {
+  const float gammaf = d2f_trunc(gamma);
+  const float caf = sqrtf(gammaf * d2f_trunc(pa) * d2f_trunc(ia));
+  const float cbf = sqrtf(gammaf * d2f_trunc(pb) * d2f_trunc(ib));
+  const float sf = fmaxf(fabsf(d2f_trunc(wa)) + caf, fabsf(d2f_trunc(wb)) + cbf);
+  unsigned long long jb = 0ull, fb = 0ull;
+#pragma unroll
+  for (int r = 0; r < MV; ++r) {
+    jb = umax64(jb, abs_bits(d[r]));
+    fb = umax64(fb, abs_bits(F[r]));
+  }
+  const bool phys = pos_finite(ra) & pos_finite(pa) & pos_finite(rb) & pos_finite(pb);
+  if (phys && sf * d2f_trunc(bitsd(jb)) * 1e-6f <= 1e-16f * d2f_trunc(bitsd(fb))) return f2d_bits(sf);
+  const double sa = fabs(wa) + sqrt64(gamma * pa * ia);
+  const double sb = fabs(wb) + sqrt64(gamma * pb * ib);
+  return rusanov_speed(ra, pa, sa, rb, pb, sb);
+}
+
 // Twice the Rusanov flux in direction D (0: x, 1: y) between a (low side) and
-// b (high side); NaN when either state is non-physical.
+// b (high side); NaN when either state is non-physical.  The speed is screened
+// in FP32 (screened_speed).
 template <int D>
 __device__ __forceinline__ void rusanov2_2d(const double* a, const double* b, double* H2,
                                             double gamma, double gm1) {
@@ -55,14 +85,15 @@ __device__ __forceinline__ void rusanov2_2d(const double* a, const double* b, do
   const double pa = gm1 * fma(neg_half(a[1]), ua, fma(neg_half(a[2]), va, a[3]));
   const double pb = gm1 * fma(neg_half(b[1]), ub, fma(neg_half(b[2]), vb, b[3]));
   const double wa = D == 0 ? ua : va, wb = D == 0 ? ub : vb;  // normal velocities
-  const double sa = fabs(wa) + sqrt64(gamma * pa * ia);
-  const double sb = fabs(wb) + sqrt64(gamma * pb * ib);
-  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
   // normal flux: m_n (rho), m u_n + p e_n, (E + p) u_n
-  H2[0] = fma(-s, b[0] - a[0], a[1 + D] + b[1 + D]);
-  H2[1] = fma(-s, b[1] - a[1], fma(a[1], wa, D == 0 ? pa : 0.0) + fma(b[1], wb, D == 0 ? pb : 0.0));
-  H2[2] = fma(-s, b[2] - a[2], fma(a[2], wa, D == 1 ? pa : 0.0) + fma(b[2], wb, D == 1 ? pb : 0.0));
-  H2[3] = fma(-s, b[3] - a[3], fma(a[3] + pa, wa, (b[3] + pb) * wb));
+  const double d[kM2] = {b[0] - a[0], b[1] - a[1], b[2] - a[2], b[3] - a[3]};
+  const double F[kM2] = {a[1 + D] + b[1 + D],
+                         fma(a[1], wa, D == 0 ? pa : 0.0) + fma(b[1], wb, D == 0 ? pb : 0.0),
+                         fma(a[2], wa, D == 1 ? pa : 0.0) + fma(b[2], wb, D == 1 ? pb : 0.0),
+                         fma(a[3] + pa, wa, (b[3] + pb) * wb)};
+  const double s = screened_speed<kM2>(d, F, a[0], b[0], wa, wb, pa, pb, ia, ib, gamma);
+#pragma unroll
+  for (int r = 0; r < kM2; ++r) H2[r] = fma(-s, d[r], F[r]);
 }
 
 // T: target threads per block.  The launcher takes T = 256 when the mesh fills

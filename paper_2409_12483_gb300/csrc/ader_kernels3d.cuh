@@ -58,7 +58,8 @@ __device__ __forceinline__ void euler3_flux(const double* U, double (*F)[kM3], d
 }
 
 // Twice the Rusanov flux in direction D between a (low side) and b (high side);
-// NaN when either state is non-physical.
+// NaN when either state is non-physical.  The speed is screened in FP32
+// (screened_speed of the 2D path).
 template <int D>
 __device__ __forceinline__ void rusanov2_3d(const double* a, const double* b, double* H2,
                                             double gamma, double gm1) {
@@ -73,15 +74,17 @@ __device__ __forceinline__ void rusanov2_3d(const double* a, const double* b, do
       gm1 * fma(neg_half(a[1]), va[0], fma(neg_half(a[2]), va[1], fma(neg_half(a[3]), va[2], a[4])));
   const double pb =
       gm1 * fma(neg_half(b[1]), vb[0], fma(neg_half(b[2]), vb[1], fma(neg_half(b[3]), vb[2], b[4])));
-  const double sa = fabs(va[D]) + sqrt64(gamma * pa * ia);
-  const double sb = fabs(vb[D]) + sqrt64(gamma * pb * ib);
-  const double s = rusanov_speed(a[0], pa, sa, b[0], pb, sb);
-  H2[0] = fma(-s, b[0] - a[0], a[1 + D] + b[1 + D]);
+  double d[kM3], F[kM3];
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) d[r] = b[r] - a[r];
+  F[0] = a[1 + D] + b[1 + D];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
-    H2[1 + c] = fma(-s, b[1 + c] - a[1 + c],
-                    fma(a[1 + c], va[D], c == D ? pa : 0.0) + fma(b[1 + c], vb[D], c == D ? pb : 0.0));
-  H2[4] = fma(-s, b[4] - a[4], fma(a[4] + pa, va[D], (b[4] + pb) * vb[D]));
+    F[1 + c] = fma(a[1 + c], va[D], c == D ? pa : 0.0) + fma(b[1 + c], vb[D], c == D ? pb : 0.0);
+  F[4] = fma(a[4] + pa, va[D], (b[4] + pb) * vb[D]);
+  const double s = screened_speed<kM3>(d, F, a[0], b[0], va[D], vb[D], pa, pb, ia, ib, gamma);
+#pragma unroll
+  for (int r = 0; r < kM3; ++r) H2[r] = fma(-s, d[r], F[r]);
 }
 
 // T: target threads per block, 256 or (small meshes) 64, as for Pred2Cfg

@@ -231,6 +231,15 @@ def measure_solve(ctx, u0, time_steps, steps, warmup, flush):
 
 def variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warmup, flush, dg=True,
                  extra=None, field=None):
+    try:
+        return _variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warmup,
+                             flush, dg, extra, field)
+    except Exception as e:  # noqa: BLE001 -- one failing line does not hide the others
+        return {"name": name, "workload": workload, "error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def _variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, warmup, flush, dg,
+                  extra, field):
     ms, prof, u = measure_solve(ctx, u0, time_steps, steps, warmup, flush)
     n = degree + 1
     iters = sum(p["mean_iters"] for p in prof) / len(prof)

@@ -316,6 +316,7 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
   bool done = !valid;
   bool ok = !valid || fixed;
   int it = 0, cell_it = 0;
+  float dl_prev = 0.0f;
   float2* my_row = sg + (size_t)((lc * n + p0) * n) * kM;
   const float2* cell_g = sg + (size_t)(lc * n) * n * kM;
   if (p0 == 0) {
@@ -438,10 +439,17 @@ __device__ __forceinline__ int picard_loop_ff(ff (&q)[N + 1][kM], const SmemRows
       if (!fixed) {
         const float dl = from_bits<float>(s_red[it & 1][lc][0]);
         const float qm = from_bits<float>(s_red[it & 1][lc][1]);
-        if (dl <= tol * (qm > 1.0f ? qm : 1.0f)) {
+        const float qs = qm > 1.0f ? qm : 1.0f;
+        // the tolerance, or the float-float noise floor: the change has stopped
+        // halving while already below 2^-36 of the state (the contractions'
+        // rounding, amplified by k~, can exceed a 1e-13 tolerance where the
+        // Picard map contracts weakly, e.g. the FV time step)
+        const bool stalled = it >= 3 && dl > 0.5f * dl_prev && dl <= 0x1p-36f * qs;
+        if (dl <= tol * qs || stalled) {
           done = true;
           ok = true;
         }
+        dl_prev = dl;
       }
     }
     if (p0 == 0) {

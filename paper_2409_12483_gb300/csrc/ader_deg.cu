@@ -336,11 +336,36 @@ cudaError_t ADER_CAT(launch_face3d_, ADER_DEG)(const Face3DParams& p, cudaStream
 }
 
 cudaError_t ADER_CAT(launch_cfl3d_, ADER_DEG)(const Cfl3DParams& p, cudaStream_t s) {
-  if constexpr (D <= kMax3DDeg) {
+  if constexpr (D <= 1) {
     constexpr int Ns = 2 * D + 1;
     const long long items = p.ncells * Ns * Ns * Ns;
     const int tpb = flat_threads(items);
     cfl3d_kernel<D><<<grid_for(items, tpb, 0x7fffffffLL), tpb, 0, s>>>(p);
+    return cudaGetLastError();
+  } else if constexpr (D <= kMax3DDeg) {
+    // the separable projection of the update kernel in its CFL mode: O(Ns n^3 +
+    // Ns^2 n^2 + Ns^3 n) per cell instead of O(Ns^3 n^3)
+    Face3DParams f{};
+    f.u_cfl = p.u;
+    f.cfl_slot = p.slot;
+    f.ncells = p.ncells;
+    f.gamma = p.gamma;
+    f.gm1 = p.gm1;
+    f.inv_dy = p.inv_dy;
+    f.inv_dz = p.inv_dz;
+    f.sp.inv_dx = p.inv_dx;
+    f.sp.ctl = p.ctl;
+    for (int j = 0; j < kMaxNs; ++j)
+      for (int k = 0; k < kMaxN; ++k) {
+        f.ops.P[j][k] = p.P[j][k];
+        f.Pf[j][k] = p.Pf[j][k];
+      }
+    using B = Upd3Cfg<D, 128>;
+    using S = Upd3Cfg<D, 64>;
+    if (B::CPB != S::CPB && !use_big_blocks(p.ncells, B::CPB))
+      update3d_kernel<D, 64><<<grid_for(p.ncells, S::CPB, 0x7fffffffLL), S::THREADS, S::kSmemBytes, s>>>(f);
+    else
+      update3d_kernel<D, 128><<<grid_for(p.ncells, B::CPB, 0x7fffffffLL), B::THREADS, B::kSmemBytes, s>>>(f);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;

@@ -830,15 +830,21 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
   extern __shared__ __align__(16) double dsm[];
   auto U = reinterpret_cast<double(*)[NNN][kM3]>(dsm);
   __shared__ unsigned long long s_wmax[C::THREADS / 32];
-  double dt;
-  int last;
-  if (!corrector_step_dt(P.sp, &dt, &last)) return;  // uniform
+  // CFL mode (u_cfl set): lambda_max of a given state by the same separable,
+  // screened projection -- the first step's time step -- without the update
+  const bool cfl_only = P.u_cfl != nullptr;
+  double dt = 0.0;
+  int last = 0;
+  if (!cfl_only && !corrector_step_dt(P.sp, &dt, &last)) return;  // uniform
   const int tid = threadIdx.x;
   const int lc = tid / NNN, k = tid - lc * NNN;
   const long long cell = (long long)blockIdx.x * CPB + lc;
   const bool valid = tid < C::USED && cell < P.ncells;
   const OpsD& o = P.ops;
-  if (valid) {
+  if (valid && cfl_only) {
+#pragma unroll
+    for (int r = 0; r < kM3; ++r) U[lc][k][r] = P.u_cfl[(cell * NNN + k) * kM3 + r];
+  } else if (valid) {
     const int k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
     const long long plane = P.nx * P.ny;
     const long long iz = cell / plane, iy = (cell - iz * plane) / P.nx, ix = cell - iz * plane - iy * P.nx;
@@ -861,8 +867,8 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
       U[lc][k][r] = val;
     }
   }
-  if (blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
-  if (!P.want_lambda) return;  // uniform
+  if (!cfl_only && blockIdx.x == 0 && tid == 0) corrector_finish(P.sp, dt, last, true);
+  if (!cfl_only && !P.want_lambda) return;  // uniform
   __syncthreads();
   // lambda_max of u_new over the Ns^3 subcells, screened as in the 1D interface
   // kernel: the wave speeds of every subcell in FP32 (FP32 pipes), then FP64
@@ -997,11 +1003,13 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
     }
   }
   const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
-  if (tid == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);
+  if (tid == 0) atomicMax(&P.sp.ctl->lam[cfl_only ? P.cfl_slot : (P.sp.par ^ 1)], bm);
   if (bad) atomicOr(&P.sp.ctl->status, kStNonPhysical);
 }
 
 // max over the Ns^3 subcells of every cell of max_d lambda_d / h_d into ctl->lam[slot]
+// (one thread per subcell; the launcher uses it for N <= 1 and the separable
+// CFL mode of update3d_kernel above that)
 template <int N>
 __global__ void __launch_bounds__(256) cfl3d_kernel(const __grid_constant__ Cfl3DParams P) {
   constexpr int n = N + 1, NNN = n * n * n, Ns = 2 * N + 1;

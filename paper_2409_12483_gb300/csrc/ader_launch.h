@@ -197,6 +197,8 @@ struct Face3DParams {
   const double* trace;
   double* gface;         // [cell][d][a][c][5]: fluxes of the low face per direction
   double* u_new;
+  const double* u_cfl;   // non-null: lambda_max of this state only (no update) into lam[cfl_slot]
+  int cfl_slot;
   long long ncells, nx, ny, nz;
   int want_lambda;       // the update also reduces lambda_max of u_new into ctl->lam[par ^ 1]
   double gamma, gm1;

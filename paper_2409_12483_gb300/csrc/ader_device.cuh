@@ -252,6 +252,56 @@ __device__ __forceinline__ double wave_speed(const double* U, double gamma, doub
   return fabs(u) + sqrt64(gamma * p * inv);
 }
 
+// Bounds lo <= lambda <= hi on the wave speed lambda = max_i w_i (|u_i| + c)
+// of an Euler state (rho, m_1 .. m_D, E), from FP32 values v of its components
+// that are within e of the exact ones.  The bound propagates e, and 4 units of
+// FP32 rounding per operation, through 1/rho, u_i = m_i / rho, the kinetic
+// energy K = sum m_i u_i, p = (gamma - 1)(E - K / 2) and c = sqrt(gamma p / rho)
+// to first order, with the first-order terms grown by 2^-8 (the relative
+// errors are held below 2^-10, so the second-order ones stay inside that) and
+// the result by a further 1/4.  The same interval then also holds the FP64
+// evaluation of lambda, whose own rounding is nine orders of magnitude
+// smaller.  A state whose FP32 evaluation cannot be trusted (rho or p not
+// positive, above 1e30, or known to less than 2^-10 relative) gives
+// [0, +inf): it is never excluded, and it never excludes another.
+template <int D>
+__device__ __forceinline__ void speed_bounds_f32(const float (&v)[D + 2], const float (&e)[D + 2],
+                                                 const float (&w)[D], float gf, float gm1f,
+                                                 float& lo, float& hi) {
+  constexpr float eps = 0x1p-22f, grow = 1.0f + 0x1p-8f;
+  lo = 0.f;
+  hi = __int_as_float(0x7f800000);
+  const float rho = v[0], E = v[D + 1];
+  if (!(rho > 0.f) || !(rho < 1e30f) || !(e[0] <= 0x1p-10f * rho)) return;
+  const float inv = 1.f / rho;
+  const float d0 = e[0] * inv;  // relative error of rho
+  float u[D], eu[D], K = 0.f, eKs = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = v[1 + i] * inv;
+    eu[i] = fmaf(e[1 + i], inv, fabsf(u[i]) * (d0 + 2.f * eps)) * grow;
+    K = fmaf(v[1 + i], u[i], K);  // every term m_i^2 / rho >= 0
+    eKs = fmaf(e[1 + i], fabsf(u[i]), fmaf(fabsf(v[1 + i]), eu[i], eKs));
+  }
+  const float eK = fmaf(eKs, grow, (float)(D + 1) * eps * K);
+  const float p = gm1f * fmaf(-0.5f, K, E);
+  const float ep = fmaf(gm1f * fmaf(0.5f, eK, e[D + 1]), grow, 3.f * eps * fabsf(p));
+  if (!(p > 0.f) || !(p < 1e30f) || !(ep <= 0x1p-10f * p)) return;
+  const float c = sqrtf(gf * p * inv);
+  const float dc = fmaf(0.5f * grow, ep / p + d0, 3.f * eps);  // relative error of c
+  float l_lo = 0.f, l_hi = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float li = (fabsf(u[i]) + c) * w[i];
+    const float el = 1.25f * fmaf(fmaf(c, dc, eu[i]) * w[i], grow, 3.f * eps * li);
+    l_lo = fmaxf(l_lo, li - el);
+    l_hi = fmaxf(l_hi, li + el);
+  }
+  if (!(l_hi < __int_as_float(0x7f800000))) return;  // an overflow: keep [0, inf)
+  lo = l_lo;
+  hi = l_hi;
+}
+
 // x > 0 and finite, tested on the bit pattern (integer pipe, no FP64 compare)
 __device__ __forceinline__ bool pos_finite(double x) {
   return dbits(x) - 1ull < 0x7fefffffffffffffull;

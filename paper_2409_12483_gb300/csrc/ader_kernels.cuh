@@ -899,46 +899,50 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   constexpr int n = N + 1, THREADS = FaceCfg<N, C>::THREADS;
   const int tid = threadIdx.x;
   // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
-  // speeds are needed only where the maximum can be: a first FP32 pass screens
-  // every subcell (speeds within 1e-3 of the block's FP32 maximum, and any
-  // subcell whose FP32 state is doubtful, go on to FP64), so the FP64 result is
-  // the same as evaluating every subcell in FP64.
+  // speeds are needed only where the maximum can be: a first FP32 pass bounds
+  // every subcell's speed (speed_bounds_f32, with the error of the FP32
+  // subcell average: truncated state, rounded P and n FMA roundings, below
+  // (n + 4) 2^-24 of sum_k |P_jk| |u_k|); the FP64 pass then evaluates only the
+  // subcells whose upper bound reaches the block's largest lower bound.  Every
+  // subcell left out is below that subcell's FP64 speed, so the result is the
+  // FP64 maximum over every subcell.
   __syncthreads();
   const int items = P.dg ? nvalid * P.Ns : nvalid;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-  float lt_loc = 0.f;
+  const float one[1] = {1.f};
+  const float eproj = P.dg ? (float)(n + 4) * 0x1p-24f : 0x1p-22f;
+  float lo_loc = 0.f;
   for (int item = tid; item < items; item += THREADS) {
-    float v[kM];
+    float v[kM], e[kM];
     if (P.dg) {
       const int lc = item / P.Ns, j = item - lc * P.Ns;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
-        float acc = 0.f;
+        float acc = 0.f, aab = 0.f;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc = fmaf(sh.Pf[j * n + k], sh.uf[(lc * n + k) * kM + r], acc);
+        for (int k = 0; k < n; ++k) {
+          const float pk = sh.Pf[j * n + k], uk = sh.uf[(lc * n + k) * kM + r];
+          acc = fmaf(pk, uk, acc);
+          aab = fmaf(fabsf(pk), fabsf(uk), aab);
+        }
         v[r] = acc;
+        e[r] = fmaf(eproj, aab, 0x1p-100f);  // + the truncation of values below 2^-126
       }
     } else {
 #pragma unroll
-      for (int r = 0; r < kM; ++r) v[r] = sh.uf[item * kM + r];
+      for (int r = 0; r < kM; ++r) {
+        v[r] = sh.uf[item * kM + r];
+        e[r] = fmaf(eproj, fabsf(v[r]), 0x1p-100f);
+      }
     }
-    const float inv = 1.f / v[0];
-    const float uu = v[1] * inv;
-    const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
-    float lt;
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
-      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
-    else
-      lt = fabsf(uu) + sqrtf(gf * pp * inv);
-    sh.lt[item] = lt;
-    lt_loc = fmaxf(lt_loc, lt);
+    float lo, hi;
+    speed_bounds_f32<1>(v, e, one, gf, gm1f, lo, hi);
+    sh.lt[item] = hi;
+    lo_loc = fmaxf(lo_loc, lo);
   }
   const unsigned long long fm =
-      block_max_bits((unsigned long long)__float_as_uint(lt_loc), sh.wmax);
-  if (tid == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    sh.lt_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+      block_max_bits((unsigned long long)__float_as_uint(lo_loc), sh.wmax);
+  if (tid == 0) sh.lt_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = sh.lt_cut;
   double lmax = 0.0;

@@ -368,8 +368,9 @@ __global__ void __launch_bounds__(Upd2Cfg<N, TB>::THREADS)
   using C = Upd2Cfg<N, TB>;
   constexpr int n = N + 1, NN = n * n, Ns = C::Ns, CPB = C::CPB, REC = Pred2Cfg<N>::REC;
   __shared__ double U[CPB][NN][kM2];
-  __shared__ float T[CPB][n][Ns][kM2];  // FP32 screen: projected along eta, [k1][j2]
-  __shared__ float LT[CPB][Ns * Ns];    // FP32 screen: subcell speeds
+  __shared__ float T[CPB][n][Ns][kM2];   // FP32 screen: projected along eta, [k1][j2]
+  __shared__ float AT[CPB][n][Ns][kM2];  // the same sums of |P| |u| (error bound)
+  __shared__ float LT[CPB][Ns * Ns];     // FP32 screen: upper bounds of the subcell speeds
   __shared__ float s_cut;
   __shared__ unsigned long long s_wmax[C::THREADS / 32];
   double dt;
@@ -403,55 +404,54 @@ __global__ void __launch_bounds__(Upd2Cfg<N, TB>::THREADS)
   if (!P.want_lambda) return;  // uniform
   __syncthreads();
   // lambda_max of u_new over the Ns^2 subcells, screened as in the 1D interface
-  // kernel: the separable projection and the wave speeds in FP32 for every
-  // subcell, then FP64 only for the subcells within 1e-3 of the block's FP32
-  // maximum and those whose FP32 state is doubtful, so the result is the FP64
-  // maximum over every subcell.
+  // kernel: the separable projection and bounds on the wave speeds in FP32 for
+  // every subcell (two FP32 passes: the subcell average is within
+  // (2n + 6) 2^-24 sum |P| |P| |u| of the exact one), then FP64 only for the
+  // subcells whose upper bound reaches the block's largest lower bound, so the
+  // result is the FP64 maximum over every subcell.
   const long long c0 = (long long)blockIdx.x * CPB;
   for (int it = tid; it < CPB * n * Ns; it += C::THREADS) {
     const int c = it / (n * Ns), rem = it - c * n * Ns, k1 = rem / Ns, j2 = rem - k1 * Ns;
     if (c0 + c >= P.ncells) continue;
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
 #pragma unroll
-      for (int k2 = 0; k2 < n; ++k2) acc = fmaf(P.Pf[j2][k2], d2f_trunc(U[c][k1 * n + k2][r]), acc);
+      for (int k2 = 0; k2 < n; ++k2) {
+        const float x = d2f_trunc(U[c][k1 * n + k2][r]);
+        acc = fmaf(P.Pf[j2][k2], x, acc);
+        aab = fmaf(fabsf(P.Pf[j2][k2]), fabsf(x), aab);
+      }
       T[c][k1][j2][r] = acc;
+      AT[c][k1][j2][r] = aab;
     }
   }
   __syncthreads();
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-  const float ihx = (float)P.sp.inv_dx, ihy = (float)P.inv_dy;
-  float lt_loc = 0.f;
+  const float ih[2] = {(float)P.sp.inv_dx, (float)P.inv_dy};
+  constexpr float eproj = (float)(2 * n + 6) * 0x1p-24f;
+  float lo_loc = 0.f;
   for (int it = tid; it < CPB * Ns * Ns; it += C::THREADS) {
     const int c = it / (Ns * Ns), rem = it - c * Ns * Ns, j1 = rem / Ns, j2 = rem - j1 * Ns;
     if (c0 + c >= P.ncells) continue;
-    float v[kM2];
+    float v[kM2], e[kM2];
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
 #pragma unroll
-      for (int k1 = 0; k1 < n; ++k1) acc = fmaf(P.Pf[j1][k1], T[c][k1][j2][r], acc);
+      for (int k1 = 0; k1 < n; ++k1) {
+        acc = fmaf(P.Pf[j1][k1], T[c][k1][j2][r], acc);
+        aab = fmaf(fabsf(P.Pf[j1][k1]), AT[c][k1][j2][r], aab);
+      }
       v[r] = acc;
+      e[r] = fmaf(eproj, aab, 0x1p-100f);  // + the truncation of values below 2^-126
     }
-    const float inv = 1.f / v[0];
-    const float uu = v[1] * inv, vv = v[2] * inv;
-    const float pp = gm1f * (v[3] - 0.5f * (v[1] * uu + v[2] * vv));
-    float lt;
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[3])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
-      lt = __int_as_float(0x7f800000);  // doubtful: always evaluated in FP64
-    } else {
-      const float cs = sqrtf(gf * pp * inv);
-      lt = fmaxf((fabsf(uu) + cs) * ihx, (fabsf(vv) + cs) * ihy);
-    }
-    LT[c][rem] = lt;
-    lt_loc = fmaxf(lt_loc, lt);
+    float lo;
+    speed_bounds_f32<2>(v, e, ih, gf, gm1f, lo, LT[c][rem]);
+    lo_loc = fmaxf(lo_loc, lo);
   }
-  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
-  if (tid == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo_loc), s_wmax);
+  if (tid == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = s_cut;
   double lmax = 0.0;
@@ -507,37 +507,34 @@ __global__ void __launch_bounds__(256) cfl2d_kernel(const __grid_constant__ Cfl2
   }
   const double* u = P.u + cell * NN * kM2;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-  const float idx = (float)P.inv_dx, idy = (float)P.inv_dy;
-  float lt = 0.f;
+  const float ih[2] = {(float)P.inv_dx, (float)P.inv_dy};
+  constexpr float eproj = (float)(2 * n + 6) * 0x1p-24f;  // two FP32 passes
+  float lt = 0.f, lo = 0.f;
   if (valid) {
-    float v[kM2];
+    float v[kM2], e[kM2];
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
 #pragma unroll
       for (int k1 = 0; k1 < n; ++k1) {
-        float t = 0.f;
+        float t = 0.f, at = 0.f;
 #pragma unroll
-        for (int k2 = 0; k2 < n; ++k2) t = fmaf(P.Pf[j2][k2], d2f_trunc(u[(k1 * n + k2) * kM2 + r]), t);
+        for (int k2 = 0; k2 < n; ++k2) {
+          const float x = d2f_trunc(u[(k1 * n + k2) * kM2 + r]);
+          t = fmaf(P.Pf[j2][k2], x, t);
+          at = fmaf(fabsf(P.Pf[j2][k2]), fabsf(x), at);
+        }
         acc = fmaf(P.Pf[j1][k1], t, acc);
+        aab = fmaf(fabsf(P.Pf[j1][k1]), at, aab);
       }
       v[r] = acc;
+      e[r] = fmaf(eproj, aab, 0x1p-100f);
     }
-    const float inv = 1.f / v[0];
-    const float uu = v[1] * inv, vv = v[2] * inv;
-    const float pp = gm1f * (v[3] - 0.5f * (v[1] * uu + v[2] * vv));
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[3])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
-      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
-    } else {
-      const float c = sqrtf(gf * pp * inv);
-      lt = fmaxf((fabsf(uu) + c) * idx, (fabsf(vv) + c) * idy);
-    }
+    speed_bounds_f32<2>(v, e, ih, gf, gm1f, lo, lt);
   }
-  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt), s_wmax);
-  if (threadIdx.x == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+  // FP64 below only where the upper bound reaches the block's largest lower bound
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo), s_wmax);
+  if (threadIdx.x == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   double lmax = 0.0;
   bool bad = false;

@@ -810,12 +810,15 @@ struct Upd3Cfg {
   // last pass is screened.
   static constexpr bool kScreenAll = N <= 1;
   // dynamic shared memory: U [CPB][NNN][5] (FP64); T1 [CPB][n n][Ns][5] (along
-  // zeta) and T2 [CPB][n][Ns Ns][5] (along eta), FP32 or FP64 as above; the FP32
-  // subcell speeds LT [CPB][Ns^3]
+  // zeta) and T2 [CPB][n][Ns Ns][5] (along eta), FP32 or FP64 as above; the upper
+  // bounds of the subcell speeds LT [CPB][Ns^3] (FP32); with an FP32 T1 and T2,
+  // their sums of |P| |u| A1 and A2 (the error bound), shaped as T1 and T2
   static constexpr size_t kTBytes = kScreenAll ? sizeof(float) : sizeof(double);
-  static constexpr size_t kSmemBytes = (size_t)CPB * NNN * kM3 * sizeof(double) +
-                                       (size_t)CPB * (n * n * Ns + n * Ns * Ns) * kM3 * kTBytes +
-                                       (size_t)CPB * Ns * Ns * Ns * sizeof(float);
+  static constexpr size_t kSmemBytes =
+      (size_t)CPB * NNN * kM3 * sizeof(double) +
+      (size_t)CPB * (n * n * Ns + n * Ns * Ns) * kM3 * kTBytes +
+      (size_t)CPB * Ns * Ns * Ns * sizeof(float) +
+      (kScreenAll ? (size_t)CPB * (n * n * Ns + n * Ns * Ns) * kM3 * sizeof(float) : 0);
 };
 
 // u^{n+1} = volume term - sum_d (psi~_{k_d} G_high - psi_{k_d} G_low) / w_{k_d}, one
@@ -871,35 +874,44 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
   if (!cfl_only && !P.want_lambda) return;  // uniform
   __syncthreads();
   // lambda_max of u_new over the Ns^3 subcells, screened as in the 1D interface
-  // kernel: the wave speeds of every subcell in FP32 (FP32 pipes), then FP64
-  // only for the subcells within 1e-3 of the block's FP32 maximum and those
-  // whose FP32 state is doubtful, so the result is the FP64 maximum over every
-  // subcell.  N <= 1 projects in FP32 throughout and re-evaluates a candidate
-  // from u_new; above that the separable passes T1 (zeta) and T2 (eta) stay
-  // FP64 and the screen covers the last (xi) pass and the speeds.
+  // kernel: bounds on the wave speeds of every subcell in FP32 (FP32 pipes),
+  // then FP64 only for the subcells whose upper bound reaches the block's
+  // largest lower bound, so the result is the FP64 maximum over every subcell.
+  // N <= 1 projects in FP32 throughout (three passes: the FP32 subcell average
+  // is within (3n + 8) 2^-24 sum |P| |P| |P| |u| of the exact one) and
+  // re-evaluates a candidate from u_new; above that the separable passes T1
+  // (zeta) and T2 (eta) stay FP64 and the screen covers the last (xi) pass
+  // (within (n + 4) 2^-24 sum |P| |T2|) and the speeds.
   __shared__ float s_cut;
   const long long c0 = (long long)blockIdx.x * CPB;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-  const float ihx = (float)P.sp.inv_dx, ihy = (float)P.inv_dy, ihz = (float)P.inv_dz;
+  const float ih[3] = {(float)P.sp.inv_dx, (float)P.inv_dy, (float)P.inv_dz};
   constexpr bool kAll = C::kScreenAll;
   using TT = typename std::conditional<kAll, float, double>::type;
   TT* T1 = reinterpret_cast<TT*>(dsm + CPB * NNN * kM3);  // [CPB][n n][Ns][5]
   TT* T2 = T1 + CPB * n * n * Ns * kM3;                    // [CPB][n][Ns Ns][5]
   float* LT = reinterpret_cast<float*>(T2 + CPB * n * Ns * Ns * kM3);  // [CPB][Ns^3]
+  float* A1 = LT + CPB * Ns * Ns * Ns;    // kAll: [CPB][n n][Ns][5]
+  float* A2 = A1 + CPB * n * n * Ns * kM3;  // kAll: [CPB][n][Ns Ns][5]
   for (int it = tid; it < CPB * n * n * Ns; it += C::THREADS) {
     const int c = it / (n * n * Ns), rem = it - c * n * n * Ns, kk = rem / Ns, j3 = rem - kk * Ns;
     if (c0 + c >= P.ncells) continue;
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
       TT acc = TT(0);
+      float aab = 0.f;
 #pragma unroll
       for (int k3 = 0; k3 < n; ++k3) {
-        if constexpr (kAll)
-          acc = fmaf(P.Pf[j3][k3], d2f_trunc(U[c][kk * n + k3][r]), acc);
-        else
+        if constexpr (kAll) {
+          const float x = d2f_trunc(U[c][kk * n + k3][r]);
+          acc = fmaf(P.Pf[j3][k3], x, acc);
+          aab = fmaf(fabsf(P.Pf[j3][k3]), fabsf(x), aab);
+        } else {
           acc = fma(o.P[j3][k3], U[c][kk * n + k3][r], acc);
+        }
       }
       T1[((c * n * n + kk) * Ns + j3) * kM3 + r] = acc;
+      if constexpr (kAll) A1[((c * n * n + kk) * Ns + j3) * kM3 + r] = aab;
     }
   }
   __syncthreads();
@@ -910,54 +922,53 @@ __global__ void __launch_bounds__(Upd3Cfg<N, TB>::THREADS)
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
       TT acc = TT(0);
+      float aab = 0.f;
 #pragma unroll
       for (int k2 = 0; k2 < n; ++k2) {
-        if constexpr (kAll)
-          acc = fmaf(P.Pf[j2][k2], T1[((c * n * n + k1 * n + k2) * Ns + j3) * kM3 + r], acc);
-        else
-          acc = fma(o.P[j2][k2], T1[((c * n * n + k1 * n + k2) * Ns + j3) * kM3 + r], acc);
+        const int i1 = ((c * n * n + k1 * n + k2) * Ns + j3) * kM3 + r;
+        if constexpr (kAll) {
+          acc = fmaf(P.Pf[j2][k2], T1[i1], acc);
+          aab = fmaf(fabsf(P.Pf[j2][k2]), A1[i1], aab);
+        } else {
+          acc = fma(o.P[j2][k2], T1[i1], acc);
+        }
       }
       T2[((c * n + k1) * Ns * Ns + jj) * kM3 + r] = acc;
+      if constexpr (kAll) A2[((c * n + k1) * Ns * Ns + jj) * kM3 + r] = aab;
     }
   }
   __syncthreads();
-  float lt_loc = 0.f;
+  constexpr float eproj = (float)(kAll ? 3 * n + 8 : n + 4) * 0x1p-24f;
+  float lo_loc = 0.f;
   for (int it = tid; it < CPB * Ns * Ns * Ns; it += C::THREADS) {
     const int c = it / (Ns * Ns * Ns), rem = it - c * Ns * Ns * Ns, j1 = rem / (Ns * Ns),
               jj = rem - j1 * Ns * Ns;
     if (c0 + c >= P.ncells) continue;
-    float v[kM3];
+    float v[kM3], e[kM3];
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
 #pragma unroll
       for (int k1 = 0; k1 < n; ++k1) {
-        const TT t = T2[((c * n + k1) * Ns * Ns + jj) * kM3 + r];
-        if constexpr (kAll)
+        const int i2 = ((c * n + k1) * Ns * Ns + jj) * kM3 + r;
+        if constexpr (kAll) {
+          acc = fmaf(P.Pf[j1][k1], T2[i2], acc);
+          aab = fmaf(fabsf(P.Pf[j1][k1]), A2[i2], aab);
+        } else {
+          const float t = d2f_trunc(T2[i2]);
           acc = fmaf(P.Pf[j1][k1], t, acc);
-        else
-          acc = fmaf(P.Pf[j1][k1], d2f_trunc(t), acc);
+          aab = fmaf(fabsf(P.Pf[j1][k1]), fabsf(t), aab);
+        }
       }
       v[r] = acc;
+      e[r] = fmaf(eproj, aab, 0x1p-100f);  // + the truncation of values below 2^-126
     }
-    const float inv = 1.f / v[0];
-    const float vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
-    const float pp = gm1f * (v[4] - 0.5f * (v[1] * vx + v[2] * vy + v[3] * vz));
-    float lt;
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[4])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
-      lt = __int_as_float(0x7f800000);  // doubtful: always evaluated in FP64
-    } else {
-      const float cs = sqrtf(gf * pp * inv);
-      lt = fmaxf(fmaxf((fabsf(vx) + cs) * ihx, (fabsf(vy) + cs) * ihy), (fabsf(vz) + cs) * ihz);
-    }
-    LT[it] = lt;
-    lt_loc = fmaxf(lt_loc, lt);
+    float lo;
+    speed_bounds_f32<3>(v, e, ih, gf, gm1f, lo, LT[it]);
+    lo_loc = fmaxf(lo_loc, lo);
   }
-  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
-  if (tid == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo_loc), s_wmax);
+  if (tid == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = s_cut;
   double lmax = 0.0;
@@ -1029,40 +1040,37 @@ __global__ void __launch_bounds__(256) cfl3d_kernel(const __grid_constant__ Cfl3
   const double* u = P.u + cell * NNN * kM3;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
   const float ih[3] = {(float)P.inv_dx, (float)P.inv_dy, (float)P.inv_dz};
-  float lt = 0.f;
+  constexpr float eproj = (float)(3 * n + 8) * 0x1p-24f;  // three FP32 passes
+  float lt = 0.f, lo = 0.f;
   if (valid) {
-    float v[kM3];
+    float v[kM3], e[kM3];
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
       for (int k1 = 0; k1 < n; ++k1) {
-        float t2 = 0.f;
+        float t2 = 0.f, a2 = 0.f;
         for (int k2 = 0; k2 < n; ++k2) {
-          float t3 = 0.f;
+          float t3 = 0.f, a3 = 0.f;
 #pragma unroll
-          for (int k3 = 0; k3 < n; ++k3)
-            t3 = fmaf(P.Pf[j3][k3], d2f_trunc(u[((k1 * n + k2) * n + k3) * kM3 + r]), t3);
+          for (int k3 = 0; k3 < n; ++k3) {
+            const float x = d2f_trunc(u[((k1 * n + k2) * n + k3) * kM3 + r]);
+            t3 = fmaf(P.Pf[j3][k3], x, t3);
+            a3 = fmaf(fabsf(P.Pf[j3][k3]), fabsf(x), a3);
+          }
           t2 = fmaf(P.Pf[j2][k2], t3, t2);
+          a2 = fmaf(fabsf(P.Pf[j2][k2]), a3, a2);
         }
         acc = fmaf(P.Pf[j1][k1], t2, acc);
+        aab = fmaf(fabsf(P.Pf[j1][k1]), a2, aab);
       }
       v[r] = acc;
+      e[r] = fmaf(eproj, aab, 0x1p-100f);
     }
-    const float inv = 1.f / v[0];
-    const float vx = v[1] * inv, vy = v[2] * inv, vz = v[3] * inv;
-    const float pp = gm1f * (v[4] - 0.5f * (v[1] * vx + v[2] * vy + v[3] * vz));
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[4])) || !(v[0] < 1e30f) || !(pp < 1e30f)) {
-      lt = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
-    } else {
-      const float c = sqrtf(gf * pp * inv);
-      lt = fmaxf(fmaxf((fabsf(vx) + c) * ih[0], (fabsf(vy) + c) * ih[1]), (fabsf(vz) + c) * ih[2]);
-    }
+    speed_bounds_f32<3>(v, e, ih, gf, gm1f, lo, lt);
   }
-  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt), s_wmax);
-  if (threadIdx.x == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+  // FP64 below only where the upper bound reaches the block's largest lower bound
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo), s_wmax);
+  if (threadIdx.x == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   double lmax = 0.0;
   bool bad = false;

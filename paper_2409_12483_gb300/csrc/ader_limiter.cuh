@@ -554,35 +554,36 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
   }
   const bool own = valid && !twin;  // this cell's subcells enter the maximum
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
-  float uf[n][kM], lt[Ns], lt_loc = 0.f;
+  float uf[n][kM], lt[Ns], lo_loc = 0.f;
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
     for (int r = 0; r < kM; ++r) uf[k][r] = d2f_trunc(u[k][r]);
+  // FP32 bounds on every subcell's speed (as in the interface kernel: the FP32
+  // subcell average is within (n + 4) 2^-24 sum_k |P_jk| |u_k| of P u); FP64
+  // below only where the upper bound reaches the block's largest lower bound.
+  const float one[1] = {1.f};
+  constexpr float eproj = (float)(n + 4) * 0x1p-24f;
 #pragma unroll
   for (int j = 0; j < Ns; ++j) {
-    float v[kM];
+    float v[kM], e[kM];
 #pragma unroll
     for (int r = 0; r < kM; ++r) {
-      float acc = 0.f;
+      float acc = 0.f, aab = 0.f;
 #pragma unroll
-      for (int k = 0; k < n; ++k) acc = fmaf(P.Pf[j][k], uf[k][r], acc);
+      for (int k = 0; k < n; ++k) {
+        acc = fmaf(P.Pf[j][k], uf[k][r], acc);
+        aab = fmaf(fabsf(P.Pf[j][k]), fabsf(uf[k][r]), aab);
+      }
       v[r] = acc;
+      e[r] = fmaf(eproj, aab, 0x1p-100f);
     }
-    const float inv = 1.f / v[0];
-    const float uu = v[1] * inv;
-    const float pp = gm1f * fmaf(-0.5f * v[1], uu, v[2]);
-    if (!(v[0] > 0.f) || !(pp > 1e-3f * fabsf(v[2])) || !(v[0] < 1e30f) || !(pp < 1e30f))
-      lt[j] = __int_as_float(0x7f800000);  // doubtful: always evaluate in FP64
-    else
-      lt[j] = fabsf(uu) + sqrtf(gf * pp * inv);
-    if (own) lt_loc = fmaxf(lt_loc, lt[j]);
+    float lo;
+    speed_bounds_f32<1>(v, e, one, gf, gm1f, lo, lt[j]);
+    if (own) lo_loc = fmaxf(lo_loc, lo);
   }
-  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lt_loc), s_wmax);
-  if (threadIdx.x == 0) {
-    const float m = __uint_as_float((unsigned)fm);
-    s_cut = isinf(m) ? 0.f : m * (1.f - 1e-3f);
-  }
+  const unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo_loc), s_wmax);
+  if (threadIdx.x == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = s_cut;
   double lmax = 0.0;

@@ -486,7 +486,8 @@ def main():
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
                          "sine-tables (the 2D / 3D sine-wave convergence tables against the paper's) | "
-                         "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells)")
+                         "sod-dg5-limiter | tracer-dg5 | reacting-dg5 (10^6 cells) | "
+                         "solve-dg5 | solve-dg5-1e5 (the FP64 time loop, 10^6 / 10^5 cells)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1409,10 +1410,13 @@ def run_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
         return
-    elif args.case in ("sod-dg5-limiter", "tracer-dg5", "reacting-dg5"):
+    elif args.case in ("sod-dg5-limiter", "tracer-dg5", "reacting-dg5", "solve-dg5", "solve-dg5-1e5"):
         # 10^6 cells (144-192 MB of state, above L2): warmup + steps time steps
         import numpy as np
-        if args.case == "sod-dg5-limiter":
+        if args.case in ("solve-dg5", "solve-dg5-1e5"):  # the interface kernel with lambda_max
+            ctx = Context(nc if args.case == "solve-dg5" else CELLS, 5, "dg")
+            u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+        elif args.case == "sod-dg5-limiter":
             ctx = Context(nc, 5, "dg", device=dev, bc="outflow", limiter=1)
             u = torch.tensor(W.riemann_initial(ctx.node_coords(), 1), device=dev).reshape(-1)
         elif args.case == "tracer-dg5":

@@ -108,6 +108,15 @@ __device__ __forceinline__ ff ff_rcp(ff x) {
   return fast_two_sum(r, r * fmaf(e, e, e));
 }
 
+// square root of x > 0: y = sqrt(x.hi) rounded, then one Newton correction
+// (x - y^2) / (2 y) with the residual from an FMA (exact for a rounded root);
+// relative error below 2^-46.
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+  const float y = sqrtf(x.hi);
+  const float r = fmaf(-y, y, x.hi) + x.lo;
+  return fast_two_sum(y, r / (y + y));
+}
+
 // Unnormalised accumulator: acc += a * x with a, x in ff.
 struct ff_acc {
   float hi, lo;

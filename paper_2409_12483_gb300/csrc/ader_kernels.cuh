@@ -876,10 +876,13 @@ struct FaceShared {
   double u[C * (N + 1) * kM];
   double P[kMaxNs * (N + 1)];
   double w[N + 1], psi0w[N + 1], psi1w[N + 1];  // w, psi_k / w_k, psi~_k / w_k
-  float lt[C * kMaxNs];       // FP32 screening value per subcell (CFL)
-  float uf[C * (N + 1) * kM];  // FP32 copy of the updated state (one conversion per value)
-  float Pf[kMaxNs * (N + 1)];
+  float lt[C * kMaxNs];        // FP32 upper bound of each subcell's speed (CFL)
+  float uf[C * (N + 1) * kM];   // updated state split into float pairs uf + ufl
+  float ufl[C * (N + 1) * kM];  // (d2ff: within 2^-47 of the FP64 value)
+  float Pf[kMaxNs * (N + 1)];   // P split the same way
+  float Pfl[kMaxNs * (N + 1)];
   float lt_cut;
+  unsigned long long lt_cut2;
   unsigned long long wmax[32];
 };
 
@@ -890,22 +893,72 @@ struct FaceIO {
   long long ncells;
 };
 
+// Order-preserving 64-bit key of a normalised float pair x = h + l, h >= 0
+// (|l| <= ulp(h) / 2): h's bits above, l's bits mapped to an unsigned order
+// below, so keys compare as the values do (to within ulp(l)).
+__device__ __forceinline__ unsigned long long ff_key(ff x) {
+  const unsigned lb = __float_as_uint(x.lo);
+  const unsigned lo = (lb & 0x80000000u) ? ~lb : (lb | 0x80000000u);
+  return ((unsigned long long)__float_as_uint(x.hi) << 32) | lo;
+}
+
+// Bounds lo <= lambda <= hi on the 1D Euler wave speed |u| + c of a state given
+// in float-float, v = (rho, m, E), each within e of the exact value, returned
+// as ff_key()s: the first-order propagation of speed_bounds_f32, with every
+// float-float operation counted at 2^-40 relative (ff_rcp, ff_mul, ff_sqrt and
+// same-sign sums are below 2^-45; the difference E - K / 2 is charged 2^-40 of
+// |E| + K / 2).  A state whose evaluation cannot be trusted gives the keys of
+// [0, +inf).
+__device__ __forceinline__ void speed_bounds_ff1(const ff (&v)[kM], const float (&e)[kM], ff gam,
+                                                 ff gm1, unsigned long long& lo,
+                                                 unsigned long long& hi) {
+  constexpr float eps = 0x1p-40f, grow = 1.0f + 0x1p-8f;
+  lo = 0ull;
+  hi = ~0ull;
+  if (!(v[0].hi > 0.f) || !(v[0].hi < 1e30f) || !(e[0] <= 0x1p-10f * v[0].hi)) return;
+  const ff inv = ff_rcp(v[0]);
+  const float d0 = e[0] * inv.hi;
+  const ff u = ff_mul(v[1], inv);
+  const float au = fabsf(u.hi);
+  const float eu = fmaf(e[1], inv.hi, au * (d0 + 2.f * eps)) * grow;
+  const ff K = ff_mul(v[1], u);  // m^2 / rho >= 0
+  const float eK = fmaf(fmaf(e[1], au, fabsf(v[1].hi) * eu), grow, 2.f * eps * K.hi);
+  const ff p = ff_mul(gm1, ff_sub(v[2], ff_scale(K, 0.5f)));
+  const float ep = fmaf(gm1.hi * fmaf(0.5f, eK, e[2]), grow,
+                        eps * (gm1.hi * fmaf(0.5f, K.hi, fabsf(v[2].hi)) + 2.f * fabsf(p.hi)));
+  if (!(p.hi > 0.f) || !(p.hi < 1e30f) || !(ep <= 0x1p-10f * p.hi)) return;
+  const ff c = ff_sqrt(ff_mul(ff_mul(gam, p), inv));
+  const float dc = fmaf(0.5f * grow, ep / p.hi + d0, 4.f * eps);
+  const ff l = ff_add(u.hi < 0.f ? ff{-u.hi, -u.lo} : u, c);
+  // 1.25 (1 + 2^-8) also covers the rounding of l.lo -/+ el and the key order
+  const float el = (1.25f * grow) * fmaf(fmaf(c.hi, dc, eu), grow, 3.f * eps * l.hi);
+  if (!(l.hi + el < 1e30f) || !(l.hi > 1e-20f)) return;
+  hi = ff_key(fast_two_sum(l.hi, l.lo + el));
+  const ff lw = fast_two_sum(l.hi, l.lo - el);
+  lo = lw.hi > 0.f ? ff_key(lw) : 0ull;
+}
+
 // lambda_max of the updated state of a tile for the next step's CFL rule, from
-// the tile's shared copies sh.u (FP64) and sh.uf (float) of the Euler variables
-// (rho, m, E) in [cell][k][3] layout; atomically maxed into ctl->lam[par ^ 1].
+// the tile's shared copies sh.u (FP64) and sh.uf + sh.ufl (float pairs) of the
+// Euler variables (rho, m, E) in [cell][k][3] layout; atomically maxed into
+// ctl->lam[par ^ 1].
 template <int N, int C>
 __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParams& sp, int nvalid,
                                             FaceShared<N, C>& sh) {
   constexpr int n = N + 1, THREADS = FaceCfg<N, C>::THREADS;
   const int tid = threadIdx.x;
   // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
-  // speeds are needed only where the maximum can be: a first FP32 pass bounds
-  // every subcell's speed (speed_bounds_f32, with the error of the FP32
-  // subcell average: truncated state, rounded P and n FMA roundings, below
-  // (n + 4) 2^-24 of sum_k |P_jk| |u_k|); the FP64 pass then evaluates only the
-  // subcells whose upper bound reaches the block's largest lower bound.  Every
-  // subcell left out is below that subcell's FP64 speed, so the result is the
-  // FP64 maximum over every subcell.
+  // speeds are needed only where the maximum can be, found in two screens:
+  // (1) FP32 bounds on every subcell's speed (speed_bounds_f32, with the error
+  //     of the FP32 subcell average: truncated state, rounded P and n FMA
+  //     roundings, below (n + 4) 2^-24 of sum_k |P_jk| |u_k|), about 1e-6 wide;
+  // (2) float-float bounds, about 1e-12 wide, for the subcells whose FP32 upper
+  //     bound reaches the block's largest FP32 lower bound (on fine smooth
+  //     meshes the speeds of a whole block lie within the FP32 width);
+  // then FP64 for the subcells whose float-float upper bound reaches the
+  // block's largest float-float lower bound.  Every subcell left out is below
+  // another subcell's FP64 speed, so the result is the FP64 maximum over every
+  // subcell.
   __syncthreads();
   const int items = P.dg ? nvalid * P.Ns : nvalid;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
@@ -940,15 +993,62 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
     sh.lt[item] = hi;
     lo_loc = fmaxf(lo_loc, lo);
   }
-  const unsigned long long fm =
-      block_max_bits((unsigned long long)__float_as_uint(lo_loc), sh.wmax);
+  unsigned long long fm = block_max_bits((unsigned long long)__float_as_uint(lo_loc), sh.wmax);
   if (tid == 0) sh.lt_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = sh.lt_cut;
+  // (2) the float-float screen; per-subcell upper bounds (ff_key; 0 marks a
+  // subcell left out by (1)) go to the flux array, free since the update
+  unsigned long long* hi2 = reinterpret_cast<unsigned long long*>(sh.G);
+  const ff gam = d2ff(P.gamma), gm1 = d2ff(P.gm1);
+  // float-float subcell average, relative to sum_k |P_jk| |u_k|: P and u split
+  // within 2^-47 each (4 units of 2^-48), each product's cross terms and dropped
+  // low x low within 12 units, and the 2n roundings of the low-part sum within
+  // n^2 / 2 + 6.5 n + 5 units: below (n^2 + 8n + 24) 2^-48 in all
+  const float eproj2 = P.dg ? (float)(n * n + 8 * n + 24) * 0x1p-48f : 0x1p-45f;
+  unsigned long long lo2_loc = 0ull;
+  for (int item = tid; item < items; item += THREADS) {
+    unsigned long long h = 0ull;
+    if (sh.lt[item] >= cut) {
+      ff v[kM];
+      float e[kM];
+      if (P.dg) {
+        const int lc = item / P.Ns, j = item - lc * P.Ns;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          ff_acc acc;
+          acc.zero();
+          float aab = 0.f;
+#pragma unroll
+          for (int k = 0; k < n; ++k) {
+            const int iu = (lc * n + k) * kM + r;
+            acc.fma_add(ff{sh.Pf[j * n + k], sh.Pfl[j * n + k]}, ff{sh.uf[iu], sh.ufl[iu]});
+            aab = fmaf(fabsf(sh.Pf[j * n + k]), fabsf(sh.uf[iu]), aab);
+          }
+          v[r] = acc.get();
+          e[r] = fmaf(eproj2, aab, 0x1p-100f);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          v[r] = ff{sh.uf[item * kM + r], sh.ufl[item * kM + r]};
+          e[r] = fmaf(eproj2, fabsf(v[r].hi), 0x1p-100f);
+        }
+      }
+      unsigned long long lo2;
+      speed_bounds_ff1(v, e, gam, gm1, lo2, h);
+      lo2_loc = umax64(lo2_loc, lo2);
+    }
+    hi2[item] = h;
+  }
+  fm = block_max_bits(lo2_loc, sh.wmax);
+  if (tid == 0) sh.lt_cut2 = fm;
+  __syncthreads();
+  const unsigned long long cut2 = sh.lt_cut2;
   double lmax = 0.0;
   bool bad = false;
   for (int item = tid; item < items; item += THREADS) {
-    if (!(sh.lt[item] >= cut)) continue;
+    if (!(hi2[item] >= cut2)) continue;
     double v[kM];
     if (P.dg) {
       const int lc = item / P.Ns, j = item - lc * P.Ns;
@@ -1073,7 +1173,9 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
             fma(-sh.psi1w[k], sh.Gs[(lc + 1) * kM + r], fma(sh.psi0w[k], sh.Gs[lc * kM + r], up[r]));
         out[r] = un;
         sh.u[(lc * n + k) * kM + r] = un;
-        sh.uf[(lc * n + k) * kM + r] = d2f_trunc(un);
+        const ff uf = d2ff(un);
+        sh.uf[(lc * n + k) * kM + r] = uf.hi;
+        sh.ufl[(lc * n + k) * kM + r] = uf.lo;
       }
     }
   } else {
@@ -1083,7 +1185,9 @@ __device__ __forceinline__ void face_tile(const FaceParams& P, const FaceIO& io,
       const double vn = io.v_old[cell * kM + r] - (sh.Gs[(lc + 1) * kM + r] - sh.Gs[lc * kM + r]);
       io.u_new[cell * kM + r] = vn;
       sh.u[lc * kM + r] = vn;
-      sh.uf[lc * kM + r] = d2f_trunc(vn);
+      const ff vf = d2ff(vn);
+      sh.uf[lc * kM + r] = vf.hi;
+      sh.ufl[lc * kM + r] = vf.lo;
     }
   }
   if (P.want_lambda) face_lambda<N, C>(P, sp, nvalid, sh);
@@ -1096,7 +1200,9 @@ __device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShare
   // per-thread table lookups in face_tile are divergent: stage the small tables in smem
   for (int i = threadIdx.x; i < P.Ns * n; i += FaceCfg<N, C>::THREADS) {
     sh.P[i] = P.ops.P[i / n][i % n];
-    sh.Pf[i] = (float)P.ops.P[i / n][i % n];
+    const ff pf = d2ff(P.ops.P[i / n][i % n]);
+    sh.Pf[i] = pf.hi;
+    sh.Pfl[i] = pf.lo;
   }
   if (threadIdx.x < n) {
     sh.w[threadIdx.x] = P.ops.w[threadIdx.x];

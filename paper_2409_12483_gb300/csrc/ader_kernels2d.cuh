@@ -106,6 +106,9 @@ struct Pred2Cfg {
   static constexpr int CPB = NST >= T / 2 ? 1 : T / NST;  // cells per block
   static constexpr int THREADS = CPB * NST;
   static constexpr int REC = 5 * NN * kM2;  // trace record doubles per cell
+  // resident blocks per SM the register allocation must allow (4 x 256 or
+  // 2 x 512 threads: 64 registers; 4 x 216 at N = 5: 72)
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 4 : 2;
 };
 
 template <int N, int T>
@@ -123,7 +126,7 @@ struct Pred2Shared {
 };
 
 template <int N, int T = 256>
-__global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
+__global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS, Pred2Cfg<N, T>::MIN_BLOCKS)
     predict2d_kernel(const __grid_constant__ Predict2DParams P) {
   using C = Pred2Cfg<N, T>;
   constexpr int n = N + 1, NN = C::NN, NST = C::NST, CPB = C::CPB;
@@ -166,43 +169,87 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
   }
   const double nkrow = -o.kaprow[p0];
   __syncthreads();
+  // Phases over the n^2 spatial nodes of each cell (the first iteration, the
+  // traces, the time averages and the volume term) run on packed items
+  // t = (cell sc, spatial node sk) over the first CPB n^2 threads, so that they
+  // fill whole warps (a space-time thread layout would leave most lanes of
+  // those warps idle for N <= 4, and the FP64 pipe issues a warp at a time).
+  // With one cell per block the item of thread t < n^2 is its own node (p0 = 0).
+  constexpr bool kPack = CPB > 1;
+  const int sc = kPack ? tid / NN : 0;
+  const int sk = kPack ? tid - sc * NN : node;
+  const int sk1 = kPack ? sk / n : p1, sk2 = kPack ? sk - (sk / n) * n : p2;
+  const long long scell = kPack ? (long long)blockIdx.x * CPB + sc : cell;
+  const bool sitem = tid < CPB * NN && scell < P.ncells;
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
     const bool active = !sh.done[lc];
-    // Iteration 1 starts from q = u in every tau row, so its fluxes and their
-    // xi / eta contractions do not depend on tau: the p0 = 0 threads form them
-    // once per (p1, p2), and q' = u - (sum_m kappa~[p0][m]) s with the row sums
-    // of kappa~ (kappa~ 1 = tau).
     const bool first = it == 0;
-    const bool work = active && (!first || p0 == 0);
-    if (work) {
-      double F[kM2], G[kM2];
-      euler2_flux(q, F, G, P.gm1);
+    if (first) {
+      // Iteration 1 starts from q = u in every tau row, so its fluxes and their
+      // xi / eta contractions do not depend on tau: the packed items form them
+      // once per (p1, p2) (the tau row p0 = 0 of the shared arrays), and
+      // q' = u - (sum_m kappa~[p0][m]) s with the row sums of kappa~ (kappa~ 1 = tau).
+      if (sitem) {
+        double qw[kM2], F[kM2], G[kM2];
 #pragma unroll
-      for (int r = 0; r < kM2; ++r) {
-        sh.A[lc][node][r] = F[r];
-        sh.B[lc][node][r] = G[r];
+        for (int r = 0; r < kM2; ++r) qw[r] = kPack ? P.u[(scell * NN + sk) * kM2 + r] : q[r];
+        euler2_flux(qw, F, G, P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM2; ++r) {
+          sh.A[sc][sk][r] = F[r];
+          sh.B[sc][sk][r] = G[r];
+        }
       }
-    }
-    __syncthreads();
-    double s[kM2];
-    if (work) {
+      __syncthreads();
+      double s[kM2];
+      if (sitem) {
 #pragma unroll
-      for (int r = 0; r < kM2; ++r) {
-        double acc = 0.0;
+        for (int r = 0; r < kM2; ++r) {
+          double acc = 0.0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fma(sh.kd[0][p1][m], sh.A[lc][(p0 * n + m) * n + p2][r], acc);
+          for (int m = 0; m < n; ++m) acc = fma(sh.kd[0][sk1][m], sh.A[sc][m * n + sk2][r], acc);
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc = fma(sh.kd[1][p2][m], sh.B[lc][(p0 * n + p1) * n + m][r], acc);
-        s[r] = acc;
+          for (int m = 0; m < n; ++m) acc = fma(sh.kd[1][sk2][m], sh.B[sc][sk1 * n + m][r], acc);
+          s[r] = acc;
+        }
       }
-    }
-    __syncthreads();
-    if (work) {
+      __syncthreads();
+      if (sitem) {
 #pragma unroll
-      for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = s[r];
+        for (int r = 0; r < kM2; ++r) sh.A[sc][sk][r] = s[r];
+      }
+      __syncthreads();
+    } else {
+      if (active) {
+        double F[kM2], G[kM2];
+        euler2_flux(q, F, G, P.gm1);
+#pragma unroll
+        for (int r = 0; r < kM2; ++r) {
+          sh.A[lc][node][r] = F[r];
+          sh.B[lc][node][r] = G[r];
+        }
+      }
+      __syncthreads();
+      double s[kM2];
+      if (active) {
+#pragma unroll
+        for (int r = 0; r < kM2; ++r) {
+          double acc = 0.0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc = fma(sh.kd[0][p1][m], sh.A[lc][(p0 * n + m) * n + p2][r], acc);
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc = fma(sh.kd[1][p2][m], sh.B[lc][(p0 * n + p1) * n + m][r], acc);
+          s[r] = acc;
+        }
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = s[r];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (active) {
       unsigned long long dmax = 0ull, qm = 0ull;
 #pragma unroll
@@ -246,24 +293,24 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
 #pragma unroll
   for (int r = 0; r < kM2; ++r) sh.A[lc][node][r] = q[r];
   __syncthreads();
-  double* rec = P.trace + cell * C::REC;
-  if (valid && node < NN) {
-    const int l0 = node / n, k = node - l0 * n;
+  // packed items: (l0, k) = (sk1, sk2) of cell sc
+  double* rec = P.trace + scell * C::REC;
+  if (sitem) {
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
       double aR = 0.0, aL = 0.0, bR = 0.0, bL = 0.0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
-        const double qx = sh.A[lc][(l0 * n + m) * n + k][r], qy = sh.A[lc][(l0 * n + k) * n + m][r];
+        const double qx = sh.A[sc][(sk1 * n + m) * n + sk2][r], qy = sh.A[sc][(sk1 * n + sk2) * n + m][r];
         aR = fma(o.psi1[m], qx, aR);
         aL = fma(o.psi0[m], qx, aL);
         bR = fma(o.psi1[m], qy, bR);
         bL = fma(o.psi0[m], qy, bL);
       }
-      rec[0 * NN * kM2 + node * kM2 + r] = aR;
-      rec[1 * NN * kM2 + node * kM2 + r] = aL;
-      rec[2 * NN * kM2 + node * kM2 + r] = bR;
-      rec[3 * NN * kM2 + node * kM2 + r] = bL;
+      rec[0 * NN * kM2 + sk * kM2 + r] = aR;
+      rec[1 * NN * kM2 + sk * kM2 + r] = aL;
+      rec[2 * NN * kM2 + sk * kM2 + r] = bR;
+      rec[3 * NN * kM2 + sk * kM2 + r] = bL;
     }
   }
   __syncthreads();
@@ -277,30 +324,30 @@ __global__ void __launch_bounds__(Pred2Cfg<N, T>::THREADS)
     }
   }
   __syncthreads();
-  if (node < NN) {
+  if (sitem) {
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
       double fa = 0.0, ga = 0.0;
 #pragma unroll
       for (int l0 = 0; l0 < n; ++l0) {
-        fa = fma(o.w[l0], sh.A[lc][l0 * NN + node][r], fa);
-        ga = fma(o.w[l0], sh.B[lc][l0 * NN + node][r], ga);
+        fa = fma(o.w[l0], sh.A[sc][l0 * NN + sk][r], fa);
+        ga = fma(o.w[l0], sh.B[sc][l0 * NN + sk][r], ga);
       }
-      sh.FB[lc][0][node][r] = fa;
-      sh.FB[lc][1][node][r] = ga;
+      sh.FB[sc][0][sk][r] = fa;
+      sh.FB[sc][1][sk][r] = ga;
     }
   }
   __syncthreads();
-  if (valid && node < NN) {
-    // this thread's (p1, p2) = (k1, k2): uo holds u[k1][k2]
+  if (sitem) {
+    // packed item (k1, k2) = (sk1, sk2) of cell sc (one cell per block: uo holds it)
 #pragma unroll
     for (int r = 0; r < kM2; ++r) {
-      double acc = uo[r];
+      double acc = kPack ? P.u[(scell * NN + sk) * kM2 + r] : uo[r];
 #pragma unroll
-      for (int l = 0; l < n; ++l) acc = fma(o.vt[p1][l], sh.FB[lc][0][l * n + p2][r], acc);
+      for (int l = 0; l < n; ++l) acc = fma(o.vt[sk1][l], sh.FB[sc][0][l * n + sk2][r], acc);
 #pragma unroll
-      for (int l = 0; l < n; ++l) acc = fma(o.vt[p2][l], sh.FB[lc][1][p1 * n + l][r], acc);
-      rec[4 * NN * kM2 + node * kM2 + r] = acc;
+      for (int l = 0; l < n; ++l) acc = fma(o.vt[sk2][l], sh.FB[sc][1][sk1 * n + l][r], acc);
+      rec[4 * NN * kM2 + sk * kM2 + r] = acc;
     }
   }
 }

@@ -155,37 +155,55 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
   // stride of direction d in the space-time node index, and this node's index along d
   const int stride[3] = {n * n, n, 1};
   const int pd[3] = {p1, p2, p3};
+  // Phases over the n^3 spatial nodes of each cell (the first iteration, the
+  // traces, the time averages and the volume term) run on packed items
+  // t = (cell sc, spatial node sk) over the first CPB n^3 threads, so that they
+  // fill whole warps (the FP64 pipe issues a warp at a time).
+  const int sc = tid / NNN, sk = tid - sc * NNN;
+  const int sd[3] = {sk / (n * n), (sk / n) % n, sk % n};
+  const long long scell = (long long)blockIdx.x * CPB + sc;
+  const bool sitem = tid < CPB * NNN && scell < P.ncells;
   const int cap = P.fixed_iter > 0 ? P.fixed_iter : P.max_iter;
   for (int it = 0; it < cap; ++it) {
     const bool active = !sh.done[lc];
     // Iteration 1 starts from q = u in every tau row: its fluxes and their
-    // contractions do not depend on tau, so the p0 = 0 threads form them once per
-    // spatial node, and q' = u - (sum_m kappa~[p0][m]) s (kappa~ 1 = tau).
+    // contractions do not depend on tau, so the packed items form them once per
+    // spatial node (the tau row p0 = 0 of the shared array), and
+    // q' = u - (sum_m kappa~[p0][m]) s (kappa~ 1 = tau).
     const bool first = it == 0;
-    const bool work = !first || p0 == 0;
+    const bool work = first ? sitem : active;
+    const int wc = first ? sc : lc, wn = first ? sk : node;
+    int wd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) wd[d] = first ? sd[d] : pd[d];
     double F[3][kM3];
-    if (work) euler3_flux(q, F, P.gm1);
+    if (work) {
+      double qw[kM3];
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) qw[r] = first ? P.u[(scell * NNN + sk) * kM3 + r] : q[r];
+      euler3_flux(qw, F, P.gm1);
+    }
     double acc[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (work) {
 #pragma unroll
-        for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = F[d][r];
+        for (int r = 0; r < kM3; ++r) sh.S[wc][wn][r] = F[d][r];
       }
       __syncthreads();
-      if (active && work) {
-        const int base = node - pd[d] * stride[d];
+      if (work) {
+        const int base = wn - wd[d] * stride[d];
 #pragma unroll
         for (int r = 0; r < kM3; ++r)
 #pragma unroll
           for (int m = 0; m < n; ++m)
-            acc[r] = fma(sh.kd[d][pd[d]][m], sh.S[lc][base + m * stride[d]][r], acc[r]);
+            acc[r] = fma(sh.kd[d][wd[d]][m], sh.S[wc][base + m * stride[d]][r], acc[r]);
       }
       __syncthreads();
     }
     if (work) {
 #pragma unroll
-      for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = acc[r];
+      for (int r = 0; r < kM3; ++r) sh.S[wc][wn][r] = acc[r];
     }
     __syncthreads();
     if (active) {
@@ -231,9 +249,10 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
 #pragma unroll
   for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = q[r];
   __syncthreads();
-  double* rec = P.trace + cell * C::REC;
-  if (valid && node < NNN) {
-    const int l0 = node / (n * n), a = (node / n) % n, c = node % n;
+  // packed items: (l0, a, c) = spatial node sk of cell sc
+  double* rec = P.trace + scell * C::REC;
+  if (sitem) {
+    const int l0 = sd[0], a = sd[1], c = sd[2];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       // the space-time index of (l0, node m along d, transverse a, c)
@@ -245,12 +264,12 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
         double lo = 0.0, hi = 0.0;
 #pragma unroll
         for (int m = 0; m < n; ++m) {
-          const double x = sh.S[lc][base + m * stride[d]][r];
+          const double x = sh.S[sc][base + m * stride[d]][r];
           lo = fma(o.psi0[m], x, lo);
           hi = fma(o.psi1[m], x, hi);
         }
-        rec[((d * 2 + 0) * NNN + node) * kM3 + r] = lo;
-        rec[((d * 2 + 1) * NNN + node) * kM3 + r] = hi;
+        rec[((d * 2 + 0) * NNN + sk) * kM3 + r] = lo;
+        rec[((d * 2 + 1) * NNN + sk) * kM3 + r] = hi;
       }
     }
   }
@@ -263,30 +282,30 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS)
 #pragma unroll
       for (int r = 0; r < kM3; ++r) sh.S[lc][node][r] = lam[d] * F[d][r];
       __syncthreads();
-      if (node < NNN) {
+      if (sitem) {
 #pragma unroll
         for (int r = 0; r < kM3; ++r) {
           double s = 0.0;
 #pragma unroll
-          for (int l0 = 0; l0 < n; ++l0) s = fma(o.w[l0], sh.S[lc][l0 * NNN + node][r], s);
-          sh.FB[lc][d][node][r] = s;
+          for (int l0 = 0; l0 < n; ++l0) s = fma(o.w[l0], sh.S[sc][l0 * NNN + sk][r], s);
+          sh.FB[sc][d][sk][r] = s;
         }
       }
     }
   }
   __syncthreads();
-  if (valid && node < NNN) {
-    // this thread's (p1, p2, p3) = (k1, k2, k3): uo holds u[k1][k2][k3]
+  if (sitem) {
+    // packed item (k1, k2, k3) = sd of cell sc
 #pragma unroll
     for (int r = 0; r < kM3; ++r) {
-      double acc = uo[r];
+      double acc = P.u[(scell * NNN + sk) * kM3 + r];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const int base = node - pd[d] * stride[d];
+        const int base = sk - sd[d] * stride[d];
 #pragma unroll
-        for (int l = 0; l < n; ++l) acc = fma(o.vt[pd[d]][l], sh.FB[lc][d][base + l * stride[d]][r], acc);
+        for (int l = 0; l < n; ++l) acc = fma(o.vt[sd[d]][l], sh.FB[sc][d][base + l * stride[d]][r], acc);
       }
-      rec[(6 * NNN + node) * kM3 + r] = acc;
+      rec[(6 * NNN + sk) * kM3 + r] = acc;
     }
   }
 }

@@ -223,38 +223,32 @@ __device__ __forceinline__ void predict_src_tile(const PredictParams& P, const T
         // The source acts on the species only and the flux rows are frozen, so
         // after the first inner iteration the Euler components of the new
         // iterate are the same numbers again: only the species are recomputed.
-        double qn[n][M];
-#pragma unroll
-        for (int p1 = 0; p1 < n; ++p1)
-#pragma unroll
-          for (int r = 0; r < M; ++r) {
-            if (r < 3 && m > 1) {
-              qn[p1][r] = q[p1][r];
-              continue;
-            }
-            double acc = uc[p1 * M + r];
-#pragma unroll
-            for (int q0 = 0; q0 < n; ++q0) acc = fma(-kap[q0], cell_d[q0 * RS + p1 * M + r], acc);
-            qn[p1][r] = acc;
-          }
-        if (!done_i) {
+        // The new iterate replaces q in place: its values come from the shared
+        // rows written before the barrier above, not from q.
+        {
           unsigned long long dmax = 0ull, qmax = 0ull;
 #pragma unroll
           for (int p1 = 0; p1 < n; ++p1)
 #pragma unroll
             for (int r = 0; r < M; ++r) {
-              dmax = umax64(dmax, abs_bits<double>(qn[p1][r] - q[p1][r]));
-              qmax = umax64(qmax, abs_bits<double>(qn[p1][r]));
+              double v = q[p1][r];
+              if (!(r < 3 && m > 1)) {
+                double acc = uc[p1 * M + r];
+#pragma unroll
+                for (int q0 = 0; q0 < n; ++q0) acc = fma(-kap[q0], cell_d[q0 * RS + p1 * M + r], acc);
+                v = acc;
+              }
+              dmax = umax64(dmax, abs_bits<double>(v - q[p1][r]));
+              qmax = umax64(qmax, abs_bits<double>(v));
+              if (!done_i) q[p1][r] = v;
             }
-          atomicMax(&sh.red[m & 1][lc][0], dmax);
-          atomicMax(&sh.red[m & 1][lc][1], qmax);
+          if (!done_i) {
+            atomicMax(&sh.red[m & 1][lc][0], dmax);
+            atomicMax(&sh.red[m & 1][lc][1], qmax);
+          }
         }
         __syncthreads();
         if (!done_i) {
-#pragma unroll
-          for (int p1 = 0; p1 < n; ++p1)
-#pragma unroll
-            for (int r = 0; r < M; ++r) q[p1][r] = qn[p1][r];
           const double dl = bitsd(sh.red[m & 1][lc][0]);
           const double qm = bitsd(sh.red[m & 1][lc][1]);
           if (dl <= P.tol * (qm > 1.0 ? qm : 1.0)) done_i = true;

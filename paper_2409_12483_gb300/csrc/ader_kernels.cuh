@@ -16,7 +16,9 @@
 //                   time (interface::w_conv), fused with the DG update of eq.
 //                   ader_dg_method_full or the FV update of eq.
 //                   ader_weno_fv_method_full, and with the lambda_max reduction of
-//                   the next step's CFL rule (Sec. 1.5) over the updated state.
+//                   the next step's CFL rule (Sec. 1.5) over the updated state
+//                   (FP32, then float-float bounds on each subcell's speed pick
+//                   the subcells that FP64 evaluates; the FP64 maximum results).
 // cfl_kernel        lambda_max = max |u| + c over the 2N+1 subcell averages P u of
 //                   Sec. 1.4 (DG) or over the cell averages (FV).
 // weno_kernel       eq. weno_reconstr: three stencils of N+1 cell averages,
@@ -874,13 +876,13 @@ struct FaceShared {
   double G[(C + 1) * (N + 1) * kM];
   double Gs[(C + 1) * kM];
   double u[C * (N + 1) * kM];
-  double P[kMaxNs * (N + 1)];
+  double P[(2 * N + 1) * (N + 1)];
   double w[N + 1], psi0w[N + 1], psi1w[N + 1];  // w, psi_k / w_k, psi~_k / w_k
-  float lt[C * kMaxNs];        // FP32 upper bound of each subcell's speed (CFL)
+  float lt[C * (2 * N + 1)];        // FP32 upper bound of each subcell's speed (CFL)
   float uf[C * (N + 1) * kM];   // updated state split into float pairs uf + ufl
   float ufl[C * (N + 1) * kM];  // (d2ff: within 2^-47 of the FP64 value)
-  float Pf[kMaxNs * (N + 1)];   // P split the same way
-  float Pfl[kMaxNs * (N + 1)];
+  float Pf[(2 * N + 1) * (N + 1)];   // P split the same way
+  float Pfl[(2 * N + 1) * (N + 1)];
   float lt_cut;
   unsigned long long lt_cut2;
   unsigned long long wmax[32];
@@ -945,7 +947,7 @@ __device__ __forceinline__ void speed_bounds_ff1(const ff (&v)[kM], const float 
 template <int N, int C>
 __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParams& sp, int nvalid,
                                             FaceShared<N, C>& sh) {
-  constexpr int n = N + 1, THREADS = FaceCfg<N, C>::THREADS;
+  constexpr int n = N + 1, Ns = 2 * N + 1, THREADS = FaceCfg<N, C>::THREADS;
   const int tid = threadIdx.x;
   // lambda_max of the new state for the next step's CFL rule.  Exact FP64 wave
   // speeds are needed only where the maximum can be, found in two screens:
@@ -960,7 +962,7 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   // another subcell's FP64 speed, so the result is the FP64 maximum over every
   // subcell.
   __syncthreads();
-  const int items = P.dg ? nvalid * P.Ns : nvalid;
+  const int items = P.dg ? nvalid * Ns : nvalid;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
   const float one[1] = {1.f};
   const float eproj = P.dg ? (float)(n + 4) * 0x1p-24f : 0x1p-22f;
@@ -968,7 +970,7 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   for (int item = tid; item < items; item += THREADS) {
     float v[kM], e[kM];
     if (P.dg) {
-      const int lc = item / P.Ns, j = item - lc * P.Ns;
+      const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
         float acc = 0.f, aab = 0.f;
@@ -1013,7 +1015,7 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
       ff v[kM];
       float e[kM];
       if (P.dg) {
-        const int lc = item / P.Ns, j = item - lc * P.Ns;
+        const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           ff_acc acc;
@@ -1051,7 +1053,7 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
     if (!(hi2[item] >= cut2)) continue;
     double v[kM];
     if (P.dg) {
-      const int lc = item / P.Ns, j = item - lc * P.Ns;
+      const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
         double acc = 0.0;
@@ -1198,7 +1200,7 @@ template <int N, int C = 64>
 __device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShared<N, C>& sh) {
   constexpr int n = N + 1;
   // per-thread table lookups in face_tile are divergent: stage the small tables in smem
-  for (int i = threadIdx.x; i < P.Ns * n; i += FaceCfg<N, C>::THREADS) {
+  for (int i = threadIdx.x; i < (2 * N + 1) * n; i += FaceCfg<N, C>::THREADS) {
     sh.P[i] = P.ops.P[i / n][i % n];
     const ff pf = d2ff(P.ops.P[i / n][i % n]);
     sh.Pf[i] = pf.hi;
@@ -1248,9 +1250,9 @@ __global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
 
 template <int N>
 __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflParams P) {
-  constexpr int n = N + 1;
+  constexpr int n = N + 1, Ns = 2 * N + 1;
   __shared__ unsigned long long s_wmax[32];
-  const long long items = P.dg ? P.ncells * P.Ns : P.ncells;
+  const long long items = P.dg ? P.ncells * Ns : P.ncells;
   double lmax = 0.0;
   bool bad = false;
   for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
@@ -1258,8 +1260,8 @@ __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflPar
     double v[kM];
     if (P.dg) {
       // the Euler variables (rho, m, E) lead each node's record of P.vars values
-      const long long cell = it / P.Ns;
-      const int j = (int)(it - cell * P.Ns);
+      const long long cell = it / Ns;
+      const int j = (int)(it - cell * Ns);
       const int stride = P.vars;
       const double* u = P.u + cell * (n * stride);
 #pragma unroll

@@ -488,10 +488,10 @@ __global__ void __launch_bounds__(32 * kLimWarps)
 
 // Every cell once its state is final: DG neighbours of troubled cells take the
 // face term with the subcell flux; then (want_lambda) lambda_max of the limited
-// state for the next step's CFL rule, screened like the interface kernel's: an
-// FP32 pass over every subcell, FP64 wave speeds only for subcells within 1e-3
-// of the block's FP32 maximum or with a doubtful FP32 state, so the result is
-// the FP64 maximum over all subcells.
+// state for the next step's CFL rule, screened like the interface kernel's
+// first screen: FP32 bounds on every subcell's speed (speed_bounds_f32), FP64
+// wave speeds only for the subcells whose upper bound reaches the block's
+// largest lower bound, so the result is the FP64 maximum over all subcells.
 template <int N>
 __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__ LimParams P) {
   constexpr int n = N + 1, Ns = 2 * N + 1;

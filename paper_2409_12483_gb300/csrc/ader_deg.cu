@@ -255,7 +255,7 @@ cudaError_t ADER_CAT(launch_limiter_, ADER_DEG)(const LimParams& p, cudaStream_t
   const unsigned g128 = grid_for(p.ncells, 128, 0x7fffffffLL);
   // the recompute kernel strides over the troubled-cell list (length known on
   // the device only): enough warps for every cell, at most 8 blocks per SM
-  const unsigned grec = grid_for(p.ncells, kLimWarps, 152LL * 8);
+  const unsigned grec = grid_for(p.ncells, 2 * kLimWarps, 152LL * 8);  // two cells per warp
   lim_minmax_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_detect_kernel<D><<<g256, 256, 0, s>>>(p);
   lim_recompute_kernel<D><<<grec, 32 * kLimWarps, 0, s>>>(p);

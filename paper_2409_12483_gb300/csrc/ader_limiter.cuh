@@ -15,12 +15,12 @@
 //                    counts them.  An FP32 pass clears the cells that pass with
 //                    the error bounds to spare; the rest are decided in FP64,
 //                    so every flag is the FP64 detectors' flag.
-// lim_recompute_kernel  one warp per listed troubled cell: the ADER-WENO2
-//                    scheme on its 2N+1 subcells from P u^n (lane j: degree-1
+// lim_recompute_kernel  one half-warp per listed troubled cell: the ADER-WENO2
+//                    scheme on its 2N+1 subcells from P u^n (item j: degree-1
 //                    WENO and the degree-1 LST-DG predictor of subcell j - 1,
-//                    the neighbours' boundary subcells included; lane f: the
+//                    the neighbours' boundary subcells included; item f: the
 //                    Rusanov flux through subcell face f averaged over the two
-//                    tau nodes), the subcell update, the pseudo-inverse
+//                    tau nodes; items spread over the group's 16 lanes), the subcell update, the pseudo-inverse
 //                    reconstruction R = (P^T P)^-1 P^T with the mean of the
 //                    subcell values as fallback when R v has an inadmissible
 //                    subcell average; the fluxes of the cell's own faces go to
@@ -382,107 +382,134 @@ struct LimWarpSmem {
   double ur[n][kM];
 };
 
+// Two listed cells per warp, one per half-warp group of kLimGroup lanes: the
+// degree-1 subcell predictors (Ns + 2 per cell, 13 at N = 5) would otherwise
+// leave most of a warp idle, and the FP64 pipe issues whole warps.  Phases wider
+// than a group (the predictors at N = 7, the (k, r) reconstruction lanes) loop
+// with the group's stride; the admissibility vote is per group.
+constexpr int kLimGroup = 16;
+
 template <int N>
 __global__ void __launch_bounds__(32 * kLimWarps)
     lim_recompute_kernel(const __grid_constant__ LimParams P) {
-  constexpr int n = N + 1, Ns = 2 * N + 1;
-  __shared__ LimWarpSmem<N> smem[kLimWarps];
+  constexpr int n = N + 1, Ns = 2 * N + 1, G = kLimGroup;
+  __shared__ LimWarpSmem<N> smem[2 * kLimWarps];
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  LimWarpSmem<N>& w = smem[warp];
+  const int grp = lane / G, l = lane - grp * G;
+  const unsigned gmask = grp ? 0xffff0000u : 0x0000ffffu;
+  LimWarpSmem<N>& w = smem[2 * warp + grp];
   const long long count = (long long)P.sp.ctl->lim_n;
   const double hlam = 0.5 * dt * P.sp.inv_dx;
   const double lam_s = dt * P.sp.inv_dx * (double)Ns;  // dt / subcell width
-  for (long long e = (long long)blockIdx.x * kLimWarps + warp; e < count;
-       e += (long long)gridDim.x * kLimWarps) {
-    const long long i = P.list[e];
+  // the loop runs over cell pairs, uniform over the warp (a group without a
+  // cell in the last pair idles through the warp's synchronisations)
+  for (long long pe = (long long)blockIdx.x * kLimWarps + warp; 2 * pe < count;
+       pe += (long long)gridDim.x * kLimWarps) {
+    const long long e = 2 * pe + grp;
+    const bool has = e < count;
+    const long long i = has ? P.list[e] : 0;
     const long long il = lim_neighbour(i - 1, P.ncells, P.bc), ir = lim_neighbour(i + 1, P.ncells, P.bc);
     // subcell averages of u^n: the cell's own, and the neighbours' two subcells
-    // next to each face (lane 0, 1: left neighbour's Ns-2, Ns-1; lane 2, 3: right
+    // next to each face (l = 0, 1: left neighbour's Ns-2, Ns-1; l = 2, 3: right
     // neighbour's 0, 1), by the same arithmetic the neighbour uses for its own,
     // so both sides of a face between troubled cells see the same bits
-    if (lane < Ns) lim_subcell<N>(P, P.u_old + i * (n * kM), lane, w.ve[lane + 2]);
-    if (lane < 4) {
-      const long long nb = lane < 2 ? il : ir;
-      if (nb >= 0)
-        lim_subcell<N>(P, P.u_old + nb * (n * kM), lane < 2 ? Ns - 2 + lane : lane - 2,
-                       w.ve[lane < 2 ? lane : Ns + lane]);
+    if (has) {
+      for (int j = l; j < Ns; j += G) lim_subcell<N>(P, P.u_old + i * (n * kM), j, w.ve[j + 2]);
+      if (l < 4) {
+        const long long nb = l < 2 ? il : ir;
+        if (nb >= 0)
+          lim_subcell<N>(P, P.u_old + nb * (n * kM), l < 2 ? Ns - 2 + l : l - 2,
+                         w.ve[l < 2 ? l : Ns + l]);
+      }
     }
     __syncwarp();
-    if (lane < 4) {  // outflow boundary: the boundary subcell itself
-      const long long nb = lane < 2 ? il : ir;
+    if (has && l < 4) {  // outflow boundary: the boundary subcell itself
+      const long long nb = l < 2 ? il : ir;
       if (nb < 0) {
 #pragma unroll
-        for (int r = 0; r < kM; ++r) w.ve[lane < 2 ? lane : Ns + lane][r] = w.ve[lane < 2 ? 2 : Ns + 1][r];
+        for (int r = 0; r < kM; ++r) w.ve[l < 2 ? l : Ns + l][r] = w.ve[l < 2 ? 2 : Ns + 1][r];
       }
     }
     __syncwarp();
-    // lane j: subcell j - 1 (ve index j + 1): degree-1 WENO and predictor
-    if (lane < Ns + 2) {
-      double wn[2][kM];
-      lim_weno2(P.s1, w.ve[lane], w.ve[lane + 1], w.ve[lane + 2], wn);
-      if (!lim_predict1(P, lam_s, wn, w.qR[lane], w.qL[lane]))
-        atomicOr(&P.sp.ctl->status, kStNotConverged);
-    }
-    __syncwarp();
-    // lane f: face between subcells f - 1 and f
-    if (lane < Ns + 1) {
-      double s[kM] = {0.0, 0.0, 0.0};
-#pragma unroll
-      for (int l0 = 0; l0 < 2; ++l0) {
-        double G2[kM];
-        rusanov2(w.qR[lane][l0], w.qL[lane + 1][l0], G2, P.gamma, P.gm1);
-#pragma unroll
-        for (int r = 0; r < kM; ++r) s[r] = fma(P.s1.w[l0], G2[r], s[r]);
-      }
-#pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        w.F[lane][r] = hlam * s[r];
-        if (lane == 0) P.gface[i * 6 + r] = hlam * s[r];
-        if (lane == Ns) P.gface[i * 6 + 3 + r] = hlam * s[r];
+    // item j: subcell j - 1 (ve index j + 1): degree-1 WENO and predictor
+    if (has) {
+      for (int j = l; j < Ns + 2; j += G) {
+        double wn[2][kM];
+        lim_weno2(P.s1, w.ve[j], w.ve[j + 1], w.ve[j + 2], wn);
+        if (!lim_predict1(P, lam_s, wn, w.qR[j], w.qL[j]))
+          atomicOr(&P.sp.ctl->status, kStNotConverged);
       }
     }
     __syncwarp();
-    if (lane < Ns) {
+    // item f: face between subcells f - 1 and f
+    if (has) {
+      for (int f = l; f < Ns + 1; f += G) {
+        double s[kM] = {0.0, 0.0, 0.0};
 #pragma unroll
-      for (int r = 0; r < kM; ++r)
-        w.vnew[lane][r] = w.ve[lane + 2][r] - (double)Ns * (w.F[lane + 1][r] - w.F[lane][r]);
+        for (int l0 = 0; l0 < 2; ++l0) {
+          double G2[kM];
+          rusanov2(w.qR[f][l0], w.qL[f + 1][l0], G2, P.gamma, P.gm1);
+#pragma unroll
+          for (int r = 0; r < kM; ++r) s[r] = fma(P.s1.w[l0], G2[r], s[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          w.F[f][r] = hlam * s[r];
+          if (f == 0) P.gface[i * 6 + r] = hlam * s[r];
+          if (f == Ns) P.gface[i * 6 + 3 + r] = hlam * s[r];
+        }
+      }
     }
     __syncwarp();
-    // reconstruction u = R v (lane = (k, r))
-    if (lane < n * kM) {
-      const int k = lane / kM, r = lane - k * kM;
-      double acc = 0.0;
-      for (int j = 0; j < Ns; ++j) acc = fma(P.R[k][j], w.vnew[j][r], acc);
-      w.ur[k][r] = acc;
+    if (has) {
+      for (int j = l; j < Ns; j += G) {
+#pragma unroll
+        for (int r = 0; r < kM; ++r)
+          w.vnew[j][r] = w.ve[j + 2][r] - (double)Ns * (w.F[j + 1][r] - w.F[j][r]);
+      }
+    }
+    __syncwarp();
+    // reconstruction u = R v (item = (k, r))
+    if (has) {
+      for (int t = l; t < n * kM; t += G) {
+        const int k = t / kM, r = t - k * kM;
+        double acc = 0.0;
+        for (int j = 0; j < Ns; ++j) acc = fma(P.R[k][j], w.vnew[j][r], acc);
+        w.ur[k][r] = acc;
+      }
     }
     __syncwarp();
     bool ok = true;
-    if (lane < Ns) {
-      double v[kM];
+    if (has) {
+      for (int j = l; j < Ns; j += G) {
+        double v[kM];
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        double acc = 0.0;
+        for (int r = 0; r < kM; ++r) {
+          double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[lane][k], w.ur[k][r], acc);
-        v[r] = acc;
+          for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], w.ur[k][r], acc);
+          v[r] = acc;
+        }
+        ok = ok && lim_admissible(v);
       }
-      ok = lim_admissible(v);
     }
-    ok = __all_sync(0xffffffffu, ok);
-    if (lane < n * kM) {
-      const int k = lane / kM, r = lane - k * kM;
-      double val = w.ur[k][r];
-      if (!ok) {  // the mean of the subcell values
-        double mean = 0.0;
-        for (int j = 0; j < Ns; ++j) mean += w.vnew[j][r];
-        val = mean / (double)Ns;
+    ok = (__ballot_sync(0xffffffffu, !ok) & gmask) == 0u;  // this group's vote
+    if (has) {
+      for (int t = l; t < n * kM; t += G) {
+        const int k = t / kM, r = t - k * kM;
+        double val = w.ur[k][r];
+        if (!ok) {  // the mean of the subcell values
+          double mean = 0.0;
+          for (int j = 0; j < Ns; ++j) mean += w.vnew[j][r];
+          val = mean / (double)Ns;
+        }
+        P.u[(i * n + k) * kM + r] = val;
       }
-      P.u[(i * n + k) * kM + r] = val;
     }
-    __syncwarp();  // shared memory is free for the next listed cell
+    __syncwarp();  // shared memory is free for the next pair
   }
 }
 

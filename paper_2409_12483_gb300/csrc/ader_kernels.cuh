@@ -23,7 +23,9 @@
 //                   Sec. 1.4 (DG) or over the cell averages (FV).
 // weno_kernel       eq. weno_reconstr: three stencils of N+1 cell averages,
 //                   smoothness sigma = sum_a int (p^(a))^2, weights
-//                   lambda_S / (sigma + eps)^8, nodal values in the cell.
+//                   lambda_S / (sigma + eps)^8, nodal values in the cell.  The
+//                   weights are taken in FP32 where a bound shows they change
+//                   the result by less than FP64 rounding, else in FP64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -1282,6 +1284,83 @@ __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflPar
   if (bad) atomicOr(&P.ctl->status, kStNonPhysical);
 }
 
+// WENO weights om_0, om_1 (om_2 = 1 - om_0 - om_1) in FP32, accepted only where
+// they change the reconstruction by less than 2^-54 of the cell mean |a_2,0|
+// (the FP64 evaluation's own rounding level).  The monomial coefficients a (and
+// the differences d_S = a_S - a_2) stay FP64; their truncations to FP32 give
+// sigma_S = sum_{j,l >= 1} a_j smono_jl a_l within (2n + 8) 2^-24 of
+// sum |a_j| |smono_jl| |a_l| (truncations and the rounded table: 5 units; the
+// row and sum FMA roundings: 1.5 (n - 1) units).  x_S = sigma_S + eps; the weights are formed as
+// lambda_S r_S / sum_T lambda_T r_T with r_S = (min_T x_T / x_S)^8 <= 1 (no
+// underflow of x^8), so a relative error rho_S of x_S moves r_S by at most
+// 8.1 (rho_min + rho_S) + 15 2^-24 and om_S by twice the largest of those plus
+// 6 2^-24.  With om_2 = 1 - om_0 - om_1 the change of the reconstruction is
+// sum_{S=0,1} dom_S (p_S - p_2), and |p_S - p_2| <= sum_j |d_S,j| on the cell
+// (|t| <= 1).  Returns false (use FP64) when that bound is too large, when a
+// relative error exceeds 2^-12, or on any non-finite value.
+template <int N>
+__device__ __forceinline__ bool weno_weights_f32(const WenoOps& wo, const double (&a)[3][N + 1],
+                                                 const double (&d)[2][N + 1], double* om0,
+                                                 double* om1) {
+  constexpr int n = N + 1;
+  constexpr float u = 0x1p-24f;
+  float x[3], rho[3];
+#pragma unroll
+  for (int S = 0; S < 3; ++S) {
+    float af[n];
+#pragma unroll
+    for (int j = 1; j < n; ++j) af[j] = d2f_trunc(a[S][j]);
+    float sig = 0.f, asig = 0.f;
+#pragma unroll
+    for (int j = 1; j < n; ++j) {
+      float row = 0.f, arow = 0.f;
+#pragma unroll
+      for (int l = 1; l < n; ++l)
+        if (((j + l) & 1) == 0) {
+          row = fmaf(wo.smonof[j][l], af[l], row);
+          arow = fmaf(fabsf(wo.smonof[j][l]), fabsf(af[l]), arow);
+        }
+      sig = fmaf(af[j], row, sig);
+      asig = fmaf(fabsf(af[j]), arow, asig);
+    }
+    x[S] = sig + wo.epsf;
+    // sigma's bound, eps rounded to FP32, the addition; + a floor for values
+    // below FP32's normal range
+    const float ex = fmaf((float)(2 * n + 8) * u, asig, u * (wo.epsf + fabsf(x[S]))) + 0x1p-120f;
+    rho[S] = ex / x[S];
+  }
+  // (each checked on its own: fmaxf / fminf would drop a NaN)
+  if (!(rho[0] <= 0x1p-12f) || !(rho[1] <= 0x1p-12f) || !(rho[2] <= 0x1p-12f)) return false;
+  const float m = fminf(x[0], fminf(x[1], x[2]));
+  const float rho_m = fmaxf(rho[0], fmaxf(rho[1], rho[2]));  // covers the minimum's
+  if (!(m > 0.f)) return false;
+  float r[3];
+#pragma unroll
+  for (int S = 0; S < 3; ++S) {
+    const float q = m / x[S];
+    const float q2 = q * q, q4 = q2 * q2;
+    r[S] = q4 * q4;
+  }
+  const float nl0 = wo.linf[0] * r[0], nl1 = wo.linf[1] * r[1], nl2 = wo.linf[2] * r[2];
+  const float W = nl0 + nl1 + nl2;
+  const float w0 = nl0 / W, w1 = nl1 / W;
+  // relative error of every om_S (om_2's included through om_0 + om_1)
+  const float eom = 2.f * (8.1f * 2.f * rho_m + 15.f * u) + 6.f * u;
+  float D0 = 0.f, D1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    D0 += fabsf(d2f_trunc(d[0][j]));
+    D1 += fabsf(d2f_trunc(d[1][j]));
+  }
+  // the truncations and the sums (n terms) stay within (n + 2) 2^-24 of D_S
+  const float dev = eom * (w0 * D0 + w1 * D1) * (1.f + (float)(n + 4) * u);
+  const float ref = 0x1p-54f * fabsf(d2f_trunc(a[2][0]));
+  if (!(dev <= ref) || !(W < 1e30f)) return false;
+  *om0 = f2d_bits(w0);
+  *om1 = f2d_bits(w1);
+  return true;
+}
+
 // Normalised WENO weights when the product form below would overflow (a
 // smoothness indicator above ~1e37): lambda_S / x8_S, divided by their sum.
 struct Weights3 {
@@ -1322,12 +1401,31 @@ __global__ void __launch_bounds__(128) weno_kernel(const __grid_constant__ WenoP
       }
       vs[s + N] = P.v[j * kM + r];
     }
-    double a[3][n], x8[3];
+    double a[3][n];
+    {
+      // central stencil (cells i - N/2 .. i + N/2, N even): mirroring the
+      // stencil mirrors t, a_j(mirrored v) = (-1)^j a_j(v), so even a_j take the
+      // sums and odd a_j the differences of the mirrored pairs (k, N - k)
+      constexpr int h = N / 2;
+      double sp[h], sm[h];
 #pragma unroll
-    for (int S = 0; S < 3; ++S) {
-      // stencil starts (central, left, right) as in WenoOps::shift, at compile
-      // time so that vs stays in registers
-      const int base = (S == 0 ? -N / 2 : (S == 1 ? -N : 0)) + N;
+      for (int k = 0; k < h; ++k) {
+        sp[k] = vs[k + h] + vs[3 * h - k];  // vs index of stencil cell k is k + N / 2
+        sm[k] = vs[k + h] - vs[3 * h - k];
+      }
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        double acc = (j & 1) ? 0.0 : P.wo.amono[0][j][h] * vs[2 * h];
+#pragma unroll
+        for (int k = 0; k < h; ++k) acc = fma(P.wo.amono[0][j][k], (j & 1) ? sm[k] : sp[k], acc);
+        a[0][j] = acc;
+      }
+    }
+#pragma unroll
+    for (int S = 1; S < 3; ++S) {
+      // left- and right-biased stencils (starts as in WenoOps::shift, at compile
+      // time so that vs stays in registers)
+      const int base = (S == 1 ? -N : 0) + N;
 #pragma unroll
       for (int j = 0; j < n; ++j) {
         double acc = 0.0;
@@ -1335,47 +1433,65 @@ __global__ void __launch_bounds__(128) weno_kernel(const __grid_constant__ WenoP
         for (int k = 0; k < n; ++k) acc = fma(P.wo.amono[S][j][k], vs[base + k], acc);
         a[S][j] = acc;
       }
-      double sigma = 0.0;
-#pragma unroll
-      for (int j = 1; j < n; ++j) {
-        double row = 0.0;
-#pragma unroll
-        for (int l = 1; l < n; ++l)
-          if (((j + l) & 1) == 0) row = fma(P.wo.smono[j][l], a[S][l], row);
-        sigma = fma(a[S][j], row, sigma);
-      }
-      const double x = sigma + P.wo.eps;
-      const double x2 = x * x, x4 = x2 * x2;
-      x8[S] = x4 * x4;
     }
-    double om[3];
-    {
+    // the weighted polynomial as a_2 + om_0 (a_0 - a_2) + om_1 (a_1 - a_2)
+    double d[2][n];
+#pragma unroll
+    for (int S = 0; S < 2; ++S)
+#pragma unroll
+      for (int j = 0; j < n; ++j) d[S][j] = a[S][j] - a[2][j];
+    double om0, om1;
+    if (!weno_weights_f32<N>(P.wo, a, d, &om0, &om1)) {
+      // FP64 weights where the FP32 ones cannot be shown to be exact enough
+      double x8[3];
+#pragma unroll
+      for (int S = 0; S < 3; ++S) {
+        double sigma = 0.0;
+#pragma unroll
+        for (int j = 1; j < n; ++j) {
+          double row = 0.0;
+#pragma unroll
+          for (int l = 1; l < n; ++l)
+            if (((j + l) & 1) == 0) row = fma(P.wo.smono[j][l], a[S][l], row);
+          sigma = fma(a[S][j], row, sigma);
+        }
+        const double x = sigma + P.wo.eps;
+        const double x2 = x * x, x4 = x2 * x2;
+        x8[S] = x4 * x4;
+      }
       const double p12 = x8[1] * x8[2], p02 = x8[0] * x8[2], p01 = x8[0] * x8[1];
       const double n0 = P.wo.lin[0] * p12, n1 = P.wo.lin[1] * p02, n2 = P.wo.lin[2] * p01;
-      const double d = n0 + n1 + n2;
-      if (d < 1.0e300) {
-        const double rd = rcp64(d);
-        om[0] = n0 * rd;
-        om[1] = n1 * rd;
-        om[2] = n2 * rd;
+      const double dn = n0 + n1 + n2;
+      if (dn < 1.0e300) {
+        const double rd = rcp64(dn);
+        om0 = n0 * rd;
+        om1 = n1 * rd;
       } else {
         const Weights3 w = weno_weights_slow(P.wo.lin[0], P.wo.lin[1], P.wo.lin[2], x8[0], x8[1], x8[2]);
-        om[0] = w.w0;
-        om[1] = w.w1;
-        om[2] = w.w2;
+        om0 = w.w0;
+        om1 = w.w1;
       }
     }
     double ah[n];
 #pragma unroll
-    for (int j = 0; j < n; ++j) ah[j] = fma(om[0], a[0][j], fma(om[1], a[1][j], om[2] * a[2][j]));
+    for (int j = 0; j < n; ++j) ah[j] = fma(om0, d[0][j], fma(om1, d[1][j], a[2][j]));
+    // nodal values at the GL nodes, symmetric about the cell centre
+    // (t_{N-q} = -t_q, t_{N/2} = 0): even and odd parts of the polynomial
     double* out = P.w + i * (n * kM) + r;
 #pragma unroll
-    for (int q = 0; q < n; ++q) {
-      double acc = 0.0;
+    for (int q = 0; q < N / 2; ++q) {
+      double ev = ah[0], od = 0.0;
 #pragma unroll
-      for (int j = 0; j < n; ++j) acc = fma(P.wo.vnod[q][j], ah[j], acc);
-      out[q * kM] = acc;
+      for (int j = 1; j < n; ++j) {
+        if (j & 1)
+          od = fma(P.wo.vnod[q][j], ah[j], od);
+        else
+          ev = fma(P.wo.vnod[q][j], ah[j], ev);
+      }
+      out[q * kM] = ev + od;
+      out[(N - q) * kM] = ev - od;
     }
+    out[(N / 2) * kM] = ah[0];
   }
 }
 

@@ -323,7 +323,10 @@ int build_basis(int N, bool weno, Basis* out) {
           s += powl(4.0L, (ld)a) * factorial_ratio(j, a) * factorial_ratio(l, a) / (ld)(m + 1);
         }
         wo.smono[j][l] = (double)s;
+        wo.smonof[j][l] = (float)wo.smono[j][l];
       }
+    wo.epsf = (float)wo.eps;
+    for (int S = 0; S < 3; ++S) wo.linf[S] = (float)wo.lin[S];
   }
   return 0;
 }

@@ -67,6 +67,8 @@ struct WenoOps {
   double smono[kMaxN][kMaxN];     // sigma = sum_{j,l >= 1} a_j smono[j][l] a_l (0 when j + l is odd)
   double amono[3][kMaxN][kMaxN];  // a_j of stencil S from its averages: sum_k amono[S][j][k] v_{S,k} (= mono ainv[S])
   double vnod[kMaxN][kMaxN];      // nodal values from monomial coefficients: c_q = sum_j vnod[q][j] a_j, t_q^j
+  float smonof[kMaxN][kMaxN];     // smono, eps and lin rounded to FP32 (the screened weights)
+  float epsf, linf[3];
 };
 
 struct Basis {

@@ -823,10 +823,11 @@ struct Upd3Cfg {
   static constexpr int USED = CPB * NNN;
   static constexpr int THREADS = (USED + 31) / 32 * 32;  // whole warps for the reductions
   // The screening of lambda_max projects in FP32 throughout for N <= 1; above
-  // that the per-subcell FP64 re-evaluation ((n^3 + n^2 + n) 5 FMAs) costs more
-  // than the two separable FP64 passes (measured at N = 2: 15.9 against 17.2 ms
-  // per face + update launch pair on 96^3 cells), so those stay FP64 and only the
-  // last pass is screened.
+  // that the two separable passes stay FP64 and only the last pass is screened.
+  // With the rigorous FP32 bounds the all-FP32 projection (per-candidate FP64
+  // re-evaluation, outer loop rolled) measured 15.2 / 13.1 / 9.0 ms per face +
+  // update pair at N = 2 / 3 / 4 (96^3, 64^3, 40^3 cells) against 15.4 / 11.5 /
+  // 6.0 ms with the FP64 passes.
   static constexpr bool kScreenAll = N <= 1;
   // dynamic shared memory: U [CPB][NNN][5] (FP64); T1 [CPB][n n][Ns][5] (along
   // zeta) and T2 [CPB][n][Ns Ns][5] (along eta), FP32 or FP64 as above; the upper

@@ -128,6 +128,12 @@ typedef struct {
                              on both sides.  2: every cell is recomputed on its subcells. */
   double nad_delta0;      /* NAD: delta = max(nad_delta0, nad_eps (max - min)) (1e-4) */
   double nad_eps;         /* (1e-3) */
+  int cfl_mode;           /* where lambda_max of the CFL rule (Sec. 1.5) is taken:
+                             0 = over the 2N+1 subcell averages P u of Sec. 1.4 (the
+                             finite-volume subcell representation; default);
+                             1 = over the nodal values u_k (1D DG, Euler system, no
+                             limiter; ADER_ERR_ARG elsewhere).  dt = CFL / (2N+1) dx /
+                             lambda_max in both. */
 } ader_options;
 
 typedef struct {

@@ -72,7 +72,7 @@ class Basis(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("fixed_iter", C.c_int)]
+                ("max_iter", C.c_int), ("fixed_iter", C.c_int), ("cfl_mode", C.c_int)]
 
 
 class Weno(C.Structure):
@@ -127,6 +127,8 @@ def lib():
                 f.argtypes = [P(Basis), P(Params), C.c_double, _DP, _DP, P(C.c_int)]
             L.ob_dg_lambda_max.argtypes = [P(Basis), C.c_double, C.c_int64, _DP]
             L.ob_dg_lambda_max.restype = C.c_double
+            L.ob_dg_lambda_max_nodal.argtypes = [P(Basis), C.c_double, C.c_int64, _DP]
+            L.ob_dg_lambda_max_nodal.restype = C.c_double
             L.ob_fv_lambda_max.argtypes = [C.c_double, C.c_int64, _DP]
             L.ob_fv_lambda_max.restype = C.c_double
             L.ob_dg_dt.argtypes = [P(Basis), P(Params), C.c_double, C.c_int64, _DP]
@@ -286,10 +288,10 @@ class Oracle:
         return out, iters
 
     # -- CFL --
-    def dg_lambda_max(self, u):
+    def dg_lambda_max(self, u, nodal: bool = False):
         u = _arr(u)
-        return lib().ob_dg_lambda_max(C.byref(self.basis), self.params.gamma,
-                                      u.size // (self.n * M), u)
+        f = lib().ob_dg_lambda_max_nodal if nodal else lib().ob_dg_lambda_max
+        return f(C.byref(self.basis), self.params.gamma, u.size // (self.n * M), u)
 
     def dg_dt(self, u, dx):
         u = _arr(u)

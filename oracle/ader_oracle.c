@@ -436,6 +436,18 @@ double ob_dg_lambda_max(const ob_basis* b, double gamma, int64_t ncells, const d
   return lmax;
 }
 
+/* The paper gives the subcell averages as one way to obtain lambda (Sec. 1.5);
+   the nodal values of the DG polynomial are the other representation at hand. */
+double ob_dg_lambda_max_nodal(const ob_basis* b, double gamma, int64_t ncells, const double* u) {
+  double lmax = 0.0;
+  for (int64_t i = 0; i < ncells * b->n; ++i) {
+    const double s = ob_wave_speed(gamma, u + i * OB_M);
+    if (isnan(s)) return NAN;
+    if (s > lmax) lmax = s;
+  }
+  return lmax;
+}
+
 double ob_fv_lambda_max(double gamma, int64_t ncells, const double* v) {
   double lmax = 0.0;
   for (int64_t i = 0; i < ncells; ++i) {
@@ -447,7 +459,8 @@ double ob_fv_lambda_max(double gamma, int64_t ncells, const double* v) {
 }
 
 double ob_dg_dt(const ob_basis* b, const ob_params* p, double dx, int64_t ncells, const double* u) {
-  const double lmax = ob_dg_lambda_max(b, p->gamma, ncells, u);
+  const double lmax = p->cfl_mode == 1 ? ob_dg_lambda_max_nodal(b, p->gamma, ncells, u)
+                                       : ob_dg_lambda_max(b, p->gamma, ncells, u);
   /* d = 1 spatial dimension */
   return p->cfl / (double)(2 * b->N + 1) * dx / lmax;
 }

@@ -54,6 +54,8 @@ typedef struct {
   double tol;       /* Picard tolerance eps_0 (relative to max(1, max|q|)) */
   int max_iter;     /* Picard iteration cap (tolerance mode) */
   int fixed_iter;   /* >0: exactly this many Picard iterations, no early exit */
+  int cfl_mode;     /* DG time step: 0 = lambda over the 2N+1 subcell averages (Sec. 1.4,
+                       1.5), 1 = over the nodal values themselves */
 } ob_params;
 
 /* WENO reconstruction tables for odd order N+1 (N even): three stencils. */
@@ -95,6 +97,8 @@ int ob_predict_cell_nested(const ob_basis* b, const ob_params* p, double lam,
 
 /* ---- CFL (Sec. 1.5) ---- */
 double ob_dg_lambda_max(const ob_basis* b, double gamma, int64_t ncells, const double* u);
+/* lambda = max over every cell and node of |u| + c at the nodal values u[cell][k][r] */
+double ob_dg_lambda_max_nodal(const ob_basis* b, double gamma, int64_t ncells, const double* u);
 double ob_fv_lambda_max(double gamma, int64_t ncells, const double* v);
 double ob_dg_dt(const ob_basis* b, const ob_params* p, double dx, int64_t ncells, const double* u);
 double ob_fv_dt(const ob_params* p, double dx, int64_t ncells, const double* v);

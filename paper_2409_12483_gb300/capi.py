@@ -27,6 +27,7 @@ SCHEMES = {"dg": 0, "fv": 1, "weno": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "ff": 2, "fp32ff": 3, "incr": 4}
 SYSTEMS = {"euler": 0, "reacting": 1, "tracer": 2}
 BOUNDARIES = {"periodic": 0, "outflow": 1}
+CFL_MODES = {"subcell": 0, "nodal": 1}  # where lambda_max is taken (ader_options.cfl_mode)
 SYSTEM_VARS = {0: 3, 1: 5, 2: 4}
 
 
@@ -57,7 +58,7 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("fp64_sweeps", C.c_int), ("fp32_tol", C.c_double),
                 ("profile", C.c_int), ("system", C.c_int), ("omega", C.c_double),
                 ("bc", C.c_int), ("limiter", C.c_int), ("nad_delta0", C.c_double),
-                ("nad_eps", C.c_double)]
+                ("nad_eps", C.c_double), ("cfl_mode", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -201,6 +202,8 @@ def default_options(**kw) -> Options:
             v = BOUNDARIES[v]
         if k == "limiter" and isinstance(v, bool):
             v = int(v)
+        if k == "cfl_mode" and isinstance(v, str):
+            v = CFL_MODES[v]
         setattr(o, k, v)
     return o
 

@@ -200,6 +200,7 @@ FaceParams make_face(const ader_ctx* c, const double* v_old, double* u_new, cons
   f.sys = c->opt.system;
   f.bc = c->opt.bc;
   f.Ns = c->basis.Ns;
+  f.nodal = c->opt.cfl_mode == 1;
   f.gamma = c->opt.gamma;
   f.gm1 = c->opt.gamma - 1.0;
   f.sp = sp;
@@ -221,6 +222,7 @@ CflParams make_cfl(const ader_ctx* ctx, const double* u, int slot) {
   p.dg = ctx->scheme == ADER_SCHEME_DG;
   p.slot = slot;
   p.Ns = ctx->basis.Ns;
+  p.nodal = ctx->opt.cfl_mode == 1;
   p.gamma = ctx->opt.gamma;
   p.gm1 = ctx->opt.gamma - 1.0;
   p.ctl = ctx->ctl;
@@ -519,6 +521,7 @@ ader_status ader_default_options(ader_options* o) {
   o->limiter = 0;
   o->nad_delta0 = 1e-4;
   o->nad_eps = 1e-3;
+  o->cfl_mode = 0;
   return ADER_OK;
 }
 
@@ -565,7 +568,9 @@ ader_status ader_init(const ader_mesh* mesh, int degree, int scheme, const ader_
       (o.bc != ADER_BC_PERIODIC && o.bc != ADER_BC_OUTFLOW) ||
       (o.bc == ADER_BC_OUTFLOW && scheme != ADER_SCHEME_DG) || (o.limiter < 0 || o.limiter > 2) ||
       (o.limiter && (scheme != ADER_SCHEME_DG || o.system != ADER_SYSTEM_EULER || degree < 1)) ||
-      !(o.nad_delta0 >= 0.0) || !(o.nad_eps >= 0.0)) {
+      !(o.nad_delta0 >= 0.0) || !(o.nad_eps >= 0.0) || (o.cfl_mode != 0 && o.cfl_mode != 1) ||
+      (o.cfl_mode == 1 &&
+       (scheme != ADER_SCHEME_DG || o.system != ADER_SYSTEM_EULER || o.limiter != 0))) {
     delete c;
     return ADER_ERR_ARG;
   }
@@ -609,9 +614,9 @@ ader_status ader_init_2d(const ader_mesh2d* mesh, int degree, const ader_options
   } else {
     ader_default_options(&o);
   }
-  // the 2D path: DG, Euler, FP64 predictor, periodic, no limiter
+  // the 2D path: DG, Euler, FP64 predictor, periodic, no limiter, subcell CFL
   if (o.system != ADER_SYSTEM_EULER || o.precision != ADER_PREC_FP64 || o.bc != ADER_BC_PERIODIC ||
-      o.limiter != 0)
+      o.limiter != 0 || o.cfl_mode != 0)
     return ADER_ERR_ARG;
   ader_mesh m1{mesh->nx * mesh->ny, mesh->x0, mesh->x1};
   ader_ctx* c = nullptr;
@@ -642,7 +647,7 @@ ader_status ader_init_3d(const ader_mesh3d* mesh, int degree, const ader_options
     ader_default_options(&o);
   }
   if (o.system != ADER_SYSTEM_EULER || o.precision != ADER_PREC_FP64 || o.bc != ADER_BC_PERIODIC ||
-      o.limiter != 0)
+      o.limiter != 0 || o.cfl_mode != 0)
     return ADER_ERR_ARG;
   ader_mesh m1{mesh->nx * mesh->ny * mesh->nz, mesh->x0, mesh->x1};
   ader_ctx* c = nullptr;

@@ -411,7 +411,7 @@ cudaError_t ADER_CAT(launch_face_multi_, ADER_DEG)(const FaceParams& p, const Mu
 }
 
 cudaError_t ADER_CAT(launch_cfl_, ADER_DEG)(const CflParams& p, cudaStream_t s) {
-  const long long items = p.dg ? p.ncells * p.Ns : p.ncells;
+  const long long items = p.dg ? p.ncells * (p.nodal ? D + 1 : p.Ns) : p.ncells;
   cfl_kernel<D><<<grid_for(items, 256, 152LL * 8), 256, 0, s>>>(p);
   return cudaGetLastError();
 }

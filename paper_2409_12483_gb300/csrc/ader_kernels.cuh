@@ -964,14 +964,17 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   // another subcell's FP64 speed, so the result is the FP64 maximum over every
   // subcell.
   __syncthreads();
-  const int items = P.dg ? nvalid * Ns : nvalid;
+  // the subcell averages P u (DG), or the values themselves: FV cell averages,
+  // DG nodal values (cfl_mode 1; item = (cell, node) as the [cell][k][r] layout)
+  const bool proj = P.dg && !P.nodal;
+  const int items = P.dg ? nvalid * (P.nodal ? n : Ns) : nvalid;
   const float gf = (float)P.gamma, gm1f = (float)P.gm1;
   const float one[1] = {1.f};
-  const float eproj = P.dg ? (float)(n + 4) * 0x1p-24f : 0x1p-22f;
+  const float eproj = proj ? (float)(n + 4) * 0x1p-24f : 0x1p-22f;
   float lo_loc = 0.f;
   for (int item = tid; item < items; item += THREADS) {
     float v[kM], e[kM];
-    if (P.dg) {
+    if (proj) {
       const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
@@ -1009,14 +1012,14 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   // within 2^-47 each (4 units of 2^-48), each product's cross terms and dropped
   // low x low within 12 units, and the 2n roundings of the low-part sum within
   // n^2 / 2 + 6.5 n + 5 units: below (n^2 + 8n + 24) 2^-48 in all
-  const float eproj2 = P.dg ? (float)(n * n + 8 * n + 24) * 0x1p-48f : 0x1p-45f;
+  const float eproj2 = proj ? (float)(n * n + 8 * n + 24) * 0x1p-48f : 0x1p-45f;
   unsigned long long lo2_loc = 0ull;
   for (int item = tid; item < items; item += THREADS) {
     unsigned long long h = 0ull;
     if (sh.lt[item] >= cut) {
       ff v[kM];
       float e[kM];
-      if (P.dg) {
+      if (proj) {
         const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
@@ -1054,7 +1057,7 @@ __device__ __forceinline__ void face_lambda(const FaceParams& P, const StepParam
   for (int item = tid; item < items; item += THREADS) {
     if (!(hi2[item] >= cut2)) continue;
     double v[kM];
-    if (P.dg) {
+    if (proj) {
       const int lc = item / Ns, j = item - lc * Ns;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
@@ -1254,13 +1257,16 @@ template <int N>
 __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflParams P) {
   constexpr int n = N + 1, Ns = 2 * N + 1;
   __shared__ unsigned long long s_wmax[32];
-  const long long items = P.dg ? P.ncells * Ns : P.ncells;
+  // subcell averages (DG), or the values themselves: FV cell averages, DG
+  // nodal values (cfl_mode 1, Euler: item = (cell, node) as the layout)
+  const bool proj = P.dg && !P.nodal;
+  const long long items = P.dg ? P.ncells * (P.nodal ? n : Ns) : P.ncells;
   double lmax = 0.0;
   bool bad = false;
   for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
     double v[kM];
-    if (P.dg) {
+    if (proj) {
       // the Euler variables (rho, m, E) lead each node's record of P.vars values
       const long long cell = it / Ns;
       const int j = (int)(it - cell * Ns);

@@ -54,6 +54,7 @@ struct FaceParams {
   int sys;               // kSysEuler or kSysReacting
   int bc;                // kBcPeriodic or kBcOutflow
   int Ns;
+  int nodal;             // DG: lambda_max over the nodal values (cfl_mode 1), not the subcells
   double gamma, gm1;
   StepParams sp;
   OpsD ops;
@@ -67,6 +68,7 @@ struct CflParams {
   int dg;
   int slot;
   int Ns;
+  int nodal;             // DG: over the nodal values (cfl_mode 1), not the subcells
   double gamma, gm1;
   DevCtl* ctl;
   OpsD ops;

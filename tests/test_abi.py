@@ -64,6 +64,32 @@ def test_init_rejects_bad_arguments(lib):
     assert rc == 1
 
 
+def test_cfl_mode_option(lib):
+    """cfl_mode 1 (lambda over the nodal values) is a 1D DG Euler option without
+    the limiter; elsewhere, and for unknown modes, ader_init refuses it."""
+    from paper_2409_12483_gb300.capi import Mesh, Mesh2D, Mesh3D, default_options
+    assert default_options().cfl_mode == 0
+    ctx = C.c_void_p()
+    m = Mesh(10, 0.0, 1.0)
+    for scheme, deg, kw in [(0, 3, {}), (0, 0, {}), (0, 5, {"precision": "incr"}),
+                            (0, 4, {"bc": "outflow"})]:
+        o = default_options(cfl_mode="nodal", **kw)
+        assert lib.ader_init(C.byref(m), deg, scheme, C.byref(o), C.byref(ctx)) == 0
+        lib.ader_destroy(ctx)
+    for scheme, deg, kw in [(1, 4, {}), (0, 3, {"limiter": 1}), (0, 3, {"system": "reacting"}),
+                            (0, 3, {"system": "tracer"})]:
+        o = default_options(cfl_mode=1, **kw)
+        assert lib.ader_init(C.byref(m), deg, scheme, C.byref(o), C.byref(ctx)) == 1, (scheme, kw)
+        assert not ctx.value
+    o = default_options(cfl_mode=2)
+    assert lib.ader_init(C.byref(m), 3, 0, C.byref(o), C.byref(ctx)) == 1
+    o = default_options(cfl_mode=1)
+    assert lib.ader_init_2d(C.byref(Mesh2D(4, 4, 0.0, 1.0, 0.0, 1.0)), 2, C.byref(o),
+                            C.byref(ctx)) == 1
+    assert lib.ader_init_3d(C.byref(Mesh3D(2, 2, 2, 0.0, 1.0, 0.0, 1.0, 0.0, 1.0)), 2,
+                            C.byref(o), C.byref(ctx)) == 1
+
+
 def test_sizes_and_coordinates(lib):
     from paper_2409_12483_gb300.capi import Mesh, default_options
     opt = default_options()

@@ -99,6 +99,29 @@ def test_step_parity_fixed_and_cfl_dt(cuda, oracle_mod, N):
     assert abs(ctx.ader_compute_dt(ud) - dt) <= 1e-14 * dt
 
 
+@pytest.mark.parametrize("N", range(0, 8))
+def test_nodal_cfl_mode(cuda, oracle_mod, N):
+    """cfl_mode 1 (lambda over the nodal values): the device time step equals
+    the oracle's, and a 20-step solve (the interface kernel's lambda reduction
+    gives steps 2..20) follows the oracle's solve in the same mode."""
+    import torch
+    o = oracle_mod.Oracle(N)
+    o.set(cfl_mode=1)
+    u = W.nodal_state(field_nonlinear(30 + N), o.node_x(NCELLS))
+    dx = 1.0 / NCELLS
+    ctx = make(cuda, NCELLS, N, cfl_mode="nodal")
+    ud = to_dev(u, cuda)
+    dt = o.dg_dt(u, dx)
+    assert abs(ctx.ader_compute_dt(ud) - dt) <= 1e-14 * dt
+    ref, steps_ref, t_ref, rc = o.solve("dg", u, dx, max_steps=20)
+    assert rc == 0
+    steps, t, rc = ctx.ader_solve(ud, max_steps=20)
+    torch.cuda.synchronize()
+    assert steps == steps_ref == 20
+    assert abs(t - t_ref) <= 1e-13 * t_ref
+    assert rel_linf(ud.cpu().numpy(), ref) < 1e-11
+
+
 @pytest.mark.parametrize("nc", [1, 2, 3, 31, 33, 65])
 def test_small_and_ragged_meshes(cuda, oracle_mod, nc):
     import torch

@@ -64,6 +64,21 @@ def test_dg_1d(cuda, oracle_mod, N, case):
 
 
 @pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("N", [1, 5])
+def test_dg_1d_nodal_mode(cuda, oracle_mod, N, case):
+    """the same screens over the nodal values (cfl_mode 1)"""
+    from paper_2409_12483_gb300 import Context
+    nc = 1000
+    o = oracle_mod.Oracle(N)
+    o.set(cfl_mode=1)
+    u = W.conserved(*prim_1d(o.node_x(nc), case, N + 3))
+    ctx = Context(nc, N, "dg", cfl_mode="nodal")
+    u1, dt2 = second_step_dt(ctx, to_dev(u))
+    ref = o.dg_dt(u1, 1.0 / nc)
+    assert abs(dt2 - ref) <= 1e-14 * ref
+
+
+@pytest.mark.parametrize("case", CASES)
 def test_weno_1d(cuda, oracle_mod, case):
     from paper_2409_12483_gb300 import Context
     nc, N = 1000, 4

@@ -98,6 +98,35 @@ def test_lambda_over_subcell_averages(oracle_mod, N):
     assert abs(np_speed(u[0]).max() - expect) > 1e-6
 
 
+@pytest.mark.parametrize("N", [0, 2, 5, 7])
+def test_lambda_nodal_mode(oracle_mod, N):
+    """cfl_mode 1: lambda over the nodal values themselves.  Pinned by the
+    primitive fields (|u| + sqrt(gamma p / rho) from u and p as given, not from
+    the conserved variables), the constant state's closed form, and a single
+    fast node among slow ones that only the nodal rule sees (the subcell
+    averages blur it)."""
+    o = oracle_mod.Oracle(N, cfl=0.4)
+    nc = 7
+    x = o.node_x(nc)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x)
+    vel = 0.4 * np.cos(2 * np.pi * x) - 0.1
+    p = 0.8 + 0.2 * np.sin(4 * np.pi * x + 0.3)
+    u = W.conserved(rho, vel, p)
+    expect = (np.abs(vel) + np.sqrt(1.4 * p / rho)).max()
+    assert abs(o.dg_lambda_max(u, nodal=True) - expect) <= 1e-14 * expect
+    o.set(cfl_mode=1)
+    assert abs(o.dg_dt(u, 1.0 / nc) - 0.4 / (2 * N + 1) / nc / expect) <= 1e-15 / nc
+    o.set(cfl_mode=0)
+    assert abs(o.dg_dt(u, 1.0 / nc) - 0.4 / (2 * N + 1) / nc / o.dg_lambda_max(u)) <= 1e-15 / nc
+    U = W.conserved(1.2, -0.3, 0.7)
+    c = np.tile(U, (3, o.n, 1))
+    assert abs(o.dg_lambda_max(c, nodal=True) - (0.3 + np.sqrt(1.4 * 0.7 / 1.2))) < 1e-14
+    if N >= 1:
+        c[1, N // 2] = W.conserved(1.2, 2.0, 0.7)  # one fast node
+        assert abs(o.dg_lambda_max(c, nodal=True) - (2.0 + np.sqrt(1.4 * 0.7 / 1.2))) < 1e-14
+        assert o.dg_lambda_max(c) < 2.0 + np.sqrt(1.4 * 0.7 / 1.2) - 1e-3
+
+
 # ---------------------------------------------------------------------------
 # DG corrector
 # ---------------------------------------------------------------------------

@@ -70,6 +70,11 @@ struct IncrCfg {
   static constexpr int FLOATS = DM + 2 * CPB;
   static constexpr size_t kSmemBytes = (size_t)FLOATS * sizeof(float);
   static constexpr bool kValid = PredCfg<N, CPB>::kValid;
+  // resident blocks the register allocation must allow.  From N = 4 the kernel
+  // is latency-bound at 2 blocks per SM (139-164 registers); capping for 3
+  // blocks of <= 192 threads (else 2) measured 10-26 % faster for the best tile
+  // shape at N = 4, 5 and 7 (DG and FV, 10^5 and 10^6 cells), slower at N = 3.
+  static constexpr int MIN_BLOCKS = N >= 4 ? (THREADS <= 192 ? 3 : 2) : 1;
 };
 
 template <int N, int CPB>
@@ -352,7 +357,7 @@ __device__ __forceinline__ void predict_tile_incr(const PredictParams& P, const 
 }
 
 template <int N, int CPB>
-__global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS)
+__global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS, IncrCfg<N, CPB>::MIN_BLOCKS)
     predict_incr_kernel(const __grid_constant__ PredictParams P) {
   extern __shared__ __align__(16) float smf[];
   __shared__ PredShared<N> sh;
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS)
 // Batched increment-form predictor over the tiles of many solves (as
 // predict_multi_kernel; every solve keeps its own device time step).
 template <int N, int CPB>
-__global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS)
+__global__ void __launch_bounds__(IncrCfg<N, CPB>::THREADS, IncrCfg<N, CPB>::MIN_BLOCKS)
     predict_incr_multi_kernel(const __grid_constant__ PredictParams P, const MultiArgs M) {
   extern __shared__ __align__(16) float smf[];
   __shared__ PredShared<N> sh;

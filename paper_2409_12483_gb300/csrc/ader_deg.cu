@@ -52,6 +52,12 @@ void launch_update2d_shape(const Face2DParams& p, cudaStream_t s) {
 
 // The helpers below are instantiated in every per-degree translation unit with
 // different bodies (they depend on ADER_DEG), so they must have internal linkage.
+// The float-float predictor forms run with a residency target (predict_ff_kernel)
+// in 32- and 64-cell tiles from N = 4; 16-cell tiles, where the target raised
+// the register count and measured slower, keep predict_kernel.
+template <int CPB>
+constexpr bool kFFCapped = D >= 4 && CPB >= 32;
+
 template <int CPB>
 cudaError_t prepare_cpb() {
   if constexpr (!PredCfg<D, CPB>::kValid) {
@@ -64,14 +70,22 @@ cudaError_t prepare_cpb() {
     e = cudaFuncSetAttribute(predict_kernel<D, 1, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(predict_kernel<D, 3, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes);
-    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(predict_incr_kernel<D, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)IncrCfg<D, CPB>::kSmemBytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(predict_kernel<D, 2, CPB>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if constexpr (kFFCapped<CPB>) {
+      e = cudaFuncSetAttribute(predict_ff_kernel<D, 3, CPB>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(predict_ff_kernel<D, 2, CPB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    } else {
+      e = cudaFuncSetAttribute(predict_kernel<D, 3, CPB>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(predict_kernel<D, 2, CPB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
   }
 }
 
@@ -85,8 +99,12 @@ cudaError_t launch_predict_cpb(const PredictParams& p, cudaStream_t s) {
     if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (p.prec == 1 && !p.from_q)
       predict_kernel<D, 1, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else if (p.prec == 2 && !p.from_q && kFFCapped<CPB>)
+      predict_ff_kernel<D, 2, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else if (p.prec == 2 && !p.from_q)
       predict_kernel<D, 2, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
+    else if (p.prec == 3 && !p.from_q && kFFCapped<CPB>)
+      predict_ff_kernel<D, 3, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else if (p.prec == 3 && !p.from_q)
       predict_kernel<D, 3, CPB><<<(unsigned)blocks, C::THREADS, C::kSmemBytes, s>>>(p);
     else if (p.prec == 4 && !p.from_q)

@@ -50,6 +50,18 @@ struct PredCfg {
   static constexpr bool kValid =
       (THREADS % 32 == 0 || CPB == 16) && THREADS <= 512 && (N <= 5 || CPB <= 32);
 };
+
+// Resident blocks the register allocation of predict_ff_kernel must allow.
+// The float-float forms (PREC 2, 3) are latency-bound at two blocks from
+// N = 4; asking for three blocks of <= 192 threads (else two) measured 1-9 %
+// faster for the best tile shape at N = 4, 5, 7 (10^5 and 10^6 cells).  The
+// FP64 forms are FP64-pipe bound and measured the same either way; they run in
+// predict_kernel, whose bounds name no block count (naming one, even 1, moved
+// the FP64 kernel at N = 5 from ~128 to ~155 registers).
+template <int N, int CPB>
+constexpr int pred_ff_min_blocks() {
+  return N >= 4 ? (PredCfg<N, CPB>::THREADS <= 192 ? 3 : 2) : 1;
+}
 constexpr int kMaxCpb = 64;
 
 // |x| as an ordered bit pattern (sign bit cleared), in a PTX integer
@@ -837,6 +849,20 @@ __device__ __forceinline__ void predict_tile(const PredictParams& P, const TileI
 template <int N, int PREC, int CPB = 32>
 __global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS)
     predict_kernel(const __grid_constant__ PredictParams P) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ PredShared<N> sh;
+  double dt;
+  if (!block_step_dt<N>(P.sp, &dt, blockIdx.x == 0, sh)) return;  // uniform
+  const TileIO io{P.u, P.trace, P.q_out, P.q_in, P.ncells, P.sp.ctl};
+  predict_tile<N, PREC, CPB>(P, io, blockIdx.x, dt * P.sp.inv_dx, smem, sh);
+}
+
+// The same predictor for the float-float forms (PREC 2, 3) with a residency
+// target (pred_ff_min_blocks).
+template <int N, int PREC, int CPB = 32>
+__global__ void __launch_bounds__(PredCfg<N, CPB>::THREADS, (pred_ff_min_blocks<N, CPB>()))
+    predict_ff_kernel(const __grid_constant__ PredictParams P) {
+  static_assert(PREC == 2 || PREC == 3, "float-float forms only");
   extern __shared__ __align__(16) double smem[];
   __shared__ PredShared<N> sh;
   double dt;

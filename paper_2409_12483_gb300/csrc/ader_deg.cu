@@ -204,7 +204,10 @@ cudaError_t launch_face_cf(const FaceParams& p, cudaStream_t s) {
   using C = FaceCfg<D, CF>;
   const long long blocks = (p.ncells + C::C - 1) / C::C;
   if (blocks <= 0 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  face_update_kernel<D, CF><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  if constexpr (D >= 5)
+    face_update_occ_kernel<D, CF><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
+  else
+    face_update_kernel<D, CF><<<(unsigned)blocks, C::THREADS, 0, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace

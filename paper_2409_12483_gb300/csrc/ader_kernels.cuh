@@ -1245,10 +1245,8 @@ __device__ __forceinline__ void face_stage_tables(const FaceParams& P, FaceShare
   __syncthreads();
 }
 
-template <int N, int C = 64>
-__global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
-    face_update_kernel(const __grid_constant__ FaceParams P) {
-  __shared__ FaceShared<N, C> sh;
+template <int N, int C>
+__device__ __forceinline__ void face_update_block(const FaceParams& P, FaceShared<N, C>& sh) {
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;
@@ -1256,6 +1254,27 @@ __global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
   const FaceIO io{P.trace, P.v_old, P.u_new, P.ncells};
   face_tile<N, C>(P, io, P.sp, blockIdx.x, dt, sh);
   corrector_finish(P.sp, dt, last, blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+template <int N, int C = 64>
+__global__ void __launch_bounds__(FaceCfg<N, C>::THREADS)
+    face_update_kernel(const __grid_constant__ FaceParams P) {
+  __shared__ FaceShared<N, C> sh;
+  face_update_block<N, C>(P, sh);
+}
+
+// The same kernel with 5 resident blocks asked of the register allocation.  The
+// compiler's choice (56-70 registers) leaves 4 blocks from N = 5, and the
+// kernel's short phases between barriers are latency-bound there: 5 blocks
+// (48 registers) measured 7-15 % faster at N = 5 and 7 on 10^6 cells and the
+// same at N = 5 on 10^5.  Below N = 5 (48 registers, 5 blocks already) naming
+// a block count only made the allocation worse, so those degrees keep
+// face_update_kernel.
+template <int N, int C = 64>
+__global__ void __launch_bounds__(FaceCfg<N, C>::THREADS, 5)
+    face_update_occ_kernel(const __grid_constant__ FaceParams P) {
+  __shared__ FaceShared<N, C> sh;
+  face_update_block<N, C>(P, sh);
 }
 
 // Batched interface flux + update over the tiles of many solves (see predict_multi_kernel).

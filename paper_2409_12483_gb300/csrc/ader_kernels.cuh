@@ -1336,8 +1336,9 @@ __global__ void __launch_bounds__(256) cfl_kernel(const __grid_constant__ CflPar
 }
 
 // WENO weights om_0, om_1 (om_2 = 1 - om_0 - om_1) in FP32, accepted only where
-// they change the reconstruction by less than 2^-54 of the cell mean |a_2,0|
-// (the FP64 evaluation's own rounding level).  The monomial coefficients a (and
+// they change the reconstruction by less than 2^-52 of the cell mean |a_2,0|:
+// two units in its last place, below the rounding bound of the FP64
+// evaluation of a nodal value (an n-term sum: n units).  The monomial coefficients a (and
 // the differences d_S = a_S - a_2) stay FP64; their truncations to FP32 give
 // sigma_S = sum_{j,l >= 1} a_j smono_jl a_l within (2n + 8) 2^-24 of
 // sum |a_j| |smono_jl| |a_l| (truncations and the rounded table: 5 units; the
@@ -1405,7 +1406,7 @@ __device__ __forceinline__ bool weno_weights_f32(const WenoOps& wo, const double
   }
   // the truncations and the sums (n terms) stay within (n + 2) 2^-24 of D_S
   const float dev = eom * (w0 * D0 + w1 * D1) * (1.f + (float)(n + 4) * u);
-  const float ref = 0x1p-54f * fabsf(d2f_trunc(a[2][0]));
+  const float ref = 0x1p-52f * fabsf(d2f_trunc(a[2][0]));
   if (!(dev <= ref) || !(W < 1e30f)) return false;
   *om0 = f2d_bits(w0);
   *om1 = f2d_bits(w1);

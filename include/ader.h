@@ -378,7 +378,8 @@ typedef struct {
 
 /* Time every valid predictor tile shape, interface tile shape and graph length on
  * the state u_dev (not modified; the solve trials run on a workspace copy) with
- * `reps` repetitions each, keep the fastest, and report them.  Valid predictor
+ * `reps` repetitions each (the tile shapes in three interleaved rounds, each
+ * keeping its fastest), keep the fastest, and report them.  Valid predictor
  * shapes have (N+1) * cells a multiple of 32 and at most 512 threads (32 cells
  * at most for N > 5).  Synchronises. */
 ader_status ader_autotune(ader_ctx* ctx, const double* u_dev, int reps, ader_tuning* out);

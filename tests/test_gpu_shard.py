@@ -32,6 +32,15 @@ def _initial(scheme, N, n_global):
     return W.cell_average_state(W.modes4(3), n_global).reshape(n_global, -1)
 
 
+def _opts(prec):
+    """'fp64', 'ff', ... or 'fp64+nodal' (cfl_mode 1) as Context options"""
+    parts = prec.split("+")
+    o = {"precision": parts[0]}
+    if "nodal" in parts[1:]:
+        o["cfl_mode"] = "nodal"
+    return o
+
+
 def _rank(rank, world, port, scheme, N, n_global, t_end, prec, out):
     import torch
     import torch.distributed as dist
@@ -47,7 +56,7 @@ def _rank(rank, world, port, scheme, N, n_global, t_end, prec, out):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     first, nl = shard.partition(n_global, world, rank)
-    ctx = ShardContext(n_global, first, nl, N, scheme, device=dev, precision=prec)
+    ctx = ShardContext(n_global, first, nl, N, scheme, device=dev, **_opts(prec))
     H, vpc = ctx.halo, ctx.values_per_cell
     u0 = _initial(scheme, N, n_global)
     u = torch.full((ctx.state_count,), float("nan"), dtype=torch.float64, device=dev)
@@ -63,7 +72,7 @@ def _rank(rank, world, port, scheme, N, n_global, t_end, prec, out):
 
 @pytest.mark.parametrize("scheme,N,n_global,world,prec", [
     ("dg", 5, 1001, 1, "fp64"), ("dg", 5, 1001, 2, "fp64"), ("dg", 3, 777, 3, "fp64"),
-    ("fv", 4, 900, 2, "fp64"), ("dg", 5, 640, 2, "ff")])
+    ("fv", 4, 900, 2, "fp64"), ("dg", 5, 640, 2, "ff"), ("dg", 5, 1001, 2, "fp64+nodal")])
 def test_sharded_equals_single_context(cuda, oracle_mod, scheme, N, n_global, world, prec):
     import torch
     import torch.multiprocessing as mp
@@ -71,7 +80,7 @@ def test_sharded_equals_single_context(cuda, oracle_mod, scheme, N, n_global, wo
     from paper_2409_12483_gb300 import Context
     t_end = 0.01
     u0 = _initial(scheme, N, n_global)
-    one = Context(n_global, N, scheme, precision=prec)
+    one = Context(n_global, N, scheme, **_opts(prec))
     ud = torch.tensor(u0.ravel(), device=cuda)
     steps_ref, t_ref, _ = one.ader_solve(ud, t_end=t_end)
     ref = ud.cpu().numpy()

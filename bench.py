@@ -268,8 +268,50 @@ def _variant_line(name, workload, ctx, u0, cells, degree, time_steps, steps, war
 # every secondary study is printed on an earlier line of its own.
 HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                  "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
-                 "roofline", "e2e", "gpu_launches", "clocks", "errors", "cpu_baseline")
+                 "roofline", "e2e", "gpu_launches", "clocks", "errors", "cpu_baseline",
+                 "fp32_predictor", "latency")
 MAX_HEADLINE_BYTES = 4096
+
+# the FP32-predictor forms of the headline workload, as named by run_variants
+FP32_FORMS = (("increment", "dg5-1e5-incr"), ("fp32_ff_sweep", "dg5-1e5-fp32ff1"),
+              ("fp32_fp64_sweeps", "dg5-1e5-fp32pred"))
+
+
+def fp32_predictor_summary(variants, fp64_value):
+    """The headline's FP32-predictor figures: each form's throughput on the
+    headline workload and its distance from the FP64 path, from the
+    precision_forms_and_variants study (None where the study has no such line)."""
+    by_name = {v.get("name"): v for v in variants or [] if isinstance(v, dict)}
+    forms = {}
+    for key, name in FP32_FORMS:
+        v = by_name.get(name)
+        if not v or "value" not in v:
+            continue
+        forms[key] = {"value": v["value"], "vs_fp64": v["value"] / fp64_value,
+                      "rel_linf_vs_fp64_path": v.get("rel_linf_vs_fp64_path"),
+                      "l1_density_vs_exact": v.get("l1_density_vs_exact")}
+    if not forms:
+        return None
+    return {"unit": UNIT, "workload": "the headline's (study precision_forms_and_variants)",
+            "forms": forms}
+
+
+def latency_summary(serving, frac=0.8):
+    """p50/p99 solve latency of the continuous-batching server at `frac` of its
+    saturation rate, with the plain per-solve FP64 path on the same arrivals,
+    from the serving study (None where the study has no such point)."""
+    if not isinstance(serving, dict):
+        return None
+    pts = [o for o in serving.get("open_loop", []) if o.get("arrival_rate_frac_of_saturation") == frac]
+    if not pts:
+        return None
+    o = pts[0]
+    return {"p50_s": o["server"]["p50_s"], "p99_s": o["server"]["p99_s"],
+            "load": f"{frac} x saturation", "solves_per_s": o["server"]["solves_per_s"],
+            "saturation_solves_per_s": serving.get("saturation", {}).get("solves_per_s"),
+            "plain_fp64": {"p50_s": o["baseline_per_solve_fp64"]["p50_s"],
+                           "p99_s": o["baseline_per_solve_fp64"]["p99_s"]},
+            "workload": "scaled request stream (study serving)"}
 
 
 def headline_line(*, world, steps, warmup, value, ms_per_step, tuning, roofline, e2e, launches,
@@ -293,7 +335,7 @@ def headline_line(*, world, steps, warmup, value, ms_per_step, tuning, roofline,
 def print_study(name, fn, *args, out=None):
     """Run one secondary study and print it as its own compact JSON line
     ({"study": name, ...}); a study that raises prints its error instead, so the
-    headline that follows is always printed."""
+    headline that follows is always printed.  Returns the result (None on error)."""
     out = out or sys.stdout
     t0 = time.perf_counter()
     try:
@@ -302,6 +344,7 @@ def print_study(name, fn, *args, out=None):
         body = {"study": name, "error": f"{type(e).__name__}: {e}"[:500]}
     body["seconds"] = round(time.perf_counter() - t0, 2)
     print(json.dumps(body, separators=(",", ":"), default=float), file=out, flush=True)
+    return body.get("result")
 
 
 def print_headline(head: dict, out=None) -> str:
@@ -617,8 +660,13 @@ def main():
         if not args.no_2d:
             studies.append(("two_d", run_2d, (args, dev, flush)))
             studies.append(("three_d", run_3d, (args, dev, flush)))
-        for name, fn, fargs in studies:
-            print_study(name, fn, *fargs)
+        results = {name: print_study(name, fn, *fargs) for name, fn, fargs in studies}
+        fp32 = fp32_predictor_summary(results.get("precision_forms_and_variants"), value)
+        if fp32:
+            head["fp32_predictor"] = fp32
+        lat = latency_summary(results.get("serving"))
+        if lat:
+            head["latency"] = lat
         if not args.no_cpu_baseline:
             rate, steps, secs = cpu_oracle_rate()
             u_in, u_or, k = cpu_oracle_rate.last

@@ -106,3 +106,42 @@ def test_headline_rejects_extra_keys_and_oversize():
     head["config"]["workload"] = "x" * 5000
     with pytest.raises(ValueError):
         bench.print_headline(head, out=io.StringIO())
+
+
+def test_headline_carries_fp32_forms_and_latency():
+    """The metric names FP64 vs the FP32 predictor and p50/p99 latency: the
+    headline summarises both studies and still fits the size limit."""
+    import io
+    sys.path.insert(0, ROOT)
+    import bench
+    long = "x" * 300  # study lines carry long workload strings; the summary drops them
+    variants = [{"name": n, "workload": long, "value": v, "rel_linf_vs_fp64_path": e,
+                 "l1_density_vs_exact": 1e-14}
+                for n, v, e in (("dg5-1e5-incr", 5.3e8, 1.4e-13), ("dg5-1e5-fp32ff1", 3.8e8, 3e-8),
+                                ("dg5-1e5-fp32pred", 1.2e8, 8e-9), ("dg7-1e6-incr", 3.8e8, 1e-13))]
+    variants.append({"name": "dg5-1e5-ffpred", "workload": long, "error": "RuntimeError: x"})
+    pt = {"server": {"p50_s": 0.058, "p99_s": 0.35, "solves_per_s": 161.0},
+          "baseline_per_solve_fp64": {"p50_s": 3.7, "p99_s": 7.6, "solves_per_s": 15.3}}
+    serving = {"workload": long, "saturation": {"solves_per_s": 238.0},
+               "open_loop": [dict(pt, arrival_rate_frac_of_saturation=f) for f in (0.5, 0.8, 1.0)]}
+    serving["open_loop"][1]["server"] = dict(pt["server"], p50_s=0.0579)
+    head = _fake_headline(bench)
+    head["fp32_predictor"] = bench.fp32_predictor_summary(variants, head["value"])
+    head["latency"] = bench.latency_summary(serving)
+    out = io.StringIO()
+    line = bench.print_headline(head, out=out)
+    assert len(line) <= bench.MAX_HEADLINE_BYTES
+    d = json.loads(line)
+    forms = d["fp32_predictor"]["forms"]
+    assert set(forms) == {"increment", "fp32_ff_sweep", "fp32_fp64_sweeps"}
+    assert forms["increment"]["value"] == 5.3e8
+    assert abs(forms["increment"]["vs_fp64"] - 5.3e8 / head["value"]) <= 1e-12
+    assert forms["fp32_fp64_sweeps"]["rel_linf_vs_fp64_path"] == 8e-9
+    lat = d["latency"]
+    assert lat["p50_s"] == 0.0579 and lat["p99_s"] == 0.35 and lat["load"] == "0.8 x saturation"
+    assert lat["saturation_solves_per_s"] == 238.0 and lat["plain_fp64"]["p50_s"] == 3.7
+    # missing or failed studies leave the keys out rather than breaking the line
+    assert bench.fp32_predictor_summary(None, 1.0) is None
+    assert bench.fp32_predictor_summary([{"name": "dg5-1e5-incr", "error": "x"}], 1.0) is None
+    assert bench.latency_summary(None) is None
+    assert bench.latency_summary({"open_loop": []}) is None

@@ -191,6 +191,50 @@ def test_full_size_n5_sampled_and_conservation(cuda, oracle_mod):
     assert l1 < 1e-12 and linf < 1e-11
 
 
+def test_headline_workload_in_the_bench_launch_configuration(cuda, oracle_mod):
+    """The headline workload as the benchmark times it: N = 5, 10^5 cells, tile
+    shapes picked by the autotuner, the device-resident graph time loop, 100
+    time steps.  The whole state against the oracle's 100 steps (the 1e-10 bar
+    at t_end), with the same final time."""
+    import torch
+    N, nc, steps = 5, 100_000, 100
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(W.modes4(), o.node_x(nc))
+    ctx = make(cuda, nc, N)
+    ud = to_dev(u, cuda)
+    tuning = ctx.ader_autotune(ud, reps=2)
+    s, t, rc = ctx.ader_solve(ud, max_steps=steps)
+    torch.cuda.synchronize()
+    ref, s_ref, t_ref, rc_ref = o.solve("dg", u, 1.0 / nc, max_steps=steps)
+    print("autotuned shapes:", tuning)
+    assert (s, rc, s_ref, rc_ref) == (steps, 0, steps, 0)
+    assert abs(t - t_ref) <= 1e-12 * t_ref
+    assert rel_linf(ud.cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "incr"])
+def test_full_size_n7_1e6_sampled(cuda, oracle_mod, prec):
+    """DG N = 7 on 10^6 cells (8 x 8 space-time nodes, 192 MB of state): one
+    step with the device CFL step against the oracle's per-cell step on sampled
+    cells, at the FP64 bar, for the FP64 predictor and the increment form"""
+    import torch
+    N, nc = 7, 1_000_000
+    o = oracle_mod.Oracle(N)
+    u = W.nodal_state(W.modes4(), o.node_x(nc))
+    dx = 1.0 / nc
+    ctx = make(cuda, nc, N, precision=prec)
+    ud = to_dev(u, cuda)
+    out = torch.empty_like(ud)
+    ctx.ader_step(ud, out, 0.0)
+    torch.cuda.synchronize()
+    dt = o.dg_dt(u, dx)
+    cells = np.unique(np.concatenate([[0, 1, nc - 1], np.random.default_rng(7).integers(0, nc, 40)]))
+    sel, rc = o.dg_step_cells(u, dx, dt, cells)
+    got = out.cpu().numpy().reshape(nc, N + 1, 3)[cells]
+    assert rc == 0 and ctx.ader_get_stats()["status"] == 0
+    assert rel_linf(got, sel) < 1e-12
+
+
 def test_nonphysical_input_is_reported(cuda, oracle_mod):
     import torch
     from paper_2409_12483_gb300 import ADER_ERR_NONPHYSICAL, AderError

@@ -314,29 +314,58 @@ __global__ void __launch_bounds__(Pred3Cfg<N, T>::THREADS, Pred3Cfg<N, T>::MIN_B
   }
 }
 
-// the d-direction flux of the 3D Euler equations
-template <int D>
-__device__ __forceinline__ void euler3_flux_dir(const double* U, double* f, double gm1) {
-  const double inv = recip(U[0]);
-  const double v[3] = {U[1] * inv, U[2] * inv, U[3] * inv};
-  const double p =
-      gm1 * fma(neg_half(U[1]), v[0], fma(neg_half(U[2]), v[1], fma(neg_half(U[3]), v[2], U[4])));
+// The d-direction flux of the 3D Euler equations (the arithmetic of
+// euler3_flux's row d) with 1/rho and p of the state kept in c[0], c[1]: the
+// first direction of a pass forms and stores them (FIRST), the other two read
+// them back, so a row pays the division and the pressure once per pass instead
+// of once per direction.
+template <int D, bool FIRST>
+__device__ __forceinline__ void euler3_flux_dir_c(const double* U, double* f, double gm1, double* c) {
+  double inv, p;
+  if constexpr (FIRST) {
+    inv = recip(U[0]);
+    const double v[3] = {U[1] * inv, U[2] * inv, U[3] * inv};
+    p = gm1 * fma(neg_half(U[1]), v[0], fma(neg_half(U[2]), v[1], fma(neg_half(U[3]), v[2], U[4])));
+    c[0] = inv;
+    c[1] = p;
+  } else {
+    inv = c[0];
+    p = c[1];
+  }
+  const double vd = U[1 + D] * inv;
   f[0] = U[1 + D];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) f[1 + c] = c == D ? fma(U[1 + c], v[D], p) : U[1 + c] * v[D];
-  f[4] = (U[4] + p) * v[D];
+  for (int k = 0; k < 3; ++k) f[1 + k] = k == D ? fma(U[1 + k], vd, p) : U[1 + k] * vd;
+  f[4] = (U[4] + p) * vd;
+}
+
+// d-direction flux of row U through the cache slot c (d known at run time in a
+// fully unrolled loop, so the branches fold)
+__device__ __forceinline__ void euler3_flux_dir_cached(int d, const double* U, double* f, double gm1,
+                                                       double* c) {
+  if (d == 0) euler3_flux_dir_c<0, true>(U, f, gm1, c);
+  if (d == 1) euler3_flux_dir_c<1, false>(U, f, gm1, c);
+  if (d == 2) euler3_flux_dir_c<2, false>(U, f, gm1, c);
 }
 
 // Degrees 5 and 6: one block per cell, one thread per SPATIAL node (p1, p2, p3)
 // owning its whole tau column q[p0][5] in registers, so kappa~ along tau is a
-// per-thread contraction; the three rescaled fluxes pass in turn through one
-// dynamic shared array [p0][node][5] (n^4 5 doubles: 52 KB at N = 5, 96 KB at
-// N = 6) for the k~ contractions along xi, eta and zeta.
+// per-thread contraction.  The fluxes reach the k~ contractions along xi, eta
+// and zeta through dynamic shared memory:
+// * N = 5: the three directions' fluxes side by side, [3][p0][node][5] (152 KB),
+//   formed together (one division and one pressure per node and row) and
+//   contracted after a single barrier;
+// * N = 6 (three directions would take 288 KB): one direction at a time through
+//   [p0][node][5] (96 KB), with 1/rho and p of every row kept in [p0][node][2]
+//   (38 KB) by the first direction for the other two.
 template <int N>
 struct Pred3HiCfg {
   static constexpr int n = N + 1, NNN = n * n * n, NST = n * n * n * n;
   static constexpr int THREADS = (NNN + 31) / 32 * 32;
-  static constexpr size_t kSmemBytes = (size_t)NST * kM3 * sizeof(double);
+  static constexpr bool kAllDirs = 3 * (size_t)NST * kM3 * sizeof(double) <= 200 * 1024;
+  static constexpr size_t kFluxDoubles = (size_t)(kAllDirs ? 3 : 1) * NST * kM3;
+  static constexpr size_t kSmemBytes =
+      (kFluxDoubles + (kAllDirs ? 0 : (size_t)NST * 2)) * sizeof(double);
 };
 
 template <int N>
@@ -396,34 +425,66 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
     for (int p0 = 0; p0 < n; ++p0)
 #pragma unroll
       for (int r = 0; r < kM3; ++r) acc[p0][r] = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    if constexpr (C::kAllDirs) {
       if (valid) {
 #pragma unroll
         for (int p0 = 0; p0 < n; ++p0) {
           if (p0 >= rows) break;
-          double f[kM3];
-          if (d == 0) euler3_flux_dir<0>(q[p0], f, P.gm1);
-          if (d == 1) euler3_flux_dir<1>(q[p0], f, P.gm1);
-          if (d == 2) euler3_flux_dir<2>(q[p0], f, P.gm1);
+          double F[3][kM3];
+          euler3_flux(q[p0], F, P.gm1);
 #pragma unroll
-          for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = f[r];
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int r = 0; r < kM3; ++r) S[((d * n + p0) * NNN + node) * kM3 + r] = F[d][r];
         }
       }
       __syncthreads();
       if (valid) {
-        const int base = node - pd[d] * stride[d];
 #pragma unroll
-        for (int p0 = 0; p0 < n; ++p0) {
-          if (p0 >= rows) break;
+        for (int d = 0; d < 3; ++d) {
+          const int base = node - pd[d] * stride[d];
 #pragma unroll
-          for (int r = 0; r < kM3; ++r)
+          for (int p0 = 0; p0 < n; ++p0) {
+            if (p0 >= rows) break;
 #pragma unroll
-            for (int m = 0; m < n; ++m)
-              acc[p0][r] = fma(kd[d][pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+            for (int r = 0; r < kM3; ++r)
+#pragma unroll
+              for (int m = 0; m < n; ++m)
+                acc[p0][r] = fma(kd[d][pd[d]][m],
+                                 S[((d * n + p0) * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+          }
         }
       }
-      __syncthreads();
+      // S is written again only after the two barriers of the convergence test
+    } else {
+      double* cache = S + C::kFluxDoubles;  // [p0][node][2]: 1/rho, p
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (valid) {
+#pragma unroll
+          for (int p0 = 0; p0 < n; ++p0) {
+            if (p0 >= rows) break;
+            double f[kM3];
+            euler3_flux_dir_cached(d, q[p0], f, P.gm1, cache + (p0 * NNN + node) * 2);
+#pragma unroll
+            for (int r = 0; r < kM3; ++r) S[(p0 * NNN + node) * kM3 + r] = f[r];
+          }
+        }
+        __syncthreads();
+        if (valid) {
+          const int base = node - pd[d] * stride[d];
+#pragma unroll
+          for (int p0 = 0; p0 < n; ++p0) {
+            if (p0 >= rows) break;
+#pragma unroll
+            for (int r = 0; r < kM3; ++r)
+#pragma unroll
+              for (int m = 0; m < n; ++m)
+                acc[p0][r] = fma(kd[d][pd[d]][m], S[(p0 * NNN + base + m * stride[d]) * kM3 + r], acc[p0][r]);
+          }
+        }
+        __syncthreads();
+      }
     }
     if (valid) {
       unsigned long long dmax = 0ull, qm = 0ull;
@@ -497,23 +558,27 @@ __global__ void __launch_bounds__(Pred3HiCfg<N>::THREADS, 1)
     }
   }
   __syncthreads();
-  // time-averaged rescaled fluxes of this node's column, per direction, into S as [d][node][5]
+  // time-averaged rescaled fluxes of this node's column, per direction, into S
+  // as [d][node][5] (the three directions of a row from one flux evaluation)
   if (valid) {
+    double fb[3][kM3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double fb[kM3] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int l0 = 0; l0 < n; ++l0) {
-        double f[kM3];
-        if (d == 0) euler3_flux_dir<0>(q[l0], f, P.gm1);
-        if (d == 1) euler3_flux_dir<1>(q[l0], f, P.gm1);
-        if (d == 2) euler3_flux_dir<2>(q[l0], f, P.gm1);
+      for (int r = 0; r < kM3; ++r) fb[d][r] = 0.0;
 #pragma unroll
-        for (int r = 0; r < kM3; ++r) fb[r] = fma(o.w[l0], lam[d] * f[r], fb[r]);
-      }
+    for (int l0 = 0; l0 < n; ++l0) {
+      double F[3][kM3];
+      euler3_flux(q[l0], F, P.gm1);
 #pragma unroll
-      for (int r = 0; r < kM3; ++r) S[(d * NNN + node) * kM3 + r] = fb[r];
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int r = 0; r < kM3; ++r) fb[d][r] = fma(o.w[l0], lam[d] * F[d][r], fb[d][r]);
     }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int r = 0; r < kM3; ++r) S[(d * NNN + node) * kM3 + r] = fb[d][r];
   }
   __syncthreads();
   if (valid) {
@@ -549,8 +614,10 @@ template <int N>
 struct Pred3ClCfg {
   static constexpr int n = N + 1, NNN = n * n * n, H = n / 2;
   static constexpr int THREADS = (NNN + 31) / 32 * 32;
-  // G and S: [H][NNN][5] doubles each (80 KB each at N = 7)
-  static constexpr size_t kSmemBytes = 2 * (size_t)H * NNN * kM3 * sizeof(double);
+  // G and S: [H][NNN][5] doubles each (80 KB each at N = 7); then 1/rho and p of
+  // this CTA's rows, [H][NNN][2] (32 KB), formed by the first flux direction of
+  // an iteration for the other two
+  static constexpr size_t kSmemBytes = (2 * (size_t)H * NNN * kM3 + (size_t)H * NNN * 2) * sizeof(double);
   static constexpr bool kValid = n % 2 == 0;  // the tau rows split evenly (launched for N = 7)
 };
 
@@ -562,6 +629,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
   extern __shared__ __align__(16) double smem[];
   double* G = smem;                 // [H][NNN][5] this CTA's rows of g
   double* S = smem + H * NNN * kM3; // [H][NNN][5] flux exchange, then q, then partial fbar
+  double* cache = S + H * NNN * kM3; // [H][NNN][2] 1/rho, p
   __shared__ unsigned long long red[2][2];  // [iteration parity][max |q'-q|, max |q'|]
   __shared__ int s_go;
   __shared__ double s_dt;
@@ -622,9 +690,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
         for (int i = 0; i < H; ++i) {
           if (i >= rows) break;
           double f[kM3];
-          if (d == 0) euler3_flux_dir<0>(q[i], f, P.gm1);
-          if (d == 1) euler3_flux_dir<1>(q[i], f, P.gm1);
-          if (d == 2) euler3_flux_dir<2>(q[i], f, P.gm1);
+          euler3_flux_dir_cached(d, q[i], f, P.gm1, cache + (i * NNN + node) * 2);
 #pragma unroll
           for (int r = 0; r < kM3; ++r) S[(i * NNN + node) * kM3 + r] = f[r];
         }
@@ -725,6 +791,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
   }
   // epilogue 2: partial time averages of the rescaled fluxes over this CTA's
   // rows, [d][node][5] in G (the peer finished reading G at the last barrier)
+  // (one direction at a time, 1/rho and p through the cache: three directions'
+  // accumulators at once would spill at this register budget)
   if (valid) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -732,9 +800,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Pred3ClCfg<N>::THREA
 #pragma unroll
       for (int i = 0; i < H; ++i) {
         double f[kM3];
-        if (d == 0) euler3_flux_dir<0>(q[i], f, P.gm1);
-        if (d == 1) euler3_flux_dir<1>(q[i], f, P.gm1);
-        if (d == 2) euler3_flux_dir<2>(q[i], f, P.gm1);
+        euler3_flux_dir_cached(d, q[i], f, P.gm1, cache + (i * NNN + node) * 2);
 #pragma unroll
         for (int r = 0; r < kM3; ++r) fb[r] = fma(o.w[row0 + i], lam[d] * f[r], fb[r]);
       }

@@ -525,7 +525,7 @@ def main():
                     help="profiling case instead of the bench line: "
                          "predict-dg5 | predict-dg5-ff | predict-dg5-incr | predict-dg7-fp32 | weno5 | "
                          "step2d-dg5 | step2d-dg3 | "
-                         "step3d-dg2 | step3d-dg2-48 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
+                         "step3d-dg2 | step3d-dg2-48 | step3d-dg5 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
                          "sine-tables (the 2D / 3D sine-wave convergence tables against the paper's) | "
@@ -1440,7 +1440,8 @@ def run_case(args):
     elif args.case == "weno5":
         ctx = Context(nc, 4, "fv", device=dev)
         u = torch.tensor(W.cell_average_state(W.modes4(SEED), nc), device=dev).reshape(-1)
-    elif args.case in ("step2d-dg5", "step2d-dg3", "step3d-dg2", "step3d-dg2-48", "step3d-dg7"):
+    elif args.case in ("step2d-dg5", "step2d-dg3", "step3d-dg2", "step3d-dg2-48", "step3d-dg5",
+                       "step3d-dg7"):
         from paper_2409_12483_gb300 import Context2D, Context3D
         if args.case == "step2d-dg5":  # 96^2 cells: 35 MB state
             ctx = Context2D(96, 96, 5, device=dev)
@@ -1448,6 +1449,9 @@ def run_case(args):
         elif args.case == "step2d-dg3":  # 512^2 cells: 134 MB state, 0.67 GB traces
             ctx = Context2D(512, 512, 3, device=dev)
             u = torch.tensor(sine2d_state(ctx).ravel(), device=dev)
+        elif args.case == "step3d-dg5":  # 24^3 cells: 119 MB state, 0.84 GB traces
+            ctx = Context3D(24, 24, 24, 5, device=dev)
+            u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)
         elif args.case == "step3d-dg7":  # 12^3 cells: 35 MB state, 248 MB traces
             ctx = Context3D(12, 12, 12, 7, device=dev)
             u = torch.tensor(sine3d_state(ctx).ravel(), device=dev)

@@ -526,6 +526,7 @@ def main():
                          "predict-dg5 | predict-dg5-ff | predict-dg5-incr | predict-dg7-fp32 | weno5 | "
                          "step2d-dg5 | step2d-dg3 | "
                          "step3d-dg2 | step3d-dg2-48 | step3d-dg5 | step3d-dg7 (multi-D: warmup + steps time steps of one solve) | "
+                         "limiter-dg5-1e5 (the headline data, limiter on) | "
                          "paper-costs (the sine wave at the meshes of the paper's cost tables) | "
                          "serving-large (512 requests, cells up to 4096) | "
                          "sine-tables (the 2D / 3D sine-wave convergence tables against the paper's) | "
@@ -1465,11 +1466,15 @@ def run_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "cells": ctx.n_cells, "steps": steps, "status": rc}))
         return
-    elif args.case in ("sod-dg5-limiter", "tracer-dg5", "reacting-dg5", "solve-dg5", "solve-dg5-1e5"):
+    elif args.case in ("sod-dg5-limiter", "tracer-dg5", "reacting-dg5", "solve-dg5", "solve-dg5-1e5",
+                       "limiter-dg5-1e5"):
         # 10^6 cells (144-192 MB of state, above L2): warmup + steps time steps
         import numpy as np
         if args.case in ("solve-dg5", "solve-dg5-1e5"):  # the interface kernel with lambda_max
             ctx = Context(nc if args.case == "solve-dg5" else CELLS, 5, "dg")
+            u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
+        elif args.case == "limiter-dg5-1e5":  # the headline data with the limiter on (never acting)
+            ctx = Context(CELLS, 5, "dg", device=dev, limiter=1)
             u = torch.tensor(W.nodal_state(W.modes4(SEED), ctx.node_coords()), device=dev).reshape(-1)
         elif args.case == "sod-dg5-limiter":
             ctx = Context(nc, 5, "dg", device=dev, bc="outflow", limiter=1)

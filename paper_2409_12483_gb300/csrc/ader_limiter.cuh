@@ -524,6 +524,9 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
   constexpr int n = N + 1, Ns = 2 * N + 1;
   __shared__ unsigned long long s_wmax[4];
   __shared__ float s_cut;
+  __shared__ int s_count;                     // candidate subcells for FP64
+  __shared__ unsigned short s_list[128 * Ns];  // their items cell * Ns + j
+  __shared__ double s_P[Ns][n];
   double dt;
   int last;
   if (!corrector_step_dt(P.sp, &dt, &last)) return;  // uniform over the grid
@@ -570,6 +573,8 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
 #pragma unroll
       for (int r = 0; r < kM; ++r) s_u[threadIdx.x][k * kM + r] = u[k][r];
   }
+  for (int t = threadIdx.x; t < Ns * n; t += blockDim.x) s_P[t / n][t % n] = P.ops.P[t / n][t % n];
+  if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
   bool twin = valid && threadIdx.x > 0;
   if (twin) {
@@ -613,22 +618,30 @@ __global__ void __launch_bounds__(128) lim_finish_kernel(const __grid_constant__
   if (threadIdx.x == 0) s_cut = __uint_as_float((unsigned)fm);
   __syncthreads();
   const float cut = s_cut;
-  double lmax = 0.0;
-  bool bad = false;
+  // The subcells left to FP64 are few and spread thinly over the cells (on a
+  // fine smooth mesh about one per cell): listed first, they are evaluated by
+  // whole warps, instead of one pass per subcell index with a few lanes of
+  // each warp busy.  The maximum of the same set is the same.
   if (own) {
 #pragma unroll
-    for (int j = 0; j < Ns; ++j) {
-      if (!(lt[j] >= cut)) continue;
-      double v[kM];
+    for (int j = 0; j < Ns; ++j)
+      if (lt[j] >= cut) s_list[atomicAdd(&s_count, 1)] = (unsigned short)(threadIdx.x * Ns + j);
+  }
+  __syncthreads();
+  const int ncand = s_count;
+  double lmax = 0.0;
+  bool bad = false;
+  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
+    const int item = s_list[t], c = item / Ns, j = item - c * Ns;
+    double v[kM];
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        double acc = 0.0;
+    for (int r = 0; r < kM; ++r) {
+      double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc = fma(P.ops.P[j][k], u[k][r], acc);
-        v[r] = acc;
-      }
-      lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
+      for (int k = 0; k < n; ++k) acc = fma(s_P[j][k], s_u[c][k * kM + r], acc);
+      v[r] = acc;
     }
+    lmax = fmax(lmax, wave_speed(v, P.gamma, P.gm1, &bad));
   }
   const unsigned long long bm = block_max_bits(dbits(lmax), s_wmax);
   if (threadIdx.x == 0) atomicMax(&P.sp.ctl->lam[P.sp.par ^ 1], bm);

@@ -145,3 +145,21 @@ def test_headline_carries_fp32_forms_and_latency():
     assert bench.fp32_predictor_summary([{"name": "dg5-1e5-incr", "error": "x"}], 1.0) is None
     assert bench.latency_summary(None) is None
     assert bench.latency_summary({"open_loop": []}) is None
+
+
+def test_reference_arm_under_two_rank_launch():
+    """Launched as the multi-GPU bench is (torch.distributed.run, two ranks), the
+    reference arm prints one line from rank 0; the other rank exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.2"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0

@@ -472,12 +472,26 @@ def cpu_oracle_rate_all_cores(steps: int):
     return procs * CELLS * steps / slowest, procs, steps, slowest
 
 
+# CPU seconds the reference arm spends in all, warm-up included, when
+# --ref-seconds is not given: each step's sample is this divided over the
+# steps, between 1 and 12 s, so that a long --steps K run still ends in minutes
+REF_TOTAL_SECONDS = 150.0
+
+
+def ref_step_seconds(warmup: int, steps: int, given=None) -> float:
+    """Seconds of oracle work per reference-arm step."""
+    if given is not None:
+        return float(given)
+    return min(12.0, max(1.0, REF_TOTAL_SECONDS / max(1, warmup + steps)))
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     rates = []
+    target = ref_step_seconds(args.warmup, args.steps, args.ref_seconds)
     for i in range(args.warmup + args.steps):
-        rate, steps, secs = cpu_oracle_rate(target_s=args.ref_seconds)
+        rate, steps, secs = cpu_oracle_rate(target_s=target)
         if i >= args.warmup:
             rates.append((rate, steps, secs))
     total_cu = sum(CELLS * s for _, s, _ in rates)
@@ -505,7 +519,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="oracle seconds per reference-arm step (default: 150 s over "
+                         "warmup + steps, between 1 and 12 s per step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the secondary workloads (FP32 predictor, WENO5 and N=7 at 10^6 cells)")

@@ -163,3 +163,17 @@ def test_reference_arm_under_two_rank_launch():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_reference_step_budget():
+    """The reference arm's per-step oracle sample shrinks with the step count so
+    the whole run stays within minutes; an explicit --ref-seconds wins."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.ref_step_seconds(3, 5) == 12.0
+    assert bench.ref_step_seconds(5, 20) == 6.0
+    assert bench.ref_step_seconds(10, 1000) == 1.0
+    assert bench.ref_step_seconds(3, 5, 0.2) == 0.2
+    for w, k in ((3, 5), (5, 20), (3, 50), (10, 200)):
+        total = (w + k) * bench.ref_step_seconds(w, k)
+        assert total <= max(bench.REF_TOTAL_SECONDS, (w + k) * 1.0)
